@@ -1,0 +1,25 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: takes tens of seconds on CPU")
+
+
+@pytest.fixture(scope="session")
+def soe16():
+    from paper_2403_01521_gb300.soe import load_soe
+    return load_soe(16)
+
+
+@pytest.fixture(scope="session")
+def soe8():
+    from paper_2403_01521_gb300.soe import load_soe
+    return load_soe(8)
