@@ -1,0 +1,353 @@
+"""Benchmark: long-range energy + potentials + forces, particles/s, on GB300.
+
+Workload (the metric's configuration): N = 1e6 charges +-1 uniform in a
+400 x 400 x 50 slab, alpha = 0.1, random batch P = 200 k-vectors per call
+drawn on the device, M = 16 SOE terms (conditioned table), compensated FP32.
+One step = one qslab_compute() call: input checks, z-sort, gather, k-sampler
+and mode table, k-space chunk aggregates, carries, bidirectional recurrences
+with the fused gather, the k = 0 term, the combine and the energy reduction.
+The same step in FP64 is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the path is
+not sharded across GPUs: replicas only); value = particles of all ranks / the
+slowest rank's time. The reference arm (--impl reference) times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "long-range energy+force particles/s at N=1e6 on 1 GB300 (FP32 vs FP64); % roofline"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+L2_BYTES = 129 * 1024 * 1024
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def algorithmic_instr(K, N, M):
+    """FP32 arithmetic instructions the recurrences + gather must execute per
+    call: per (k, beta, particle) a forward step, a backward step and the
+    gather (~24), per (k, particle) the phase and the combination (~20)."""
+    return float(K) * N * (24 * (M + 1) + 20)
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_sample(sl, soe, P, seed, sample_modes=8, reps=1):
+    """Time the FP64 oracle on a bounded sample: the k = 0 term in full and
+    `sample_modes` of the P random-batch modes; scale the k-space time to P.
+    Returns (seconds per full call, description, cores)."""
+    from oracle import lattice, soe_ewald2d
+    Lx, Ly, _ = sl.box
+    mx, my = lattice.sample_modes(P, seed, 0, sl.alpha, Lx, Ly)
+    H = lattice.H_direct(sl.alpha, Lx, Ly)
+    gam = soe_ewald2d.rbe_prefactor(sl.alpha, Lx, Ly, mx, my, H, P)
+    soe_ewald2d._load()
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        soe_ewald2d.kspace_pairs(sl.pos, sl.q, sl.box, sl.alpha, *soe, mx[:sample_modes],
+                                 my[:sample_modes], gam[:sample_modes])
+        t1 = time.perf_counter()
+        soe_ewald2d.kzero_pairs(sl.pos, sl.q, sl.box, sl.alpha, *soe)
+        t2 = time.perf_counter()
+        est = (t1 - t0) * P / sample_modes + (t2 - t1)
+        best = est if best is None else min(best, est)
+    desc = (f"oracle (C FP64 recursion, OpenMP) on the full N={sl.N} with {sample_modes} of "
+            f"the {P} sampled k plus the whole k=0 term; k-space time scaled by {P}/{sample_modes}")
+    return best, desc, os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import workloads
+    from paper_2403_01521_gb300.soe import load_soe
+    sl = workloads.rbe_large()
+    soe = load_soe(16)
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        cpu_oracle_sample(sl, soe, 200, 11, sample_modes=2)
+    times = []
+    desc = cores = None
+    for _ in range(args.steps):
+        t, desc, cores = cpu_oracle_sample(sl, soe, 200, 11, sample_modes=8)
+        times.append(t)
+    sec = float(np.mean(times))
+    value = sl.N / sec
+    line = {"metric": METRIC, "impl": "reference", "value": value, "unit": "particles/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "rbe_large: N=1e6 charges +-1 uniform in 400x400x50, "
+                                   "alpha=0.1, P=200 random-batch k per call, M=16 SOE",
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2403_01521_gb300 as qslab
+    import workloads
+    from paper_2403_01521_gb300.soe import load_soe
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    peaks, peak_kind = _peaks()
+    M = 16
+    P = 200
+    soe = load_soe(M)
+    sl = workloads.rbe_large(seed=3 + rank)
+    N = sl.N
+
+    def make(prec):
+        s = qslab.QSlab(local, prec).configure(sl.box, sl.alpha, soe, rbe=(P, 1000 + rank))
+        qslab.qslab_set_timing(s.h, True)
+        return s
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(slab, dtype, steps, warmup, sampler=None):
+        pos = torch.tensor(sl.pos, device=dev, dtype=dtype)
+        q = torch.tensor(sl.q, device=dev, dtype=dtype)
+        e = torch.empty(1, dtype=torch.float64, device=dev)
+        phi = torch.empty(N, dtype=dtype, device=dev)
+        F = torch.empty((N, 3), dtype=dtype, device=dev)
+        for _ in range(warmup):
+            slab.compute(pos, q, e, phi, F)
+        slab.check()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        phases = []
+        launches = 0
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.start()
+        for i in range(steps):
+            flush.zero_()                       # evict L2 between steps (not timed)
+            ev0[i].record(stream)
+            slab.compute(pos, q, e, phi, F)
+            ev1[i].record(stream)
+            ph, nl = qslab.qslab_get_timings(slab.h)
+            phases.append(ph)
+            launches += nl
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop() if sampler else None
+        if ws > 1:
+            torch.distributed.barrier()
+        slab.check()
+        ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        return float(np.mean(ms)), phases, launches, clocks, float(e.item())
+
+    # ---- FP32C (headline)
+    s32 = make("fp32c")
+    ms32, ph32, nl32, clocks, E32 = timed(s32, torch.float32, args.steps, args.warmup,
+                                          ClockSampler(local))
+    # ---- FP64 (reported beside it)
+    s64 = make("fp64")
+    st64 = max(1, min(args.steps, 3))
+    ms64, ph64, nl64, _, E64 = timed(s64, torch.float64, st64, 1)
+    s64.close()
+
+    # slowest rank decides
+    ms32_max = ms32
+    if ws > 1:
+        t = torch.tensor([ms32], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms32_max = float(t.item())
+    value = ws * N / (ms32_max * 1e-3)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    pos_h = torch.tensor(sl.pos, dtype=torch.float32).pin_memory()
+    q_h = torch.tensor(sl.q, dtype=torch.float32).pin_memory()
+    e_h = torch.zeros(1, dtype=torch.float64).pin_memory()
+    phi_h = torch.zeros(N, dtype=torch.float32).pin_memory()
+    F_h = torch.zeros((N, 3), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        qslab.qslab_compute_host(s32.h, N, pos_h.data_ptr(), q_h.data_ptr(), e_h.data_ptr(),
+                                 phi_h.data_ptr(), F_h.data_ptr(), stream.cuda_stream)
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        qslab.qslab_compute_host(s32.h, N, pos_h.data_ptr(), q_h.data_ptr(), e_h.data_ptr(),
+                                 phi_h.data_ptr(), F_h.data_ptr(), stream.cuda_stream)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = float(np.mean(e2e_ms))
+    if ws > 1:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    s32.close()
+
+    # ---- roofline of the dominant kernel (the recurrences + gather)
+    rec_ms = float(np.mean([p["recurrence"] for p in ph32]))
+    work = algorithmic_instr(P, N, M)
+    achieved = work / (rec_ms * 1e-3) / 1e12
+    smax = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = SM_COUNT * FP32_LANES_PER_SM * smax * 1e6 / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            with open(tpath) as fh:
+                tj = json.load(fh)
+            from paper_2403_01521_gb300 import build as _b
+            import hashlib
+            h = hashlib.sha256(open(os.path.join(_b.CSRC, "qslab_kernels.cu"), "rb").read()).hexdigest()
+            if tj.get("kernels_sha256") == h:
+                traffic = tj.get("recurrence_bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    phases = {k: float(np.mean([p[k] for p in ph32])) for k in qslab.TIMING_PHASES}
+    line = {
+        "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "rbe_large: N=1e6 charges +-1 uniform in 400x400x50, alpha=0.1, "
+                               "P=200 random-batch k per call (sampled on the device), "
+                               "M=16 SOE (conditioned table), compensated FP32 "
+                               "(FP64 chunk carries, FP64 k=0 term and reductions)",
+                   "N": N, "P": P, "M": M, "per_rank": "independent replica",
+                   "l2": "flushed between steps (256 MB write, untimed)"},
+        "fp64": {"value": ws * N / (ms64 * 1e-3), "unit": "particles/s", "ms_per_step": ms64,
+                 "steps": st64, "energy": E64},
+        "energy_fp32c": E32,
+        "phases_ms": phases,
+        "roofline": {"bound": "alu", "kernel": "kspace_final_kernel (recurrences + gather)",
+                     "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                                   f"{smax:.0f} MHz ({peak_kind} max SM clock)",
+                     "work": "K*N*(24*(M+1)+20) FP32 instructions per launch"},
+        "e2e": {"value": ws * N / (e2e_ms * 1e-3), "unit": "particles/s",
+                "h2d_bytes_per_step": int(N * 3 * 4 + N * 4),
+                "d2h_bytes_per_step": int(8 + N * 4 + N * 12)},
+        "clocks": clocks,
+        "gpu_launches": int(nl32),
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        t, desc, cores = cpu_oracle_sample(sl, soe, P, 1000, sample_modes=8)
+        line["cpu_baseline"] = {"value": N / t, "unit": "particles/s", "cores": cores,
+                                "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,166 @@
+/*
+ * qslab - long-range electrostatics of quasi-2D slabs on one GB300 GPU.
+ *
+ * C ABI of the SOE-Ewald2D / random-batch SOE-Ewald2D (RBSE2D) long-range
+ * path of Gan, Gao, Liang and Xu, "Fast algorithm for quasi-2D Coulomb
+ * systems" (arXiv 2403.01521).
+ *
+ * Problem (Section 2.1, Eqs. 2.1 and 2.8): N point charges q_i at r_i in the
+ * slab [0,Lx) x [0,Ly) x [0,Lz], periodic in x and y, free in z, with
+ *   U = 1/2 sum_m sum_i sum'_j q_i q_j / |r_i - r_j + (m_x Lx, m_y Ly, 0)|
+ * in Gaussian units. Ewald splitting with parameter alpha (Eq. 2.9) gives a
+ * short-range part (not computed here) and the long-range part this library
+ * computes (Lemma 2.1 minus the self term, Eq. 2.12):
+ *   E_long = sum_{k != 0} U^k + U^0 - U_self,
+ * with the z-kernels replaced by their sum-of-exponentials (SOE) forms
+ * (Eqs. 3.21 and 3.26) and each k handled by sorted forward/backward
+ * recursions in z (Eqs. 3.27-3.30, Appendix E). Two ways to sum over k:
+ *   - full k-sum over 0 < |k| <= kc (Algorithm 1);
+ *   - random batch: P vectors drawn i.i.d. from h(k) ~ e^{-k^2/(4 alpha^2)}
+ *     on the whole lattice, weighted by H/P (Eqs. 4.5-4.9, Algorithm 2).
+ * The k = 0 term is always computed exactly (in its SOE form).
+ *
+ * Outputs, for every particle: the long-range potential phi_i (including the
+ * j = i constants, so that E_long = 1/2 sum_i q_i phi_i and dE/dq_i = phi_i)
+ * and the long-range force F_i = -dE_long/dr_i.
+ *
+ * Conventions shared by all calls:
+ *   - Return value 0 on success, a negative QSLAB_ERR_* code otherwise.
+ *     qslab_strerror() gives a message. A failed call changes nothing.
+ *   - A context belongs to one host thread at a time and to one CUDA device
+ *     (chosen at creation; every call makes it current).
+ *   - Device pointers are plain CUDA device addresses (for example from
+ *     torch.Tensor.data_ptr()); the caller owns them. The library owns its
+ *     workspace, allocated on first use and grown as needed, and frees it in
+ *     qslab_destroy().
+ *   - Work is ordered on the caller's stream (cudaStream_t passed as void*;
+ *     NULL = legacy default stream). qslab_compute() does not synchronise.
+ */
+#ifndef QSLAB_H
+#define QSLAB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qslab_ctx qslab_ctx;
+
+/* Precision of positions, charges, potentials and forces, and of the
+ * arithmetic. QSLAB_FP64: everything in FP64. QSLAB_FP32C: FP32 inputs and
+ * outputs, FP32 phases and scans, with FP64 chunk carries, an FP64 k = 0
+ * term and FP64 reductions. */
+#define QSLAB_FP64 0
+#define QSLAB_FP32C 1
+
+#define QSLAB_OK 0
+#define QSLAB_ERR_INVALID_ARG (-1)    /* bad argument or unsupported size    */
+#define QSLAB_ERR_NOT_CONFIGURED (-2) /* box, alpha, SOE or k-set missing    */
+#define QSLAB_ERR_NONFINITE (-3)      /* NaN or Inf in positions or charges  */
+#define QSLAB_ERR_Z_OUT_OF_RANGE (-4) /* some z outside [0, Lz]              */
+#define QSLAB_ERR_NONNEUTRAL (-5)     /* |sum q| above tolerance (Thm 2.1)   */
+#define QSLAB_ERR_ALLOC (-6)          /* device or host allocation failed    */
+#define QSLAB_ERR_CUDA (-7)           /* a CUDA runtime call failed          */
+#define QSLAB_ERR_TIMEOUT (-8)        /* a bounded device wait gave up       */
+
+/* Create a context on CUDA device `cuda_device` with precision `prec`
+ * (QSLAB_FP64 or QSLAB_FP32C). *out receives the handle. */
+int qslab_create(qslab_ctx** out, int cuda_device, int prec);
+
+/* Release the context and all its device memory. NULL is ignored. */
+void qslab_destroy(qslab_ctx* ctx);
+
+/* Box lengths (Section 2.1): x in [0,Lx), y in [0,Ly) (taken modulo the
+ * box), z in [0, Lz]. All must be finite and > 0. */
+int qslab_set_box(qslab_ctx* ctx, double Lx, double Ly, double Lz);
+
+/* Ewald splitting parameter alpha > 0 (Eq. 2.9). */
+int qslab_set_alpha(qslab_ctx* ctx, double alpha);
+
+/* Full k-sum (Algorithm 1): every k = 2 pi (m_x/Lx, m_y/Ly) != 0 with
+ * (2 pi m_x/Lx)^2 + (2 pi m_y/Ly)^2 <= kc^2. Selects the full-k mode. */
+int qslab_set_kcut(qslab_ctx* ctx, double kc);
+
+/* Random batch (Section 4.1, Algorithm 2): each qslab_compute() draws P
+ * lattice vectors i.i.d. from h(k) (origin excluded) with a counter-based
+ * generator keyed by `seed`; the counter starts at 0 and advances by one per
+ * call. Selects the random-batch mode. 1 <= P <= 65536. */
+int qslab_set_rbe(qslab_ctx* ctx, int P, uint64_t seed);
+
+/* SOE of the Gaussian, e^{-x^2} ~ sum_l w_l e^{-s_l |x|} (Eqs. 3.1, 3.6):
+ * M complex nodes s and weights w given as real/imaginary host arrays of
+ * length M (copied). Requirements: 1 <= M <= 32, Re s_l > 0, and the set is
+ * closed under complex conjugation (a real node is its own conjugate). */
+int qslab_set_soe(qslab_ctx* ctx, int M, const double* s_re, const double* s_im,
+                  const double* w_re, const double* w_im);
+
+/* Neutrality tolerance: compute() flags QSLAB_ERR_NONNEUTRAL when
+ * |sum q| > tol * sum |q|. Default 64 x the unit roundoff of the precision.
+ * A negative tol disables the check. */
+int qslab_set_neutrality_tol(qslab_ctx* ctx, double tol);
+
+/* Launch shape: particles per chunk (0 = automatic; at most 512 for FP32C,
+ * 256 for FP64) and modes per CTA (0 = automatic; a multiple of 32, at most
+ * 256). Results do not depend on it beyond rounding. */
+int qslab_set_tuning(qslab_ctx* ctx, int chunk, int modes_per_cta);
+
+/* Long-range energy, potentials and forces (Algorithm 1 steps 4-5, 7-9, or
+ * Algorithm 2 steps 4-7, 9; the real-space part is not included).
+ *   N       number of particles, 1 <= N <= 2^31 - 1
+ *   pos     device, N x 3 row-major (x, y, z), double (FP64) or float (FP32C)
+ *   q       device, N charges, same type
+ *   energy  device, one double (always FP64), or NULL
+ *   phi     device, N potentials (same type as pos), or NULL
+ *   force   device, N x 3 forces (same type as pos), or NULL
+ *   stream  cudaStream_t or NULL
+ * Host-side argument errors are returned at once. Input errors found on the
+ * device (NONFINITE, Z_OUT_OF_RANGE, NONNEUTRAL) are recorded in the
+ * context's status word and returned by qslab_last_status(); the outputs of
+ * such a call are unspecified. */
+int qslab_compute(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
+                  double* energy, void* phi, void* force, void* stream);
+
+/* The same computation from host buffers: copies pos and q (host, layout as
+ * above; pinned memory makes the copies asynchronous) to the device, runs,
+ * copies energy/phi/force back to host buffers (any may be NULL) and waits
+ * for the stream. Returns the call's full status, including device-side
+ * input errors. */
+int qslab_compute_host(qslab_ctx* ctx, int64_t N, const void* pos_host,
+                       const void* q_host, double* energy_host,
+                       void* phi_host, void* force_host, void* stream);
+
+/* Random-batch mode: copy the P lattice vectors used by the latest
+ * qslab_compute() into mxy (host, 2*P int32: m_x, m_y pairs) and, if weight
+ * is not NULL, the sample weight H/P. Synchronises the context's stream. */
+int qslab_get_sampled_modes(qslab_ctx* ctx, int32_t* mxy, double* weight);
+
+/* Generator state (seed, number of compute calls made), for bit-exact
+ * resumption of a random-batch sequence. */
+int qslab_get_rng_state(qslab_ctx* ctx, uint64_t* seed, uint64_t* counter);
+int qslab_set_rng_state(qslab_ctx* ctx, uint64_t seed, uint64_t counter);
+
+/* Number of k vectors summed per call: half-plane count for the full k-sum
+ * (each stands for k and -k), P for the random batch. */
+int qslab_num_modes(qslab_ctx* ctx);
+
+/* Wait for the stream of the latest compute() and return its device-side
+ * status (QSLAB_OK or the first input error), then clear it. */
+int qslab_last_status(qslab_ctx* ctx);
+
+/* Per-phase timings of the latest compute(), measured with CUDA events on its
+ * stream while timing is enabled (qslab_set_timing(ctx, 1)). ms8 receives, in
+ * milliseconds: [0] checks + z-sort + gather, [1] mode table (RBE sampler),
+ * [2] k-space chunk aggregates, [3] carries, [4] k-space recurrences with the
+ * gather, [5] k = 0 term, [6] combine + energy, [7] total. *launches (may be
+ * NULL) receives the number of kernels the call launched. Synchronises. */
+int qslab_set_timing(qslab_ctx* ctx, int enable);
+int qslab_get_timings(qslab_ctx* ctx, double* ms8, int* launches);
+
+/* Message for a return code. */
+const char* qslab_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSLAB_H */

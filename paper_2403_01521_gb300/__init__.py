@@ -1,0 +1,327 @@
+"""qslab: long-range electrostatics of quasi-2D slabs on one GB300 GPU.
+
+Python binding of the C ABI in include/qslab.h (argument marshalling only:
+every step of the computation runs in the CUDA library libqslab.so). The
+module-level functions carry the C names; ``QSlab`` wraps a context for
+torch tensors, and ``SlabEnergy`` is the autograd function whose backward is
+the exact adjoint of the long-range energy (dE/dr = -F, dE/dq = phi; E is a
+quadratic form in q).
+
+Method: Gan, Gao, Liang, Xu, "Fast algorithm for quasi-2D Coulomb systems"
+(arXiv 2403.01521): the SOE-Ewald2D long-range part with the full k-sum
+(Algorithm 1) or the random-batch importance sampler (Algorithm 2).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+from .soe import load_soe  # noqa: F401  (tables are method parameters)
+
+QSLAB_FP64 = 0
+QSLAB_FP32C = 1
+_PREC = {"fp64": QSLAB_FP64, "fp32c": QSLAB_FP32C}
+
+_lib = None
+
+
+class QslabError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.qslab_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libqslab.so (building it first if allowed). Raises if the CUDA
+    library cannot be built or loaded: there is no fallback."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not _build.up_to_date():
+        if not build_if_missing:
+            raise RuntimeError(f"libqslab.so missing or stale at {path}")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.c_double
+    I = ctypes.c_int
+    sig = {
+        "qslab_create": ([ctypes.POINTER(P), I, I], I),
+        "qslab_destroy": ([P], None),
+        "qslab_set_box": ([P, D, D, D], I),
+        "qslab_set_alpha": ([P, D], I),
+        "qslab_set_kcut": ([P, D], I),
+        "qslab_set_rbe": ([P, I, ctypes.c_uint64], I),
+        "qslab_set_soe": ([P, I, P, P, P, P], I),
+        "qslab_set_neutrality_tol": ([P, D], I),
+        "qslab_set_tuning": ([P, I, I], I),
+        "qslab_compute": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
+        "qslab_compute_host": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
+        "qslab_get_sampled_modes": ([P, P, P], I),
+        "qslab_get_rng_state": ([P, P, P], I),
+        "qslab_set_rng_state": ([P, ctypes.c_uint64, ctypes.c_uint64], I),
+        "qslab_num_modes": ([P], I),
+        "qslab_last_status": ([P], I),
+        "qslab_set_timing": ([P, I], I),
+        "qslab_get_timings": ([P, P, P], I),
+        "qslab_strerror": ([I], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise QslabError(rc, where)
+
+
+# ---------------------------------------------------------------- C names
+
+
+def qslab_create(device: int = 0, prec: int = QSLAB_FP64) -> int:
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.qslab_create(ctypes.byref(h), device, prec), "qslab_create")
+    return h.value
+
+
+def qslab_destroy(h: int):
+    load().qslab_destroy(h)
+
+
+def qslab_set_box(h, Lx, Ly, Lz):
+    _check(load().qslab_set_box(h, Lx, Ly, Lz), "qslab_set_box")
+
+
+def qslab_set_alpha(h, alpha):
+    _check(load().qslab_set_alpha(h, alpha), "qslab_set_alpha")
+
+
+def qslab_set_kcut(h, kc):
+    _check(load().qslab_set_kcut(h, kc), "qslab_set_kcut")
+
+
+def qslab_set_rbe(h, P, seed):
+    _check(load().qslab_set_rbe(h, int(P), int(seed)), "qslab_set_rbe")
+
+
+def qslab_set_soe(h, s, w):
+    s = np.asarray(s, complex)
+    w = np.asarray(w, complex)
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (s.real, s.imag, w.real, w.imag)]
+    ptrs = [a.ctypes.data for a in arrs]
+    _check(load().qslab_set_soe(h, len(s), *ptrs), "qslab_set_soe")
+
+
+def qslab_set_neutrality_tol(h, tol):
+    _check(load().qslab_set_neutrality_tol(h, tol), "qslab_set_neutrality_tol")
+
+
+def qslab_set_tuning(h, chunk=0, modes_per_cta=0):
+    _check(load().qslab_set_tuning(h, chunk, modes_per_cta), "qslab_set_tuning")
+
+
+def qslab_compute(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr, stream_ptr):
+    _check(load().qslab_compute(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr,
+                                stream_ptr), "qslab_compute")
+
+
+def qslab_compute_host(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr, stream_ptr):
+    _check(load().qslab_compute_host(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr,
+                                     stream_ptr), "qslab_compute_host")
+
+
+def qslab_get_sampled_modes(h, P):
+    mxy = np.zeros(2 * P, np.int32)
+    wt = ctypes.c_double()
+    _check(load().qslab_get_sampled_modes(h, mxy.ctypes.data, ctypes.addressof(wt)),
+           "qslab_get_sampled_modes")
+    return mxy[0::2].copy(), mxy[1::2].copy(), wt.value
+
+
+def qslab_get_rng_state(h):
+    s = ctypes.c_uint64()
+    c = ctypes.c_uint64()
+    _check(load().qslab_get_rng_state(h, ctypes.addressof(s), ctypes.addressof(c)),
+           "qslab_get_rng_state")
+    return s.value, c.value
+
+
+def qslab_set_rng_state(h, seed, counter):
+    _check(load().qslab_set_rng_state(h, seed, counter), "qslab_set_rng_state")
+
+
+def qslab_num_modes(h) -> int:
+    r = load().qslab_num_modes(h)
+    if r < 0:
+        raise QslabError(r, "qslab_num_modes")
+    return r
+
+
+def qslab_last_status(h) -> int:
+    return load().qslab_last_status(h)
+
+
+def qslab_set_timing(h, enable: bool):
+    _check(load().qslab_set_timing(h, int(bool(enable))), "qslab_set_timing")
+
+
+TIMING_PHASES = ("sort", "modes", "aggregate", "carry", "recurrence", "kzero", "combine", "total")
+
+
+def qslab_get_timings(h):
+    """Per-phase milliseconds of the latest call and its kernel-launch count."""
+    out = np.zeros(8)
+    nl = ctypes.c_int()
+    _check(load().qslab_get_timings(h, out.ctypes.data, ctypes.addressof(nl)), "qslab_get_timings")
+    return dict(zip(TIMING_PHASES, out.tolist())), nl.value
+
+
+def qslab_strerror(code: int) -> str:
+    return load().qslab_strerror(code).decode()
+
+
+# ---------------------------------------------------------------- wrapper
+
+
+def kcut_for_tail(alpha: float, tail: float) -> float:
+    """k_c with Gaussian tail e^{-k_c^2/(4 alpha^2)} = tail (Section 2.3)."""
+    return 2.0 * alpha * math.sqrt(math.log(1.0 / tail))
+
+
+class QSlab:
+    """One configured context. Inputs/outputs are torch CUDA tensors."""
+
+    def __init__(self, device: int = 0, precision: str = "fp64"):
+        import torch
+        self.torch = torch
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.np_dtype = np.float64 if precision == "fp64" else np.float32
+        self.device = device
+        self.h = qslab_create(device, _PREC[precision])
+        self.P = 0
+
+    def close(self):
+        if self.h:
+            qslab_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def configure(self, box, alpha, soe, kcut=None, rbe=None, tail=1e-8):
+        """box=(Lx,Ly,Lz); soe=(s,w) or M; kcut (full k-sum) or rbe=(P, seed)."""
+        if isinstance(soe, int):
+            soe = load_soe(soe)
+        qslab_set_box(self.h, *map(float, box))
+        qslab_set_alpha(self.h, float(alpha))
+        qslab_set_soe(self.h, *soe)
+        if rbe is not None:
+            self.P = int(rbe[0])
+            qslab_set_rbe(self.h, self.P, int(rbe[1]))
+        else:
+            qslab_set_kcut(self.h, float(kcut if kcut is not None else kcut_for_tail(alpha, tail)))
+        return self
+
+    def tuning(self, chunk=0, modes_per_cta=0):
+        qslab_set_tuning(self.h, chunk, modes_per_cta)
+        return self
+
+    def num_modes(self):
+        return qslab_num_modes(self.h)
+
+    def compute(self, pos, q, energy=None, phi=None, force=None, want_phi=True, want_force=True):
+        """Returns (energy[1] float64, phi[N], force[N,3]) as CUDA tensors."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        if pos.device != dev or q.device != dev:
+            raise ValueError("pos and q must be CUDA tensors on the context's device")
+        pos = pos.to(self.dtype).contiguous()
+        q = q.to(self.dtype).contiguous()
+        N = q.shape[0]
+        if energy is None:
+            energy = torch.empty(1, dtype=torch.float64, device=dev)
+        if phi is None and want_phi:
+            phi = torch.empty(N, dtype=self.dtype, device=dev)
+        if force is None and want_force:
+            force = torch.empty((N, 3), dtype=self.dtype, device=dev)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        qslab_compute(self.h, N, pos.data_ptr(), q.data_ptr(), energy.data_ptr(),
+                      phi.data_ptr() if phi is not None else None,
+                      force.data_ptr() if force is not None else None, st)
+        return energy, phi, force
+
+    def compute_host(self, pos, q, stream=None):
+        """Host numpy in, host numpy out, through qslab_compute_host."""
+        pos = np.ascontiguousarray(pos, self.np_dtype)
+        q = np.ascontiguousarray(q, self.np_dtype)
+        N = q.shape[0]
+        e = np.zeros(1)
+        phi = np.zeros(N, self.np_dtype)
+        F = np.zeros((N, 3), self.np_dtype)
+        qslab_compute_host(self.h, N, pos.ctypes.data, q.ctypes.data, e.ctypes.data,
+                           phi.ctypes.data, F.ctypes.data, stream)
+        return float(e[0]), phi, F
+
+    def status(self):
+        return qslab_last_status(self.h)
+
+    def check(self):
+        rc = qslab_last_status(self.h)
+        if rc != 0:
+            raise QslabError(rc, "device status")
+
+    def sampled_modes(self):
+        return qslab_get_sampled_modes(self.h, self.P)
+
+    def rng_state(self):
+        return qslab_get_rng_state(self.h)
+
+    def set_rng_state(self, seed, counter):
+        qslab_set_rng_state(self.h, seed, counter)
+
+
+def _autograd():
+    import torch
+
+    class SlabEnergy(torch.autograd.Function):
+        """E(pos, q) with the exact adjoint: dE/dpos = -F, dE/dq = phi."""
+
+        @staticmethod
+        def forward(ctx, pos, q, slab: QSlab):
+            e, phi, F = slab.compute(pos.detach(), q.detach())
+            ctx.save_for_backward(phi, F)
+            ctx.dtypes = (pos.dtype, q.dtype)
+            return e[0].to(pos.dtype)
+
+        @staticmethod
+        def backward(ctx, gE):
+            phi, F = ctx.saved_tensors
+            gpos = (-gE * F).to(ctx.dtypes[0])
+            gq = (gE * phi).to(ctx.dtypes[1])
+            return gpos, gq, None
+
+    return SlabEnergy
+
+
+def slab_energy(pos, q, slab: QSlab):
+    """Differentiable long-range energy (torch autograd)."""
+    return _autograd().apply(pos, q, slab)

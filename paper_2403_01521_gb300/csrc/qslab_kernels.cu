@@ -1,0 +1,942 @@
+// qslab device kernels: input checks and sort keys, the sorted gather, the
+// k != 0 SOE scans (chunk aggregates, carries, bidirectional recurrences with
+// the fused potential/force gather), the k = 0 term, the final combine and
+// the random-batch k-sampler.
+//
+// Method: Gan, Gao, Liang, Xu, "Fast algorithm for quasi-2D Coulomb systems".
+// For a mode k and beta in {k, alpha s_1, ..., alpha s_M} the pair sums over
+// j < i and j > i of u_j e^{-beta |z_i - z_j|}, u_j = q_j e^{-i k.rho_j}, are
+// first-order linear recurrences over the z-sorted particles (Eqs. 3.28-3.30,
+// Remark 3.3). Forces need both directions (Appendix E). Here the sorted
+// particles are cut into chunks of L; one CTA owns one chunk and a range of
+// modes, one thread one mode:
+//   pass A   chunk aggregates sum_j u_j e^{-beta(z_end - z_j)} (forward) and
+//            sum_j u_j e^{-beta(z_j - z_start)} (backward), by dot products
+//            with k-independent exponential tables kept in shared memory;
+//   carries  an FP64 recurrence over chunks per (mode, beta, direction);
+//   pass B   the recurrences over the chunk from the carried state, with the
+//            gather of Eq. 3.21 / Appendix E fused: per particle and mode the
+//            potential and force contributions are formed, summed over the
+//            warp's 32 modes by shuffles and over warps in shared memory.
+// SOE nodes come in conjugate pairs; one representative a_p per pair drives
+// two complex states, fed by the real inputs q cos(k.rho) and q sin(k.rho),
+// whose combination 2 Re(c F(a)) - 2i Re(c F(b)) equals the pair's
+// contribution (the conjugate partner needs no scan of its own).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qslab_internal.h"
+#include "qslab_math.cuh"
+
+namespace qslab {
+
+// ====================================================================== prep
+
+template <typename T> struct KeyOf;
+template <> struct KeyOf<float> {
+  using type = uint32_t;
+  __device__ static type key(float z) { return __float_as_uint(z == 0.0f ? 0.0f : z); }
+};
+template <> struct KeyOf<double> {
+  using type = uint64_t;
+  __device__ static type key(double z) {
+    return (uint64_t)__double_as_longlong(z == 0.0 ? 0.0 : z);
+  }
+};
+
+template <typename T>
+__global__ void prepare_kernel(int64_t N, const T* __restrict__ pos,
+                               const T* __restrict__ q, double Lz,
+                               typename KeyOf<T>::type* keys, uint32_t* vals,
+                               double* sums, unsigned* status) {
+  __shared__ double red[2][32];
+  double sq = 0.0, sa = 0.0;
+  unsigned flags = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2], qi = q[i];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) flags |= kStNonfinite;
+    else if (!(z >= (T)0) || !((double)z <= Lz)) flags |= kStZRange;
+    keys[i] = KeyOf<T>::key(z);
+    vals[i] = (uint32_t)i;
+    sq += (double)qi;
+    sa += fabs((double)qi);
+  }
+  if (flags) atomicOr(status, flags);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 16; o; o >>= 1) {
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+  }
+  if (lane == 0) { red[0][w] = sq; red[1][w] = sa; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { a += red[0][j]; b += red[1][j]; }
+    atomicAdd(&sums[0], a);
+    atomicAdd(&sums[1], b);
+  }
+}
+
+template <typename T>
+void launch_prepare(int64_t N, const T* pos, const T* q, double Lz, void* keys,
+                    uint32_t* vals, double* sums, unsigned* status,
+                    cudaStream_t st) {
+  const int threads = 256;
+  int blocks = (int)((N + threads - 1) / threads);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  prepare_kernel<T><<<blocks, threads, 0, st>>>(
+      N, pos, q, Lz, static_cast<typename KeyOf<T>::type*>(keys), vals, sums, status);
+}
+
+__global__ void check_neutral_kernel(const double* sums, double tol, unsigned* status) {
+  if (tol >= 0.0 && fabs(sums[0]) > tol * sums[1]) atomicOr(status, kStNonneutral);
+}
+
+void launch_check_neutral(const double* sums, double tol, unsigned* status,
+                          cudaStream_t st) {
+  check_neutral_kernel<<<1, 1, 0, st>>>(sums, tol, status);
+}
+
+// ==================================================================== gather
+
+__device__ __forceinline__ uint32_t to_fixed(float x, double L) {
+  double f = (double)x / L;
+  f -= floor(f);
+  if (!(f < 1.0)) f = 0.0;
+  return (uint32_t)(uint64_t)(f * 4294967296.0);
+}
+__device__ __forceinline__ uint64_t to_fixed(double x, double L) {
+  double f = x / L;
+  f -= floor(f);
+  if (!(f < 1.0)) f = 0.0;
+  return (uint64_t)(f * 18446744073709551616.0);
+}
+
+template <typename T>
+__global__ void gather_kernel(int64_t N, const T* __restrict__ pos,
+                              const T* __restrict__ q,
+                              const uint32_t* __restrict__ perm, double Lx,
+                              double Ly, T* zs, T* dz, T* qs,
+                              typename PhaseT<T>::type* xh,
+                              typename PhaseT<T>::type* yh, int32_t* perm_out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t o = perm[i];
+    const T z = pos[3 * (int64_t)o + 2];
+    zs[i] = z;
+    dz[i] = (i > 0) ? z - pos[3 * (int64_t)perm[i - 1] + 2] : (T)0;
+    qs[i] = q[o];
+    xh[i] = to_fixed(pos[3 * (int64_t)o], Lx);
+    yh[i] = to_fixed(pos[3 * (int64_t)o + 1], Ly);
+    perm_out[i] = (int32_t)o;
+  }
+}
+
+template <typename T>
+void launch_gather(int64_t N, const T* pos, const T* q, const uint32_t* perm,
+                   double Lx, double Ly, T* zs, T* dz, T* qs,
+                   typename PhaseT<T>::type* xh, typename PhaseT<T>::type* yh,
+                   int32_t* perm_out, cudaStream_t st) {
+  const int threads = 256;
+  int blocks = (int)((N + threads - 1) / threads);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  gather_kernel<T><<<blocks, threads, 0, st>>>(N, pos, q, perm, Lx, Ly, zs, dz,
+                                               qs, xh, yh, perm_out);
+}
+
+// ============================================================ k != 0 scans
+
+// Shared-memory layout of one chunk (L particles, plus one dz of the next
+// chunk's first particle).
+template <typename T>
+struct ChunkSmem {
+  using PH = typename PhaseT<T>::type;
+  Cplx<T>* tab;   // [NP][L+1] decays (pass B) or [2][NP][L] E tables (pass A)
+  T* dzs;         // [L+1]
+  T* zl;          // [L]
+  T* ql;          // [L]
+  PH* xl;         // [L]
+  PH* yl;         // [L]
+  T* slots;       // pass B: [W][L][4]
+};
+
+template <typename T>
+__host__ __device__ inline size_t align_up(size_t x) { return (x + 15) & ~size_t(15); }
+
+template <typename T>
+__host__ __device__ inline size_t chunk_smem_bytes(int L, int NP, int W, bool passB) {
+  using PH = typename PhaseT<T>::type;
+  size_t b = 0;
+  b += align_up<T>(sizeof(Cplx<T>) * (size_t)NP * (passB ? (L + 1) : 2 * L));
+  b += align_up<T>(sizeof(T) * (L + 1));
+  b += align_up<T>(sizeof(T) * L) * 2;
+  b += align_up<T>(sizeof(PH) * L) * 2;
+  if (passB) b += align_up<T>(sizeof(T) * (size_t)W * L * 4);
+  return b;
+}
+
+template <typename T>
+__device__ inline ChunkSmem<T> carve(char* base, int L, int NP, int W, bool passB) {
+  using PH = typename PhaseT<T>::type;
+  ChunkSmem<T> s;
+  char* p = base;
+  s.tab = reinterpret_cast<Cplx<T>*>(p);
+  p += align_up<T>(sizeof(Cplx<T>) * (size_t)NP * (passB ? (L + 1) : 2 * L));
+  s.dzs = reinterpret_cast<T*>(p); p += align_up<T>(sizeof(T) * (L + 1));
+  s.zl = reinterpret_cast<T*>(p); p += align_up<T>(sizeof(T) * L);
+  s.ql = reinterpret_cast<T*>(p); p += align_up<T>(sizeof(T) * L);
+  s.xl = reinterpret_cast<PH*>(p); p += align_up<T>(sizeof(PH) * L);
+  s.yl = reinterpret_cast<PH*>(p); p += align_up<T>(sizeof(PH) * L);
+  s.slots = passB ? reinterpret_cast<T*>(p) : nullptr;
+  return s;
+}
+
+template <typename T>
+struct KParams {
+  ScanPlan plan;
+  ModeTab<T> modes;
+  const T* zs;
+  const T* dz;
+  const T* qs;
+  const typename PhaseT<T>::type* xh;
+  const typename PhaseT<T>::type* yh;
+  Cplx<T>* agg;     // [2][nchunks][nstates][Kpad]
+  Cplx<T>* carry;   // same layout
+  T* part;          // [nkr][4][N]
+};
+
+// Per-thread (per-mode) coefficients.
+template <typename T, int NP>
+struct ModeCoef {
+  int32_t mx, my;
+  T kx, ky, kk, ck, ckk, sY, sZ;
+  T cpr[NP], cpi[NP], cbr[NP], cbi[NP];
+};
+
+template <typename T, int NP>
+__device__ __forceinline__ void load_mode(const ModeTab<T>& mt, int Kpad, int m,
+                                          ModeCoef<T, NP>& c) {
+  c.mx = mt.mx[m]; c.my = mt.my[m];
+  c.kx = mt.kx[m]; c.ky = mt.ky[m]; c.kk = mt.kk[m];
+  c.ck = mt.ck[m]; c.ckk = mt.ckk[m]; c.sY = mt.sY[m]; c.sZ = mt.sZ[m];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    c.cpr[p] = mt.cp[(0 * NP + p) * (size_t)Kpad + m];
+    c.cpi[p] = mt.cp[(1 * NP + p) * (size_t)Kpad + m];
+    c.cbr[p] = mt.cp[(2 * NP + p) * (size_t)Kpad + m];
+    c.cbi[p] = mt.cp[(3 * NP + p) * (size_t)Kpad + m];
+  }
+}
+
+// Load the chunk's particles into shared memory.
+template <typename T>
+__device__ inline void load_chunk(const KParams<T>& P, ChunkSmem<T>& s,
+                                  int64_t start, int cnt) {
+  const int64_t N = P.plan.N;
+  for (int t = threadIdx.x; t <= cnt; t += blockDim.x) {
+    const int64_t i = start + t;
+    s.dzs[t] = (i < N) ? P.dz[i] : (T)0;
+    if (t < cnt) {
+      s.zl[t] = P.zs[i];
+      s.ql[t] = P.qs[i];
+      s.xl[t] = P.xh[i];
+      s.yl[t] = P.yh[i];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ pass A
+template <typename T, int NP>
+__global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
+  extern __shared__ __align__(16) char smem[];
+  const ScanPlan& pl = P.plan;
+  const int c = blockIdx.x;
+  const int64_t start = (int64_t)c * pl.L;
+  const int cnt = (int)imin64(pl.L, pl.N - start);
+  ChunkSmem<T> s = carve<T>(smem, pl.L, NP, 0, false);
+  load_chunk<T>(P, s, start, cnt);
+  __syncthreads();
+  // E tables: Ef[p][t] = e^{-a_p (z_end - z_t)}, Eb[p][t] = e^{-a_p (z_t - z_start)}
+  const T zend = s.zl[cnt - 1], zst = s.zl[0];
+  for (int e = threadIdx.x; e < NP * cnt; e += blockDim.x) {
+    const int p = e / cnt, t = e - p * cnt;
+    const T ar = (T)pairs.a_re[p], ai = (T)pairs.a_im[p];
+    s.tab[p * pl.L + t] = cexp_neg(ar, ai, zend - s.zl[t]);
+    s.tab[(NP + p) * pl.L + t] = cexp_neg(ar, ai, s.zl[t] - zst);
+  }
+  __syncthreads();
+  const int m = blockIdx.y * pl.KR + threadIdx.x;
+  ModeCoef<T, NP> mc;
+  load_mode<T, NP>(P.modes, pl.Kpad, m, mc);
+  // accumulators: state 0 (beta = k, complex input) and pair states
+  Cplx<T> f0 = {0, 0}, b0 = {0, 0};
+  Cplx<T> fa[NP], fb[NP], ba[NP], bb[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) fa[p] = fb[p] = ba[p] = bb[p] = Cplx<T>{0, 0};
+  for (int t = 0; t < cnt; ++t) {
+    T cs, sn;
+    sincos_turns(phase_turns(mc.mx, mc.my, s.xl[t], s.yl[t]), cs, sn);
+    const T a = s.ql[t] * cs, b = s.ql[t] * sn;   // u = a - i b
+    const T ef = exp_neg(mc.kk * (zend - s.zl[t]));
+    const T eb = exp_neg(mc.kk * (s.zl[t] - zst));
+    f0.re = fma(ef, a, f0.re); f0.im = fma(-ef, b, f0.im);
+    b0.re = fma(eb, a, b0.re); b0.im = fma(-eb, b, b0.im);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const Cplx<T> Ef = s.tab[p * pl.L + t];
+      const Cplx<T> Eb = s.tab[(NP + p) * pl.L + t];
+      fa[p].re = fma(Ef.re, a, fa[p].re); fa[p].im = fma(Ef.im, a, fa[p].im);
+      fb[p].re = fma(Ef.re, b, fb[p].re); fb[p].im = fma(Ef.im, b, fb[p].im);
+      ba[p].re = fma(Eb.re, a, ba[p].re); ba[p].im = fma(Eb.im, a, ba[p].im);
+      bb[p].re = fma(Eb.re, b, bb[p].re); bb[p].im = fma(Eb.im, b, bb[p].im);
+    }
+  }
+  const int S = pl.nstates;
+  const size_t dirstride = (size_t)pl.nchunks * S * pl.Kpad;
+  Cplx<T>* af = P.agg + ((size_t)c * S) * pl.Kpad + m;
+  Cplx<T>* ab = af + dirstride;
+  af[0] = f0;
+  ab[0] = b0;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    af[(size_t)(1 + 2 * p) * pl.Kpad] = fa[p];
+    af[(size_t)(2 + 2 * p) * pl.Kpad] = fb[p];
+    ab[(size_t)(1 + 2 * p) * pl.Kpad] = ba[p];
+    ab[(size_t)(2 + 2 * p) * pl.Kpad] = bb[p];
+  }
+}
+
+// --------------------------------------------------- chunk-to-chunk decays
+// pdec[dir][c][p]: forward e^{-a_p (z_end(c) - z_end(c-1))}, backward
+// e^{-a_p (z_start(c+1) - z_start(c))}, in FP64.
+template <typename T>
+__global__ void pair_decay_kernel(ScanPlan pl, const T* zs, PairTab pairs,
+                                  Cplx<double>* pdec) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int np = pl.np;
+  if (e >= 2 * pl.nchunks * np) return;
+  const int dir = e / (pl.nchunks * np);
+  const int r = e - dir * pl.nchunks * np;
+  const int c = r / np, p = r - c * np;
+  double dzc = 0.0;
+  if (dir == 0 && c > 0) {
+    const int64_t e1 = imin64((int64_t)(c + 1) * pl.L, pl.N) - 1;
+    const int64_t e0 = (int64_t)c * pl.L - 1;
+    dzc = (double)zs[e1] - (double)zs[e0];
+  } else if (dir == 1 && c < pl.nchunks - 1) {
+    dzc = (double)zs[(int64_t)(c + 1) * pl.L] - (double)zs[(int64_t)c * pl.L];
+  }
+  pdec[e] = cexp_neg(pairs.a_re[p], pairs.a_im[p], dzc);
+}
+
+// ------------------------------------------------------------------ carries
+template <typename T>
+__global__ void kspace_carry_kernel(KParams<T> P, const Cplx<double>* pdec) {
+  const ScanPlan& pl = P.plan;
+  const int S = pl.nstates;
+  const int total = 2 * S * pl.Kpad;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  const int dir = e / (S * pl.Kpad);
+  const int r = e - dir * S * pl.Kpad;
+  const int st = r / pl.Kpad, m = r - st * pl.Kpad;
+  const double kk = (double)P.modes.kk[m];
+  const size_t dirstride = (size_t)pl.nchunks * S * pl.Kpad;
+  const Cplx<T>* A = P.agg + dir * dirstride + (size_t)st * pl.Kpad + m;
+  Cplx<T>* C = P.carry + dir * dirstride + (size_t)st * pl.Kpad + m;
+  const size_t cs = (size_t)S * pl.Kpad;
+  const int p = (st - 1) >> 1;
+  double cr = 0.0, ci = 0.0;
+  const int nc = pl.nchunks;
+  for (int j = 0; j < nc; ++j) {
+    const int c = dir == 0 ? j : nc - 1 - j;
+    C[c * cs] = Cplx<T>{(T)cr, (T)ci};
+    // decay from this chunk's reference point to the next one
+    double dr, di;
+    if (st == 0) {
+      double dzc;
+      if (dir == 0) {
+        const int64_t e1 = imin64((int64_t)(c + 1) * pl.L, pl.N) - 1;
+        dzc = c > 0 ? (double)P.zs[e1] - (double)P.zs[(int64_t)c * pl.L - 1] : 0.0;
+      } else {
+        dzc = c < nc - 1 ? (double)P.zs[(int64_t)(c + 1) * pl.L] - (double)P.zs[(int64_t)c * pl.L] : 0.0;
+      }
+      dr = exp(-kk * dzc);
+      di = 0.0;
+    } else {
+      const Cplx<double> d = pdec[((size_t)dir * nc + c) * pl.np + p];
+      dr = d.re; di = d.im;
+    }
+    const Cplx<T> a = A[c * cs];
+    const double nr = dr * cr - di * ci + (double)a.re;
+    const double ni = dr * ci + di * cr + (double)a.im;
+    cr = nr; ci = ni;
+  }
+}
+
+// ------------------------------------------------------------------ pass B
+template <typename T, int NP>
+__global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
+  extern __shared__ __align__(16) char smem[];
+  const ScanPlan& pl = P.plan;
+  const int c = blockIdx.x;
+  const int W = pl.KR / kWarp;
+  const int64_t start = (int64_t)c * pl.L;
+  const int cnt = (int)imin64(pl.L, pl.N - start);
+  ChunkSmem<T> s = carve<T>(smem, pl.L, NP, W, true);
+  load_chunk<T>(P, s, start, cnt);
+  __syncthreads();
+  // per-step decays d[p][t] = e^{-a_p dz_t}, t = 0..cnt (t = cnt: next chunk)
+  for (int e = threadIdx.x; e < NP * (cnt + 1); e += blockDim.x) {
+    const int p = e / (cnt + 1), t = e - p * (cnt + 1);
+    s.tab[p * (pl.L + 1) + t] = cexp_neg((T)pairs.a_re[p], (T)pairs.a_im[p], s.dzs[t]);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int m = blockIdx.y * pl.KR + threadIdx.x;
+  ModeCoef<T, NP> mc;
+  load_mode<T, NP>(P.modes, pl.Kpad, m, mc);
+  const int S = pl.nstates;
+  const size_t dirstride = (size_t)pl.nchunks * S * pl.Kpad;
+  T* slot = s.slots + (size_t)w * pl.L * 4;
+
+  for (int dir = 0; dir < 2; ++dir) {
+    const Cplx<T>* cin = P.carry + dir * dirstride + ((size_t)c * S) * pl.Kpad + m;
+    Cplx<T> g0 = cin[0];
+    Cplx<T> ga[NP], gb[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      ga[p] = cin[(size_t)(1 + 2 * p) * pl.Kpad];
+      gb[p] = cin[(size_t)(2 + 2 * p) * pl.Kpad];
+    }
+    const T zsign = dir == 0 ? (T)1 : (T)-1;
+    T buf[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) buf[j] = (T)0;
+    for (int n = 0; n < cnt; ++n) {
+      const int t = dir == 0 ? n : cnt - 1 - n;
+      const int td = dir == 0 ? t : t + 1;      // index of the decay to apply
+      T cs, sn;
+      sincos_turns(phase_turns(mc.mx, mc.my, s.xl[t], s.yl[t]), cs, sn);
+      const T a = s.ql[t] * cs, b = s.ql[t] * sn;
+      // beta = k: real decay, complex input u = a - i b
+      const T dk = exp_neg(mc.kk * s.dzs[td]);
+      g0.re = fma(dk, g0.re, a);
+      g0.im = fma(dk, g0.im, -b);
+      T Yr = mc.ck * g0.re, Yi = mc.ck * g0.im;
+      T Zr = mc.ckk * g0.re, Zi = mc.ckk * g0.im;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const Cplx<T> d = s.tab[p * (pl.L + 1) + td];
+        const T ar = fma(d.re, ga[p].re, fma(-d.im, ga[p].im, a));
+        const T ai = fma(d.re, ga[p].im, d.im * ga[p].re);
+        const T br = fma(d.re, gb[p].re, fma(-d.im, gb[p].im, b));
+        const T bi = fma(d.re, gb[p].im, d.im * gb[p].re);
+        ga[p].re = ar; ga[p].im = ai; gb[p].re = br; gb[p].im = bi;
+        Yr = fma(mc.cpr[p], ar, fma(-mc.cpi[p], ai, Yr));
+        Yi = fma(-mc.cpr[p], br, fma(mc.cpi[p], bi, Yi));
+        Zr = fma(mc.cbr[p], ar, fma(-mc.cbi[p], ai, Zr));
+        Zi = fma(-mc.cbr[p], br, fma(mc.cbi[p], bi, Zi));
+      }
+      // the sums above include j = i; remove it (coefficient sY, sZ times u_i)
+      Yr = fma(-mc.sY, a, Yr); Yi = fma(mc.sY, b, Yi);
+      Zr = fma(-mc.sZ, a, Zr); Zi = fma(mc.sZ, b, Zi);
+      const T W1 = cs * Yr - sn * Yi;         // Re e^{i k.rho} Y
+      const T W2 = cs * Yi + sn * Yr;         // Im e^{i k.rho} Y
+      const T W3 = cs * Zr - sn * Zi;         // Re e^{i k.rho} Z
+      const int k4 = (n & 3) * 4;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (k4 == 4 * j) {
+          buf[4 * j + 0] = W1;
+          buf[4 * j + 1] = mc.kx * W2;
+          buf[4 * j + 2] = mc.ky * W2;
+          buf[4 * j + 3] = zsign * W3;
+        }
+      }
+      if ((n & 3) == 3 || n == cnt - 1) {
+        const T v = warp_reduce16<T>(buf, lane);
+        const int idx = lane >> 1, g = idx >> 2, qn = idx & 3;
+        const int n0 = n & ~3;
+        if (!(lane & 1) && n0 + g <= n) {
+          const int tt = dir == 0 ? n0 + g : cnt - 1 - (n0 + g);
+          if (dir == 0) slot[tt * 4 + qn] = v;
+          else slot[tt * 4 + qn] += v;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) buf[j] = (T)0;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // sum the warps' slots and write this mode range's partial outputs
+  T* out = P.part + (size_t)blockIdx.y * 4 * pl.N;
+  for (int e = threadIdx.x; e < cnt * 4; e += blockDim.x) {
+    const int t = e >> 2, qn = e & 3;
+    T acc = 0;
+    for (int ww = 0; ww < W; ++ww) acc += s.slots[((size_t)ww * pl.L + t) * 4 + qn];
+    out[(size_t)qn * pl.N + start + t] = acc;
+  }
+}
+
+template <typename T, int NP>
+static void kspace_run(const KParams<T>& P, const PairTab& pairs,
+                       Cplx<double>* pdec, cudaStream_t st, cudaEvent_t* ev) {
+  const ScanPlan& pl = P.plan;
+  dim3 grid(pl.nchunks, pl.nkr);
+  const size_t smA = chunk_smem_bytes<T>(pl.L, NP, 0, false);
+  const size_t smB = chunk_smem_bytes<T>(pl.L, NP, pl.KR / kWarp, true);
+  cudaFuncSetAttribute(kspace_aggregate_kernel<T, NP>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
+  cudaFuncSetAttribute(kspace_final_kernel<T, NP>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB);
+  kspace_aggregate_kernel<T, NP><<<grid, pl.KR, smA, st>>>(P, pairs);
+  if (ev) cudaEventRecord(ev[0], st);
+  const int ne = 2 * pl.nchunks * pl.np;
+  pair_decay_kernel<T><<<(ne + 255) / 256, 256, 0, st>>>(pl, P.zs, pairs, pdec);
+  const int nt = 2 * pl.nstates * pl.Kpad;
+  kspace_carry_kernel<T><<<(nt + 127) / 128, 128, 0, st>>>(P, pdec);
+  if (ev) cudaEventRecord(ev[1], st);
+  kspace_final_kernel<T, NP><<<grid, pl.KR, smB, st>>>(P, pairs);
+  if (ev) cudaEventRecord(ev[2], st);
+}
+
+template <typename T>
+void launch_kspace(const ScanPlan& plan, const ModeTab<T>& modes,
+                   const PairTab& pairs, const T* zs, const T* dz, const T* qs,
+                   const typename PhaseT<T>::type* xh,
+                   const typename PhaseT<T>::type* yh, Cplx<T>* agg,
+                   Cplx<T>* carry, Cplx<double>* pdec, T* part,
+                   cudaStream_t st, cudaEvent_t* ev3) {
+  KParams<T> P{plan, modes, zs, dz, qs, xh, yh, agg, carry, part};
+  switch (plan.np) {
+    case 4: kspace_run<T, 4>(P, pairs, pdec, st, ev3); break;
+    case 8: kspace_run<T, 8>(P, pairs, pdec, st, ev3); break;
+    case 12: kspace_run<T, 12>(P, pairs, pdec, st, ev3); break;
+    default: kspace_run<T, 16>(P, pairs, pdec, st, ev3); break;
+  }
+}
+
+// ================================================================ k = 0 term
+// Pair sums of g0_SOE(|z_ij|) (Eq. 3.26) and of its derivative (Eq. E.6):
+//   sum_{j != i} q_j g0(|z_ij|) = c1 sum_j q_j |z_ij|
+//        + sum_l (w_l/sqrt(pi)) [ (1/alpha) S_l - (2/s_l) H_l ]
+//   sum_{j != i} q_j g0'(|z_ij|) sgn(z_i - z_j) = c1 (Q< - Q>)
+//        + sum_l (w_l/sqrt(pi)) [ -(2/s_l + s_l)(S_l^f - S_l^b) + 2 alpha (H_l^f - H_l^b) ]
+// with S_l = sum_j q_j e^{-a_l |z_ij|} and H_l = sum_j q_j |z_ij| e^{-a_l |z_ij|}
+// split into j < i (f) and j > i (b). The |z| sums use FP64 prefix sums of q
+// and q z. H is carried without cancellation:
+//   H_i = d_i (H_{i-1} + dz_i S_{i-1}),  S_i = d_i S_{i-1} + q_i  (inclusive).
+// Everything here is FP64.
+
+constexpr int kK0Threads = 128;
+
+struct K0Params {
+  int64_t N;
+  int L0, nch;
+  int npad;          // lanes per chunk (power of two >= np)
+  double alpha, area, c1;
+};
+
+template <typename T>
+__global__ void kzero_aggregate_kernel(K0Params Q, PairTab pr, const T* zs,
+                                       const T* qs, double* agg, double* csum) {
+  const int lanes = Q.npad;
+  const int g = (blockIdx.x * blockDim.x + threadIdx.x);
+  const int c = g / lanes, p = g - c * lanes;
+  if (c >= Q.nch) return;
+  const int64_t start = (int64_t)c * Q.L0;
+  const int cnt = (int)imin64(Q.L0, Q.N - start);
+  const double zst = (double)zs[start], zen = (double)zs[start + cnt - 1];
+  double sfr = 0, sfi = 0, hfr = 0, hfi = 0, sbr = 0, sbi = 0, hbr = 0, hbi = 0;
+  double q0 = 0, q1 = 0;
+  const bool act = p < pr.np;
+  const double ar = act ? pr.a_re[p] : 0.0, ai = act ? pr.a_im[p] : 0.0;
+  for (int t = 0; t < cnt; ++t) {
+    const double z = (double)zs[start + t], qq = (double)qs[start + t];
+    q0 += qq;
+    q1 += qq * z;
+    if (!act) continue;
+    const double xf = zen - z, xb = z - zst;
+    const Cplx<double> ef = cexp_neg(ar, ai, xf);
+    const Cplx<double> eb = cexp_neg(ar, ai, xb);
+    sfr += qq * ef.re; sfi += qq * ef.im;
+    hfr += qq * xf * ef.re; hfi += qq * xf * ef.im;
+    sbr += qq * eb.re; sbi += qq * eb.im;
+    hbr += qq * xb * eb.re; hbi += qq * xb * eb.im;
+  }
+  if (act) {
+    double* a = agg + ((size_t)c * lanes + p) * 8;
+    a[0] = sfr; a[1] = sfi; a[2] = hfr; a[3] = hfi;
+    a[4] = sbr; a[5] = sbi; a[6] = hbr; a[7] = hbi;
+  }
+  if (p == 0) { csum[2 * c] = q0; csum[2 * c + 1] = q1; }
+}
+
+// One thread per (direction, pair); thread (0, 0) also scans the chunk sums.
+template <typename T>
+__global__ void kzero_carry_kernel(K0Params Q, PairTab pr, const T* zs,
+                                   const double* agg, double* carry,
+                                   const double* csum, double* cpre) {
+  const int e = threadIdx.x;
+  if (e == 2 * Q.npad) {
+    double a = 0, b = 0;
+    for (int c = 0; c < Q.nch; ++c) {
+      cpre[2 * c] = a; cpre[2 * c + 1] = b;
+      a += csum[2 * c]; b += csum[2 * c + 1];
+    }
+    cpre[2 * Q.nch] = a; cpre[2 * Q.nch + 1] = b;
+    return;
+  }
+  if (e >= 2 * Q.npad) return;
+  const int dir = e / Q.npad, p = e - dir * Q.npad;
+  if (p >= pr.np) return;
+  const double ar = pr.a_re[p], ai = pr.a_im[p];
+  double sr = 0, si = 0, hr = 0, hi = 0;
+  for (int j = 0; j < Q.nch; ++j) {
+    const int c = dir == 0 ? j : Q.nch - 1 - j;
+    double* out = carry + (((size_t)dir * Q.nch + c) * Q.npad + p) * 4;
+    out[0] = sr; out[1] = si; out[2] = hr; out[3] = hi;
+    double dzc = 0.0;
+    const int64_t s0 = (int64_t)c * Q.L0;
+    if (dir == 0) {
+      const int64_t e1 = imin64(s0 + Q.L0, Q.N) - 1;
+      dzc = c > 0 ? (double)zs[e1] - (double)zs[s0 - 1] : 0.0;
+    } else {
+      dzc = c < Q.nch - 1 ? (double)zs[s0 + Q.L0] - (double)zs[s0] : 0.0;
+    }
+    const Cplx<double> d = cexp_neg(ar, ai, dzc);
+    const double* a = agg + ((size_t)c * Q.npad + p) * 8 + 4 * dir;
+    // S' = d S + S_loc ; H' = d (H + dz S) + H_loc
+    const double tr = hr + dzc * sr, ti = hi + dzc * si;
+    const double nhr = d.re * tr - d.im * ti + a[2];
+    const double nhi = d.re * ti + d.im * tr + a[3];
+    const double nsr = d.re * sr - d.im * si + a[0];
+    const double nsi = d.re * si + d.im * sr + a[1];
+    sr = nsr; si = nsi; hr = nhr; hi = nhi;
+  }
+}
+
+template <typename T>
+__global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
+                                   const T* dz, const T* qs, const double* carry,
+                                   const double* cpre, double* phi0,
+                                   double* fz0) {
+  extern __shared__ double ksm[];   // [chunks per block][L0][2]
+  const int lanes = Q.npad;
+  const int cpb = blockDim.x / lanes;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = g / lanes, p = g - c * lanes;
+  const int lc = threadIdx.x / lanes;
+  double* acc = ksm + (size_t)lc * Q.L0 * 2;
+  const bool valid = c < Q.nch;
+  const int64_t start = (int64_t)c * Q.L0;
+  const int cnt = valid ? (int)imin64(Q.L0, Q.N - start) : 0;
+  const bool act = valid && p < pr.np;
+  const double sq = 1.7724538509055160;   // sqrt(pi)
+  double cwr = 0, cwi = 0, sr_ = 1, si_ = 0;
+  double ar = 0, ai = 0;
+  if (act) {
+    // multiplicity times w_p/sqrt(pi); s_p
+    cwr = pr.mult[p] * pr.w_re[p] / sq; cwi = pr.mult[p] * pr.w_im[p] / sq;
+    sr_ = pr.s_re[p]; si_ = pr.s_im[p];
+    ar = pr.a_re[p]; ai = pr.a_im[p];
+  }
+  // 1/s and (2/s + s)
+  const double den = sr_ * sr_ + si_ * si_;
+  const double isr = sr_ / den, isi = -si_ / den;
+  const double csr = 2 * isr + sr_, csi = 2 * isi + si_;
+  for (int t = threadIdx.x % lanes; t < Q.L0; t += lanes) { acc[2 * t] = 0; acc[2 * t + 1] = 0; }
+  __syncwarp();
+  for (int dir = 0; dir < 2; ++dir) {
+    double sr = 0, si = 0, hr = 0, hi = 0;
+    if (act) {
+      const double* in = carry + (((size_t)dir * Q.nch + c) * Q.npad + p) * 4;
+      sr = in[0]; si = in[1]; hr = in[2]; hi = in[3];
+    }
+    // every lane runs L0 steps so that the shuffles below see the whole warp
+    for (int n = 0; n < Q.L0; ++n) {
+      const bool live = n < cnt;
+      const int t = dir == 0 ? n : cnt - 1 - n;
+      const int64_t i = start + t;
+      const double qq = live ? (double)qs[i] : 0.0;
+      double pot = 0, der = 0;
+      if (act && live) {
+        const int64_t id = dir == 0 ? i : i + 1;
+        const double dzi = id < Q.N ? (double)dz[id] : 0.0;
+        const Cplx<double> d = cexp_neg(ar, ai, dzi);
+        // H first (uses the previous inclusive S), then S
+        const double tr = hr + dzi * sr, ti = hi + dzi * si;
+        hr = d.re * tr - d.im * ti; hi = d.re * ti + d.im * tr;
+        const double nsr = d.re * sr - d.im * si + qq;
+        const double nsi = d.re * si + d.im * sr;
+        sr = nsr; si = nsi;
+        // exclusive S (j != i): S - q_i ; H has no j = i term
+        const double xr = sr - qq, xi = si;
+        // pot part: cw [ (1/alpha) S - 2 (1/s) H ]
+        const double ur = xr / Q.alpha - 2 * (isr * hr - isi * hi);
+        const double ui = xi / Q.alpha - 2 * (isr * hi + isi * hr);
+        pot = cwr * ur - cwi * ui;
+        // der part: cw [ -(2/s + s) S + 2 alpha H ] with sign +/- by direction
+        const double vr = -(csr * xr - csi * xi) + 2 * Q.alpha * hr;
+        const double vi = -(csr * xi + csi * xr) + 2 * Q.alpha * hi;
+        der = (dir == 0 ? 1.0 : -1.0) * (cwr * vr - cwi * vi);
+      }
+      // sum over the chunk's lanes
+      for (int o = lanes >> 1; o; o >>= 1) {
+        pot += __shfl_xor_sync(0xffffffffu, pot, o);
+        der += __shfl_xor_sync(0xffffffffu, der, o);
+      }
+      if (p == 0 && live) { acc[2 * t] += pot; acc[2 * t + 1] += der; }
+    }
+  }
+  __syncwarp();
+  if (p == 0 && valid) {
+    const double Qlt0 = cpre[2 * c], Plt0 = cpre[2 * c + 1];
+    const double Qt = cpre[2 * Q.nch], Pt = cpre[2 * Q.nch + 1];
+    double Ql = Qlt0, Pl = Plt0;
+    const double pre = 2.0 * 3.14159265358979323846 / Q.area;
+    for (int t = 0; t < cnt; ++t) {
+      const int64_t i = start + t;
+      const double z = (double)zs[i], qq = (double)qs[i];
+      const double Qg = Qt - Ql - qq, Pg = Pt - Pl - qq * z;
+      const double lin = z * Ql - Pl + Pg - z * Qg;
+      const double pot = Q.c1 * lin + acc[2 * t];
+      const double der = Q.c1 * (Ql - Qg) + acc[2 * t + 1];
+      phi0[i] = -pre * pot;
+      fz0[i] = pre * qq * der;
+      Ql += qq;
+      Pl += qq * z;
+    }
+  }
+  (void)cpb;
+}
+
+template <typename T>
+void launch_kzero(int64_t N, int L0, int nchunks0, const PairTab& pairs,
+                  double alpha, double area, const T* zs, const T* dz,
+                  const T* qs, double* work, double* phi0, double* fz0,
+                  cudaStream_t st) {
+  K0Params Q;
+  Q.N = N; Q.L0 = L0; Q.nch = nchunks0; Q.alpha = alpha; Q.area = area;
+  int npad = 1;
+  while (npad < pairs.np) npad <<= 1;
+  Q.npad = npad;
+  double c1 = 0.0;
+  for (int p = 0; p < pairs.np; ++p) {
+    // c1 = sum_l 2 w_l/(s_l sqrt(pi)): the pair gives 2 Re(w/s) times mult/2... per node
+    const double den = pairs.s_re[p] * pairs.s_re[p] + pairs.s_im[p] * pairs.s_im[p];
+    const double re = (pairs.w_re[p] * pairs.s_re[p] + pairs.w_im[p] * pairs.s_im[p]) / den;
+    c1 += pairs.mult[p] * 2.0 * re / 1.7724538509055160;
+  }
+  Q.c1 = c1;
+  double* agg = work;                                   // [nch][npad][8]
+  double* csum = agg + (size_t)nchunks0 * npad * 8;     // [nch][2]
+  double* carry = csum + (size_t)nchunks0 * 2;          // [2][nch][npad][4]
+  double* cpre = carry + (size_t)2 * nchunks0 * npad * 4;  // [nch+1][2]
+  const int tot = nchunks0 * npad;
+  kzero_aggregate_kernel<T><<<(tot + kK0Threads - 1) / kK0Threads, kK0Threads, 0, st>>>(
+      Q, pairs, zs, qs, agg, csum);
+  kzero_carry_kernel<T><<<1, 2 * npad + 1, 0, st>>>(Q, pairs, zs, agg, carry, csum, cpre);
+  const int cpb = kK0Threads / npad;
+  const size_t sm = (size_t)cpb * L0 * 2 * sizeof(double);
+  kzero_final_kernel<T><<<(tot + kK0Threads - 1) / kK0Threads, kK0Threads, sm, st>>>(
+      Q, pairs, zs, dz, qs, carry, cpre, phi0, fz0);
+}
+
+size_t kzero_work_doubles(int nchunks0, int np) {
+  int npad = 1;
+  while (npad < np) npad <<= 1;
+  return (size_t)nchunks0 * npad * 8 + (size_t)nchunks0 * 2 +
+         (size_t)2 * nchunks0 * npad * 4 + (size_t)(nchunks0 + 1) * 2;
+}
+
+// ================================================================== combine
+
+template <typename T>
+__global__ void combine_kernel(int64_t N, int nkr, const T* __restrict__ part,
+                               const double* __restrict__ phi0,
+                               const double* __restrict__ fz0,
+                               const T* __restrict__ qs,
+                               const int32_t* __restrict__ perm, double diagq,
+                               double* eblock, T* phi_out, T* force_out) {
+  __shared__ double red[32];
+  double e = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double ph = 0, fx = 0, fy = 0, fz = 0;
+    for (int r = 0; r < nkr; ++r) {
+      const T* b = part + (size_t)r * 4 * N;
+      ph += (double)b[i];
+      fx += (double)b[N + i];
+      fy += (double)b[2 * N + i];
+      fz += (double)b[3 * N + i];
+    }
+    const double qq = (double)qs[i];
+    ph += phi0[i] + qq * diagq;
+    fx *= qq; fy *= qq;
+    fz = fz * qq + fz0[i];
+    const int32_t o = perm[i];
+    if (phi_out) phi_out[o] = (T)ph;
+    if (force_out) {
+      force_out[3 * (int64_t)o] = (T)fx;
+      force_out[3 * (int64_t)o + 1] = (T)fy;
+      force_out[3 * (int64_t)o + 2] = (T)fz;
+    }
+    e += 0.5 * qq * ph;
+  }
+  for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[j];
+    eblock[blockIdx.x] = s;
+  }
+}
+
+__global__ void energy_sum_kernel(const double* eblock, int n, double* energy) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) s += eblock[j];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += red[j];
+    *energy = t;
+  }
+}
+
+template <typename T>
+void launch_combine(int64_t N, int nkr, const T* part, const double* phi0,
+                    const double* fz0, const T* qs, const int32_t* perm,
+                    double diagq, double* eblock, int nblk, T* phi_out,
+                    T* force_out, double* energy, cudaStream_t st) {
+  combine_kernel<T><<<nblk, 256, 0, st>>>(N, nkr, part, phi0, fz0, qs, perm,
+                                          diagq, eblock, phi_out, force_out);
+  if (energy) energy_sum_kernel<<<1, 256, 0, st>>>(eblock, nblk, energy);
+}
+
+// ========================================================= random-batch modes
+
+__device__ int upper_index(const double* cdf, int n, double u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (u < cdf[mid]) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double uniform53(uint64_t w) {
+  return (double)(w >> 11) * 1.1102230246251565e-16;   // 2^-53
+}
+
+// Fill the mode table. Full k-sum: (mx, my) from the host's half-plane list,
+// weight 2 (k and -k), gam = (pi/A) C_k 2. Random batch: (mx, my) drawn here
+// (Philox4x64-10 with counter (m, attempt, call, tag) and key (seed, 0); words
+// 0,1 then 2,3 are inverted through the per-axis cumulative tables; the origin
+// is rejected), gam = (pi/A) (H/P) 2 alpha/(sqrt(pi) k) (Eq. 4.7 with 4.9: the
+// Gaussian of C_k cancels against e^{k^2/(4 alpha^2)}).
+template <typename T>
+__global__ void mode_coef_kernel(int K, int Kpad, int npc, const int32_t* list,
+                                 int rbe, uint64_t seed, uint64_t counter,
+                                 SamplerTab sp, PairTab pr, double alpha,
+                                 double Lx, double Ly, double H,
+                                 ModeTab<T> mt, int32_t* sampled) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= Kpad) return;
+  const double pi = 3.14159265358979323846;
+  const double sqpi = 1.7724538509055160;
+  int mx = 0, my = 0;
+  if (m < K) {
+    if (!rbe) {
+      mx = list[2 * m];
+      my = list[2 * m + 1];
+    } else {
+      for (uint64_t attempt = 0; attempt < 64; ++attempt) {
+        U64x4 c;
+        c.v[0] = (uint64_t)m; c.v[1] = attempt; c.v[2] = counter; c.v[3] = 0x52424531ull;
+        const U64x4 r = philox4x64_10(c, seed, 0ull);
+        const int ax = upper_index(sp.cdfx, sp.nx, uniform53(r.v[0])) - sp.mxmax;
+        const int ay = upper_index(sp.cdfy, sp.ny, uniform53(r.v[1])) - sp.mymax;
+        if (ax != 0 || ay != 0) { mx = ax; my = ay; break; }
+        const int bx = upper_index(sp.cdfx, sp.nx, uniform53(r.v[2])) - sp.mxmax;
+        const int by = upper_index(sp.cdfy, sp.ny, uniform53(r.v[3])) - sp.mymax;
+        if (bx != 0 || by != 0) { mx = bx; my = by; break; }
+      }
+    }
+    if (sampled) { sampled[2 * m] = mx; sampled[2 * m + 1] = my; }
+  }
+  const bool live = (m < K) && (mx != 0 || my != 0);
+  const double kx = 2 * pi * mx / Lx, ky = 2 * pi * my / Ly;
+  const double k = live ? sqrt(kx * kx + ky * ky) : 1.0;
+  double gam = 0.0;
+  if (live) {
+    gam = rbe ? pi / (Lx * Ly) * (H / K) * 2.0 * alpha / (sqpi * k)
+              : pi / (Lx * Ly) * 2.0 * (2.0 * alpha * exp(-k * k / (4.0 * alpha * alpha)) / (sqpi * k));
+  }
+  double ckk = 0.0, sY = 0.0, sZ = 0.0;
+  for (int p = 0; p < npc; ++p) {
+    double cr = 0, ci = 0, br = 0, bi = 0;
+    if (p < pr.np) {
+      const double ar = pr.a_re[p], ai = pr.a_im[p];
+      const double wr = pr.w_re[p], wi = pr.w_im[p];
+      const double dr = ar * ar - ai * ai - k * k, di = 2 * ar * ai;   // a^2 - k^2
+      const double dd = dr * dr + di * di;
+      const double qr = (wr * dr + wi * di) / dd, qi = (wi * dr - wr * di) / dd;  // w/(a^2-k^2)
+      ckk += pr.mult[p] * 2.0 * (ar * qr - ai * qi);     // sum over both nodes of 2 a w/(a^2-k^2)
+      cr = -2.0 * k * qr * pr.mult[p] * gam;             // m_p gam c_{k,p}
+      ci = -2.0 * k * qi * pr.mult[p] * gam;
+      br = cr * ar - ci * ai;                            // times a_p
+      bi = cr * ai + ci * ar;
+      sY += cr;
+      sZ += br;
+    }
+    mt.cp[((size_t)0 * npc + p) * Kpad + m] = (T)cr;
+    mt.cp[((size_t)1 * npc + p) * Kpad + m] = (T)ci;
+    mt.cp[((size_t)2 * npc + p) * Kpad + m] = (T)br;
+    mt.cp[((size_t)3 * npc + p) * Kpad + m] = (T)bi;
+  }
+  const double ck = gam * ckk;
+  mt.mx[m] = mx;
+  mt.my[m] = my;
+  mt.kx[m] = (T)kx;
+  mt.ky[m] = (T)ky;
+  mt.kk[m] = (T)k;
+  mt.ck[m] = (T)ck;
+  mt.ckk[m] = (T)(ck * k);
+  mt.sY[m] = (T)(ck + sY);
+  mt.sZ[m] = (T)(ck * k + sZ);
+}
+
+template <typename T>
+void launch_mode_coef(int K, int Kpad, int npc, const int32_t* list, int rbe,
+                      uint64_t seed, uint64_t counter, const SamplerTab& sp,
+                      const PairTab& pairs, double alpha, double Lx, double Ly,
+                      double H, ModeTab<T> modes, int32_t* sampled,
+                      cudaStream_t st) {
+  mode_coef_kernel<T><<<(Kpad + 127) / 128, 128, 0, st>>>(
+      K, Kpad, npc, list, rbe, seed, counter, sp, pairs, alpha, Lx, Ly, H,
+      modes, sampled);
+}
+
+// ============================================================ instantiations
+template void launch_prepare<float>(int64_t, const float*, const float*, double, void*, uint32_t*, double*, unsigned*, cudaStream_t);
+template void launch_prepare<double>(int64_t, const double*, const double*, double, void*, uint32_t*, double*, unsigned*, cudaStream_t);
+template void launch_gather<float>(int64_t, const float*, const float*, const uint32_t*, double, double, float*, float*, float*, uint32_t*, uint32_t*, int32_t*, cudaStream_t);
+template void launch_gather<double>(int64_t, const double*, const double*, const uint32_t*, double, double, double*, double*, double*, uint64_t*, uint64_t*, int32_t*, cudaStream_t);
+template void launch_kspace<float>(const ScanPlan&, const ModeTab<float>&, const PairTab&, const float*, const float*, const float*, const uint32_t*, const uint32_t*, Cplx<float>*, Cplx<float>*, Cplx<double>*, float*, cudaStream_t, cudaEvent_t*);
+template void launch_kspace<double>(const ScanPlan&, const ModeTab<double>&, const PairTab&, const double*, const double*, const double*, const uint64_t*, const uint64_t*, Cplx<double>*, Cplx<double>*, Cplx<double>*, double*, cudaStream_t, cudaEvent_t*);
+template void launch_kzero<float>(int64_t, int, int, const PairTab&, double, double, const float*, const float*, const float*, double*, double*, double*, cudaStream_t);
+template void launch_kzero<double>(int64_t, int, int, const PairTab&, double, double, const double*, const double*, const double*, double*, double*, double*, cudaStream_t);
+template void launch_combine<float>(int64_t, int, const float*, const double*, const double*, const float*, const int32_t*, double, double*, int, float*, float*, double*, cudaStream_t);
+template void launch_combine<double>(int64_t, int, const double*, const double*, const double*, const double*, const int32_t*, double, double*, int, double*, double*, double*, cudaStream_t);
+template void launch_mode_coef<float>(int, int, int, const int32_t*, int, uint64_t, uint64_t, const SamplerTab&, const PairTab&, double, double, double, double, ModeTab<float>, int32_t*, cudaStream_t);
+template void launch_mode_coef<double>(int, int, int, const int32_t*, int, uint64_t, uint64_t, const SamplerTab&, const PairTab&, double, double, double, double, ModeTab<double>, int32_t*, cudaStream_t);
+
+}  // namespace qslab

@@ -1,0 +1,176 @@
+// Stable LSD radix sort of z keys with a 32-bit payload (the particle index).
+//
+// The paper sorts particles by z before the recursions (Section 3.2; it
+// notes that a bucket sort makes this O(N), Section 3.4). The recursions need
+// the exact order z_1 <= ... <= z_N (Remark 3.3: every exponent must be
+// non-positive), so the keys are the IEEE bits of z >= 0 themselves, which
+// order exactly like the values; no quantisation.
+//
+// One pass per 8-bit digit, three kernels per pass:
+//   hist    per-tile digit counts, counts[digit][tile]
+//   scan    exclusive prefix over counts in digit-major order (one CTA)
+//   scatter stable placement: within a warp, keys are ranked in input order
+//           with __match_any_sync; warps of a tile are ordered by a per-digit
+//           prefix over their counts; tiles by the global scan.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qslab_internal.h"
+
+namespace qslab {
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kItems = 8;
+constexpr int kTile = kSortThreads * kItems;
+constexpr int kRadix = 256;
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads)
+hist_kernel(const K* __restrict__ keys, int64_t N, int shift, uint32_t* counts,
+            int nblocks) {
+  __shared__ uint32_t h[kRadix];
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) h[d] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * kTile;
+  for (int s = 0; s < kItems; ++s) {
+    int64_t idx = base + (int64_t)s * kSortThreads + threadIdx.x;
+    if (idx < N) atomicAdd(&h[(unsigned)(keys[idx] >> shift) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+    counts[(int64_t)d * nblocks + blockIdx.x] = h[d];
+}
+
+// Exclusive scan of n uint32 values in place, one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* a, int64_t n) {
+  __shared__ uint32_t wsum[32];
+  const int t = threadIdx.x;
+  const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+  const int64_t lo = t * per;
+  const int64_t hi = (lo + per < n) ? lo + per : n;
+  uint32_t sum = 0;
+  for (int64_t i = lo; i < hi; ++i) sum += a[i];
+  // block-wide exclusive scan of the per-thread sums
+  const int lane = t & 31, w = t >> 5;
+  uint32_t v = sum;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) wsum[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t x = wsum[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    wsum[lane] = x;  // inclusive over warps
+  }
+  __syncthreads();
+  uint32_t run = v - sum + (w > 0 ? wsum[w - 1] : 0u);
+  for (int64_t i = lo; i < hi; ++i) {
+    uint32_t c = a[i];
+    a[i] = run;
+    run += c;
+  }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads)
+scatter_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+               K* __restrict__ kout, uint32_t* __restrict__ vout, int64_t N,
+               int shift, const uint32_t* __restrict__ offsets, int nblocks) {
+  __shared__ uint32_t wcnt[kSortWarps][kRadix];
+  __shared__ uint32_t goff[kRadix];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+    goff[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
+    for (int ww = 0; ww < kSortWarps; ++ww) wcnt[ww][d] = 0;
+  }
+  __syncthreads();
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)w * 32 * kItems;
+  K key[kItems];
+  uint32_t val[kItems], loc[kItems], dig[kItems];
+  for (int s = 0; s < kItems; ++s) {
+    const int64_t idx = base + s * 32 + lane;
+    const bool valid = idx < N;
+    key[s] = valid ? kin[idx] : (K)0;
+    val[s] = valid ? vin[idx] : 0u;
+    const unsigned d = valid ? ((unsigned)(key[s] >> shift) & 0xFFu) : 0x100u;
+    dig[s] = d;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned before = valid ? wcnt[w][d & 0xFFu] : 0u;
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) wcnt[w][d & 0xFFu] = before + __popc(peers);
+    __syncwarp();
+    loc[s] = before + __popc(peers & lt);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+    uint32_t run = 0;
+    for (int ww = 0; ww < kSortWarps; ++ww) {
+      uint32_t c = wcnt[ww][d];
+      wcnt[ww][d] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  for (int s = 0; s < kItems; ++s) {
+    if (dig[s] < 0x100u) {
+      const uint32_t pos = goff[dig[s]] + wcnt[w][dig[s]] + loc[s];
+      kout[pos] = key[s];
+      vout[pos] = val[s];
+    }
+  }
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+size_t sort_workspace_bytes(int64_t N, int key_bytes) {
+  const int64_t nb = (N + kTile - 1) / kTile;
+  return 2 * align256((size_t)N * key_bytes) + 2 * align256((size_t)N * 4) +
+         align256((size_t)nb * kRadix * 4);
+}
+
+void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes) {
+  char* p = static_cast<char*>(base);
+  w.nblocks = (int)((N + kTile - 1) / kTile);
+  w.keys[0] = p; p += align256((size_t)N * key_bytes);
+  w.keys[1] = p; p += align256((size_t)N * key_bytes);
+  w.vals[0] = reinterpret_cast<uint32_t*>(p); p += align256((size_t)N * 4);
+  w.vals[1] = reinterpret_cast<uint32_t*>(p); p += align256((size_t)N * 4);
+  w.counts = reinterpret_cast<uint32_t*>(p);
+}
+
+int radix_sort(SortWork& w, int64_t N, int key_bytes, cudaStream_t st) {
+  const int passes = key_bytes;  // 8-bit digits
+  int cur = 0;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = 8 * p;
+    if (key_bytes == 4) {
+      auto* kin = static_cast<const uint32_t*>(w.keys[cur]);
+      auto* kout = static_cast<uint32_t*>(w.keys[cur ^ 1]);
+      hist_kernel<uint32_t><<<w.nblocks, kSortThreads, 0, st>>>(kin, N, shift, w.counts, w.nblocks);
+      scan_kernel<<<1, 1024, 0, st>>>(w.counts, (int64_t)w.nblocks * kRadix);
+      scatter_kernel<uint32_t><<<w.nblocks, kSortThreads, 0, st>>>(
+          kin, w.vals[cur], kout, w.vals[cur ^ 1], N, shift, w.counts, w.nblocks);
+    } else {
+      auto* kin = static_cast<const uint64_t*>(w.keys[cur]);
+      auto* kout = static_cast<uint64_t*>(w.keys[cur ^ 1]);
+      hist_kernel<uint64_t><<<w.nblocks, kSortThreads, 0, st>>>(kin, N, shift, w.counts, w.nblocks);
+      scan_kernel<<<1, 1024, 0, st>>>(w.counts, (int64_t)w.nblocks * kRadix);
+      scatter_kernel<uint64_t><<<w.nblocks, kSortThreads, 0, st>>>(
+          kin, w.vals[cur], kout, w.vals[cur ^ 1], N, shift, w.counts, w.nblocks);
+    }
+    cur ^= 1;
+  }
+  return cur;
+}
+
+}  // namespace qslab
