@@ -11,7 +11,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/qslab.h"
+#include "qslab.h"
 #include "qslab_internal.h"
 
 using namespace qslab;
@@ -305,7 +305,7 @@ Plan make_plan(const qslab_ctx* c, int64_t N, bool host_io) {
   s.nchunks = (int)((N + L - 1) / L);
   s.np = c->npc;
   s.nstates = 1 + 2 * c->npc;
-  P.L0 = 64;
+  P.L0 = 256;
   P.nch0 = (int)((N + P.L0 - 1) / P.L0);
   P.nblk = (int)((N + 255) / 256);
   if (P.nblk > 152 * 8) P.nblk = 152 * 8;
@@ -321,7 +321,7 @@ Plan make_plan(const qslab_ctx* c, int64_t N, bool host_io) {
   const size_t aggn = (size_t)2 * s.nchunks * s.nstates * s.Kpad;
   P.off_agg = take(2 * tsz * aggn);
   P.off_carry = take(2 * tsz * aggn);
-  P.off_pdec = take(16 * (size_t)2 * s.nchunks * s.np);
+  P.off_pdec = take(kspace_decay_bytes(s, dp ? 1 : 0));
   P.off_part = take(tsz * 4 * (size_t)s.nkr * N);
   P.off_k0 = take(8 * kzero_work_doubles(P.nch0, c->pairs.np));
   P.off_phi0 = take(8 * (size_t)N);
@@ -366,7 +366,7 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energy,
   int32_t* perm = reinterpret_cast<int32_t*>(ws + P.off_perm);
   Cplx<T>* agg = reinterpret_cast<Cplx<T>*>(ws + P.off_agg);
   Cplx<T>* carry = reinterpret_cast<Cplx<T>*>(ws + P.off_carry);
-  Cplx<double>* pdec = reinterpret_cast<Cplx<double>*>(ws + P.off_pdec);
+  void* pdec = ws + P.off_pdec;
   T* part = reinterpret_cast<T*>(ws + P.off_part);
   double* k0w = reinterpret_cast<double*>(ws + P.off_k0);
   double* phi0 = reinterpret_cast<double*>(ws + P.off_phi0);
@@ -384,7 +384,7 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energy,
   launch_check_neutral(c->d_sums, tol, c->d_status, st);
   const int r = radix_sort(sw, N, (int)sizeof(T), st);
   launch_gather<T>(N, pos, q, sw.vals[r], c->Lx, c->Ly, zs, dz, qs, xh, yh, perm, st);
-  nl += 3 + 3 * (int)sizeof(T);
+  nl += 3 + 3 * (int)sizeof(T);   // prepare, check, gather + 3 kernels per sort pass
   if (ev) cudaEventRecord(ev[1], st);
   // mode table: once per configuration for the full k-sum, every call for RBE
   if (c->mode == 2 || !c->coef_ready) {

@@ -77,6 +77,7 @@ struct SortWork {
   void* keys[2];          // uint32 or uint64 keys, ping-pong
   uint32_t* vals[2];      // payload (original index), ping-pong
   uint32_t* counts;       // [256][nblocks]
+  uint32_t* totals;       // [passes][256] digit totals
   int nblocks;
 };
 size_t sort_workspace_bytes(int64_t N, int key_bytes);
@@ -113,18 +114,22 @@ void launch_kspace(const ScanPlan& plan, const ModeTab<T>& modes,
                    const PairTab& pairs, const T* zs, const T* dz, const T* qs,
                    const typename PhaseT<T>::type* xh,
                    const typename PhaseT<T>::type* yh, Cplx<T>* agg,
-                   Cplx<T>* carry, Cplx<double>* pdec, T* part,
+                   Cplx<T>* carry, void* dec, T* part,
                    cudaStream_t st, cudaEvent_t* ev3);  // ev3: 3 events or NULL
+// bytes of the chunk-to-chunk decay tables (pair and mode decays)
+size_t kspace_decay_bytes(const ScanPlan& pl, int fp64);
 
+// phi0 / fz0: per sorted particle, in the carry type (FP64 on the FP64 path,
+// double-float on the FP32 path)
 template <typename T>
 void launch_kzero(int64_t N, int L0, int nchunks0, const PairTab& pairs,
                   double alpha, double area, const T* zs, const T* dz,
-                  const T* qs, double* work, double* phi0, double* fz0,
+                  const T* qs, double* work, void* phi0, void* fz0,
                   cudaStream_t st);
 
 template <typename T>
-void launch_combine(int64_t N, int nkr, const T* part, const double* phi0,
-                    const double* fz0, const T* qs, const int32_t* perm,
+void launch_combine(int64_t N, int nkr, const T* part, const void* phi0,
+                    const void* fz0, const T* qs, const int32_t* perm,
                     double diagq, double* eblock, int nblk, T* phi_out,
                     T* force_out, double* energy, cudaStream_t st);
 

@@ -25,6 +25,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "qslab_df.cuh"
 #include "qslab_internal.h"
 #include "qslab_math.cuh"
 
@@ -147,47 +148,44 @@ void launch_gather(int64_t N, const T* pos, const T* q, const uint32_t* perm,
 
 // ============================================================ k != 0 scans
 
-// Shared-memory layout of one chunk (L particles, plus one dz of the next
-// chunk's first particle).
+// Shared-memory layout of one chunk: L particle records (plus one more whose
+// dz belongs to the next chunk's first particle), the exponential tables in
+// particle-major order (all pairs of one particle are contiguous), and in
+// pass B the per-warp output slots.
 template <typename T>
-struct ChunkSmem {
-  using PH = typename PhaseT<T>::type;
-  Cplx<T>* tab;   // [NP][L+1] decays (pass B) or [2][NP][L] E tables (pass A)
-  T* dzs;         // [L+1]
-  T* zl;          // [L]
-  T* ql;          // [L]
-  PH* xl;         // [L]
-  PH* yl;         // [L]
-  T* slots;       // pass B: [W][L][4]
+struct __align__(4 * sizeof(T)) Rec {
+  typename PhaseT<T>::type xh, yh;   // fixed-point x/Lx, y/Ly
+  T q, dz;
 };
 
 template <typename T>
-__host__ __device__ inline size_t align_up(size_t x) { return (x + 15) & ~size_t(15); }
+struct ChunkSmem {
+  Cplx<T>* tab;   // pass B: [L+1][NP] decays; pass A: [L][2][NP] (E_f, E_b)
+  Rec<T>* rec;    // [L+1]
+  T* zl;          // [L]
+  T* slots;       // pass B: [W][L][4]
+};
+
+__host__ __device__ inline size_t align_up(size_t x) { return (x + 31) & ~size_t(31); }
 
 template <typename T>
 __host__ __device__ inline size_t chunk_smem_bytes(int L, int NP, int W, bool passB) {
-  using PH = typename PhaseT<T>::type;
   size_t b = 0;
-  b += align_up<T>(sizeof(Cplx<T>) * (size_t)NP * (passB ? (L + 1) : 2 * L));
-  b += align_up<T>(sizeof(T) * (L + 1));
-  b += align_up<T>(sizeof(T) * L) * 2;
-  b += align_up<T>(sizeof(PH) * L) * 2;
-  if (passB) b += align_up<T>(sizeof(T) * (size_t)W * L * 4);
+  b += align_up(sizeof(Cplx<T>) * (size_t)NP * (passB ? (L + 1) : 2 * L));
+  b += align_up(sizeof(Rec<T>) * (L + 1));
+  b += align_up(sizeof(T) * L);
+  if (passB) b += align_up(sizeof(T) * (size_t)W * L * 4);
   return b;
 }
 
 template <typename T>
 __device__ inline ChunkSmem<T> carve(char* base, int L, int NP, int W, bool passB) {
-  using PH = typename PhaseT<T>::type;
   ChunkSmem<T> s;
   char* p = base;
   s.tab = reinterpret_cast<Cplx<T>*>(p);
-  p += align_up<T>(sizeof(Cplx<T>) * (size_t)NP * (passB ? (L + 1) : 2 * L));
-  s.dzs = reinterpret_cast<T*>(p); p += align_up<T>(sizeof(T) * (L + 1));
-  s.zl = reinterpret_cast<T*>(p); p += align_up<T>(sizeof(T) * L);
-  s.ql = reinterpret_cast<T*>(p); p += align_up<T>(sizeof(T) * L);
-  s.xl = reinterpret_cast<PH*>(p); p += align_up<T>(sizeof(PH) * L);
-  s.yl = reinterpret_cast<PH*>(p); p += align_up<T>(sizeof(PH) * L);
+  p += align_up(sizeof(Cplx<T>) * (size_t)NP * (passB ? (L + 1) : 2 * L));
+  s.rec = reinterpret_cast<Rec<T>*>(p); p += align_up(sizeof(Rec<T>) * (L + 1));
+  s.zl = reinterpret_cast<T*>(p); p += align_up(sizeof(T) * L);
   s.slots = passB ? reinterpret_cast<T*>(p) : nullptr;
   return s;
 }
@@ -236,20 +234,24 @@ __device__ inline void load_chunk(const KParams<T>& P, ChunkSmem<T>& s,
   const int64_t N = P.plan.N;
   for (int t = threadIdx.x; t <= cnt; t += blockDim.x) {
     const int64_t i = start + t;
-    s.dzs[t] = (i < N) ? P.dz[i] : (T)0;
+    Rec<T> r;
+    r.dz = (i < N) ? P.dz[i] : (T)0;
     if (t < cnt) {
+      r.xh = P.xh[i];
+      r.yh = P.yh[i];
+      r.q = P.qs[i];
       s.zl[t] = P.zs[i];
-      s.ql[t] = P.qs[i];
-      s.xl[t] = P.xh[i];
-      s.yl[t] = P.yh[i];
+    } else {
+      r.xh = 0; r.yh = 0; r.q = 0;
     }
+    s.rec[t] = r;
   }
 }
 
 // ------------------------------------------------------------------ pass A
 template <typename T, int NP>
 __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
-  extern __shared__ __align__(16) char smem[];
+  extern __shared__ __align__(32) char smem[];
   const ScanPlan& pl = P.plan;
   const int c = blockIdx.x;
   const int64_t start = (int64_t)c * pl.L;
@@ -257,35 +259,37 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
   ChunkSmem<T> s = carve<T>(smem, pl.L, NP, 0, false);
   load_chunk<T>(P, s, start, cnt);
   __syncthreads();
-  // E tables: Ef[p][t] = e^{-a_p (z_end - z_t)}, Eb[p][t] = e^{-a_p (z_t - z_start)}
+  // E tables: [t][0][p] = e^{-a_p (z_end - z_t)}, [t][1][p] = e^{-a_p (z_t - z_start)}
   const T zend = s.zl[cnt - 1], zst = s.zl[0];
   for (int e = threadIdx.x; e < NP * cnt; e += blockDim.x) {
-    const int p = e / cnt, t = e - p * cnt;
+    const int t = e / NP, p = e - t * NP;
     const T ar = (T)pairs.a_re[p], ai = (T)pairs.a_im[p];
-    s.tab[p * pl.L + t] = cexp_neg(ar, ai, zend - s.zl[t]);
-    s.tab[(NP + p) * pl.L + t] = cexp_neg(ar, ai, s.zl[t] - zst);
+    s.tab[(2 * t) * NP + p] = cexp_neg(ar, ai, zend - s.zl[t]);
+    s.tab[(2 * t + 1) * NP + p] = cexp_neg(ar, ai, s.zl[t] - zst);
   }
   __syncthreads();
   const int m = blockIdx.y * pl.KR + threadIdx.x;
   ModeCoef<T, NP> mc;
   load_mode<T, NP>(P.modes, pl.Kpad, m, mc);
-  // accumulators: state 0 (beta = k, complex input) and pair states
   Cplx<T> f0 = {0, 0}, b0 = {0, 0};
   Cplx<T> fa[NP], fb[NP], ba[NP], bb[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) fa[p] = fb[p] = ba[p] = bb[p] = Cplx<T>{0, 0};
   for (int t = 0; t < cnt; ++t) {
+    const Rec<T> r = s.rec[t];
     T cs, sn;
-    sincos_turns(phase_turns(mc.mx, mc.my, s.xl[t], s.yl[t]), cs, sn);
-    const T a = s.ql[t] * cs, b = s.ql[t] * sn;   // u = a - i b
-    const T ef = exp_neg(mc.kk * (zend - s.zl[t]));
-    const T eb = exp_neg(mc.kk * (s.zl[t] - zst));
+    sincos_turns(phase_turns(mc.mx, mc.my, r.xh, r.yh), cs, sn);
+    const T a = r.q * cs, b = r.q * sn;   // u = a - i b
+    const T zt = s.zl[t];
+    const T ef = exp_neg(mc.kk * (zend - zt));
+    const T eb = exp_neg(mc.kk * (zt - zst));
     f0.re = fma(ef, a, f0.re); f0.im = fma(-ef, b, f0.im);
     b0.re = fma(eb, a, b0.re); b0.im = fma(-eb, b, b0.im);
+    const Cplx<T>* Et = s.tab + 2 * t * NP;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      const Cplx<T> Ef = s.tab[p * pl.L + t];
-      const Cplx<T> Eb = s.tab[(NP + p) * pl.L + t];
+      const Cplx<T> Ef = Et[p];
+      const Cplx<T> Eb = Et[NP + p];
       fa[p].re = fma(Ef.re, a, fa[p].re); fa[p].im = fma(Ef.im, a, fa[p].im);
       fb[p].re = fma(Ef.re, b, fb[p].re); fb[p].im = fma(Ef.im, b, fb[p].im);
       ba[p].re = fma(Eb.re, a, ba[p].re); ba[p].im = fma(Eb.im, a, ba[p].im);
@@ -308,31 +312,81 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
 }
 
 // --------------------------------------------------- chunk-to-chunk decays
-// pdec[dir][c][p]: forward e^{-a_p (z_end(c) - z_end(c-1))}, backward
-// e^{-a_p (z_start(c+1) - z_start(c))}, in FP64.
+// All decays between chunk reference points are computed in FP64 by these
+// parallel kernels and stored in the carry type (FP64, or double-float on the
+// FP32 path), so that the sequential chains below only multiply and add.
+//   pair decays  pdec[dir][c][p]: forward e^{-a_p (z_end(c) - z_end(c-1))},
+//                backward e^{-a_p (z_start(c+1) - z_start(c))}
+//   mode decays  kdec[dir][c][m]: the same with beta = |k_m|
 template <typename T>
-__global__ void pair_decay_kernel(ScanPlan pl, const T* zs, PairTab pairs,
-                                  Cplx<double>* pdec) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  const int np = pl.np;
-  if (e >= 2 * pl.nchunks * np) return;
-  const int dir = e / (pl.nchunks * np);
-  const int r = e - dir * pl.nchunks * np;
-  const int c = r / np, p = r - c * np;
-  double dzc = 0.0;
-  if (dir == 0 && c > 0) {
-    const int64_t e1 = imin64((int64_t)(c + 1) * pl.L, pl.N) - 1;
-    const int64_t e0 = (int64_t)c * pl.L - 1;
-    dzc = (double)zs[e1] - (double)zs[e0];
-  } else if (dir == 1 && c < pl.nchunks - 1) {
-    dzc = (double)zs[(int64_t)(c + 1) * pl.L] - (double)zs[(int64_t)c * pl.L];
+__device__ inline double chunk_gap(const T* zs, int64_t N, int L, int nch, int dir, int c) {
+  if (dir == 0) {
+    if (c == 0) return 0.0;
+    const int64_t e1 = imin64((int64_t)(c + 1) * L, N) - 1;
+    return (double)zs[e1] - (double)zs[(int64_t)c * L - 1];
   }
-  pdec[e] = cexp_neg(pairs.a_re[p], pairs.a_im[p], dzc);
+  if (c >= nch - 1) return 0.0;
+  return (double)zs[(int64_t)(c + 1) * L] - (double)zs[(int64_t)c * L];
+}
+
+template <typename T>
+__global__ void pair_decay_kernel(int64_t N, int L, int nch, int np, const T* zs,
+                                  PairTab pairs,
+                                  Cplx<typename CarryNum<T>::type>* pdec,
+                                  typename CarryNum<T>::type* gaps) {
+  using CN = typename CarryNum<T>::type;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * nch * np) return;
+  const int dir = e / (nch * np);
+  const int r = e - dir * nch * np;
+  const int c = r / np, p = r - c * np;
+  const double gap = chunk_gap(zs, N, L, nch, dir, c);
+  const Cplx<double> d = cexp_neg(pairs.a_re[p], pairs.a_im[p], gap);
+  pdec[e] = Cplx<CN>{cn_from(d.re, (CN*)nullptr), cn_from(d.im, (CN*)nullptr)};
+  if (gaps && p == 0) gaps[dir * nch + c] = cn_from(gap, (CN*)nullptr);
+}
+
+// e^{-x} in FP64 for x >= 0: the Taylor series to x^11 when x < 1/16
+// (truncation below 2e-21), the library exp otherwise.
+__device__ __forceinline__ double exp_neg_small(double x) {
+  if (x >= 0.0625) return exp(-x);
+  double r = -1.0 / 39916800.0;
+  r = fma(r, x, 1.0 / 3628800.0);
+  r = fma(r, x, -1.0 / 362880.0);
+  r = fma(r, x, 1.0 / 40320.0);
+  r = fma(r, x, -1.0 / 5040.0);
+  r = fma(r, x, 1.0 / 720.0);
+  r = fma(r, x, -1.0 / 120.0);
+  r = fma(r, x, 1.0 / 24.0);
+  r = fma(r, x, -1.0 / 6.0);
+  r = fma(r, x, 0.5);
+  r = fma(r, x, -1.0);
+  return fma(r, x, 1.0);
+}
+
+template <typename T>
+__global__ void mode_decay_kernel(ScanPlan pl, const T* zs, const T* kk,
+                                  typename CarryNum<T>::type* kdec) {
+  using CN = typename CarryNum<T>::type;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t tot = (int64_t)2 * pl.nchunks * pl.Kpad;
+  if (e >= tot) return;
+  const int dir = (int)(e / ((int64_t)pl.nchunks * pl.Kpad));
+  const int64_t r = e - (int64_t)dir * pl.nchunks * pl.Kpad;
+  const int c = (int)(r / pl.Kpad), m = (int)(r - (int64_t)c * pl.Kpad);
+  const double x = (double)kk[m] * chunk_gap(zs, pl.N, pl.L, pl.nchunks, dir, c);
+  kdec[e] = cn_from(exp_neg_small(x), (CN*)nullptr);
 }
 
 // ------------------------------------------------------------------ carries
+// One thread per (direction, state, mode): carry_in[c+1] = D_c carry_in[c] +
+// A_c (forward; mirrored backward), in the carry type. Inputs for a batch of
+// chunks are loaded first so the dependent chain waits for arithmetic only.
 template <typename T>
-__global__ void kspace_carry_kernel(KParams<T> P, const Cplx<double>* pdec) {
+__global__ void kspace_carry_kernel(KParams<T> P,
+                                    const Cplx<typename CarryNum<T>::type>* pdec,
+                                    const typename CarryNum<T>::type* kdec) {
+  using CN = typename CarryNum<T>::type;
   const ScanPlan& pl = P.plan;
   const int S = pl.nstates;
   const int total = 2 * S * pl.Kpad;
@@ -341,44 +395,51 @@ __global__ void kspace_carry_kernel(KParams<T> P, const Cplx<double>* pdec) {
   const int dir = e / (S * pl.Kpad);
   const int r = e - dir * S * pl.Kpad;
   const int st = r / pl.Kpad, m = r - st * pl.Kpad;
-  const double kk = (double)P.modes.kk[m];
   const size_t dirstride = (size_t)pl.nchunks * S * pl.Kpad;
   const Cplx<T>* A = P.agg + dir * dirstride + (size_t)st * pl.Kpad + m;
   Cplx<T>* C = P.carry + dir * dirstride + (size_t)st * pl.Kpad + m;
   const size_t cs = (size_t)S * pl.Kpad;
   const int p = (st - 1) >> 1;
-  double cr = 0.0, ci = 0.0;
   const int nc = pl.nchunks;
-  for (int j = 0; j < nc; ++j) {
-    const int c = dir == 0 ? j : nc - 1 - j;
-    C[c * cs] = Cplx<T>{(T)cr, (T)ci};
-    // decay from this chunk's reference point to the next one
-    double dr, di;
-    if (st == 0) {
-      double dzc;
-      if (dir == 0) {
-        const int64_t e1 = imin64((int64_t)(c + 1) * pl.L, pl.N) - 1;
-        dzc = c > 0 ? (double)P.zs[e1] - (double)P.zs[(int64_t)c * pl.L - 1] : 0.0;
-      } else {
-        dzc = c < nc - 1 ? (double)P.zs[(int64_t)(c + 1) * pl.L] - (double)P.zs[(int64_t)c * pl.L] : 0.0;
+  CN cr = cn_zero((CN*)nullptr), ci = cn_zero((CN*)nullptr);
+  const CN zero = cn_zero((CN*)nullptr);
+  constexpr int B = 16;
+  for (int j0 = 0; j0 < nc; j0 += B) {
+    Cplx<T> a[B];
+    CN dr[B], di[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int j = j0 + u;
+      dr[u] = zero; di[u] = zero; a[u] = Cplx<T>{0, 0};
+      if (j < nc) {
+        const int c = dir == 0 ? j : nc - 1 - j;
+        a[u] = A[c * cs];
+        if (st == 0) {
+          dr[u] = kdec[((size_t)dir * nc + c) * pl.Kpad + m];
+        } else {
+          const Cplx<CN> d = pdec[((size_t)dir * nc + c) * pl.np + p];
+          dr[u] = d.re; di[u] = d.im;
+        }
       }
-      dr = exp(-kk * dzc);
-      di = 0.0;
-    } else {
-      const Cplx<double> d = pdec[((size_t)dir * nc + c) * pl.np + p];
-      dr = d.re; di = d.im;
     }
-    const Cplx<T> a = A[c * cs];
-    const double nr = dr * cr - di * ci + (double)a.re;
-    const double ni = dr * ci + di * cr + (double)a.im;
-    cr = nr; ci = ni;
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int j = j0 + u;
+      if (j < nc) {
+        const int c = dir == 0 ? j : nc - 1 - j;
+        C[c * cs] = Cplx<T>{cn_to_t(cr), cn_to_t(ci)};
+        const CN nr = dr[u] * cr - di[u] * ci + cn_from_t(a[u].re, (CN*)nullptr);
+        const CN ni = dr[u] * ci + di[u] * cr + cn_from_t(a[u].im, (CN*)nullptr);
+        cr = nr; ci = ni;
+      }
+    }
   }
 }
 
 // ------------------------------------------------------------------ pass B
 template <typename T, int NP>
 __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
-  extern __shared__ __align__(16) char smem[];
+  extern __shared__ __align__(32) char smem[];
   const ScanPlan& pl = P.plan;
   const int c = blockIdx.x;
   const int W = pl.KR / kWarp;
@@ -387,10 +448,10 @@ __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
   ChunkSmem<T> s = carve<T>(smem, pl.L, NP, W, true);
   load_chunk<T>(P, s, start, cnt);
   __syncthreads();
-  // per-step decays d[p][t] = e^{-a_p dz_t}, t = 0..cnt (t = cnt: next chunk)
+  // per-step decays [t][p] = e^{-a_p dz_t}, t = 0..cnt (t = cnt: next chunk)
   for (int e = threadIdx.x; e < NP * (cnt + 1); e += blockDim.x) {
-    const int p = e / (cnt + 1), t = e - p * (cnt + 1);
-    s.tab[p * (pl.L + 1) + t] = cexp_neg((T)pairs.a_re[p], (T)pairs.a_im[p], s.dzs[t]);
+    const int t = e / NP, p = e - t * NP;
+    s.tab[t * NP + p] = cexp_neg((T)pairs.a_re[p], (T)pairs.a_im[p], s.rec[t].dz);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -411,61 +472,58 @@ __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
       gb[p] = cin[(size_t)(2 + 2 * p) * pl.Kpad];
     }
     const T zsign = dir == 0 ? (T)1 : (T)-1;
-    T buf[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) buf[j] = (T)0;
-    for (int n = 0; n < cnt; ++n) {
-      const int t = dir == 0 ? n : cnt - 1 - n;
-      const int td = dir == 0 ? t : t + 1;      // index of the decay to apply
-      T cs, sn;
-      sincos_turns(phase_turns(mc.mx, mc.my, s.xl[t], s.yl[t]), cs, sn);
-      const T a = s.ql[t] * cs, b = s.ql[t] * sn;
-      // beta = k: real decay, complex input u = a - i b
-      const T dk = exp_neg(mc.kk * s.dzs[td]);
-      g0.re = fma(dk, g0.re, a);
-      g0.im = fma(dk, g0.im, -b);
-      T Yr = mc.ck * g0.re, Yi = mc.ck * g0.im;
-      T Zr = mc.ckk * g0.re, Zi = mc.ckk * g0.im;
-#pragma unroll
-      for (int p = 0; p < NP; ++p) {
-        const Cplx<T> d = s.tab[p * (pl.L + 1) + td];
-        const T ar = fma(d.re, ga[p].re, fma(-d.im, ga[p].im, a));
-        const T ai = fma(d.re, ga[p].im, d.im * ga[p].re);
-        const T br = fma(d.re, gb[p].re, fma(-d.im, gb[p].im, b));
-        const T bi = fma(d.re, gb[p].im, d.im * gb[p].re);
-        ga[p].re = ar; ga[p].im = ai; gb[p].re = br; gb[p].im = bi;
-        Yr = fma(mc.cpr[p], ar, fma(-mc.cpi[p], ai, Yr));
-        Yi = fma(-mc.cpr[p], br, fma(mc.cpi[p], bi, Yi));
-        Zr = fma(mc.cbr[p], ar, fma(-mc.cbi[p], ai, Zr));
-        Zi = fma(-mc.cbr[p], br, fma(mc.cbi[p], bi, Zi));
-      }
-      // the sums above include j = i; remove it (coefficient sY, sZ times u_i)
-      Yr = fma(-mc.sY, a, Yr); Yi = fma(mc.sY, b, Yi);
-      Zr = fma(-mc.sZ, a, Zr); Zi = fma(mc.sZ, b, Zi);
-      const T W1 = cs * Yr - sn * Yi;         // Re e^{i k.rho} Y
-      const T W2 = cs * Yi + sn * Yr;         // Im e^{i k.rho} Y
-      const T W3 = cs * Zr - sn * Zi;         // Re e^{i k.rho} Z
-      const int k4 = (n & 3) * 4;
+    for (int n0 = 0; n0 < cnt; n0 += 4) {
+      T buf[16];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        if (k4 == 4 * j) {
-          buf[4 * j + 0] = W1;
+        const int n = n0 + j;
+        if (n < cnt) {
+          const int t = dir == 0 ? n : cnt - 1 - n;
+          const int td = dir == 0 ? t : t + 1;      // index of the decay to apply
+          const Rec<T> r = s.rec[t];
+          const T dzd = dir == 0 ? r.dz : s.rec[td].dz;
+          T cs, sn;
+          sincos_turns(phase_turns(mc.mx, mc.my, r.xh, r.yh), cs, sn);
+          const T a = r.q * cs, b = r.q * sn;
+          // beta = k: real decay e^{-k dz}, complex input u = a - i b, as
+          // G <- G + (u - e G) with e = 1 - e^{-k dz} (see one_minus_exp_neg)
+          const T ek = one_minus_exp_neg(mc.kk * dzd);
+          g0.re += fma(-ek, g0.re, a);
+          g0.im += fma(-ek, g0.im, -b);
+          T Yr = mc.ck * g0.re, Yi = mc.ck * g0.im;
+          T Zr = mc.ckk * g0.re, Zi = mc.ckk * g0.im;
+          const Cplx<T>* dt = s.tab + td * NP;
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            const Cplx<T> d = dt[p];
+            const T ar = fma(d.re, ga[p].re, fma(-d.im, ga[p].im, a));
+            const T ai = fma(d.re, ga[p].im, d.im * ga[p].re);
+            const T br = fma(d.re, gb[p].re, fma(-d.im, gb[p].im, b));
+            const T bi = fma(d.re, gb[p].im, d.im * gb[p].re);
+            ga[p].re = ar; ga[p].im = ai; gb[p].re = br; gb[p].im = bi;
+            Yr = fma(mc.cpr[p], ar, fma(-mc.cpi[p], ai, Yr));
+            Yi = fma(-mc.cpr[p], br, fma(mc.cpi[p], bi, Yi));
+            Zr = fma(mc.cbr[p], ar, fma(-mc.cbi[p], ai, Zr));
+            Zi = fma(-mc.cbr[p], br, fma(mc.cbi[p], bi, Zi));
+          }
+          // the sums above include j = i; remove it (coefficients sY, sZ times u_i)
+          Yr = fma(-mc.sY, a, Yr); Yi = fma(mc.sY, b, Yi);
+          Zr = fma(-mc.sZ, a, Zr); Zi = fma(mc.sZ, b, Zi);
+          const T W2 = cs * Yi + sn * Yr;         // Im e^{i k.rho} Y
+          buf[4 * j + 0] = cs * Yr - sn * Yi;     // Re e^{i k.rho} Y
           buf[4 * j + 1] = mc.kx * W2;
           buf[4 * j + 2] = mc.ky * W2;
-          buf[4 * j + 3] = zsign * W3;
+          buf[4 * j + 3] = zsign * (cs * Zr - sn * Zi);   // Re e^{i k.rho} Z
+        } else {
+          buf[4 * j + 0] = buf[4 * j + 1] = buf[4 * j + 2] = buf[4 * j + 3] = (T)0;
         }
       }
-      if ((n & 3) == 3 || n == cnt - 1) {
-        const T v = warp_reduce16<T>(buf, lane);
-        const int idx = lane >> 1, g = idx >> 2, qn = idx & 3;
-        const int n0 = n & ~3;
-        if (!(lane & 1) && n0 + g <= n) {
-          const int tt = dir == 0 ? n0 + g : cnt - 1 - (n0 + g);
-          if (dir == 0) slot[tt * 4 + qn] = v;
-          else slot[tt * 4 + qn] += v;
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) buf[j] = (T)0;
+      const T v = warp_reduce16<T>(buf, lane);
+      const int idx = lane >> 1, g = idx >> 2, qn = idx & 3;
+      if (!(lane & 1) && n0 + g < cnt) {
+        const int tt = dir == 0 ? n0 + g : cnt - 1 - (n0 + g);
+        if (dir == 0) slot[tt * 4 + qn] = v;
+        else slot[tt * 4 + qn] += v;
       }
     }
     __syncwarp();
@@ -482,8 +540,9 @@ __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
 }
 
 template <typename T, int NP>
-static void kspace_run(const KParams<T>& P, const PairTab& pairs,
-                       Cplx<double>* pdec, cudaStream_t st, cudaEvent_t* ev) {
+static void kspace_run(const KParams<T>& P, const PairTab& pairs, void* dec,
+                       cudaStream_t st, cudaEvent_t* ev) {
+  using CN = typename CarryNum<T>::type;
   const ScanPlan& pl = P.plan;
   dim3 grid(pl.nchunks, pl.nkr);
   const size_t smA = chunk_smem_bytes<T>(pl.L, NP, 0, false);
@@ -494,13 +553,23 @@ static void kspace_run(const KParams<T>& P, const PairTab& pairs,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB);
   kspace_aggregate_kernel<T, NP><<<grid, pl.KR, smA, st>>>(P, pairs);
   if (ev) cudaEventRecord(ev[0], st);
+  Cplx<CN>* pdec = static_cast<Cplx<CN>*>(dec);
+  CN* kdec = reinterpret_cast<CN*>(pdec + (size_t)2 * pl.nchunks * pl.np);
   const int ne = 2 * pl.nchunks * pl.np;
-  pair_decay_kernel<T><<<(ne + 255) / 256, 256, 0, st>>>(pl, P.zs, pairs, pdec);
+  pair_decay_kernel<T><<<(ne + 255) / 256, 256, 0, st>>>(pl.N, pl.L, pl.nchunks, pl.np, P.zs,
+                                                         pairs, pdec, nullptr);
+  const int64_t nk = (int64_t)2 * pl.nchunks * pl.Kpad;
+  mode_decay_kernel<T><<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(pl, P.zs, P.modes.kk, kdec);
   const int nt = 2 * pl.nstates * pl.Kpad;
-  kspace_carry_kernel<T><<<(nt + 127) / 128, 128, 0, st>>>(P, pdec);
+  kspace_carry_kernel<T><<<(nt + 127) / 128, 128, 0, st>>>(P, pdec, kdec);
   if (ev) cudaEventRecord(ev[1], st);
   kspace_final_kernel<T, NP><<<grid, pl.KR, smB, st>>>(P, pairs);
   if (ev) cudaEventRecord(ev[2], st);
+}
+
+size_t kspace_decay_bytes(const ScanPlan& pl, int fp64) {
+  const size_t cn = fp64 ? sizeof(double) : sizeof(DF);
+  return 2 * cn * (size_t)2 * pl.nchunks * pl.np + cn * (size_t)2 * pl.nchunks * pl.Kpad;
 }
 
 template <typename T>
@@ -508,14 +577,14 @@ void launch_kspace(const ScanPlan& plan, const ModeTab<T>& modes,
                    const PairTab& pairs, const T* zs, const T* dz, const T* qs,
                    const typename PhaseT<T>::type* xh,
                    const typename PhaseT<T>::type* yh, Cplx<T>* agg,
-                   Cplx<T>* carry, Cplx<double>* pdec, T* part,
+                   Cplx<T>* carry, void* dec, T* part,
                    cudaStream_t st, cudaEvent_t* ev3) {
   KParams<T> P{plan, modes, zs, dz, qs, xh, yh, agg, carry, part};
   switch (plan.np) {
-    case 4: kspace_run<T, 4>(P, pairs, pdec, st, ev3); break;
-    case 8: kspace_run<T, 8>(P, pairs, pdec, st, ev3); break;
-    case 12: kspace_run<T, 12>(P, pairs, pdec, st, ev3); break;
-    default: kspace_run<T, 16>(P, pairs, pdec, st, ev3); break;
+    case 4: kspace_run<T, 4>(P, pairs, dec, st, ev3); break;
+    case 8: kspace_run<T, 8>(P, pairs, dec, st, ev3); break;
+    case 12: kspace_run<T, 12>(P, pairs, dec, st, ev3); break;
+    default: kspace_run<T, 16>(P, pairs, dec, st, ev3); break;
   }
 }
 
@@ -526,66 +595,98 @@ void launch_kspace(const ScanPlan& plan, const ModeTab<T>& modes,
 //   sum_{j != i} q_j g0'(|z_ij|) sgn(z_i - z_j) = c1 (Q< - Q>)
 //        + sum_l (w_l/sqrt(pi)) [ -(2/s_l + s_l)(S_l^f - S_l^b) + 2 alpha (H_l^f - H_l^b) ]
 // with S_l = sum_j q_j e^{-a_l |z_ij|} and H_l = sum_j q_j |z_ij| e^{-a_l |z_ij|}
-// split into j < i (f) and j > i (b). The |z| sums use FP64 prefix sums of q
-// and q z. H is carried without cancellation:
+// split into j < i (f) and j > i (b), c1 = sum_l 2 w_l/(s_l sqrt(pi)). The
+// |z| sums come from FP64 prefix sums of q and q z (they cancel heavily).
+// S and H are scanned in the path precision T, per chunk of L0 particles
+// with FP64 carries between chunks; H is carried without cancellation:
 //   H_i = d_i (H_{i-1} + dz_i S_{i-1}),  S_i = d_i S_{i-1} + q_i  (inclusive).
-// Everything here is FP64.
-
-constexpr int kK0Threads = 128;
+// One thread per (chunk, SOE pair representative); the lanes of a chunk sit
+// in one warp and are summed by shuffles.
 
 struct K0Params {
   int64_t N;
   int L0, nch;
-  int npad;          // lanes per chunk (power of two >= np)
+  int npad;          // lanes per chunk (power of two >= np, at least 4)
   double alpha, area, c1;
 };
 
+// acc + a b, with the product kept exact on the double-float path
+__device__ __forceinline__ double cn_add_prod(double acc, double a, double b) { return fma(a, b, acc); }
+__device__ __forceinline__ DF cn_add_prod(DF acc, float a, float b) {
+  const float p = a * b;
+  const DF pr = df_fast_two_sum(p, fmaf(a, b, -p));
+  return acc + pr;
+}
+__device__ __forceinline__ double cn_add(double acc, double a) { return acc + a; }
+__device__ __forceinline__ DF cn_add(DF acc, float a) { return acc + a; }
+
 template <typename T>
 __global__ void kzero_aggregate_kernel(K0Params Q, PairTab pr, const T* zs,
-                                       const T* qs, double* agg, double* csum) {
+                                       const T* qs, Cplx<T>* agg,
+                                       typename CarryNum<T>::type* csum) {
+  using CN = typename CarryNum<T>::type;
   const int lanes = Q.npad;
   const int g = (blockIdx.x * blockDim.x + threadIdx.x);
   const int c = g / lanes, p = g - c * lanes;
   if (c >= Q.nch) return;
   const int64_t start = (int64_t)c * Q.L0;
   const int cnt = (int)imin64(Q.L0, Q.N - start);
-  const double zst = (double)zs[start], zen = (double)zs[start + cnt - 1];
-  double sfr = 0, sfi = 0, hfr = 0, hfi = 0, sbr = 0, sbi = 0, hbr = 0, hbi = 0;
-  double q0 = 0, q1 = 0;
+  const T zst = zs[start], zen = zs[start + cnt - 1];
   const bool act = p < pr.np;
-  const double ar = act ? pr.a_re[p] : 0.0, ai = act ? pr.a_im[p] : 0.0;
+  const T ar = act ? (T)pr.a_re[p] : (T)0, ai = act ? (T)pr.a_im[p] : (T)0;
+  Cplx<T> sf{0, 0}, hf{0, 0}, sb{0, 0}, hb{0, 0};
+  CN q0 = cn_zero((CN*)nullptr), q1 = cn_zero((CN*)nullptr);
   for (int t = 0; t < cnt; ++t) {
-    const double z = (double)zs[start + t], qq = (double)qs[start + t];
-    q0 += qq;
-    q1 += qq * z;
+    const T z = zs[start + t], qq = qs[start + t];
+    if (p == 0) { q0 = cn_add(q0, qq); q1 = cn_add_prod(q1, qq, z); }
     if (!act) continue;
-    const double xf = zen - z, xb = z - zst;
-    const Cplx<double> ef = cexp_neg(ar, ai, xf);
-    const Cplx<double> eb = cexp_neg(ar, ai, xb);
-    sfr += qq * ef.re; sfi += qq * ef.im;
-    hfr += qq * xf * ef.re; hfi += qq * xf * ef.im;
-    sbr += qq * eb.re; sbi += qq * eb.im;
-    hbr += qq * xb * eb.re; hbi += qq * xb * eb.im;
+    const T xf = zen - z, xb = z - zst;
+    const Cplx<T> ef = cexp_neg(ar, ai, xf);
+    const Cplx<T> eb = cexp_neg(ar, ai, xb);
+    sf.re = fma(qq, ef.re, sf.re); sf.im = fma(qq, ef.im, sf.im);
+    hf.re = fma(qq * xf, ef.re, hf.re); hf.im = fma(qq * xf, ef.im, hf.im);
+    sb.re = fma(qq, eb.re, sb.re); sb.im = fma(qq, eb.im, sb.im);
+    hb.re = fma(qq * xb, eb.re, hb.re); hb.im = fma(qq * xb, eb.im, hb.im);
   }
   if (act) {
-    double* a = agg + ((size_t)c * lanes + p) * 8;
-    a[0] = sfr; a[1] = sfi; a[2] = hfr; a[3] = hfi;
-    a[4] = sbr; a[5] = sbi; a[6] = hbr; a[7] = hbi;
+    Cplx<T>* a = agg + ((size_t)c * lanes + p) * 4;
+    a[0] = sf; a[1] = hf; a[2] = sb; a[3] = hb;
   }
   if (p == 0) { csum[2 * c] = q0; csum[2 * c + 1] = q1; }
 }
 
-// One thread per (direction, pair); thread (0, 0) also scans the chunk sums.
+// One thread per (direction, pair) runs the chain over the chunks in the
+// carry type; thread 2*npad scans the chunk sums of q and q z.
 template <typename T>
-__global__ void kzero_carry_kernel(K0Params Q, PairTab pr, const T* zs,
-                                   const double* agg, double* carry,
-                                   const double* csum, double* cpre) {
+__global__ void kzero_carry_kernel(K0Params Q, PairTab pr, const typename CarryNum<T>::type* gaps,
+                                   const Cplx<T>* agg,
+                                   const Cplx<typename CarryNum<T>::type>* pdec,
+                                   typename CarryNum<T>::type* carry,
+                                   const typename CarryNum<T>::type* csum,
+                                   typename CarryNum<T>::type* cpre) {
+  using CN = typename CarryNum<T>::type;
+  const CN zero = cn_zero((CN*)nullptr);
   const int e = threadIdx.x;
-  if (e == 2 * Q.npad) {
-    double a = 0, b = 0;
-    for (int c = 0; c < Q.nch; ++c) {
-      cpre[2 * c] = a; cpre[2 * c + 1] = b;
-      a += csum[2 * c]; b += csum[2 * c + 1];
+  // the prefix of the chunk sums runs in its own warp (thread 32*k), with
+  // batched loads, so it neither diverges from the chains nor waits on memory
+  const int pre_thread = ((2 * Q.npad + 31) / 32) * 32;
+  if (e == pre_thread) {
+    CN a = zero, b = zero;
+    constexpr int B = 16;
+    for (int c0 = 0; c0 < Q.nch; c0 += B) {
+      CN va[B], vb[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        va[u] = zero; vb[u] = zero;
+        if (c0 + u < Q.nch) { va[u] = csum[2 * (c0 + u)]; vb[u] = csum[2 * (c0 + u) + 1]; }
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        if (c0 + u < Q.nch) {
+          cpre[2 * (c0 + u)] = a; cpre[2 * (c0 + u) + 1] = b;
+          a = a + va[u]; b = b + vb[u];
+        }
+      }
     }
     cpre[2 * Q.nch] = a; cpre[2 * Q.nch + 1] = b;
     return;
@@ -593,98 +694,111 @@ __global__ void kzero_carry_kernel(K0Params Q, PairTab pr, const T* zs,
   if (e >= 2 * Q.npad) return;
   const int dir = e / Q.npad, p = e - dir * Q.npad;
   if (p >= pr.np) return;
-  const double ar = pr.a_re[p], ai = pr.a_im[p];
-  double sr = 0, si = 0, hr = 0, hi = 0;
-  for (int j = 0; j < Q.nch; ++j) {
-    const int c = dir == 0 ? j : Q.nch - 1 - j;
-    double* out = carry + (((size_t)dir * Q.nch + c) * Q.npad + p) * 4;
-    out[0] = sr; out[1] = si; out[2] = hr; out[3] = hi;
-    double dzc = 0.0;
-    const int64_t s0 = (int64_t)c * Q.L0;
-    if (dir == 0) {
-      const int64_t e1 = imin64(s0 + Q.L0, Q.N) - 1;
-      dzc = c > 0 ? (double)zs[e1] - (double)zs[s0 - 1] : 0.0;
-    } else {
-      dzc = c < Q.nch - 1 ? (double)zs[s0 + Q.L0] - (double)zs[s0] : 0.0;
+  const int np = pr.np;
+  CN sr = zero, si = zero, hr = zero, hi = zero;
+  constexpr int B = 8;
+  for (int j0 = 0; j0 < Q.nch; j0 += B) {
+    Cplx<T> as[B], ah[B];
+    Cplx<CN> d[B];
+    CN dzc[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int j = j0 + u;
+      if (j < Q.nch) {
+        const int c = dir == 0 ? j : Q.nch - 1 - j;
+        const Cplx<T>* a = agg + ((size_t)c * Q.npad + p) * 4 + 2 * dir;
+        as[u] = a[0];
+        ah[u] = a[1];
+        d[u] = pdec[((size_t)dir * Q.nch + c) * np + p];
+        dzc[u] = gaps[dir * Q.nch + c];
+      }
     }
-    const Cplx<double> d = cexp_neg(ar, ai, dzc);
-    const double* a = agg + ((size_t)c * Q.npad + p) * 8 + 4 * dir;
-    // S' = d S + S_loc ; H' = d (H + dz S) + H_loc
-    const double tr = hr + dzc * sr, ti = hi + dzc * si;
-    const double nhr = d.re * tr - d.im * ti + a[2];
-    const double nhi = d.re * ti + d.im * tr + a[3];
-    const double nsr = d.re * sr - d.im * si + a[0];
-    const double nsi = d.re * si + d.im * sr + a[1];
-    sr = nsr; si = nsi; hr = nhr; hi = nhi;
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int j = j0 + u;
+      if (j < Q.nch) {
+        const int c = dir == 0 ? j : Q.nch - 1 - j;
+        CN* out = carry + (((size_t)dir * Q.nch + c) * Q.npad + p) * 4;
+        out[0] = sr; out[1] = si; out[2] = hr; out[3] = hi;
+        // S' = d S + S_loc ; H' = d (H + dz S) + H_loc
+        const CN tr = hr + dzc[u] * sr, ti = hi + dzc[u] * si;
+        const CN nhr = d[u].re * tr - d[u].im * ti + cn_from_t(ah[u].re, (CN*)nullptr);
+        const CN nhi = d[u].re * ti + d[u].im * tr + cn_from_t(ah[u].im, (CN*)nullptr);
+        const CN nsr = d[u].re * sr - d[u].im * si + cn_from_t(as[u].re, (CN*)nullptr);
+        const CN nsi = d[u].re * si + d[u].im * sr + cn_from_t(as[u].im, (CN*)nullptr);
+        sr = nsr; si = nsi; hr = nhr; hi = nhi;
+      }
+    }
   }
 }
 
 template <typename T>
 __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
-                                   const T* dz, const T* qs, const double* carry,
-                                   const double* cpre, double* phi0,
-                                   double* fz0) {
-  extern __shared__ double ksm[];   // [chunks per block][L0][2]
+                                   const T* dz, const T* qs,
+                                   const typename CarryNum<T>::type* carry,
+                                   const typename CarryNum<T>::type* cpre,
+                                   typename CarryNum<T>::type* phi0,
+                                   typename CarryNum<T>::type* fz0) {
+  using CN = typename CarryNum<T>::type;
+  extern __shared__ __align__(16) char ksm_raw[];   // [chunks per block][L0][2] of T
+  T* ksm = reinterpret_cast<T*>(ksm_raw);
   const int lanes = Q.npad;
-  const int cpb = blockDim.x / lanes;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int c = g / lanes, p = g - c * lanes;
   const int lc = threadIdx.x / lanes;
-  double* acc = ksm + (size_t)lc * Q.L0 * 2;
+  T* acc = ksm + (size_t)lc * Q.L0 * 2;
   const bool valid = c < Q.nch;
   const int64_t start = (int64_t)c * Q.L0;
   const int cnt = valid ? (int)imin64(Q.L0, Q.N - start) : 0;
   const bool act = valid && p < pr.np;
   const double sq = 1.7724538509055160;   // sqrt(pi)
-  double cwr = 0, cwi = 0, sr_ = 1, si_ = 0;
-  double ar = 0, ai = 0;
+  T cwr = 0, cwi = 0, isr = 0, isi = 0, csr = 0, csi = 0, ar = 1, ai = 0;
   if (act) {
-    // multiplicity times w_p/sqrt(pi); s_p
-    cwr = pr.mult[p] * pr.w_re[p] / sq; cwi = pr.mult[p] * pr.w_im[p] / sq;
-    sr_ = pr.s_re[p]; si_ = pr.s_im[p];
-    ar = pr.a_re[p]; ai = pr.a_im[p];
+    // multiplicity times w_p/sqrt(pi), 1/s_p and 2/s_p + s_p
+    const double sr_ = pr.s_re[p], si_ = pr.s_im[p];
+    const double den = sr_ * sr_ + si_ * si_;
+    cwr = (T)(pr.mult[p] * pr.w_re[p] / sq); cwi = (T)(pr.mult[p] * pr.w_im[p] / sq);
+    isr = (T)(sr_ / den); isi = (T)(-si_ / den);
+    csr = (T)(2 * sr_ / den + sr_); csi = (T)(-2 * si_ / den + si_);
+    ar = (T)pr.a_re[p]; ai = (T)pr.a_im[p];
   }
-  // 1/s and (2/s + s)
-  const double den = sr_ * sr_ + si_ * si_;
-  const double isr = sr_ / den, isi = -si_ / den;
-  const double csr = 2 * isr + sr_, csi = 2 * isi + si_;
+  const T alpha = (T)Q.alpha, ialpha = (T)(1.0 / Q.alpha);
   for (int t = threadIdx.x % lanes; t < Q.L0; t += lanes) { acc[2 * t] = 0; acc[2 * t + 1] = 0; }
   __syncwarp();
   for (int dir = 0; dir < 2; ++dir) {
-    double sr = 0, si = 0, hr = 0, hi = 0;
+    T sr = 0, si = 0, hr = 0, hi = 0;
     if (act) {
-      const double* in = carry + (((size_t)dir * Q.nch + c) * Q.npad + p) * 4;
-      sr = in[0]; si = in[1]; hr = in[2]; hi = in[3];
+      const CN* in = carry + (((size_t)dir * Q.nch + c) * Q.npad + p) * 4;
+      sr = cn_to_t(in[0]); si = cn_to_t(in[1]); hr = cn_to_t(in[2]); hi = cn_to_t(in[3]);
     }
     // every lane runs L0 steps so that the shuffles below see the whole warp
     for (int n = 0; n < Q.L0; ++n) {
       const bool live = n < cnt;
       const int t = dir == 0 ? n : cnt - 1 - n;
       const int64_t i = start + t;
-      const double qq = live ? (double)qs[i] : 0.0;
-      double pot = 0, der = 0;
+      T pot = 0, der = 0;
       if (act && live) {
+        const T qq = qs[i];
         const int64_t id = dir == 0 ? i : i + 1;
-        const double dzi = id < Q.N ? (double)dz[id] : 0.0;
-        const Cplx<double> d = cexp_neg(ar, ai, dzi);
+        const T dzi = id < Q.N ? dz[id] : (T)0;
+        const Cplx<T> d = cexp_neg(ar, ai, dzi);
         // H first (uses the previous inclusive S), then S
-        const double tr = hr + dzi * sr, ti = hi + dzi * si;
-        hr = d.re * tr - d.im * ti; hi = d.re * ti + d.im * tr;
-        const double nsr = d.re * sr - d.im * si + qq;
-        const double nsi = d.re * si + d.im * sr;
+        const T tr = fma(dzi, sr, hr), ti = fma(dzi, si, hi);
+        hr = d.re * tr - d.im * ti; hi = fma(d.re, ti, d.im * tr);
+        const T nsr = fma(d.re, sr, fma(-d.im, si, qq));
+        const T nsi = fma(d.re, si, d.im * sr);
         sr = nsr; si = nsi;
         // exclusive S (j != i): S - q_i ; H has no j = i term
-        const double xr = sr - qq, xi = si;
+        const T xr = sr - qq, xi = si;
         // pot part: cw [ (1/alpha) S - 2 (1/s) H ]
-        const double ur = xr / Q.alpha - 2 * (isr * hr - isi * hi);
-        const double ui = xi / Q.alpha - 2 * (isr * hi + isi * hr);
+        const T ur = xr * ialpha - 2 * (isr * hr - isi * hi);
+        const T ui = xi * ialpha - 2 * (isr * hi + isi * hr);
         pot = cwr * ur - cwi * ui;
         // der part: cw [ -(2/s + s) S + 2 alpha H ] with sign +/- by direction
-        const double vr = -(csr * xr - csi * xi) + 2 * Q.alpha * hr;
-        const double vi = -(csr * xi + csi * xr) + 2 * Q.alpha * hi;
-        der = (dir == 0 ? 1.0 : -1.0) * (cwr * vr - cwi * vi);
+        const T vr = -(csr * xr - csi * xi) + 2 * alpha * hr;
+        const T vi = -(csr * xi + csi * xr) + 2 * alpha * hi;
+        der = (dir == 0 ? (T)1 : (T)-1) * (cwr * vr - cwi * vi);
       }
-      // sum over the chunk's lanes
       for (int o = lanes >> 1; o; o >>= 1) {
         pot += __shfl_xor_sync(0xffffffffu, pot, o);
         der += __shfl_xor_sync(0xffffffffu, der, o);
@@ -694,71 +808,94 @@ __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
   }
   __syncwarp();
   if (p == 0 && valid) {
-    const double Qlt0 = cpre[2 * c], Plt0 = cpre[2 * c + 1];
-    const double Qt = cpre[2 * Q.nch], Pt = cpre[2 * Q.nch + 1];
-    double Ql = Qlt0, Pl = Plt0;
-    const double pre = 2.0 * 3.14159265358979323846 / Q.area;
+    // sum_j q_j |z_i - z_j| = z_i (Q< - Q>) - P< + P>, from prefix sums in
+    // the carry type (the terms cancel heavily); the result stays in the
+    // carry type and the combine kernel widens it to FP64
+    CN Ql = cpre[2 * c], Pl = cpre[2 * c + 1];
+    const CN Qt = cpre[2 * Q.nch], Pt = cpre[2 * Q.nch + 1];
+    const CN c1 = cn_from(Q.c1, (CN*)nullptr);
+    const CN pre = cn_from(2.0 * 3.14159265358979323846 / Q.area, (CN*)nullptr);
     for (int t = 0; t < cnt; ++t) {
       const int64_t i = start + t;
-      const double z = (double)zs[i], qq = (double)qs[i];
-      const double Qg = Qt - Ql - qq, Pg = Pt - Pl - qq * z;
-      const double lin = z * Ql - Pl + Pg - z * Qg;
-      const double pot = Q.c1 * lin + acc[2 * t];
-      const double der = Q.c1 * (Ql - Qg) + acc[2 * t + 1];
-      phi0[i] = -pre * pot;
-      fz0[i] = pre * qq * der;
-      Ql += qq;
-      Pl += qq * z;
+      const T zt = zs[i], qt = qs[i];
+      const CN zc = cn_from_t(zt, (CN*)nullptr);
+      const CN Qg = Qt - Ql - cn_from_t(qt, (CN*)nullptr);
+      const CN Pg = cn_add_prod(Pt - Pl, -qt, zt);
+      const CN lin = zc * (Ql - Qg) - Pl + Pg;
+      const CN pot = c1 * lin + cn_from_t(acc[2 * t], (CN*)nullptr);
+      const CN der = c1 * (Ql - Qg) + cn_from_t(acc[2 * t + 1], (CN*)nullptr);
+      phi0[i] = -(pre * pot);
+      fz0[i] = pre * der * cn_from_t(qt, (CN*)nullptr);
+      Ql = cn_add(Ql, qt);
+      Pl = cn_add_prod(Pl, qt, zt);
     }
   }
-  (void)cpb;
 }
 
 template <typename T>
 void launch_kzero(int64_t N, int L0, int nchunks0, const PairTab& pairs,
                   double alpha, double area, const T* zs, const T* dz,
-                  const T* qs, double* work, double* phi0, double* fz0,
+                  const T* qs, double* work, void* phi0v, void* fz0v,
                   cudaStream_t st) {
+  using CN = typename CarryNum<T>::type;
   K0Params Q;
   Q.N = N; Q.L0 = L0; Q.nch = nchunks0; Q.alpha = alpha; Q.area = area;
-  int npad = 1;
+  int npad = 4;                 // at least 4 lanes per chunk: 8 chunks fill a warp multiple
   while (npad < pairs.np) npad <<= 1;
   Q.npad = npad;
   double c1 = 0.0;
   for (int p = 0; p < pairs.np; ++p) {
-    // c1 = sum_l 2 w_l/(s_l sqrt(pi)): the pair gives 2 Re(w/s) times mult/2... per node
+    // c1 = sum over nodes of 2 w/(s sqrt(pi)) = sum over representatives of mult 2 Re(w/s)/sqrt(pi)
     const double den = pairs.s_re[p] * pairs.s_re[p] + pairs.s_im[p] * pairs.s_im[p];
     const double re = (pairs.w_re[p] * pairs.s_re[p] + pairs.w_im[p] * pairs.s_im[p]) / den;
     c1 += pairs.mult[p] * 2.0 * re / 1.7724538509055160;
   }
   Q.c1 = c1;
-  double* agg = work;                                   // [nch][npad][8]
-  double* csum = agg + (size_t)nchunks0 * npad * 8;     // [nch][2]
-  double* carry = csum + (size_t)nchunks0 * 2;          // [2][nch][npad][4]
-  double* cpre = carry + (size_t)2 * nchunks0 * npad * 4;  // [nch+1][2]
+  // work layout: agg [nch][npad][4] Cplx<T>, csum [nch][2] CN,
+  // pdec [2][nch][np] Cplx<CN>, carry [2][nch][npad][4] CN, cpre [nch+1][2] CN
+  char* w = reinterpret_cast<char*>(work);
+  auto take = [&w](size_t b) { char* r = w; w += (b + 255) & ~size_t(255); return r; };
+  Cplx<T>* agg = reinterpret_cast<Cplx<T>*>(take(sizeof(Cplx<T>) * (size_t)nchunks0 * npad * 4));
+  CN* csum = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)nchunks0 * 2));
+  Cplx<CN>* pdec = reinterpret_cast<Cplx<CN>*>(take(sizeof(Cplx<CN>) * (size_t)2 * nchunks0 * pairs.np));
+  CN* carry = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)2 * nchunks0 * npad * 4));
+  CN* cpre = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)(nchunks0 + 1) * 2));
+  CN* gaps = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)2 * nchunks0));
+  CN* phi0 = static_cast<CN*>(phi0v);
+  CN* fz0 = static_cast<CN*>(fz0v);
   const int tot = nchunks0 * npad;
+  constexpr int kK0Threads = 128;
   kzero_aggregate_kernel<T><<<(tot + kK0Threads - 1) / kK0Threads, kK0Threads, 0, st>>>(
       Q, pairs, zs, qs, agg, csum);
-  kzero_carry_kernel<T><<<1, 2 * npad + 1, 0, st>>>(Q, pairs, zs, agg, carry, csum, cpre);
-  const int cpb = kK0Threads / npad;
-  const size_t sm = (size_t)cpb * L0 * 2 * sizeof(double);
-  kzero_final_kernel<T><<<(tot + kK0Threads - 1) / kK0Threads, kK0Threads, sm, st>>>(
+  const int ne = 2 * nchunks0 * pairs.np;
+  pair_decay_kernel<T><<<(ne + 255) / 256, 256, 0, st>>>(N, L0, nchunks0, pairs.np, zs, pairs, pdec,
+                                                         gaps);
+  kzero_carry_kernel<T><<<1, ((2 * npad + 31) / 32) * 32 + 32, 0, st>>>(Q, pairs, gaps, agg, pdec,
+                                                                      carry, csum, cpre);
+  // 8 chunks per CTA: npad * 8 threads is a whole number of warps for npad >= 4
+  const int cpb = 8;
+  const int thr = npad * cpb;
+  const size_t sm = (size_t)cpb * L0 * 2 * sizeof(T);
+  cudaFuncSetAttribute(kzero_final_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  kzero_final_kernel<T><<<(tot + thr - 1) / thr, thr, sm, st>>>(
       Q, pairs, zs, dz, qs, carry, cpre, phi0, fz0);
 }
 
 size_t kzero_work_doubles(int nchunks0, int np) {
-  int npad = 1;
+  int npad = 4;
   while (npad < np) npad <<= 1;
-  return (size_t)nchunks0 * npad * 8 + (size_t)nchunks0 * 2 +
-         (size_t)2 * nchunks0 * npad * 4 + (size_t)(nchunks0 + 1) * 2;
+  // in 8-byte units, with room for 256-byte alignment of each of 5 arrays
+  return (size_t)nchunks0 * npad * 4 * 2 + (size_t)nchunks0 * 2 +
+         (size_t)2 * nchunks0 * kMaxPairs * 2 + (size_t)2 * nchunks0 * npad * 4 +
+         (size_t)(nchunks0 + 1) * 2 + (size_t)2 * nchunks0 + 6 * 32 + 64;
 }
 
 // ================================================================== combine
 
 template <typename T>
 __global__ void combine_kernel(int64_t N, int nkr, const T* __restrict__ part,
-                               const double* __restrict__ phi0,
-                               const double* __restrict__ fz0,
+                               const typename CarryNum<T>::type* __restrict__ phi0,
+                               const typename CarryNum<T>::type* __restrict__ fz0,
                                const T* __restrict__ qs,
                                const int32_t* __restrict__ perm, double diagq,
                                double* eblock, T* phi_out, T* force_out) {
@@ -775,9 +912,9 @@ __global__ void combine_kernel(int64_t N, int nkr, const T* __restrict__ part,
       fz += (double)b[3 * N + i];
     }
     const double qq = (double)qs[i];
-    ph += phi0[i] + qq * diagq;
+    ph += cn_to_double(phi0[i]) + qq * diagq;
     fx *= qq; fy *= qq;
-    fz = fz * qq + fz0[i];
+    fz = fz * qq + cn_to_double(fz0[i]);
     const int32_t o = perm[i];
     if (phi_out) phi_out[o] = (T)ph;
     if (force_out) {
@@ -812,10 +949,13 @@ __global__ void energy_sum_kernel(const double* eblock, int n, double* energy) {
 }
 
 template <typename T>
-void launch_combine(int64_t N, int nkr, const T* part, const double* phi0,
-                    const double* fz0, const T* qs, const int32_t* perm,
+void launch_combine(int64_t N, int nkr, const T* part, const void* phi0v,
+                    const void* fz0v, const T* qs, const int32_t* perm,
                     double diagq, double* eblock, int nblk, T* phi_out,
                     T* force_out, double* energy, cudaStream_t st) {
+  using CN = typename CarryNum<T>::type;
+  const CN* phi0 = static_cast<const CN*>(phi0v);
+  const CN* fz0 = static_cast<const CN*>(fz0v);
   combine_kernel<T><<<nblk, 256, 0, st>>>(N, nkr, part, phi0, fz0, qs, perm,
                                           diagq, eblock, phi_out, force_out);
   if (energy) energy_sum_kernel<<<1, 256, 0, st>>>(eblock, nblk, energy);
@@ -930,12 +1070,12 @@ template void launch_prepare<float>(int64_t, const float*, const float*, double,
 template void launch_prepare<double>(int64_t, const double*, const double*, double, void*, uint32_t*, double*, unsigned*, cudaStream_t);
 template void launch_gather<float>(int64_t, const float*, const float*, const uint32_t*, double, double, float*, float*, float*, uint32_t*, uint32_t*, int32_t*, cudaStream_t);
 template void launch_gather<double>(int64_t, const double*, const double*, const uint32_t*, double, double, double*, double*, double*, uint64_t*, uint64_t*, int32_t*, cudaStream_t);
-template void launch_kspace<float>(const ScanPlan&, const ModeTab<float>&, const PairTab&, const float*, const float*, const float*, const uint32_t*, const uint32_t*, Cplx<float>*, Cplx<float>*, Cplx<double>*, float*, cudaStream_t, cudaEvent_t*);
-template void launch_kspace<double>(const ScanPlan&, const ModeTab<double>&, const PairTab&, const double*, const double*, const double*, const uint64_t*, const uint64_t*, Cplx<double>*, Cplx<double>*, Cplx<double>*, double*, cudaStream_t, cudaEvent_t*);
-template void launch_kzero<float>(int64_t, int, int, const PairTab&, double, double, const float*, const float*, const float*, double*, double*, double*, cudaStream_t);
-template void launch_kzero<double>(int64_t, int, int, const PairTab&, double, double, const double*, const double*, const double*, double*, double*, double*, cudaStream_t);
-template void launch_combine<float>(int64_t, int, const float*, const double*, const double*, const float*, const int32_t*, double, double*, int, float*, float*, double*, cudaStream_t);
-template void launch_combine<double>(int64_t, int, const double*, const double*, const double*, const double*, const int32_t*, double, double*, int, double*, double*, double*, cudaStream_t);
+template void launch_kspace<float>(const ScanPlan&, const ModeTab<float>&, const PairTab&, const float*, const float*, const float*, const uint32_t*, const uint32_t*, Cplx<float>*, Cplx<float>*, void*, float*, cudaStream_t, cudaEvent_t*);
+template void launch_kspace<double>(const ScanPlan&, const ModeTab<double>&, const PairTab&, const double*, const double*, const double*, const uint64_t*, const uint64_t*, Cplx<double>*, Cplx<double>*, void*, double*, cudaStream_t, cudaEvent_t*);
+template void launch_kzero<float>(int64_t, int, int, const PairTab&, double, double, const float*, const float*, const float*, double*, void*, void*, cudaStream_t);
+template void launch_kzero<double>(int64_t, int, int, const PairTab&, double, double, const double*, const double*, const double*, double*, void*, void*, cudaStream_t);
+template void launch_combine<float>(int64_t, int, const float*, const void*, const void*, const float*, const int32_t*, double, double*, int, float*, float*, double*, cudaStream_t);
+template void launch_combine<double>(int64_t, int, const double*, const void*, const void*, const double*, const int32_t*, double, double*, int, double*, double*, double*, cudaStream_t);
 template void launch_mode_coef<float>(int, int, int, const int32_t*, int, uint64_t, uint64_t, const SamplerTab&, const PairTab&, double, double, double, double, ModeTab<float>, int32_t*, cudaStream_t);
 template void launch_mode_coef<double>(int, int, int, const int32_t*, int, uint64_t, uint64_t, const SamplerTab&, const PairTab&, double, double, double, double, ModeTab<double>, int32_t*, cudaStream_t);
 

@@ -61,6 +61,23 @@ __device__ __forceinline__ void sincos_turns(uint64_t ph, double& c, double& s) 
 __device__ __forceinline__ float exp_neg(float x) { return expf(-x); }
 __device__ __forceinline__ double exp_neg(double x) { return exp(-x); }
 
+// 1 - e^{-x} for x >= 0, accurate relative to itself. A decay e^{-x} close
+// to 1 cannot be stored in FP32 to better than about 6e-8 absolute, which for
+// the x ~ 1e-6 of neighbouring particles is a relative error of several
+// percent in 1 - e^{-x}; carrying e = 1 - e^{-x} instead keeps it exact to
+// rounding. Taylor series to x^6 below 1/16 (truncation < 3e-13 relative).
+__device__ __forceinline__ float one_minus_exp_neg(float x) {
+  // branch-free: for x >= 1/16, 1 - e^{-x} >= 0.06 and the plain form is exact enough
+  const float big = 1.0f - __expf(-x);
+  float r = fmaf(x, -1.0f / 720.0f, 1.0f / 120.0f);
+  r = fmaf(x, r, -1.0f / 24.0f);
+  r = fmaf(x, r, 1.0f / 6.0f);
+  r = fmaf(x, r, -0.5f);
+  r = fmaf(x, r, 1.0f);
+  return x < 0.0625f ? x * r : big;
+}
+__device__ __forceinline__ double one_minus_exp_neg(double x) { return -expm1(-x); }
+
 // e^{-a x} for complex a and real x >= 0.
 __device__ __forceinline__ Cplx<float> cexp_neg(float ar, float ai, float x) {
   float s, c;

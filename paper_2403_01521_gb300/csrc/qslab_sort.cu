@@ -29,7 +29,7 @@ constexpr int kRadix = 256;
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
 hist_kernel(const K* __restrict__ keys, int64_t N, int shift, uint32_t* counts,
-            int nblocks) {
+            uint32_t* totals, int nblocks) {
   __shared__ uint32_t h[kRadix];
   for (int d = threadIdx.x; d < kRadix; d += blockDim.x) h[d] = 0;
   __syncthreads();
@@ -39,42 +39,50 @@ hist_kernel(const K* __restrict__ keys, int64_t N, int shift, uint32_t* counts,
     if (idx < N) atomicAdd(&h[(unsigned)(keys[idx] >> shift) & 0xFFu], 1u);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
     counts[(int64_t)d * nblocks + blockIdx.x] = h[d];
+    if (h[d]) atomicAdd(&totals[d], h[d]);
+  }
 }
 
-// Exclusive scan of n uint32 values in place, one CTA of 1024 threads.
-__global__ void __launch_bounds__(1024) scan_kernel(uint32_t* a, int64_t n) {
-  __shared__ uint32_t wsum[32];
-  const int t = threadIdx.x;
-  const int64_t per = (n + blockDim.x - 1) / blockDim.x;
-  const int64_t lo = t * per;
-  const int64_t hi = (lo + per < n) ? lo + per : n;
-  uint32_t sum = 0;
-  for (int64_t i = lo; i < hi; ++i) sum += a[i];
-  // block-wide exclusive scan of the per-thread sums
-  const int lane = t & 31, w = t >> 5;
-  uint32_t v = sum;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += y;
-  }
-  if (lane == 31) wsum[w] = v;
+// Exclusive scan of counts[digit][tile] in digit-major order: one CTA per
+// digit scans its row (coalesced) and starts from the sum of the totals of
+// the smaller digits.
+__global__ void __launch_bounds__(kSortThreads)
+scan_kernel(uint32_t* counts, const uint32_t* totals, int nblocks) {
+  __shared__ uint32_t wsum[kSortWarps];
+  __shared__ uint32_t carry;
+  const int d = blockIdx.x;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  // offset of this digit: sum of totals[0..d)
+  uint32_t v = (t < d) ? totals[t] : 0u;
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) wsum[w] = v;
   __syncthreads();
-  if (w == 0) {
-    uint32_t x = wsum[lane];
+  if (t == 0) {
+    uint32_t a = 0;
+    for (int j = 0; j < kSortWarps; ++j) a += wsum[j];
+    carry = a;
+  }
+  __syncthreads();
+  uint32_t* row = counts + (int64_t)d * nblocks;
+  for (int b0 = 0; b0 < nblocks; b0 += kSortThreads) {
+    const int b = b0 + t;
+    const uint32_t x = b < nblocks ? row[b] : 0u;
+    uint32_t y = x;
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+      const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
     }
-    wsum[lane] = x;  // inclusive over warps
-  }
-  __syncthreads();
-  uint32_t run = v - sum + (w > 0 ? wsum[w - 1] : 0u);
-  for (int64_t i = lo; i < hi; ++i) {
-    uint32_t c = a[i];
-    a[i] = run;
-    run += c;
+    __syncthreads();
+    if (lane == 31) wsum[w] = y;
+    __syncthreads();
+    uint32_t before = carry;
+    for (int j = 0; j < w; ++j) before += wsum[j];
+    if (b < nblocks) row[b] = before + y - x;
+    __syncthreads();
+    if (t == kSortThreads - 1) carry = before + y;
+    __syncthreads();
   }
 }
 
@@ -135,7 +143,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t sort_workspace_bytes(int64_t N, int key_bytes) {
   const int64_t nb = (N + kTile - 1) / kTile;
   return 2 * align256((size_t)N * key_bytes) + 2 * align256((size_t)N * 4) +
-         align256((size_t)nb * kRadix * 4);
+         align256((size_t)nb * kRadix * 4) + align256(8 * kRadix * 4);
 }
 
 void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes) {
@@ -146,25 +154,29 @@ void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes) {
   w.vals[0] = reinterpret_cast<uint32_t*>(p); p += align256((size_t)N * 4);
   w.vals[1] = reinterpret_cast<uint32_t*>(p); p += align256((size_t)N * 4);
   w.counts = reinterpret_cast<uint32_t*>(p);
+  p += align256((size_t)w.nblocks * kRadix * 4);
+  w.totals = reinterpret_cast<uint32_t*>(p);
 }
 
 int radix_sort(SortWork& w, int64_t N, int key_bytes, cudaStream_t st) {
   const int passes = key_bytes;  // 8-bit digits
   int cur = 0;
+  cudaMemsetAsync(w.totals, 0, (size_t)passes * kRadix * 4, st);
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
+    uint32_t* tot = w.totals + p * kRadix;
     if (key_bytes == 4) {
       auto* kin = static_cast<const uint32_t*>(w.keys[cur]);
       auto* kout = static_cast<uint32_t*>(w.keys[cur ^ 1]);
-      hist_kernel<uint32_t><<<w.nblocks, kSortThreads, 0, st>>>(kin, N, shift, w.counts, w.nblocks);
-      scan_kernel<<<1, 1024, 0, st>>>(w.counts, (int64_t)w.nblocks * kRadix);
+      hist_kernel<uint32_t><<<w.nblocks, kSortThreads, 0, st>>>(kin, N, shift, w.counts, tot, w.nblocks);
+      scan_kernel<<<kRadix, kSortThreads, 0, st>>>(w.counts, tot, w.nblocks);
       scatter_kernel<uint32_t><<<w.nblocks, kSortThreads, 0, st>>>(
           kin, w.vals[cur], kout, w.vals[cur ^ 1], N, shift, w.counts, w.nblocks);
     } else {
       auto* kin = static_cast<const uint64_t*>(w.keys[cur]);
       auto* kout = static_cast<uint64_t*>(w.keys[cur ^ 1]);
-      hist_kernel<uint64_t><<<w.nblocks, kSortThreads, 0, st>>>(kin, N, shift, w.counts, w.nblocks);
-      scan_kernel<<<1, 1024, 0, st>>>(w.counts, (int64_t)w.nblocks * kRadix);
+      hist_kernel<uint64_t><<<w.nblocks, kSortThreads, 0, st>>>(kin, N, shift, w.counts, tot, w.nblocks);
+      scan_kernel<<<kRadix, kSortThreads, 0, st>>>(w.counts, tot, w.nblocks);
       scatter_kernel<uint64_t><<<w.nblocks, kSortThreads, 0, st>>>(
           kin, w.vals[cur], kout, w.vals[cur ^ 1], N, shift, w.counts, w.nblocks);
     }
