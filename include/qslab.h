@@ -152,8 +152,9 @@ int qslab_last_status(qslab_ctx* ctx);
  * stream while timing is enabled (qslab_set_timing(ctx, 1)). ms8 receives, in
  * milliseconds: [0] checks + z-sort + gather, [1] mode table (RBE sampler),
  * [2] k-space chunk aggregates, [3] carries, [4] k-space recurrences with the
- * gather, [5] k = 0 term, [6] combine + energy, [7] total. *launches (may be
- * NULL) receives the number of kernels the call launched. Synchronises. */
+ * gather, [5] k = 0 term (it runs on an internal stream concurrently with
+ * [1]-[4]), [6] combine + energy, [7] total. *launches (may be NULL)
+ * receives the number of kernels the call launched. Synchronises. */
 int qslab_set_timing(qslab_ctx* ctx, int enable);
 int qslab_get_timings(qslab_ctx* ctx, double* ms8, int* launches);
 

@@ -68,6 +68,10 @@ struct qslab_ctx {
   bool have_sample = false;
   cudaEvent_t ev[9] = {};
   int launches = 0;
+  // the k = 0 term runs on a side stream, forked from and joined to the
+  // caller's stream with these events (capturable in a CUDA graph)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -386,6 +390,14 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energy,
   launch_gather<T>(N, pos, q, sw.vals[r], c->Lx, c->Ly, zs, dz, qs, xh, yh, perm, st);
   nl += 3 + 3 * (int)sizeof(T);   // prepare, check, gather + 3 kernels per sort pass
   if (ev) cudaEventRecord(ev[1], st);
+  // k = 0 term on the side stream, concurrent with the k-space kernels
+  QS_CUDA(cudaEventRecord(c->fork, st));
+  QS_CUDA(cudaStreamWaitEvent(c->side, c->fork, 0));
+  launch_kzero<T>(N, P.L0, P.nch0, c->pairs, c->alpha, c->Lx * c->Ly, zs, dz, qs, k0w,
+                  phi0, fz0, c->side);
+  nl += 4;
+  if (ev) cudaEventRecord(ev[8], c->side);
+  QS_CUDA(cudaEventRecord(c->join, c->side));
   // mode table: once per configuration for the full k-sum, every call for RBE
   if (c->mode == 2 || !c->coef_ready) {
     SamplerTab sp{c->d_cdfx, c->d_cdfy, c->cdf_nx, c->cdf_ny, c->mxmax, c->mymax};
@@ -403,10 +415,8 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energy,
   if (ev) cudaEventRecord(ev[2], st);
   launch_kspace<T>(P.sp, modes, c->pairs, zs, dz, qs, xh, yh, agg, carry, pdec, part, st,
                    ev ? ev + 3 : nullptr);
-  nl += 4;
-  launch_kzero<T>(N, P.L0, P.nch0, c->pairs, c->alpha, c->Lx * c->Ly, zs, dz, qs, k0w,
-                  phi0, fz0, st);
-  nl += 3;
+  nl += 7;
+  QS_CUDA(cudaStreamWaitEvent(st, c->join, 0));
   if (ev) cudaEventRecord(ev[6], st);
   const double D0 = -(kPi / (c->Lx * c->Ly)) / (c->alpha * kSqrtPi);
   const double diagq = 2.0 * c->diag_k + 2.0 * D0 - 2.0 * c->alpha / kSqrtPi;
@@ -465,6 +475,12 @@ int qslab_create(qslab_ctx** out, int cuda_device, int prec) {
   c->d_energy = reinterpret_cast<double*>(static_cast<char*>(small) + 128);
   cudaMemset(small, 0, 256);
   for (auto& ev : c->ev) cudaEventCreate(&ev);
+  if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+    qslab_destroy(c);
+    return QSLAB_ERR_CUDA;
+  }
   *out = c;
   return QSLAB_OK;
 }
@@ -478,6 +494,9 @@ void qslab_destroy(qslab_ctx* c) {
   if (c->d_status) cudaFree(c->d_status);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->join) cudaEventDestroy(c->join);
+  if (c->side) cudaStreamDestroy(c->side);
   delete c;
 }
 
@@ -660,8 +679,9 @@ int qslab_get_timings(qslab_ctx* c, double* ms8, int* launches) {
   QS_CUDA(cudaSetDevice(c->device));
   QS_CUDA(cudaEventSynchronize(c->ev[7]));
   // event order: 0 start, 1 sorted, 2 modes, 3 aggregates, 4 carries,
-  // 5 recurrences, 6 k = 0, 7 end
-  const int pairs[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {5, 6}, {6, 7}, {0, 7}};
+  // 5 recurrences, 6 joined with the k = 0 stream, 7 end, 8 end of the k = 0
+  // term (side stream; it runs concurrently from event 1)
+  const int pairs[8][2] = {{0, 1}, {1, 2}, {2, 3}, {3, 4}, {4, 5}, {1, 8}, {6, 7}, {0, 7}};
   for (int i = 0; i < 8; ++i) {
     float t = 0;
     QS_CUDA(cudaEventElapsedTime(&t, c->ev[pairs[i][0]], c->ev[pairs[i][1]]));

@@ -379,61 +379,131 @@ __global__ void mode_decay_kernel(ScanPlan pl, const T* zs, const T* kk,
 }
 
 // ------------------------------------------------------------------ carries
-// One thread per (direction, state, mode): carry_in[c+1] = D_c carry_in[c] +
-// A_c (forward; mirrored backward), in the carry type. Inputs for a batch of
-// chunks are loaded first so the dependent chain waits for arithmetic only.
+// carry_in[c+1] = D_c carry_in[c] + A_c over the chunks (forward; mirrored
+// backward), one chain per (direction, state, mode), in the carry type. The
+// chunks are cut into G groups of g, and the chains run in three parallel
+// phases: (1) every group composes its transfer (D_g = prod D_c, A_g = the
+// group's output from a zero input); (2) a short chain over the G groups
+// gives each group's input; (3) every group replays its chunks from that
+// input and writes the carries. Depth 2g + G instead of G g. All loads and
+// stores are coalesced across modes.
+
 template <typename T>
-__global__ void kspace_carry_kernel(KParams<T> P,
-                                    const Cplx<typename CarryNum<T>::type>* pdec,
-                                    const typename CarryNum<T>::type* kdec) {
+struct CarryCtx {
+  int nc, G, g, S, Kpad, np;
+  size_t cs;        // stride between chunks in agg/carry (S * Kpad)
+  size_t dirstride; // nchunks * S * Kpad
+};
+
+template <typename T>
+__device__ __forceinline__ void chunk_decay(const CarryCtx<T>& X, const Cplx<typename CarryNum<T>::type>* pdec,
+                                            const typename CarryNum<T>::type* kdec, int dir, int st,
+                                            int m, int c, typename CarryNum<T>::type& dr,
+                                            typename CarryNum<T>::type& di) {
   using CN = typename CarryNum<T>::type;
-  const ScanPlan& pl = P.plan;
-  const int S = pl.nstates;
-  const int total = 2 * S * pl.Kpad;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= total) return;
-  const int dir = e / (S * pl.Kpad);
-  const int r = e - dir * S * pl.Kpad;
-  const int st = r / pl.Kpad, m = r - st * pl.Kpad;
-  const size_t dirstride = (size_t)pl.nchunks * S * pl.Kpad;
-  const Cplx<T>* A = P.agg + dir * dirstride + (size_t)st * pl.Kpad + m;
-  Cplx<T>* C = P.carry + dir * dirstride + (size_t)st * pl.Kpad + m;
-  const size_t cs = (size_t)S * pl.Kpad;
-  const int p = (st - 1) >> 1;
-  const int nc = pl.nchunks;
-  CN cr = cn_zero((CN*)nullptr), ci = cn_zero((CN*)nullptr);
-  const CN zero = cn_zero((CN*)nullptr);
-  constexpr int B = 16;
-  for (int j0 = 0; j0 < nc; j0 += B) {
+  if (st == 0) {
+    dr = kdec[((size_t)dir * X.nc + c) * X.Kpad + m];
+    di = cn_zero((CN*)nullptr);
+  } else {
+    const Cplx<CN> d = pdec[((size_t)dir * X.nc + c) * X.np + ((st - 1) >> 1)];
+    dr = d.re; di = d.im;
+  }
+}
+
+// phase 1 (replay = false) and phase 3 (replay = true); thread = (dir, state, group, mode)
+template <typename T>
+__global__ void carry_group_kernel(CarryCtx<T> X, const Cplx<T>* agg, Cplx<T>* carry,
+                                   const Cplx<typename CarryNum<T>::type>* pdec,
+                                   const typename CarryNum<T>::type* kdec,
+                                   Cplx<typename CarryNum<T>::type>* gD,
+                                   Cplx<typename CarryNum<T>::type>* gA, bool replay) {
+  using CN = typename CarryNum<T>::type;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per_dir = (int64_t)X.S * X.G * X.Kpad;
+  if (e >= 2 * per_dir) return;
+  const int dir = (int)(e / per_dir);
+  int64_t r = e - dir * per_dir;
+  const int st = (int)(r / ((int64_t)X.G * X.Kpad));
+  r -= (int64_t)st * X.G * X.Kpad;
+  const int grp = (int)(r / X.Kpad), m = (int)(r - (int64_t)grp * X.Kpad);
+  const size_t gidx = (((size_t)dir * X.S + st) * X.G + grp) * X.Kpad + m;
+  const CN zero = cn_zero((CN*)nullptr), one = cn_from(1.0, (CN*)nullptr);
+  CN cr = zero, ci = zero, pr = one, pi = zero;
+  if (replay) { cr = gA[gidx].re; ci = gA[gidx].im; }
+  const Cplx<T>* A = agg + dir * X.dirstride + (size_t)st * X.Kpad + m;
+  Cplx<T>* C = carry + dir * X.dirstride + (size_t)st * X.Kpad + m;
+  const int j0 = grp * X.g, j1 = min(X.nc, j0 + X.g);
+  constexpr int B = 8;
+  for (int jb = j0; jb < j1; jb += B) {
     Cplx<T> a[B];
     CN dr[B], di[B];
 #pragma unroll
     for (int u = 0; u < B; ++u) {
-      const int j = j0 + u;
+      const int j = jb + u;
       dr[u] = zero; di[u] = zero; a[u] = Cplx<T>{0, 0};
-      if (j < nc) {
-        const int c = dir == 0 ? j : nc - 1 - j;
-        a[u] = A[c * cs];
-        if (st == 0) {
-          dr[u] = kdec[((size_t)dir * nc + c) * pl.Kpad + m];
-        } else {
-          const Cplx<CN> d = pdec[((size_t)dir * nc + c) * pl.np + p];
-          dr[u] = d.re; di[u] = d.im;
-        }
+      if (j < j1) {
+        const int c = dir == 0 ? j : X.nc - 1 - j;
+        a[u] = A[c * X.cs];
+        chunk_decay<T>(X, pdec, kdec, dir, st, m, c, dr[u], di[u]);
       }
     }
 #pragma unroll
     for (int u = 0; u < B; ++u) {
-      const int j = j0 + u;
-      if (j < nc) {
-        const int c = dir == 0 ? j : nc - 1 - j;
-        C[c * cs] = Cplx<T>{cn_to_t(cr), cn_to_t(ci)};
+      const int j = jb + u;
+      if (j < j1) {
+        const int c = dir == 0 ? j : X.nc - 1 - j;
+        if (replay) C[c * X.cs] = Cplx<T>{cn_to_t(cr), cn_to_t(ci)};
         const CN nr = dr[u] * cr - di[u] * ci + cn_from_t(a[u].re, (CN*)nullptr);
         const CN ni = dr[u] * ci + di[u] * cr + cn_from_t(a[u].im, (CN*)nullptr);
         cr = nr; ci = ni;
+        if (!replay) {
+          const CN npr = dr[u] * pr - di[u] * pi;
+          const CN npi = dr[u] * pi + di[u] * pr;
+          pr = npr; pi = npi;
+        }
       }
     }
   }
+  if (!replay) {
+    gD[gidx] = Cplx<CN>{pr, pi};
+    gA[gidx] = Cplx<CN>{cr, ci};
+  }
+}
+
+// phase 2: thread = (dir, state, mode); turns gA into each group's input
+template <typename T>
+__global__ void carry_chain_kernel(CarryCtx<T> X, const Cplx<typename CarryNum<T>::type>* gD,
+                                   Cplx<typename CarryNum<T>::type>* gA) {
+  using CN = typename CarryNum<T>::type;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * X.S * X.Kpad) return;
+  const int dir = e / (X.S * X.Kpad);
+  const int r = e - dir * X.S * X.Kpad;
+  const int st = r / X.Kpad, m = r - st * X.Kpad;
+  const CN zero = cn_zero((CN*)nullptr);
+  CN cr = zero, ci = zero;
+  for (int grp = 0; grp < X.G; ++grp) {
+    const size_t gidx = (((size_t)dir * X.S + st) * X.G + grp) * X.Kpad + m;
+    const Cplx<CN> d = gD[gidx], a = gA[gidx];
+    gA[gidx] = Cplx<CN>{cr, ci};
+    const CN nr = d.re * cr - d.im * ci + a.re;
+    const CN ni = d.re * ci + d.im * cr + a.im;
+    cr = nr; ci = ni;
+  }
+}
+
+template <typename T>
+inline CarryCtx<T> carry_ctx(const ScanPlan& pl) {
+  CarryCtx<T> X;
+  X.nc = pl.nchunks;
+  X.G = pl.nchunks >= 64 ? 32 : 1;
+  X.g = (pl.nchunks + X.G - 1) / X.G;
+  X.S = pl.nstates;
+  X.Kpad = pl.Kpad;
+  X.np = pl.np;
+  X.cs = (size_t)pl.nstates * pl.Kpad;
+  X.dirstride = (size_t)pl.nchunks * pl.nstates * pl.Kpad;
+  return X;
 }
 
 // ------------------------------------------------------------------ pass B
@@ -560,8 +630,16 @@ static void kspace_run(const KParams<T>& P, const PairTab& pairs, void* dec,
                                                          pairs, pdec, nullptr);
   const int64_t nk = (int64_t)2 * pl.nchunks * pl.Kpad;
   mode_decay_kernel<T><<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(pl, P.zs, P.modes.kk, kdec);
-  const int nt = 2 * pl.nstates * pl.Kpad;
-  kspace_carry_kernel<T><<<(nt + 127) / 128, 128, 0, st>>>(P, pdec, kdec);
+  const CarryCtx<T> X = carry_ctx<T>(pl);
+  Cplx<CN>* gD = reinterpret_cast<Cplx<CN>*>(kdec + (size_t)2 * pl.nchunks * pl.Kpad);
+  Cplx<CN>* gA = gD + (size_t)2 * X.S * X.G * X.Kpad;
+  const int64_t ng = (int64_t)2 * X.S * X.G * X.Kpad;
+  carry_group_kernel<T><<<(unsigned)((ng + 127) / 128), 128, 0, st>>>(X, P.agg, P.carry, pdec, kdec,
+                                                                      gD, gA, false);
+  const int nt = 2 * X.S * X.Kpad;
+  carry_chain_kernel<T><<<(nt + 127) / 128, 128, 0, st>>>(X, gD, gA);
+  carry_group_kernel<T><<<(unsigned)((ng + 127) / 128), 128, 0, st>>>(X, P.agg, P.carry, pdec, kdec,
+                                                                      gD, gA, true);
   if (ev) cudaEventRecord(ev[1], st);
   kspace_final_kernel<T, NP><<<grid, pl.KR, smB, st>>>(P, pairs);
   if (ev) cudaEventRecord(ev[2], st);
@@ -569,7 +647,9 @@ static void kspace_run(const KParams<T>& P, const PairTab& pairs, void* dec,
 
 size_t kspace_decay_bytes(const ScanPlan& pl, int fp64) {
   const size_t cn = fp64 ? sizeof(double) : sizeof(DF);
-  return 2 * cn * (size_t)2 * pl.nchunks * pl.np + cn * (size_t)2 * pl.nchunks * pl.Kpad;
+  // pair decays, mode decays, group transfers (D and A)
+  return 2 * cn * (size_t)2 * pl.nchunks * pl.np + cn * (size_t)2 * pl.nchunks * pl.Kpad +
+         2 * 2 * cn * (size_t)2 * pl.nstates * 32 * pl.Kpad + 1024;
 }
 
 template <typename T>
