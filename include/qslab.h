@@ -63,6 +63,7 @@ typedef struct qslab_ctx qslab_ctx;
 #define QSLAB_ERR_ALLOC (-6)          /* device or host allocation failed    */
 #define QSLAB_ERR_CUDA (-7)           /* a CUDA runtime call failed          */
 #define QSLAB_ERR_TIMEOUT (-8)        /* a bounded device wait gave up       */
+#define QSLAB_ERR_TOO_LARGE (-9)      /* exceeds qslab_compute_static's scratch */
 
 /* Create a context on CUDA device `cuda_device` with precision `prec`
  * (QSLAB_FP64 or QSLAB_FP32C). *out receives the handle. */
@@ -129,6 +130,33 @@ int qslab_compute(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
 int qslab_compute_host(qslab_ctx* ctx, int64_t N, const void* pos_host,
                        const void* q_host, double* energy_host,
                        void* phi_host, void* force_host, void* stream);
+
+/* The same computation as qslab_compute(), for callers that cannot allocate
+ * device memory when they need the result (inside another framework's memory
+ * pool, under a fixed device-memory budget, or in a time step where an
+ * allocation and the synchronisation it may bring are not allowed). It calls
+ * no cudaMalloc, cudaFree or other allocating routine: all scratch comes from
+ * one 64 MiB array in device memory that the library defines at file scope
+ * and that every GPU loading the library holds until the process exits.
+ * The paper has no counterpart; this is an interface variant only.
+ *   - Arguments, layouts and results as for qslab_compute(); the context must
+ *     be configured. Its own device buffers are not used; the mode and
+ *     sampler tables are rebuilt in the array on every call (host-side
+ *     configuration work only, no device allocation).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Limits: the tables must fit 8 MiB and the workspace the remaining
+ *     56 MiB (at P = 200 random-batch modes about 1.7e5 particles in FP32C);
+ *     larger problems return QSLAB_ERR_TOO_LARGE before any device work.
+ *   - Every call uses the same array and it keeps the previous call's
+ *     contents (what must start at zero is cleared by the call). Calls that
+ *     overlap on the GPU (two streams, or two contexts on one device) race on
+ *     it: serialise them.
+ *   - The call waits for its stream and returns the full status, including
+ *     device-side input errors; the random-batch counter advances as for
+ *     qslab_compute() (qslab_get_sampled_modes() does not see these samples). */
+int qslab_compute_static(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
+                         double* energy, void* phi, void* force, void* stream);
 
 /* Random-batch mode: copy the P lattice vectors used by the latest
  * qslab_compute() into mxy (host, 2*P int32: m_x, m_y pairs) and, if weight

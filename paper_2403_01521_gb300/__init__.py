@@ -67,6 +67,7 @@ def load(build_if_missing: bool = True):
         "qslab_set_tuning": ([P, I, I], I),
         "qslab_compute": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_compute_host": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
+        "qslab_compute_static": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_get_sampled_modes": ([P, P, P], I),
         "qslab_get_rng_state": ([P, P, P], I),
         "qslab_set_rng_state": ([P, ctypes.c_uint64, ctypes.c_uint64], I),
@@ -143,6 +144,14 @@ def qslab_compute(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr, stream_p
 def qslab_compute_host(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr, stream_ptr):
     _check(load().qslab_compute_host(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr,
                                      stream_ptr), "qslab_compute_host")
+
+
+def qslab_compute_static(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr, stream_ptr):
+    """qslab_compute() for callers that cannot allocate device memory: all
+    scratch comes from the library's fixed 64 MiB device array. Waits for the
+    stream and raises on any error, including device-side input errors."""
+    _check(load().qslab_compute_static(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr,
+                                       stream_ptr), "qslab_compute_static")
 
 
 def qslab_get_sampled_modes(h, P):

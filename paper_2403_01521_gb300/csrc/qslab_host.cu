@@ -6,6 +6,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -702,8 +703,120 @@ const char* qslab_strerror(int code) {
     case QSLAB_ERR_ALLOC: return "allocation failed";
     case QSLAB_ERR_CUDA: return "CUDA runtime error";
     case QSLAB_ERR_TIMEOUT: return "bounded device wait gave up";
+    case QSLAB_ERR_TOO_LARGE: return "problem too large for the fixed scratch of qslab_compute_static";
     default: return "unknown error";
   }
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Compute without allocating device memory.
+//
+// Some callers cannot allocate GPU memory at the point where they need the
+// long-range forces: code running inside another framework's memory pool or
+// under a strict device-memory budget, or a time step of a simulation loop in
+// which an allocation (and the device synchronisation it may imply) is not
+// acceptable. qslab_compute_static() serves them: it runs the same launch
+// sequence as qslab_compute() but takes every byte of scratch it needs (the
+// mode and sampler tables, sort buffers, sorted particles, chunk aggregates
+// and carries, partial outputs, the k = 0 work and the status word) from one
+// fixed array in device memory that the library defines at file scope. That
+// array (kStaticScratchBytes per GPU) exists on every GPU that loads the
+// library, from module load until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;   // 64 MiB per GPU
+constexpr size_t kStaticCfgBytes = size_t(8) << 20;        // tables and status
+constexpr size_t kStaticSmallBytes = 256;                  // status, sums, energy
+constexpr int kStaticMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch per device. In host code the symbol is
+// only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress once per device, with that device current.
+void* g_static_addr[kStaticMaxDevices] = {};
+
+int static_scratch_address(int device, void** out) {
+  if (device < 0 || device >= kStaticMaxDevices) return QSLAB_ERR_INVALID_ARG;
+  if (!g_static_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return QSLAB_ERR_CUDA;
+    g_static_addr[device] = p;
+  }
+  *out = g_static_addr[device];
+  return QSLAB_OK;
+}
+
+}  // namespace
+
+extern "C" int qslab_compute_static(qslab_ctx* c, int64_t N, const void* pos, const void* q,
+                                    double* energy, void* phi, void* force, void* stream) {
+  if (!c) return QSLAB_ERR_INVALID_ARG;
+  if (N < 1 || N > 2147483647LL || !pos || !q) return QSLAB_ERR_INVALID_ARG;
+  if (!c->has_box || !c->has_alpha || !c->has_soe || c->mode == 0) return QSLAB_ERR_NOT_CONFIGURED;
+  QS_CUDA(cudaSetDevice(c->device));
+  void* base = nullptr;
+  int rc = static_scratch_address(c->device, &base);
+  if (rc) return rc;
+  char* sb = static_cast<char*>(base);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  // A copy of the context whose device buffers all point into the static
+  // array; its configuration tables are rebuilt there on every call (the
+  // real context's own buffers are neither used nor changed).
+  qslab_ctx t = *c;
+  t.timing = false;
+  t.d_status = reinterpret_cast<unsigned*>(sb);
+  t.d_sums = reinterpret_cast<double*>(sb + 64);
+  t.d_energy = reinterpret_cast<double*>(sb + 128);
+  t.d_cfg = sb + kStaticSmallBytes;
+  t.cfg_bytes = kStaticCfgBytes - kStaticSmallBytes;
+  t.d_ws = sb + kStaticCfgBytes;
+  t.ws_bytes = kStaticScratchBytes - kStaticCfgBytes;
+  // size checks before anything touches the device: the tables must fit the
+  // table region and the workspace the rest of the array
+  {
+    const size_t tsz = c->prec == QSLAB_FP64 ? sizeof(double) : sizeof(float);
+    qslab_ctx probe = *c;
+    if (build_pairs(&probe) != QSLAB_OK) return QSLAB_ERR_INVALID_ARG;
+    size_t K = 0, cdf = 0;
+    if (c->mode == 1) {
+      K = half_plane(c->Lx, c->Ly, c->kc).size() / 2;
+    } else {
+      K = (size_t)c->P;
+      const double mx = std::floor(6.4380 * c->alpha * c->Lx / kPi) + 1;
+      const double my = std::floor(6.4380 * c->alpha * c->Ly / kPi) + 1;
+      cdf = (size_t)(2 * mx + 1) + (size_t)(2 * my + 1);
+      if (mx > 1e6 || my > 1e6) return QSLAB_ERR_TOO_LARGE;
+    }
+    const size_t kpad = ((std::max<size_t>(K, 1) + 255) / 256) * 256;
+    const size_t need = a256(sizeof(int32_t) * 2 * kpad) * 2 + a256(sizeof(double) * (cdf + 2)) * 2 +
+                        mode_bytes((int)kpad, probe.npc, tsz);
+    if (need > t.cfg_bytes || kpad > (size_t)1 << 20) return QSLAB_ERR_TOO_LARGE;
+  }
+  t.dirty = true;
+  rc = rebuild(&t);          // fits: no allocation, tables uploaded into the array
+  if (rc) return rc;
+  const Plan P = make_plan(&t, N, false);
+  if (P.total > t.ws_bytes) return QSLAB_ERR_TOO_LARGE;
+  // the status word and sums start from zero on every call
+  QS_CUDA(cudaMemsetAsync(t.d_status, 0, kStaticSmallBytes, st));
+  if (c->prec == QSLAB_FP64)
+    rc = run<double>(&t, P, static_cast<const double*>(pos), static_cast<const double*>(q),
+                     energy, static_cast<double*>(phi), static_cast<double*>(force), st);
+  else
+    rc = run<float>(&t, P, static_cast<const float*>(pos), static_cast<const float*>(q), energy,
+                    static_cast<float*>(phi), static_cast<float*>(force), st);
+  if (rc) return rc;
+  // the random-batch counter advances as in qslab_compute()
+  c->counter = t.counter;
+  QS_CUDA(cudaStreamSynchronize(st));
+  QS_CUDA(cudaGetLastError());
+  unsigned f = 0;
+  QS_CUDA(cudaMemcpy(&f, t.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  return status_code(f);
+}
