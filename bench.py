@@ -108,6 +108,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(x, device=None):
+    """Maximum of x over all ranks (x itself without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms_slowest):
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / (ms_slowest * 1e-3)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -246,12 +262,9 @@ def run_ours(args):
     s64.close()
 
     # slowest rank decides
-    ms32_max = ms32
-    if ws > 1:
-        t = torch.tensor([ms32], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms32_max = float(t.item())
-    value = ws * N / (ms32_max * 1e-3)
+    ms32_max = reduce_max(ms32, dev)
+    ms64_max = reduce_max(ms64, dev)
+    value = job_throughput(N, ws, ms32_max)
 
     # ---- end to end through the C ABI with pinned host buffers
     pos_h = torch.tensor(sl.pos, dtype=torch.float32).pin_memory()
@@ -270,11 +283,7 @@ def run_ours(args):
         qslab.qslab_compute_host(s32.h, N, pos_h.data_ptr(), q_h.data_ptr(), e_h.data_ptr(),
                                  phi_h.data_ptr(), F_h.data_ptr(), stream.cuda_stream)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_ms = float(np.mean(e2e_ms))
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = reduce_max(float(np.mean(e2e_ms)), dev)
     s32.close()
 
     # ---- roofline of the dominant kernel (the recurrences + gather)
@@ -309,7 +318,7 @@ def run_ours(args):
                                "(FP64 chunk carries, FP64 k=0 term and reductions)",
                    "N": N, "P": P, "M": M, "per_rank": "independent replica",
                    "l2": "flushed between steps (256 MB write, untimed)"},
-        "fp64": {"value": ws * N / (ms64 * 1e-3), "unit": "particles/s", "ms_per_step": ms64,
+        "fp64": {"value": job_throughput(N, ws, ms64_max), "unit": "particles/s", "ms_per_step": ms64_max,
                  "steps": st64, "energy": E64},
         "energy_fp32c": E32,
         "phases_ms": phases,
@@ -319,7 +328,7 @@ def run_ours(args):
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                    f"{smax:.0f} MHz ({peak_kind} max SM clock)",
                      "work": "K*N*(24*(M+1)+20) FP32 instructions per launch"},
-        "e2e": {"value": ws * N / (e2e_ms * 1e-3), "unit": "particles/s",
+        "e2e": {"value": job_throughput(N, ws, e2e_ms), "unit": "particles/s",
                 "h2d_bytes_per_step": int(N * 3 * 4 + N * 4),
                 "d2h_bytes_per_step": int(8 + N * 4 + N * 12)},
         "clocks": clocks,
@@ -336,6 +345,24 @@ def run_ours(args):
     return 0
 
 
+def profile_case():
+    """Two FP32 random-batch calls on the benchmark workload (for ncu)."""
+    import torch
+
+    import paper_2403_01521_gb300 as qslab
+    import workloads
+    sl = workloads.rbe_large()
+    slab = qslab.QSlab(0, "fp32c").configure(sl.box, sl.alpha, qslab.load_soe(16), rbe=(200, 5))
+    pos = torch.tensor(sl.pos, device="cuda", dtype=torch.float32)
+    q = torch.tensor(sl.q, device="cuda", dtype=torch.float32)
+    for _ in range(2):
+        e, _, _ = slab.compute(pos, q)
+    slab.check()
+    torch.cuda.synchronize()
+    print("profile case done, E =", float(e.item()))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,7 +370,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="only run two FP32 random-batch calls (for profilers)")
     args = ap.parse_args()
+    if args.profile_case:
+        return profile_case()
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

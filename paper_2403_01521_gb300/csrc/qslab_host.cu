@@ -310,7 +310,7 @@ Plan make_plan(const qslab_ctx* c, int64_t N, bool host_io) {
   s.nchunks = (int)((N + L - 1) / L);
   s.np = c->npc;
   s.nstates = 1 + 2 * c->npc;
-  P.L0 = 256;
+  P.L0 = dp ? 512 : 1024;   // k = 0 chunks: longer chunks, a shorter carry chain
   P.nch0 = (int)((N + P.L0 - 1) / P.L0);
   P.nblk = (int)((N + 255) / 256);
   if (P.nblk > 152 * 8) P.nblk = 152 * 8;
