@@ -189,12 +189,15 @@ def uniform53(word: np.ndarray) -> np.ndarray:
     return (np.asarray(word, np.uint64) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
 
 
-def sample_modes(P: int, seed: int, call: int, alpha: float, Lx: float, Ly: float):
+def sample_modes(P: int, seed: int, call: int, alpha: float, Lx: float, Ly: float,
+                 stream: int = 0):
     """P i.i.d. lattice vectors from h(k) (origin excluded).
 
-    Sample eta, attempt a uses Philox4x64-10 with counter (eta, a, call, TAG)
-    and key (seed, 0). Words 0,1 give (mx, my); if that is the origin, words
-    2,3 are tried; if that is the origin too, the next attempt is used.
+    Sample eta, attempt a uses Philox4x64-10 with counter
+    (eta, a, call, TAG + stream * 2^32) and key (seed, 0); `stream` separates
+    independent systems drawn in the same call (one per slab of a batch).
+    Words 0,1 give (mx, my); if that is the origin, words 2,3 are tried; if
+    that is the origin too, the next attempt is used.
     """
     cx, mxm = axis_cdf(alpha, Lx)
     cy, mym = axis_cdf(alpha, Ly)
@@ -207,7 +210,7 @@ def sample_modes(P: int, seed: int, call: int, alpha: float, Lx: float, Ly: floa
         ctr[:, 0] = todo
         ctr[:, 1] = attempt
         ctr[:, 2] = np.uint64(call)
-        ctr[:, 3] = SAMPLER_TAG
+        ctr[:, 3] = np.uint64(SAMPLER_TAG + (int(stream) << 32))
         key = np.zeros((todo.size, 2), np.uint64)
         key[:, 0] = np.uint64(seed)
         wds = philox4x64_10(ctr, key)
