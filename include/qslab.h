@@ -122,6 +122,36 @@ int qslab_set_tuning(qslab_ctx* ctx, int chunk, int modes_per_cta);
 int qslab_compute(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
                   double* energy, void* phi, void* force, void* stream);
 
+/* Many independent slabs ("replicas") in one call: the same computation as
+ * qslab_compute() for each replica, batched into one launch sequence (every
+ * kernel covers all replicas; no launch per replica). The paper treats one
+ * slab at a time; this is the same method applied to R of them at once.
+ *   R        number of replicas, 1 <= R <= 2^20
+ *   offsets  host, R + 1 int64: replica r owns particles
+ *            [offsets[r], offsets[r+1]) of pos, q, phi and force;
+ *            offsets[0] = 0, non-decreasing (empty replicas allowed),
+ *            1 <= offsets[R] <= 2^31 - 1
+ *   boxes    host, R x 3 doubles (Lx, Ly, Lz) per replica; the box set by
+ *            qslab_set_box() is not used
+ *   energies device, R doubles (FP64), or NULL: the energy of each replica
+ *   pos, q, phi, force, stream: as for qslab_compute(), over all particles
+ * alpha, the SOE and the k-set (k cutoff, or P and seed) are the context's
+ * and are shared by all replicas; the full k-sum uses each replica's own
+ * half-plane lattice, the random batch draws P vectors per replica from the
+ * replica's own h(k), with the stream index r in the generator's counter.
+ * Every replica must be charge neutral on its own.
+ * Tables derived from offsets and boxes are cached in the context: calls
+ * that repeat them do no host-side set-up and no synchronous transfer. Such a
+ * repeat call (after one ordinary call with the same arguments and buffers
+ * has sized the context) issues only stream-ordered work and may be captured
+ * in a CUDA graph; a graph replay recomputes everything, including a fresh
+ * random-batch sample. Device-side input errors go to the status word as for
+ * qslab_compute(). */
+int qslab_compute_batched(qslab_ctx* ctx, int R, const int64_t* offsets,
+                          const double* boxes, const void* pos, const void* q,
+                          double* energies, void* phi, void* force,
+                          void* stream);
+
 /* The same computation from host buffers: copies pos and q (host, layout as
  * above; pinned memory makes the copies asynchronous) to the device, runs,
  * copies energy/phi/force back to host buffers (any may be NULL) and waits
@@ -158,13 +188,18 @@ int qslab_compute_host(qslab_ctx* ctx, int64_t N, const void* pos_host,
 int qslab_compute_static(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
                          double* energy, void* phi, void* force, void* stream);
 
-/* Random-batch mode: copy the P lattice vectors used by the latest
- * qslab_compute() into mxy (host, 2*P int32: m_x, m_y pairs) and, if weight
- * is not NULL, the sample weight H/P. Synchronises the context's stream. */
+/* Random-batch mode: copy the lattice vectors used by the latest
+ * qslab_compute() or qslab_compute_batched() into mxy (host, 2*P*R int32:
+ * (m_x, m_y) pairs, replica by replica; R = 1 after qslab_compute()) and, if
+ * weight is not NULL, the sample weights H_r/P (R doubles). Synchronises
+ * the context's stream. */
 int qslab_get_sampled_modes(qslab_ctx* ctx, int32_t* mxy, double* weight);
 
-/* Generator state (seed, number of compute calls made), for bit-exact
- * resumption of a random-batch sequence. */
+/* Generator state (seed, number of random-batch compute calls made), for
+ * bit-exact resumption of a random-batch sequence. The counter lives in
+ * device memory and is advanced on the stream by every call (so that a call
+ * replayed from a CUDA graph draws a fresh sample); both functions
+ * synchronise the stream of the latest call. */
 int qslab_get_rng_state(qslab_ctx* ctx, uint64_t* seed, uint64_t* counter);
 int qslab_set_rng_state(qslab_ctx* ctx, uint64_t seed, uint64_t counter);
 

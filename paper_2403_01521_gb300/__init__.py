@@ -68,6 +68,7 @@ def load(build_if_missing: bool = True):
         "qslab_compute": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_compute_host": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_compute_static": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
+        "qslab_compute_batched": ([P, I, P, P, P, P, P, P, P, P], I),
         "qslab_get_sampled_modes": ([P, P, P], I),
         "qslab_get_rng_state": ([P, P, P], I),
         "qslab_set_rng_state": ([P, ctypes.c_uint64, ctypes.c_uint64], I),
@@ -154,12 +155,31 @@ def qslab_compute_static(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr, s
                                        stream_ptr), "qslab_compute_static")
 
 
-def qslab_get_sampled_modes(h, P):
-    mxy = np.zeros(2 * P, np.int32)
-    wt = ctypes.c_double()
-    _check(load().qslab_get_sampled_modes(h, mxy.ctypes.data, ctypes.addressof(wt)),
+def qslab_compute_batched(h, offsets, boxes, pos_ptr, q_ptr, energies_ptr, phi_ptr, force_ptr,
+                          stream_ptr):
+    """R slabs in one call. offsets: R+1 int64 (host), boxes: R x 3 float64
+    (host); the other arguments as for qslab_compute()."""
+    off = np.ascontiguousarray(offsets, np.int64)
+    box = np.ascontiguousarray(boxes, np.float64).reshape(-1, 3)
+    R = off.shape[0] - 1
+    if box.shape[0] != R:
+        raise ValueError("boxes must have one row per replica")
+    _check(load().qslab_compute_batched(h, R, off.ctypes.data, box.ctypes.data, pos_ptr, q_ptr,
+                                        energies_ptr, phi_ptr, force_ptr, stream_ptr),
+           "qslab_compute_batched")
+
+
+def qslab_get_sampled_modes(h, P, R=1):
+    """(mx, my, weight) of the latest random-batch call: arrays of P (R = 1)
+    or R x P, and the weight H/P (a float, or R of them)."""
+    mxy = np.zeros(2 * P * R, np.int32)
+    wt = np.zeros(R)
+    _check(load().qslab_get_sampled_modes(h, mxy.ctypes.data, wt.ctypes.data),
            "qslab_get_sampled_modes")
-    return mxy[0::2].copy(), mxy[1::2].copy(), wt.value
+    mx, my = mxy[0::2].copy(), mxy[1::2].copy()
+    if R == 1:
+        return mx, my, float(wt[0])
+    return mx.reshape(R, P), my.reshape(R, P), wt
 
 
 def qslab_get_rng_state(h):
@@ -224,6 +244,7 @@ class QSlab:
         self.device = device
         self.h = qslab_create(device, _PREC[precision])
         self.P = 0
+        self.last_R = 1
 
     def close(self):
         if self.h:
@@ -276,7 +297,41 @@ class QSlab:
         qslab_compute(self.h, N, pos.data_ptr(), q.data_ptr(), energy.data_ptr(),
                       phi.data_ptr() if phi is not None else None,
                       force.data_ptr() if force is not None else None, st)
+        self.last_R = 1
         return energy, phi, force
+
+    def compute_batched(self, pos, q, offsets, boxes, energies=None, phi=None, force=None,
+                        want_phi=True, want_force=True):
+        """R slabs in one call: replica r owns rows offsets[r]:offsets[r+1] of
+        pos (N x 3) and q (N), in the box boxes[r] = (Lx, Ly, Lz). offsets and
+        boxes are host arrays. Returns (energies[R] float64, phi[N],
+        force[N,3]) as CUDA tensors; passing the output tensors in reuses them
+        (as a CUDA-graph replay needs)."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        if pos.device != dev or q.device != dev:
+            raise ValueError("pos and q must be CUDA tensors on the context's device")
+        if pos.dtype != self.dtype or q.dtype != self.dtype or not pos.is_contiguous() \
+                or not q.is_contiguous():
+            raise ValueError("pos and q must be contiguous tensors of the context's precision")
+        off = np.ascontiguousarray(offsets, np.int64)
+        R = off.shape[0] - 1
+        N = q.shape[0]
+        if int(off[-1]) != N:
+            raise ValueError("offsets[-1] must equal the number of particles")
+        if energies is None:
+            energies = torch.empty(R, dtype=torch.float64, device=dev)
+        if phi is None and want_phi:
+            phi = torch.empty(N, dtype=self.dtype, device=dev)
+        if force is None and want_force:
+            force = torch.empty((N, 3), dtype=self.dtype, device=dev)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        qslab_compute_batched(self.h, off, boxes, pos.data_ptr(), q.data_ptr(),
+                              energies.data_ptr(),
+                              phi.data_ptr() if phi is not None else None,
+                              force.data_ptr() if force is not None else None, st)
+        self.last_R = R
+        return energies, phi, force
 
     def compute_host(self, pos, q, stream=None):
         """Host numpy in, host numpy out, through qslab_compute_host."""
@@ -299,13 +354,51 @@ class QSlab:
             raise QslabError(rc, "device status")
 
     def sampled_modes(self):
-        return qslab_get_sampled_modes(self.h, self.P)
+        return qslab_get_sampled_modes(self.h, self.P, self.last_R)
 
     def rng_state(self):
         return qslab_get_rng_state(self.h)
 
     def set_rng_state(self, seed, counter):
         qslab_set_rng_state(self.h, seed, counter)
+
+
+class GraphedBatch:
+    """qslab_compute_batched captured once in a CUDA graph and replayed.
+
+    The inputs pos and q (CUDA tensors of the context's precision) are read
+    in place at every replay: write new coordinates into them, then call
+    replay(). Outputs land in self.energies, self.phi and self.force. A
+    random-batch context draws a fresh sample at every replay (its counter
+    lives on the device). The replica layout (offsets, boxes) is fixed by the
+    capture."""
+
+    def __init__(self, slab: QSlab, pos, q, offsets, boxes, warmup: int = 1):
+        import torch
+        self.slab = slab
+        self.pos, self.q = pos, q
+        self.offsets = np.ascontiguousarray(offsets, np.int64)
+        self.boxes = np.ascontiguousarray(boxes, np.float64)
+        dev = pos.device
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            # sizes the context (tables, workspace) so that the captured call
+            # only issues stream-ordered work
+            out = slab.compute_batched(pos, q, self.offsets, self.boxes)
+            for _ in range(max(0, warmup - 1)):
+                slab.compute_batched(pos, q, self.offsets, self.boxes, *out)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        self.energies, self.phi, self.force = out
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            slab.compute_batched(pos, q, self.offsets, self.boxes, self.energies, self.phi,
+                                 self.force)
+
+    def replay(self):
+        self.graph.replay()
+        return self.energies, self.phi, self.force
 
 
 def _autograd():

@@ -8,6 +8,8 @@
 #include <cstdlib>
 #include <algorithm>
 #include <cstring>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -26,6 +28,29 @@ inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+// Host-side description of a call's replicas and the tables derived from
+// it. Cached in the context: rebuilt only when the configuration, the
+// replica offsets, the boxes or the tuning change.
+struct Tables {
+  bool valid = false;
+  uint64_t cfg_version = 0;
+  // key
+  int R = 0;
+  std::vector<int64_t> off;     // R + 1
+  std::vector<double> box;      // 3 R
+  int tune_L = 0, tune_KR = 0;
+  // derived
+  std::vector<RepInfo> info;
+  std::vector<int32_t> chunk_rep, zchunk_rep, gstart, group_rep, list;
+  std::vector<double> cdf;
+  int Kpad = 32, KR = 32, nkr = 1, L = 32, L0 = 512;
+  int nchunks = 0, nz = 0, ngroups = 0;
+  int64_t N = 0;
+  // device layout of the table buffer
+  size_t o_info = 0, o_crep = 0, o_zrep = 0, o_gstart = 0, o_grep = 0, o_list = 0, o_cdf = 0,
+         o_sampled = 0, o_modes = 0, bytes = 0;
+};
+
 struct qslab_ctx {
   int device = 0;
   int prec = QSLAB_FP64;
@@ -35,38 +60,32 @@ struct qslab_ctx {
   int mode = 0;                 // 1 full k-sum, 2 random batch
   double kc = 0;
   int P = 0;
-  uint64_t seed = 0, counter = 0;
+  uint64_t seed = 0;
   std::vector<double> s_re, s_im, w_re, w_im;
   double neutral_tol = -2.0;    // < -1: default for the precision
   int tune_L = 0, tune_KR = 0;
   bool timing = false;
   // derived configuration
-  bool dirty = true;
+  bool cfg_dirty = true;
+  uint64_t cfg_version = 0;
   PairTab pairs{};
   int npc = 4;                  // pair count the kernels are compiled for
-  std::vector<int32_t> half_modes;
-  int K = 0, Kpad = 0, KR = 32, nkr = 1;
-  double diag_k = 0;            // sum over all summed k of (pi/A) erfc(k/2a)/k
-  double H = 0;
-  int cdf_nx = 0, cdf_ny = 0, mxmax = 0, mymax = 0;
-  // persistent device data (per configuration)
-  void* d_cfg = nullptr;
-  size_t cfg_bytes = 0;
-  int32_t* d_list = nullptr;
-  double* d_cdfx = nullptr;
-  double* d_cdfy = nullptr;
-  int32_t* d_sampled = nullptr;
-  void* d_modes = nullptr;      // mode table storage
-  bool coef_ready = false;
-  // small persistent buffers
+  Tables tab;
+  // device tables (per configuration and replica geometry)
+  void* d_tab = nullptr;
+  size_t tab_bytes = 0;
+  bool coef_ready = false;      // full-k mode tables filled for tab
+  // small persistent buffers: status word, energy, random-batch counter
+  // (ctr[0] = counter of the next call, ctr[1] = counter of the last one)
   unsigned* d_status = nullptr;
-  double* d_sums = nullptr;
   double* d_energy = nullptr;
-  // per-N workspace
+  uint64_t* d_ctr = nullptr;
+  // per-call workspace
   void* d_ws = nullptr;
   size_t ws_bytes = 0;
   cudaStream_t last_stream = nullptr;
   bool have_sample = false;
+  int last_R = 1;
   cudaEvent_t ev[9] = {};
   int launches = 0;
   // the k = 0 term runs on a side stream, forked from and joined to the
@@ -90,6 +109,8 @@ int cuda_fail(cudaError_t e) {
   } while (0)
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+constexpr int kMaxReplicas = 1 << 20;
 
 // Representatives of conjugate pairs of SOE nodes (multiplicity 2) and real
 // nodes (multiplicity 1); padded with zero-weight entries to a compiled size.
@@ -142,15 +163,48 @@ int build_pairs(qslab_ctx* c) {
   return QSLAB_OK;
 }
 
-// sum over the listed (half-plane) modes of (pi/A) erfc(k/(2 alpha))/k, times 2
-double diag_half(const qslab_ctx* c, const std::vector<int32_t>& list) {
+int ensure_config(qslab_ctx* c) {
+  if (!c->has_alpha || !c->has_soe || c->mode == 0) return QSLAB_ERR_NOT_CONFIGURED;
+  if (!c->cfg_dirty) return QSLAB_OK;
+  const int rc = build_pairs(c);
+  if (rc) return rc;
+  ++c->cfg_version;
+  c->cfg_dirty = false;
+  return QSLAB_OK;
+}
+
+// (pi/A) erfc(k/(2 alpha))/k summed over the listed (half-plane) modes, times 2
+double diag_half(double alpha, double Lx, double Ly, const int32_t* list, size_t K) {
   double s = 0.0;
-  const double A = c->Lx * c->Ly;
-  for (size_t m = 0; m < list.size() / 2; ++m) {
-    const double kx = 2 * kPi * list[2 * m] / c->Lx;
-    const double ky = 2 * kPi * list[2 * m + 1] / c->Ly;
+  const double A = Lx * Ly;
+  for (size_t m = 0; m < K; ++m) {
+    const double kx = 2 * kPi * list[2 * m] / Lx;
+    const double ky = 2 * kPi * list[2 * m + 1] / Ly;
     const double k = std::sqrt(kx * kx + ky * ky);
-    s += kPi / A * std::erfc(k / (2 * c->alpha)) / k;
+    s += kPi / A * std::erfc(k / (2 * alpha)) / k;
+  }
+  return 2.0 * s;
+}
+
+// The same over every k != 0 (the random batch samples the whole lattice);
+// erfc(k/(2 alpha)) < 1e-21 beyond |k| = 14 alpha. The terms of (mx, my) and
+// (mx, -my) are equal and are summed once.
+double diag_all(double alpha, double Lx, double Ly) {
+  const double kc = 14.0 * alpha;
+  const int mxm = (int)std::floor(kc * Lx / (2 * kPi)) + 1;
+  const int mym = (int)std::floor(kc * Ly / (2 * kPi)) + 1;
+  const double A = Lx * Ly;
+  double s = 0.0;
+  for (int mx = 0; mx <= mxm; ++mx) {
+    for (int my = (mx == 0 ? 1 : 0); my <= mym; ++my) {
+      const double kx = 2 * kPi * mx / Lx;
+      const double ky = 2 * kPi * my / Ly;
+      const double k2 = kx * kx + ky * ky;
+      if (k2 > kc * kc) break;
+      const double k = std::sqrt(k2);
+      const double t = kPi / A * std::erfc(k / (2 * alpha)) / k;
+      s += (mx > 0 && my > 0) ? 2.0 * t : t;
+    }
   }
   return 2.0 * s;
 }
@@ -186,8 +240,10 @@ double H_direct(double alpha, double Lx, double Ly) {
   return axis(Lx) * axis(Ly) - 1.0;
 }
 
+int axis_mmax(double alpha, double L) { return (int)std::floor(6.4380 * alpha * L / kPi) + 1; }
+
 std::vector<double> axis_cdf(double alpha, double L, int* mmax_out) {
-  const int mmax = (int)std::floor(6.4380 * alpha * L / kPi) + 1;
+  const int mmax = axis_mmax(alpha, L);
   std::vector<double> c(2 * mmax + 1);
   double run = 0.0;
   for (int j = 0; j <= 2 * mmax; ++j) {
@@ -202,136 +258,270 @@ std::vector<double> axis_cdf(double alpha, double L, int* mmax_out) {
 }
 
 template <typename T>
-ModeTab<T> mode_views(void* base, int Kpad, int npc) {
+ModeTab<T> mode_views(void* base, size_t n, int npc) {
   ModeTab<T> m;
   char* p = static_cast<char*>(base);
-  m.mx = reinterpret_cast<int32_t*>(p); p += a256(sizeof(int32_t) * Kpad);
-  m.my = reinterpret_cast<int32_t*>(p); p += a256(sizeof(int32_t) * Kpad);
+  m.mx = reinterpret_cast<int32_t*>(p); p += a256(sizeof(int32_t) * n);
+  m.my = reinterpret_cast<int32_t*>(p); p += a256(sizeof(int32_t) * n);
   T** f[] = {&m.kx, &m.ky, &m.kk, &m.ck, &m.ckk, &m.sY, &m.sZ};
-  for (T** q : f) { *q = reinterpret_cast<T*>(p); p += a256(sizeof(T) * Kpad); }
+  for (T** q : f) { *q = reinterpret_cast<T*>(p); p += a256(sizeof(T) * n); }
   m.cp = reinterpret_cast<T*>(p);
+  (void)npc;
   return m;
 }
 
-size_t mode_bytes(int Kpad, int npc, size_t tsz) {
-  return 2 * a256(sizeof(int32_t) * Kpad) + 7 * a256(tsz * Kpad) + a256(tsz * 4 * npc * (size_t)Kpad);
+size_t mode_bytes(size_t n, int npc, size_t tsz) {
+  return 2 * a256(sizeof(int32_t) * n) + 7 * a256(tsz * n) + a256(tsz * 4 * npc * n);
 }
 
-int rebuild(qslab_ctx* c) {
-  if (!c->has_box || !c->has_alpha || !c->has_soe || c->mode == 0)
-    return QSLAB_ERR_NOT_CONFIGURED;
-  int rc = build_pairs(c);
-  if (rc) return rc;
-  c->coef_ready = false;
-  std::vector<double> cdfx, cdfy;
-  if (c->mode == 1) {
-    c->half_modes = half_plane(c->Lx, c->Ly, c->kc);
-    c->K = (int)(c->half_modes.size() / 2);
-    c->diag_k = diag_half(c, c->half_modes);
-  } else {
-    c->K = c->P;
-    c->H = H_direct(c->alpha, c->Lx, c->Ly);
-    // the random batch covers the whole lattice: the j = i constant sums every k
-    std::vector<int32_t> all = half_plane(c->Lx, c->Ly, 14.0 * c->alpha);
-    c->diag_k = diag_half(c, all);
-    cdfx = axis_cdf(c->alpha, c->Lx, &c->mxmax);
-    cdfy = axis_cdf(c->alpha, c->Ly, &c->mymax);
-    c->cdf_nx = (int)cdfx.size();
-    c->cdf_ny = (int)cdfy.size();
+bool same_key(const Tables& t, const qslab_ctx* c, int R, const int64_t* off, const double* box) {
+  if (!t.valid || t.cfg_version != c->cfg_version || t.R != R || t.tune_L != c->tune_L ||
+      t.tune_KR != c->tune_KR)
+    return false;
+  return std::memcmp(t.off.data(), off, sizeof(int64_t) * (R + 1)) == 0 &&
+         std::memcmp(t.box.data(), box, sizeof(double) * 3 * R) == 0;
+}
+
+// Host part of the tables of a call (no device work). Validates the replica
+// offsets and boxes.
+int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* box, Tables& t) {
+  if (R < 1 || R > kMaxReplicas || !off || !box) return QSLAB_ERR_INVALID_ARG;
+  if (off[0] != 0) return QSLAB_ERR_INVALID_ARG;
+  for (int r = 0; r < R; ++r) {
+    const int64_t n = off[r + 1] - off[r];
+    if (n < 0 || n > 2147483647LL) return QSLAB_ERR_INVALID_ARG;
+    if (!finite_pos(box[3 * r]) || !finite_pos(box[3 * r + 1]) || !finite_pos(box[3 * r + 2]))
+      return QSLAB_ERR_INVALID_ARG;
+  }
+  const int64_t N = off[R];
+  if (N < 1 || N > 2147483647LL) return QSLAB_ERR_INVALID_ARG;
+  const bool dp = c->prec == QSLAB_FP64;
+  t = Tables();
+  t.cfg_version = c->cfg_version;
+  t.R = R;
+  t.off.assign(off, off + R + 1);
+  t.box.assign(box, box + 3 * R);
+  t.tune_L = c->tune_L;
+  t.tune_KR = c->tune_KR;
+  t.N = N;
+  t.info.assign(R, RepInfo{});
+  const double alpha = c->alpha;
+  // modes, sampler tables and j = i constants per replica (memoised by box)
+  std::map<std::pair<double, double>, int> seen;
+  int Kmax = 1;
+  for (int r = 0; r < R; ++r) {
+    RepInfo& ri = t.info[r];
+    ri.off = off[r];
+    ri.n = (int32_t)(off[r + 1] - off[r]);
+    ri.Lx = box[3 * r]; ri.Ly = box[3 * r + 1]; ri.Lz = box[3 * r + 2];
+    ri.area = ri.Lx * ri.Ly;
+    auto it = seen.find({ri.Lx, ri.Ly});
+    if (it != seen.end()) {
+      const RepInfo& o = t.info[it->second];
+      ri.K = o.K; ri.list0 = o.list0; ri.cdfx0 = o.cdfx0; ri.nx = o.nx;
+      ri.cdfy0 = o.cdfy0; ri.ny = o.ny; ri.mxmax = o.mxmax; ri.mymax = o.mymax;
+      ri.H = o.H; ri.diagq = o.diagq;
+    } else {
+      seen[{ri.Lx, ri.Ly}] = r;
+      double dk = 0.0;
+      if (c->mode == 1) {
+        const std::vector<int32_t> l = half_plane(ri.Lx, ri.Ly, c->kc);
+        ri.K = (int32_t)(l.size() / 2);
+        ri.list0 = (int32_t)(t.list.size() / 2);
+        dk = diag_half(alpha, ri.Lx, ri.Ly, l.data(), l.size() / 2);
+        t.list.insert(t.list.end(), l.begin(), l.end());
+        if (t.list.size() > (size_t)1 << 30) return QSLAB_ERR_INVALID_ARG;
+      } else {
+        ri.K = c->P;
+        ri.H = H_direct(alpha, ri.Lx, ri.Ly);
+        dk = diag_all(alpha, ri.Lx, ri.Ly);
+        int mx = 0, my = 0;
+        const std::vector<double> cx = axis_cdf(alpha, ri.Lx, &mx);
+        const std::vector<double> cy = axis_cdf(alpha, ri.Ly, &my);
+        ri.cdfx0 = (int32_t)t.cdf.size(); ri.nx = (int32_t)cx.size(); ri.mxmax = mx;
+        t.cdf.insert(t.cdf.end(), cx.begin(), cx.end());
+        ri.cdfy0 = (int32_t)t.cdf.size(); ri.ny = (int32_t)cy.size(); ri.mymax = my;
+        t.cdf.insert(t.cdf.end(), cy.begin(), cy.end());
+        if (t.cdf.size() > (size_t)1 << 28) return QSLAB_ERR_INVALID_ARG;
+      }
+      // j = i constant per unit q_i^2 of the potential: k != 0 (Eq. 3.20),
+      // k = 0 (-2 sqrt(pi)/(alpha A), the j = i term of Eq. 2.16) and the
+      // self term -2 alpha/sqrt(pi) (Eq. 2.12)
+      const double D0 = -(kPi / ri.area) / (alpha * kSqrtPi);
+      ri.diagq = 2.0 * dk + 2.0 * D0 - 2.0 * alpha / kSqrtPi;
+    }
+    Kmax = std::max(Kmax, (int)ri.K);
   }
   // modes per CTA (KR) and the number of mode ranges tile Kpad exactly
   {
-    const int k32 = c->K > 0 ? ((c->K + 31) / 32) * 32 : 32;
+    const int k32 = ((Kmax + 31) / 32) * 32;
     int kr = c->tune_KR > 0 ? c->tune_KR : 256;
     if (kr > k32) kr = k32;
     const int nkr = (k32 + kr - 1) / kr;
     kr = (((k32 + nkr - 1) / nkr + 31) / 32) * 32;
-    c->KR = kr;
-    c->nkr = nkr;
-    c->Kpad = kr * nkr;
+    t.KR = kr;
+    t.nkr = nkr;
+    t.Kpad = kr * nkr;
   }
-  const size_t tsz = c->prec == QSLAB_FP64 ? sizeof(double) : sizeof(float);
-  const size_t need = a256(sizeof(int32_t) * 2 * (size_t)c->Kpad) * 2 +
-                      a256(sizeof(double) * (cdfx.size() + 1)) +
-                      a256(sizeof(double) * (cdfy.size() + 1)) +
-                      mode_bytes(c->Kpad, c->npc, tsz);
-  if (need > c->cfg_bytes) {
-    if (c->d_cfg) cudaFree(c->d_cfg);
-    c->d_cfg = nullptr;
-    c->cfg_bytes = 0;
-    QS_CUDA(cudaMalloc(&c->d_cfg, need));
-    c->cfg_bytes = need;
-  }
-  char* p = static_cast<char*>(c->d_cfg);
-  c->d_list = reinterpret_cast<int32_t*>(p); p += a256(sizeof(int32_t) * 2 * (size_t)c->Kpad);
-  c->d_sampled = reinterpret_cast<int32_t*>(p); p += a256(sizeof(int32_t) * 2 * (size_t)c->Kpad);
-  c->d_cdfx = reinterpret_cast<double*>(p); p += a256(sizeof(double) * (cdfx.size() + 1));
-  c->d_cdfy = reinterpret_cast<double*>(p); p += a256(sizeof(double) * (cdfy.size() + 1));
-  c->d_modes = p;
-  if (c->mode == 1 && c->K > 0)
-    QS_CUDA(cudaMemcpy(c->d_list, c->half_modes.data(), sizeof(int32_t) * c->half_modes.size(),
-                       cudaMemcpyHostToDevice));
-  if (c->mode == 2) {
-    QS_CUDA(cudaMemcpy(c->d_cdfx, cdfx.data(), sizeof(double) * cdfx.size(), cudaMemcpyHostToDevice));
-    QS_CUDA(cudaMemcpy(c->d_cdfy, cdfy.data(), sizeof(double) * cdfy.size(), cudaMemcpyHostToDevice));
-  }
-  c->have_sample = false;
-  c->dirty = false;
-  return QSLAB_OK;
-}
-
-struct Plan {
-  ScanPlan sp;
-  int L0, nch0, nblk;
-  size_t off_sort, off_zs, off_dz, off_qs, off_xh, off_yh, off_perm, off_agg,
-      off_carry, off_pdec, off_part, off_k0, off_phi0, off_fz0, off_eblk,
-      off_in_pos, off_in_q, off_out_phi, off_out_f, total;
-};
-
-Plan make_plan(const qslab_ctx* c, int64_t N, bool host_io) {
-  Plan P{};
-  const bool dp = c->prec == QSLAB_FP64;
-  const size_t tsz = dp ? 8 : 4;
-  const size_t phsz = dp ? 8 : 4;
-  ScanPlan& s = P.sp;
-  s.N = N;
-  s.Kpad = c->Kpad;
-  s.KR = c->KR;
-  s.nkr = c->nkr;
+  if ((size_t)R * t.Kpad > ((size_t)1 << 31) / 64) return QSLAB_ERR_INVALID_ARG;
+  // chunk length: about two CTAs per SM over all replicas and mode ranges
   const int Lmax = dp ? 256 : 512;
   int L = c->tune_L;
   if (L <= 0) {
-    const int64_t target = (2 * 152 + s.nkr - 1) / s.nkr;
+    const int64_t target = (2 * 152 + t.nkr - 1) / t.nkr;
     int64_t want = (N + target - 1) / target;
     want = ((want + 31) / 32) * 32;
     L = (int)(want < 32 ? 32 : (want > Lmax ? Lmax : want));
   }
-  s.L = L;
-  s.nchunks = (int)((N + L - 1) / L);
+  t.L = L;
+  t.L0 = 512;
+  // chunks, k = 0 chunks and carry groups per replica
+  for (int r = 0; r < R; ++r) {
+    RepInfo& ri = t.info[r];
+    ri.c0 = (int32_t)t.chunk_rep.size();
+    ri.nch = (int32_t)((ri.n + (int64_t)L - 1) / L);
+    t.chunk_rep.insert(t.chunk_rep.end(), ri.nch, r);
+    ri.z0 = (int32_t)t.zchunk_rep.size();
+    ri.nz = (int32_t)((ri.n + (int64_t)t.L0 - 1) / t.L0);
+    t.zchunk_rep.insert(t.zchunk_rep.end(), ri.nz, r);
+    // groups: 32 groups when the chain has 64 chunks or more, else one
+    ri.g0 = (int32_t)t.group_rep.size();
+    ri.ng = 0;
+    if (ri.nch > 0) {
+      const int G = ri.nch >= 64 ? 32 : 1;
+      const int g = (ri.nch + G - 1) / G;
+      for (int a = 0; a < ri.nch; a += g) {
+        t.gstart.push_back(ri.c0 + a);
+        t.group_rep.push_back(r);
+        ++ri.ng;
+      }
+    }
+  }
+  t.nchunks = (int)t.chunk_rep.size();
+  t.nz = (int)t.zchunk_rep.size();
+  t.ngroups = (int)t.group_rep.size();
+  t.gstart.push_back(t.nchunks);
+  // device layout
+  const size_t tsz = dp ? sizeof(double) : sizeof(float);
+  size_t o = 0;
+  auto take = [&o](size_t b) { size_t r = o; o += a256(b); return r; };
+  t.o_info = take(sizeof(RepInfo) * R);
+  t.o_crep = take(sizeof(int32_t) * t.nchunks);
+  t.o_zrep = take(sizeof(int32_t) * t.nz);
+  t.o_gstart = take(sizeof(int32_t) * t.gstart.size());
+  t.o_grep = take(sizeof(int32_t) * std::max(t.ngroups, 1));
+  t.o_list = take(sizeof(int32_t) * std::max<size_t>(t.list.size(), 2));
+  t.o_cdf = take(sizeof(double) * std::max<size_t>(t.cdf.size(), 1));
+  t.o_sampled = take(sizeof(int32_t) * 2 * (size_t)R * t.Kpad);
+  t.o_modes = take(mode_bytes((size_t)R * t.Kpad, c->npc, tsz));
+  t.bytes = o;
+  t.valid = true;
+  return QSLAB_OK;
+}
+
+// Upload the host tables into a device buffer of at least t.bytes.
+int upload_tables(const Tables& t, void* dst) {
+  std::vector<char> stage(t.o_sampled, 0);
+  auto put = [&stage](size_t o, const void* src, size_t b) {
+    if (b) std::memcpy(stage.data() + o, src, b);
+  };
+  put(t.o_info, t.info.data(), sizeof(RepInfo) * t.R);
+  put(t.o_crep, t.chunk_rep.data(), sizeof(int32_t) * t.chunk_rep.size());
+  put(t.o_zrep, t.zchunk_rep.data(), sizeof(int32_t) * t.zchunk_rep.size());
+  put(t.o_gstart, t.gstart.data(), sizeof(int32_t) * t.gstart.size());
+  put(t.o_grep, t.group_rep.data(), sizeof(int32_t) * t.group_rep.size());
+  put(t.o_list, t.list.data(), sizeof(int32_t) * t.list.size());
+  put(t.o_cdf, t.cdf.data(), sizeof(double) * t.cdf.size());
+  QS_CUDA(cudaMemcpy(dst, stage.data(), stage.size(), cudaMemcpyHostToDevice));
+  return QSLAB_OK;
+}
+
+// Make c->tab describe (R, off, box), rebuilding and uploading if needed.
+int select_tables(qslab_ctx* c, int R, const int64_t* off, const double* box) {
+  int rc = ensure_config(c);
+  if (rc) return rc;
+  if (same_key(c->tab, c, R, off, box)) return QSLAB_OK;
+  Tables t;
+  rc = build_tables(c, R, off, box, t);
+  if (rc) return rc;
+  c->tab.valid = false;
+  if (t.bytes > c->tab_bytes) {
+    if (c->d_tab) {
+      cudaDeviceSynchronize();
+      cudaFree(c->d_tab);
+    }
+    c->d_tab = nullptr;
+    c->tab_bytes = 0;
+    QS_CUDA(cudaMalloc(&c->d_tab, t.bytes));
+    c->tab_bytes = t.bytes;
+  }
+  rc = upload_tables(t, c->d_tab);
+  if (rc) return rc;
+  c->tab = std::move(t);
+  c->coef_ready = false;
+  c->have_sample = false;
+  return QSLAB_OK;
+}
+
+Reps reps_view(const qslab_ctx* c) {
+  const Tables& t = c->tab;
+  const char* b = static_cast<const char*>(c->d_tab);
+  Reps rp;
+  rp.R = t.R;
+  rp.L = t.L;
+  rp.L0 = t.L0;
+  rp.nchunks = t.nchunks;
+  rp.nzchunks = t.nz;
+  rp.ngroups = t.ngroups;
+  rp.Kpad = t.Kpad;
+  rp.N = t.N;
+  rp.info = reinterpret_cast<const RepInfo*>(b + t.o_info);
+  rp.chunk_rep = reinterpret_cast<const int32_t*>(b + t.o_crep);
+  rp.zchunk_rep = reinterpret_cast<const int32_t*>(b + t.o_zrep);
+  rp.gstart = reinterpret_cast<const int32_t*>(b + t.o_gstart);
+  rp.group_rep = reinterpret_cast<const int32_t*>(b + t.o_grep);
+  return rp;
+}
+
+struct Plan {
+  ScanPlan sp;
+  size_t off_sort, off_rid, off_sums, off_zs, off_dz, off_qs, off_xh, off_yh, off_perm,
+      off_agg, off_carry, off_dec, off_part, off_k0, off_phi0, off_fz0, off_echunk, off_in_pos,
+      off_in_q, off_out_phi, off_out_f, total;
+};
+
+Plan make_plan(const qslab_ctx* c, bool host_io) {
+  Plan P{};
+  const Tables& t = c->tab;
+  const bool dp = c->prec == QSLAB_FP64;
+  const size_t tsz = dp ? 8 : 4;
+  const int64_t N = t.N;
+  ScanPlan& s = P.sp;
+  s.KR = t.KR;
+  s.nkr = t.nkr;
   s.np = c->npc;
   s.nstates = 1 + 2 * c->npc;
-  P.L0 = dp ? 512 : 1024;   // k = 0 chunks: longer chunks, a shorter carry chain
-  P.nch0 = (int)((N + P.L0 - 1) / P.L0);
-  P.nblk = (int)((N + 255) / 256);
-  if (P.nblk > 152 * 8) P.nblk = 152 * 8;
+  const Reps rp = reps_view(c);
   size_t o = 0;
   auto take = [&o](size_t b) { size_t r = o; o += a256(b); return r; };
   P.off_sort = take(sort_workspace_bytes(N, dp ? 8 : 4));
+  P.off_rid = take(t.R > 1 ? 4 * (size_t)N : 0);
+  P.off_sums = take(16 * (size_t)t.R);
   P.off_zs = take(tsz * N);
   P.off_dz = take(tsz * N);
   P.off_qs = take(tsz * N);
-  P.off_xh = take(phsz * N);
-  P.off_yh = take(phsz * N);
+  P.off_xh = take(tsz * N);
+  P.off_yh = take(tsz * N);
   P.off_perm = take(4 * (size_t)N);
-  const size_t aggn = (size_t)2 * s.nchunks * s.nstates * s.Kpad;
+  const size_t aggn = (size_t)2 * t.nchunks * s.nstates * t.Kpad;
   P.off_agg = take(2 * tsz * aggn);
   P.off_carry = take(2 * tsz * aggn);
-  P.off_pdec = take(kspace_decay_bytes(s, dp ? 1 : 0));
+  P.off_dec = take(kspace_decay_bytes(s, rp, dp ? 1 : 0));
   P.off_part = take(tsz * 4 * (size_t)s.nkr * N);
-  P.off_k0 = take(8 * kzero_work_doubles(P.nch0, c->pairs.np));
+  P.off_k0 = take(8 * kzero_work_doubles(t.nz, t.R, c->pairs.np));
   P.off_phi0 = take(8 * (size_t)N);
   P.off_fz0 = take(8 * (size_t)N);
-  P.off_eblk = take(8 * (size_t)P.nblk);
+  P.off_echunk = take(8 * (size_t)t.nchunks);
   if (host_io) {
     P.off_in_pos = take(3 * tsz * N);
     P.off_in_q = take(tsz * N);
@@ -356,13 +546,19 @@ int ensure_ws(qslab_ctx* c, size_t bytes) {
 }
 
 template <typename T>
-int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energy,
-        T* phi, T* force, cudaStream_t st) {
+int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies, T* phi,
+        T* force, cudaStream_t st) {
   using PH = typename PhaseT<T>::type;
-  const int64_t N = P.sp.N;
+  const Tables& tb = c->tab;
+  const int64_t N = tb.N;
+  const int R = tb.R;
+  const Reps rp = reps_view(c);
   char* ws = static_cast<char*>(c->d_ws);
+  char* tab = static_cast<char*>(c->d_tab);
   SortWork sw;
   sort_bind_workspace(sw, ws + P.off_sort, N, sizeof(T));
+  int32_t* rid = reinterpret_cast<int32_t*>(ws + P.off_rid);
+  double* sums = reinterpret_cast<double*>(ws + P.off_sums);
   T* zs = reinterpret_cast<T*>(ws + P.off_zs);
   T* dz = reinterpret_cast<T*>(ws + P.off_dz);
   T* qs = reinterpret_cast<T*>(ws + P.off_qs);
@@ -371,73 +567,66 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energy,
   int32_t* perm = reinterpret_cast<int32_t*>(ws + P.off_perm);
   Cplx<T>* agg = reinterpret_cast<Cplx<T>*>(ws + P.off_agg);
   Cplx<T>* carry = reinterpret_cast<Cplx<T>*>(ws + P.off_carry);
-  void* pdec = ws + P.off_pdec;
+  void* dec = ws + P.off_dec;
   T* part = reinterpret_cast<T*>(ws + P.off_part);
   double* k0w = reinterpret_cast<double*>(ws + P.off_k0);
   double* phi0 = reinterpret_cast<double*>(ws + P.off_phi0);
   double* fz0 = reinterpret_cast<double*>(ws + P.off_fz0);
-  double* eblk = reinterpret_cast<double*>(ws + P.off_eblk);
-  ModeTab<T> modes = mode_views<T>(c->d_modes, c->Kpad, c->npc);
+  double* echunk = reinterpret_cast<double*>(ws + P.off_echunk);
+  ModeTab<T> modes = mode_views<T>(tab + tb.o_modes, (size_t)R * tb.Kpad, c->npc);
+  const bool rbe = c->mode == 2;
 
   cudaEvent_t* ev = c->timing ? c->ev : nullptr;
   int nl = 0;
   if (ev) cudaEventRecord(ev[0], st);
-  QS_CUDA(cudaMemsetAsync(c->d_sums, 0, 2 * sizeof(double), st));
-  launch_prepare<T>(N, pos, q, c->Lz, sw.keys[0], sw.vals[0], c->d_sums, c->d_status, st);
+  QS_CUDA(cudaMemsetAsync(sums, 0, 16 * (size_t)R, st));
+  launch_prepare<T>(rp, pos, q, sw.keys[0], sw.vals[0], R > 1 ? rid : nullptr, sums,
+                    c->d_status, st);
   double tol = c->neutral_tol;
   if (tol < -1.0) tol = 64.0 * (sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
-  launch_check_neutral(c->d_sums, tol, c->d_status, st);
-  const int r = radix_sort(sw, N, (int)sizeof(T), st);
-  launch_gather<T>(N, pos, q, sw.vals[r], c->Lx, c->Ly, zs, dz, qs, xh, yh, perm, st);
-  nl += 3 + 3 * (int)sizeof(T);   // prepare, check, gather + 3 kernels per sort pass
+  launch_check_neutral(rp, sums, tol, c->d_status, rbe ? c->d_ctr : nullptr, st);
+  int r = radix_sort(sw, N, (int)sizeof(T), (int)sizeof(T), 0, st);
+  nl += 2 + 3 * (int)sizeof(T);   // prepare, check + 3 kernels per sort pass
+  if (R > 1) {
+    // stable second sort on the replica index: replicas contiguous, z-ordered within
+    launch_rep_keys(N, sw.vals[r], rid, static_cast<uint32_t*>(sw.keys[r]), st);
+    const int passes = R <= 256 ? 1 : (R <= 65536 ? 2 : 3);
+    r = radix_sort(sw, N, 4, passes, r, st);
+    nl += 1 + 3 * passes;
+  }
+  launch_gather<T>(rp, pos, q, sw.vals[r], zs, dz, qs, xh, yh, perm, st);
+  ++nl;
   if (ev) cudaEventRecord(ev[1], st);
   // k = 0 term on the side stream, concurrent with the k-space kernels
   QS_CUDA(cudaEventRecord(c->fork, st));
   QS_CUDA(cudaStreamWaitEvent(c->side, c->fork, 0));
-  launch_kzero<T>(N, P.L0, P.nch0, c->pairs, c->alpha, c->Lx * c->Ly, zs, dz, qs, k0w,
-                  phi0, fz0, c->side);
+  launch_kzero<T>(rp, c->pairs, c->alpha, zs, dz, qs, k0w, phi0, fz0, c->side);
   nl += 4;
   if (ev) cudaEventRecord(ev[8], c->side);
   QS_CUDA(cudaEventRecord(c->join, c->side));
-  // mode table: once per configuration for the full k-sum, every call for RBE
-  if (c->mode == 2 || !c->coef_ready) {
-    SamplerTab sp{c->d_cdfx, c->d_cdfy, c->cdf_nx, c->cdf_ny, c->mxmax, c->mymax};
-    launch_mode_coef<T>(c->K, c->Kpad, c->npc, c->d_list, c->mode == 2 ? 1 : 0,
-                        c->seed, c->counter, sp, c->pairs, c->alpha, c->Lx, c->Ly,
-                        c->H, modes, c->mode == 2 ? c->d_sampled : nullptr, st);
+  // mode tables: once per configuration for the full k-sum, every call for RBE
+  if (rbe || !c->coef_ready) {
+    launch_mode_coef<T>(rp, c->npc, reinterpret_cast<const int32_t*>(tab + tb.o_list), rbe ? 1 : 0,
+                        c->seed, c->d_ctr, reinterpret_cast<const double*>(tab + tb.o_cdf),
+                        c->pairs, c->alpha, modes,
+                        rbe ? reinterpret_cast<int32_t*>(tab + tb.o_sampled) : nullptr, st);
     ++nl;
-    if (c->mode == 2) {
-      ++c->counter;
-      c->have_sample = true;
-    } else {
-      c->coef_ready = true;
-    }
+    if (rbe) c->have_sample = true;
+    else c->coef_ready = true;
   }
   if (ev) cudaEventRecord(ev[2], st);
-  launch_kspace<T>(P.sp, modes, c->pairs, zs, dz, qs, xh, yh, agg, carry, pdec, part, st,
+  launch_kspace<T>(P.sp, rp, modes, c->pairs, zs, dz, qs, xh, yh, agg, carry, dec, part, st,
                    ev ? ev + 3 : nullptr);
   nl += 7;
   QS_CUDA(cudaStreamWaitEvent(st, c->join, 0));
   if (ev) cudaEventRecord(ev[6], st);
-  const double D0 = -(kPi / (c->Lx * c->Ly)) / (c->alpha * kSqrtPi);
-  const double diagq = 2.0 * c->diag_k + 2.0 * D0 - 2.0 * c->alpha / kSqrtPi;
-  launch_combine<T>(N, P.sp.nkr, part, phi0, fz0, qs, perm, diagq, eblk, P.nblk, phi,
-                    force, energy, st);
-  nl += energy ? 2 : 1;
+  launch_combine<T>(rp, P.sp.nkr, part, phi0, fz0, qs, perm, echunk, phi, force, energies, st);
+  nl += energies ? 2 : 1;
   if (ev) cudaEventRecord(ev[7], st);
   c->launches = nl;
+  c->last_R = R;
   QS_CUDA(cudaGetLastError());
   c->last_stream = st;
-  return QSLAB_OK;
-}
-
-int check_common(qslab_ctx* c, int64_t N) {
-  if (!c) return QSLAB_ERR_INVALID_ARG;
-  if (N < 1 || N > 2147483647LL) return QSLAB_ERR_INVALID_ARG;
-  if (c->dirty) {
-    const int rc = rebuild(c);
-    if (rc) return rc;
-  }
   return QSLAB_OK;
 }
 
@@ -447,6 +636,25 @@ int status_code(unsigned f) {
   if (f & kStNonneutral) return QSLAB_ERR_NONNEUTRAL;
   if (f & kStTimeout) return QSLAB_ERR_TIMEOUT;
   return QSLAB_OK;
+}
+
+// Tables and workspace for one call; on success P describes the workspace.
+int setup_call(qslab_ctx* c, int R, const int64_t* off, const double* box, bool host_io,
+               Plan& P) {
+  QS_CUDA(cudaSetDevice(c->device));
+  int rc = select_tables(c, R, off, box);
+  if (rc) return rc;
+  P = make_plan(c, host_io);
+  return ensure_ws(c, P.total);
+}
+
+int dispatch(qslab_ctx* c, const Plan& P, const void* pos, const void* q, double* energies,
+             void* phi, void* force, cudaStream_t st) {
+  if (c->prec == QSLAB_FP64)
+    return run<double>(c, P, static_cast<const double*>(pos), static_cast<const double*>(q),
+                       energies, static_cast<double*>(phi), static_cast<double*>(force), st);
+  return run<float>(c, P, static_cast<const float*>(pos), static_cast<const float*>(q), energies,
+                    static_cast<float*>(phi), static_cast<float*>(force), st);
 }
 
 }  // namespace
@@ -472,9 +680,13 @@ int qslab_create(qslab_ctx** out, int cuda_device, int prec) {
     return cuda_fail(e);
   }
   c->d_status = static_cast<unsigned*>(small);
-  c->d_sums = reinterpret_cast<double*>(static_cast<char*>(small) + 64);
   c->d_energy = reinterpret_cast<double*>(static_cast<char*>(small) + 128);
-  cudaMemset(small, 0, 256);
+  c->d_ctr = reinterpret_cast<uint64_t*>(static_cast<char*>(small) + 192);
+  if (cudaMemset(small, 0, 256) != cudaSuccess) {
+    cudaFree(small);
+    delete c;
+    return QSLAB_ERR_CUDA;
+  }
   for (auto& ev : c->ev) cudaEventCreate(&ev);
   if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -491,7 +703,7 @@ void qslab_destroy(qslab_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   if (c->d_ws) cudaFree(c->d_ws);
-  if (c->d_cfg) cudaFree(c->d_cfg);
+  if (c->d_tab) cudaFree(c->d_tab);
   if (c->d_status) cudaFree(c->d_status);
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
@@ -505,7 +717,6 @@ int qslab_set_box(qslab_ctx* c, double Lx, double Ly, double Lz) {
   if (!c || !finite_pos(Lx) || !finite_pos(Ly) || !finite_pos(Lz)) return QSLAB_ERR_INVALID_ARG;
   c->Lx = Lx; c->Ly = Ly; c->Lz = Lz;
   c->has_box = true;
-  c->dirty = true;
   return QSLAB_OK;
 }
 
@@ -513,7 +724,7 @@ int qslab_set_alpha(qslab_ctx* c, double alpha) {
   if (!c || !finite_pos(alpha)) return QSLAB_ERR_INVALID_ARG;
   c->alpha = alpha;
   c->has_alpha = true;
-  c->dirty = true;
+  c->cfg_dirty = true;
   return QSLAB_OK;
 }
 
@@ -521,17 +732,19 @@ int qslab_set_kcut(qslab_ctx* c, double kc) {
   if (!c || !finite_pos(kc)) return QSLAB_ERR_INVALID_ARG;
   c->kc = kc;
   c->mode = 1;
-  c->dirty = true;
+  c->cfg_dirty = true;
   return QSLAB_OK;
 }
 
 int qslab_set_rbe(qslab_ctx* c, int P, uint64_t seed) {
   if (!c || P < 1 || P > 65536) return QSLAB_ERR_INVALID_ARG;
+  QS_CUDA(cudaSetDevice(c->device));
+  const uint64_t zero[2] = {0, 0};
+  QS_CUDA(cudaMemcpy(c->d_ctr, zero, sizeof(zero), cudaMemcpyHostToDevice));
   c->P = P;
   c->seed = seed;
-  c->counter = 0;
   c->mode = 2;
-  c->dirty = true;
+  c->cfg_dirty = true;
   return QSLAB_OK;
 }
 
@@ -554,7 +767,7 @@ int qslab_set_soe(qslab_ctx* c, int M, const double* s_re, const double* s_im,
   c->s_re = trial.s_re; c->s_im = trial.s_im;
   c->w_re = trial.w_re; c->w_im = trial.w_im;
   c->has_soe = true;
-  c->dirty = true;
+  c->cfg_dirty = true;
   return QSLAB_OK;
 }
 
@@ -570,36 +783,41 @@ int qslab_set_tuning(qslab_ctx* c, int chunk, int modes_per_cta) {
   if (chunk > Lmax || (modes_per_cta > 0 && (modes_per_cta % 32 || modes_per_cta > 256)))
     return QSLAB_ERR_INVALID_ARG;
   c->tune_L = chunk;
-  if (c->tune_KR != modes_per_cta) c->dirty = true;
   c->tune_KR = modes_per_cta;
   return QSLAB_OK;
 }
 
 int qslab_compute(qslab_ctx* c, int64_t N, const void* pos, const void* q,
                   double* energy, void* phi, void* force, void* stream) {
-  int rc = check_common(c, N);
+  if (!c || !pos || !q || N < 1 || N > 2147483647LL) return QSLAB_ERR_INVALID_ARG;
+  if (!c->has_box) return QSLAB_ERR_NOT_CONFIGURED;
+  const int64_t off[2] = {0, N};
+  const double box[3] = {c->Lx, c->Ly, c->Lz};
+  Plan P;
+  const int rc = setup_call(c, 1, off, box, false, P);
   if (rc) return rc;
-  if (!pos || !q) return QSLAB_ERR_INVALID_ARG;
-  QS_CUDA(cudaSetDevice(c->device));
-  const Plan P = make_plan(c, N, false);
-  rc = ensure_ws(c, P.total);
+  return dispatch(c, P, pos, q, energy, phi, force, static_cast<cudaStream_t>(stream));
+}
+
+int qslab_compute_batched(qslab_ctx* c, int R, const int64_t* offsets, const double* boxes,
+                          const void* pos, const void* q, double* energies, void* phi,
+                          void* force, void* stream) {
+  if (!c || !pos || !q || !offsets || !boxes || R < 1 || R > kMaxReplicas)
+    return QSLAB_ERR_INVALID_ARG;
+  Plan P;
+  const int rc = setup_call(c, R, offsets, boxes, false, P);
   if (rc) return rc;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (c->prec == QSLAB_FP64)
-    return run<double>(c, P, static_cast<const double*>(pos), static_cast<const double*>(q),
-                       energy, static_cast<double*>(phi), static_cast<double*>(force), st);
-  return run<float>(c, P, static_cast<const float*>(pos), static_cast<const float*>(q), energy,
-                    static_cast<float*>(phi), static_cast<float*>(force), st);
+  return dispatch(c, P, pos, q, energies, phi, force, static_cast<cudaStream_t>(stream));
 }
 
 int qslab_compute_host(qslab_ctx* c, int64_t N, const void* pos_host, const void* q_host,
                        double* energy_host, void* phi_host, void* force_host, void* stream) {
-  int rc = check_common(c, N);
-  if (rc) return rc;
-  if (!pos_host || !q_host) return QSLAB_ERR_INVALID_ARG;
-  QS_CUDA(cudaSetDevice(c->device));
-  const Plan P = make_plan(c, N, true);
-  rc = ensure_ws(c, P.total);
+  if (!c || !pos_host || !q_host || N < 1 || N > 2147483647LL) return QSLAB_ERR_INVALID_ARG;
+  if (!c->has_box) return QSLAB_ERR_NOT_CONFIGURED;
+  const int64_t off[2] = {0, N};
+  const double box[3] = {c->Lx, c->Ly, c->Lz};
+  Plan P;
+  int rc = setup_call(c, 1, off, box, true, P);
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t tsz = c->prec == QSLAB_FP64 ? 8 : 4;
@@ -610,12 +828,7 @@ int qslab_compute_host(qslab_ctx* c, int64_t N, const void* pos_host, const void
   void* df = force_host ? ws + P.off_out_f : nullptr;
   QS_CUDA(cudaMemcpyAsync(dpos, pos_host, 3 * tsz * N, cudaMemcpyHostToDevice, st));
   QS_CUDA(cudaMemcpyAsync(dq, q_host, tsz * N, cudaMemcpyHostToDevice, st));
-  if (c->prec == QSLAB_FP64)
-    rc = run<double>(c, P, static_cast<const double*>(dpos), static_cast<const double*>(dq),
-                     c->d_energy, static_cast<double*>(dphi), static_cast<double*>(df), st);
-  else
-    rc = run<float>(c, P, static_cast<const float*>(dpos), static_cast<const float*>(dq),
-                    c->d_energy, static_cast<float*>(dphi), static_cast<float*>(df), st);
+  rc = dispatch(c, P, dpos, dq, c->d_energy, dphi, df, st);
   if (rc) return rc;
   if (energy_host)
     QS_CUDA(cudaMemcpyAsync(energy_host, c->d_energy, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -626,35 +839,40 @@ int qslab_compute_host(qslab_ctx* c, int64_t N, const void* pos_host, const void
 
 int qslab_get_sampled_modes(qslab_ctx* c, int32_t* mxy, double* weight) {
   if (!c || !mxy) return QSLAB_ERR_INVALID_ARG;
-  if (c->mode != 2 || !c->have_sample) return QSLAB_ERR_NOT_CONFIGURED;
+  if (c->mode != 2 || !c->have_sample || !c->tab.valid) return QSLAB_ERR_NOT_CONFIGURED;
   QS_CUDA(cudaSetDevice(c->device));
   QS_CUDA(cudaStreamSynchronize(c->last_stream));
-  QS_CUDA(cudaMemcpy(mxy, c->d_sampled, sizeof(int32_t) * 2 * (size_t)c->P, cudaMemcpyDeviceToHost));
-  if (weight) *weight = c->H / c->P;
+  const Tables& t = c->tab;
+  QS_CUDA(cudaMemcpy(mxy, static_cast<char*>(c->d_tab) + t.o_sampled,
+                     sizeof(int32_t) * 2 * (size_t)t.R * c->P, cudaMemcpyDeviceToHost));
+  if (weight)
+    for (int r = 0; r < t.R; ++r) weight[r] = t.info[r].H / c->P;
   return QSLAB_OK;
 }
 
 int qslab_get_rng_state(qslab_ctx* c, uint64_t* seed, uint64_t* counter) {
   if (!c || !seed || !counter) return QSLAB_ERR_INVALID_ARG;
+  QS_CUDA(cudaSetDevice(c->device));
+  QS_CUDA(cudaStreamSynchronize(c->last_stream));
+  QS_CUDA(cudaMemcpy(counter, c->d_ctr, sizeof(uint64_t), cudaMemcpyDeviceToHost));
   *seed = c->seed;
-  *counter = c->counter;
   return QSLAB_OK;
 }
 
 int qslab_set_rng_state(qslab_ctx* c, uint64_t seed, uint64_t counter) {
   if (!c) return QSLAB_ERR_INVALID_ARG;
+  QS_CUDA(cudaSetDevice(c->device));
+  QS_CUDA(cudaStreamSynchronize(c->last_stream));
+  QS_CUDA(cudaMemcpy(c->d_ctr, &counter, sizeof(uint64_t), cudaMemcpyHostToDevice));
   c->seed = seed;
-  c->counter = counter;
   return QSLAB_OK;
 }
 
 int qslab_num_modes(qslab_ctx* c) {
   if (!c) return QSLAB_ERR_INVALID_ARG;
-  if (c->dirty) {
-    const int rc = rebuild(c);
-    if (rc) return rc;
-  }
-  return c->K;
+  if (!c->has_box || !c->has_alpha || !c->has_soe || c->mode == 0) return QSLAB_ERR_NOT_CONFIGURED;
+  if (c->mode == 2) return c->P;
+  return (int)(half_plane(c->Lx, c->Ly, c->kc).size() / 2);
 }
 
 int qslab_last_status(qslab_ctx* c) {
@@ -729,7 +947,7 @@ namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;   // 64 MiB per GPU
 constexpr size_t kStaticCfgBytes = size_t(8) << 20;        // tables and status
-constexpr size_t kStaticSmallBytes = 256;                  // status, sums, energy
+constexpr size_t kStaticSmallBytes = 256;                  // status word
 constexpr int kStaticMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -757,63 +975,45 @@ extern "C" int qslab_compute_static(qslab_ctx* c, int64_t N, const void* pos, co
                                     double* energy, void* phi, void* force, void* stream) {
   if (!c) return QSLAB_ERR_INVALID_ARG;
   if (N < 1 || N > 2147483647LL || !pos || !q) return QSLAB_ERR_INVALID_ARG;
-  if (!c->has_box || !c->has_alpha || !c->has_soe || c->mode == 0) return QSLAB_ERR_NOT_CONFIGURED;
+  if (!c->has_box) return QSLAB_ERR_NOT_CONFIGURED;
+  int rc = ensure_config(c);
+  if (rc) return rc;
   QS_CUDA(cudaSetDevice(c->device));
   void* base = nullptr;
-  int rc = static_scratch_address(c->device, &base);
+  rc = static_scratch_address(c->device, &base);
   if (rc) return rc;
   char* sb = static_cast<char*>(base);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
 
   // A copy of the context whose device buffers all point into the static
-  // array; its configuration tables are rebuilt there on every call (the
-  // real context's own buffers are neither used nor changed).
+  // array (the random-batch counter word excepted: it stays the context's);
+  // its tables are rebuilt there on every call (the real context's own
+  // buffers are neither used nor changed).
   qslab_ctx t = *c;
   t.timing = false;
   t.d_status = reinterpret_cast<unsigned*>(sb);
-  t.d_sums = reinterpret_cast<double*>(sb + 64);
-  t.d_energy = reinterpret_cast<double*>(sb + 128);
-  t.d_cfg = sb + kStaticSmallBytes;
-  t.cfg_bytes = kStaticCfgBytes - kStaticSmallBytes;
+  t.d_tab = sb + kStaticSmallBytes;
+  t.tab_bytes = kStaticCfgBytes - kStaticSmallBytes;
   t.d_ws = sb + kStaticCfgBytes;
   t.ws_bytes = kStaticScratchBytes - kStaticCfgBytes;
   // size checks before anything touches the device: the tables must fit the
   // table region and the workspace the rest of the array
-  {
-    const size_t tsz = c->prec == QSLAB_FP64 ? sizeof(double) : sizeof(float);
-    qslab_ctx probe = *c;
-    if (build_pairs(&probe) != QSLAB_OK) return QSLAB_ERR_INVALID_ARG;
-    size_t K = 0, cdf = 0;
-    if (c->mode == 1) {
-      K = half_plane(c->Lx, c->Ly, c->kc).size() / 2;
-    } else {
-      K = (size_t)c->P;
-      const double mx = std::floor(6.4380 * c->alpha * c->Lx / kPi) + 1;
-      const double my = std::floor(6.4380 * c->alpha * c->Ly / kPi) + 1;
-      cdf = (size_t)(2 * mx + 1) + (size_t)(2 * my + 1);
-      if (mx > 1e6 || my > 1e6) return QSLAB_ERR_TOO_LARGE;
-    }
-    const size_t kpad = ((std::max<size_t>(K, 1) + 255) / 256) * 256;
-    const size_t need = a256(sizeof(int32_t) * 2 * kpad) * 2 + a256(sizeof(double) * (cdf + 2)) * 2 +
-                        mode_bytes((int)kpad, probe.npc, tsz);
-    if (need > t.cfg_bytes || kpad > (size_t)1 << 20) return QSLAB_ERR_TOO_LARGE;
-  }
-  t.dirty = true;
-  rc = rebuild(&t);          // fits: no allocation, tables uploaded into the array
+  const int64_t off[2] = {0, N};
+  const double box[3] = {c->Lx, c->Ly, c->Lz};
+  if (c->mode == 2 && (axis_mmax(c->alpha, c->Lx) > 1000000 || axis_mmax(c->alpha, c->Ly) > 1000000))
+    return QSLAB_ERR_TOO_LARGE;
+  rc = build_tables(&t, 1, off, box, t.tab);
   if (rc) return rc;
-  const Plan P = make_plan(&t, N, false);
+  if (t.tab.bytes > t.tab_bytes) return QSLAB_ERR_TOO_LARGE;
+  const Plan P = make_plan(&t, false);
   if (P.total > t.ws_bytes) return QSLAB_ERR_TOO_LARGE;
-  // the status word and sums start from zero on every call
-  QS_CUDA(cudaMemsetAsync(t.d_status, 0, kStaticSmallBytes, st));
-  if (c->prec == QSLAB_FP64)
-    rc = run<double>(&t, P, static_cast<const double*>(pos), static_cast<const double*>(q),
-                     energy, static_cast<double*>(phi), static_cast<double*>(force), st);
-  else
-    rc = run<float>(&t, P, static_cast<const float*>(pos), static_cast<const float*>(q), energy,
-                    static_cast<float*>(phi), static_cast<float*>(force), st);
+  rc = upload_tables(t.tab, t.d_tab);   // fits: no allocation
   if (rc) return rc;
-  // the random-batch counter advances as in qslab_compute()
-  c->counter = t.counter;
+  t.coef_ready = false;
+  // the status word starts from zero on every call
+  QS_CUDA(cudaMemsetAsync(t.d_status, 0, kStaticSmallBytes, st));
+  rc = dispatch(&t, P, pos, q, energy, phi, force, st);
+  if (rc) return rc;
   QS_CUDA(cudaStreamSynchronize(st));
   QS_CUDA(cudaGetLastError());
   unsigned f = 0;

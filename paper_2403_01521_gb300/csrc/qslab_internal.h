@@ -1,15 +1,25 @@
 // Internal declarations shared by the qslab CUDA translation units.
 //
-// Data layout in HBM (all arrays indexed by the z-sorted particle index i):
-//   zs[i], dz[i] = zs[i] - zs[i-1] (dz[0] = 0), qs[i]          type T
-//   xh[i], yh[i]  fixed-point fractions x/Lx, y/Ly              uint32 (FP32C)
-//                 (2^32 or 2^64 units of a turn)                uint64 (FP64)
+// A call processes R independent slabs ("replicas"; R = 1 for
+// qslab_compute). Replica r owns the particles [off_r, off_r + n_r) of the
+// caller's arrays; after sorting it owns the same index range, ordered by z.
+//
+// Data layout in HBM (all arrays indexed by the sorted particle index i):
+//   zs[i], qs[i]
+//   dz[i] = zs[i] - zs[i-1] within a replica, 0 at a replica's first
+//           particle                                            type T
+//   xh[i], yh[i]  fixed-point fractions x/Lx, y/Ly of the replica's box
+//                 (2^32 or 2^64 units of a turn)                uint32 (FP32C)
+//                                                               uint64 (FP64)
 //   perm[i]       original index of sorted particle i           int32
-// Mode tables (one entry per k vector, padded to a multiple of 32 with
-// zero-weight modes) are structure-of-arrays, see ModeTab.
-// Chunk aggregates and carries: [dir][chunk][state][mode] complex, with
+// Each replica is cut into k-space chunks of L particles and k = 0 chunks of
+// L0 particles (the last one of a replica may be shorter); no chunk spans
+// two replicas. Chunks are numbered globally, replica by replica.
+// Mode tables are structure-of-arrays with R * Kpad entries: replica r owns
+// [r * Kpad, (r + 1) * Kpad), padded with zero-weight modes; see ModeTab.
+// Chunk aggregates and carries: [dir][chunk][state][Kpad] complex, with
 // state 0 = beta = k and states 1+2p, 2+2p = SOE pair p driven by the real
-// inputs q cos(k.rho) and q sin(k.rho).
+// inputs q cos(k.rho) and q sin(k.rho); the mode index is replica-local.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -26,8 +36,8 @@ template <typename T> struct PhaseT;
 template <> struct PhaseT<float>  { using type = uint32_t; };
 template <> struct PhaseT<double> { using type = uint64_t; };
 
-// Structure-of-arrays mode table (device pointers). For the SOE pair
-// representative p of a mode:
+// Structure-of-arrays mode table (device pointers), R * Kpad entries. For
+// the SOE pair representative p of a mode:
 //   cp   = m_p gam_k c_{k,p},          c_{k,p} = -2 k w_p / (a_p^2 - k^2)
 //   cbp  = m_p gam_k c_{k,p} a_p
 // for beta = k:
@@ -48,10 +58,10 @@ struct ModeTab {
   T* ckk;
   T* sY;
   T* sZ;
-  T* cp;      // [4][NP][Kpad]: cp.re, cp.im, cbp.re, cbp.im
+  T* cp;      // [4][NP][R * Kpad]: cp.re, cp.im, cbp.re, cbp.im
 };
 
-// SOE pair representatives, shared by all modes (constant over a call).
+// SOE pair representatives, shared by all modes and replicas.
 struct PairTab {
   int np;                 // number of representatives (padded entries have w = 0)
   double a_re[kMaxPairs]; // a_p = alpha s_p
@@ -63,6 +73,35 @@ struct PairTab {
   double mult[kMaxPairs]; // 2 (complex pair) or 1 (real node) or 0 (padding)
 };
 
+// One replica of a call (device array of R).
+struct RepInfo {
+  int64_t off;            // first particle
+  int32_t n;              // particles (may be 0)
+  int32_t c0, nch;        // k-space chunks [c0, c0 + nch)
+  int32_t z0, nz;         // k = 0 chunks [z0, z0 + nz)
+  int32_t g0, ng;         // carry groups [g0, g0 + ng)
+  int32_t K;              // modes (half-plane list length, or P)
+  int32_t list0;          // offset (in modes) into the concatenated full-k lists
+  int32_t cdfx0, nx;      // sampler tables: offsets into the concatenated
+  int32_t cdfy0, ny;      //   cumulative tables and their lengths
+  int32_t mxmax, mymax;
+  double Lx, Ly, Lz, area, H, diagq;
+};
+
+// Geometry of a call, passed to kernels by value.
+struct Reps {
+  int R;
+  int L, L0;              // particles per k-space / k = 0 chunk
+  int nchunks, nzchunks, ngroups;
+  int Kpad;               // modes per replica (multiple of 32)
+  int64_t N;              // particles in all replicas
+  const RepInfo* info;        // [R]
+  const int32_t* chunk_rep;   // [nchunks]
+  const int32_t* zchunk_rep;  // [nzchunks]
+  const int32_t* gstart;      // [ngroups + 1] first k-space chunk of each carry group
+  const int32_t* group_rep;   // [ngroups]
+};
+
 // Status flags set by kernels (bitwise OR into a device word).
 enum StatusBits : unsigned {
   kStNonfinite = 1u,
@@ -71,10 +110,9 @@ enum StatusBits : unsigned {
   kStTimeout = 8u,
 };
 
-// Launch wrappers implemented in the .cu files. All take the caller's stream.
 // ---- sort (qslab_sort.cu)
 struct SortWork {
-  void* keys[2];          // uint32 or uint64 keys, ping-pong
+  void* keys[2];          // keys, ping-pong (room for N keys of key_bytes)
   uint32_t* vals[2];      // payload (original index), ping-pong
   uint32_t* counts;       // [256][nblocks]
   uint32_t* totals;       // [passes][256] digit totals
@@ -82,74 +120,70 @@ struct SortWork {
 };
 size_t sort_workspace_bytes(int64_t N, int key_bytes);
 void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes);
-// Sorts keys[0]/vals[0]; returns the index (0 or 1) of the buffer holding the result.
-int radix_sort(SortWork& w, int64_t N, int key_bytes, cudaStream_t st);
+// Stable sort of keys[src]/vals[src] (keys of key_bytes = 4 or 8) on their
+// low `passes` bytes; returns the index (0 or 1) of the buffer holding the
+// result.
+int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaStream_t st);
 
 // ---- kernels (qslab_kernels.cu)
+// Input checks and z keys, one CTA per k-space chunk; per-replica sums of q
+// and |q| (sums[2r], sums[2r+1]); rid (may be NULL) receives the replica of
+// every particle.
 template <typename T>
-void launch_prepare(int64_t N, const T* pos, const T* q, double Lz, void* keys,
-                    uint32_t* vals, double* sums, unsigned* status,
-                    cudaStream_t st);
+void launch_prepare(const Reps& rp, const T* pos, const T* q, void* keys, uint32_t* vals,
+                    int32_t* rid, double* sums, unsigned* status, cudaStream_t st);
+// Per-replica neutrality check; when ctr is not NULL also advances the
+// random-batch counter: ctr[1] = ctr[0]++ (the counter this call uses).
+void launch_check_neutral(const Reps& rp, const double* sums, double tol, unsigned* status,
+                          uint64_t* ctr, cudaStream_t st);
+// Second sort key: keys[i] = rid[perm[i]].
+void launch_rep_keys(int64_t N, const uint32_t* perm, const int32_t* rid, uint32_t* keys,
+                     cudaStream_t st);
 template <typename T>
-void launch_gather(int64_t N, const T* pos, const T* q, const uint32_t* perm,
-                   double Lx, double Ly, T* zs, T* dz, T* qs,
-                   typename PhaseT<T>::type* xh, typename PhaseT<T>::type* yh,
-                   int32_t* perm_out, cudaStream_t st);
-void launch_check_neutral(const double* sums, double tol, unsigned* status,
-                          cudaStream_t st);
+void launch_gather(const Reps& rp, const T* pos, const T* q, const uint32_t* perm, T* zs,
+                   T* dz, T* qs, typename PhaseT<T>::type* xh,
+                   typename PhaseT<T>::type* yh, int32_t* perm_out, cudaStream_t st);
 
 struct ScanPlan {
-  int64_t N;
-  int L;            // particles per chunk
-  int nchunks;
-  int Kpad;         // modes, multiple of 32
   int KR;           // modes per CTA (threads), multiple of 32
-  int nkr;          // number of mode ranges
+  int nkr;          // number of mode ranges (KR * nkr = Kpad)
   int np;           // pair representatives compiled for (4, 8, 12, 16)
   int nstates;      // 1 + 2 np
 };
 
 template <typename T>
-void launch_kspace(const ScanPlan& plan, const ModeTab<T>& modes,
+void launch_kspace(const ScanPlan& plan, const Reps& rp, const ModeTab<T>& modes,
                    const PairTab& pairs, const T* zs, const T* dz, const T* qs,
                    const typename PhaseT<T>::type* xh,
                    const typename PhaseT<T>::type* yh, Cplx<T>* agg,
                    Cplx<T>* carry, void* dec, T* part,
                    cudaStream_t st, cudaEvent_t* ev3);  // ev3: 3 events or NULL
-// bytes of the chunk-to-chunk decay tables (pair and mode decays)
-size_t kspace_decay_bytes(const ScanPlan& pl, int fp64);
+// bytes of the chunk-to-chunk decay tables and carry-group transfers
+size_t kspace_decay_bytes(const ScanPlan& pl, const Reps& rp, int fp64);
 
 // phi0 / fz0: per sorted particle, in the carry type (FP64 on the FP64 path,
 // double-float on the FP32 path)
 template <typename T>
-void launch_kzero(int64_t N, int L0, int nchunks0, const PairTab& pairs,
-                  double alpha, double area, const T* zs, const T* dz,
-                  const T* qs, double* work, void* phi0, void* fz0,
+void launch_kzero(const Reps& rp, const PairTab& pairs, double alpha, const T* zs,
+                  const T* dz, const T* qs, double* work, void* phi0, void* fz0,
                   cudaStream_t st);
+size_t kzero_work_doubles(int nzchunks, int R, int np);
 
+// Potential, forces and per-chunk energies (echunk[nchunks]) back in the
+// caller's order; energies[r] (if not NULL) = the sum over replica r's chunks.
 template <typename T>
-void launch_combine(int64_t N, int nkr, const T* part, const void* phi0,
-                    const void* fz0, const T* qs, const int32_t* perm,
-                    double diagq, double* eblock, int nblk, T* phi_out,
-                    T* force_out, double* energy, cudaStream_t st);
+void launch_combine(const Reps& rp, int nkr, const T* part, const void* phi0,
+                    const void* fz0, const T* qs, const int32_t* perm, double* echunk,
+                    T* phi_out, T* force_out, double* energies, cudaStream_t st);
 
-// Mode table fill. rbe = 0: modes from `list` (host half-plane list, 2K
-// int32). rbe = 1: K = P modes drawn on the device; if `sampled` is not NULL
-// the drawn (mx, my) are stored there. npc = pair count the table is laid out
-// for (compiled NP).
-struct SamplerTab {
-  const double* cdfx;
-  const double* cdfy;
-  int nx, ny;       // table lengths (2 mmax + 1)
-  int mxmax, mymax;
-};
+// Mode tables of all replicas. rbe = 0: modes from `list` (the replicas'
+// half-plane lists, concatenated). rbe = 1: K_r = P modes per replica drawn
+// on the device from the replica's sampler tables, with the counter ctr[1];
+// the drawn (mx, my) go to `sampled` ([R][P] pairs) if it is not NULL.
+// npc = pair count the table is laid out for (compiled NP).
 template <typename T>
-void launch_mode_coef(int K, int Kpad, int npc, const int32_t* list, int rbe,
-                      uint64_t seed, uint64_t counter, const SamplerTab& sp,
-                      const PairTab& pairs, double alpha, double Lx, double Ly,
-                      double H, ModeTab<T> modes, int32_t* sampled,
-                      cudaStream_t st);
-
-size_t kzero_work_doubles(int nchunks0, int np);
+void launch_mode_coef(const Reps& rp, int npc, const int32_t* list, int rbe, uint64_t seed,
+                      const uint64_t* ctr, const double* cdf, const PairTab& pairs,
+                      double alpha, ModeTab<T> modes, int32_t* sampled, cudaStream_t st);
 
 }  // namespace qslab

@@ -31,6 +31,50 @@
 
 namespace qslab {
 
+// ================================================================= geometry
+
+// Particle range of one chunk of a replica.
+struct CRange {
+  int64_t start;
+  int cnt;
+  int r;          // replica
+  bool first;     // first chunk of the replica
+  bool last;      // last chunk of the replica
+};
+
+// k-space chunk c (chunks of L)
+__device__ __forceinline__ CRange kchunk(const Reps& rp, int c) {
+  CRange x;
+  x.r = rp.chunk_rep[c];
+  const RepInfo& ri = rp.info[x.r];
+  const int j = c - ri.c0;
+  x.start = ri.off + (int64_t)j * rp.L;
+  const int left = ri.n - j * rp.L;
+  x.cnt = left < rp.L ? left : rp.L;
+  x.first = j == 0;
+  x.last = j == ri.nch - 1;
+  return x;
+}
+
+// k = 0 chunk c (chunks of L0)
+__device__ __forceinline__ CRange zchunk(const Reps& rp, int c) {
+  CRange x;
+  x.r = rp.zchunk_rep[c];
+  const RepInfo& ri = rp.info[x.r];
+  const int j = c - ri.z0;
+  x.start = ri.off + (int64_t)j * rp.L0;
+  const int left = ri.n - j * rp.L0;
+  x.cnt = left < rp.L0 ? left : rp.L0;
+  x.first = j == 0;
+  x.last = j == ri.nz - 1;
+  return x;
+}
+
+inline int chunk_threads(int L) {
+  const int t = ((L + 31) / 32) * 32;
+  return t < 256 ? t : 256;
+}
+
 // ====================================================================== prep
 
 template <typename T> struct KeyOf;
@@ -45,21 +89,26 @@ template <> struct KeyOf<double> {
   }
 };
 
+// One CTA per k-space chunk (chunks are contiguous in the caller's order as
+// well): finiteness and z-range checks, the z keys, the replica index and
+// the replica's sums of q and |q|.
 template <typename T>
-__global__ void prepare_kernel(int64_t N, const T* __restrict__ pos,
-                               const T* __restrict__ q, double Lz,
-                               typename KeyOf<T>::type* keys, uint32_t* vals,
+__global__ void prepare_kernel(Reps rp, const T* __restrict__ pos, const T* __restrict__ q,
+                               typename KeyOf<T>::type* keys, uint32_t* vals, int32_t* rid,
                                double* sums, unsigned* status) {
   __shared__ double red[2][32];
+  const CRange ch = kchunk(rp, blockIdx.x);
+  const double Lz = rp.info[ch.r].Lz;
   double sq = 0.0, sa = 0.0;
   unsigned flags = 0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
+    const int64_t i = ch.start + t;
     const T x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2], qi = q[i];
     if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) flags |= kStNonfinite;
     else if (!(z >= (T)0) || !((double)z <= Lz)) flags |= kStZRange;
     keys[i] = KeyOf<T>::key(z);
     vals[i] = (uint32_t)i;
+    if (rid) rid[i] = ch.r;
     sq += (double)qi;
     sa += fabs((double)qi);
   }
@@ -74,29 +123,47 @@ __global__ void prepare_kernel(int64_t N, const T* __restrict__ pos,
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
     for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { a += red[0][j]; b += red[1][j]; }
-    atomicAdd(&sums[0], a);
-    atomicAdd(&sums[1], b);
+    atomicAdd(&sums[2 * ch.r], a);
+    atomicAdd(&sums[2 * ch.r + 1], b);
   }
 }
 
 template <typename T>
-void launch_prepare(int64_t N, const T* pos, const T* q, double Lz, void* keys,
-                    uint32_t* vals, double* sums, unsigned* status,
-                    cudaStream_t st) {
-  const int threads = 256;
-  int blocks = (int)((N + threads - 1) / threads);
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  prepare_kernel<T><<<blocks, threads, 0, st>>>(
-      N, pos, q, Lz, static_cast<typename KeyOf<T>::type*>(keys), vals, sums, status);
+void launch_prepare(const Reps& rp, const T* pos, const T* q, void* keys, uint32_t* vals,
+                    int32_t* rid, double* sums, unsigned* status, cudaStream_t st) {
+  prepare_kernel<T><<<rp.nchunks, chunk_threads(rp.L), 0, st>>>(
+      rp, pos, q, static_cast<typename KeyOf<T>::type*>(keys), vals, rid, sums, status);
 }
 
-__global__ void check_neutral_kernel(const double* sums, double tol, unsigned* status) {
-  if (tol >= 0.0 && fabs(sums[0]) > tol * sums[1]) atomicOr(status, kStNonneutral);
+__global__ void check_neutral_kernel(int R, const double* sums, double tol, unsigned* status,
+                                     uint64_t* ctr) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < R && tol >= 0.0 && fabs(sums[2 * r]) > tol * sums[2 * r + 1])
+    atomicOr(status, kStNonneutral);
+  if (ctr && r == 0) {
+    const uint64_t c = ctr[0];
+    ctr[1] = c;
+    ctr[0] = c + 1;
+  }
 }
 
-void launch_check_neutral(const double* sums, double tol, unsigned* status,
-                          cudaStream_t st) {
-  check_neutral_kernel<<<1, 1, 0, st>>>(sums, tol, status);
+void launch_check_neutral(const Reps& rp, const double* sums, double tol, unsigned* status,
+                          uint64_t* ctr, cudaStream_t st) {
+  check_neutral_kernel<<<(rp.R + 255) / 256, 256, 0, st>>>(rp.R, sums, tol, status, ctr);
+}
+
+__global__ void rep_keys_kernel(int64_t N, const uint32_t* __restrict__ perm,
+                                const int32_t* __restrict__ rid, uint32_t* keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    keys[i] = (uint32_t)rid[perm[i]];
+}
+
+void launch_rep_keys(int64_t N, const uint32_t* perm, const int32_t* rid, uint32_t* keys,
+                     cudaStream_t st) {
+  int blocks = (int)((N + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  rep_keys_kernel<<<blocks, 256, 0, st>>>(N, perm, rid, keys);
 }
 
 // ==================================================================== gather
@@ -114,19 +181,21 @@ __device__ __forceinline__ uint64_t to_fixed(double x, double L) {
   return (uint64_t)(f * 18446744073709551616.0);
 }
 
+// One CTA per k-space chunk: the sorted SoA arrays, with dz = 0 at the first
+// particle of every replica.
 template <typename T>
-__global__ void gather_kernel(int64_t N, const T* __restrict__ pos,
-                              const T* __restrict__ q,
-                              const uint32_t* __restrict__ perm, double Lx,
-                              double Ly, T* zs, T* dz, T* qs,
-                              typename PhaseT<T>::type* xh,
-                              typename PhaseT<T>::type* yh, int32_t* perm_out) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
+__global__ void gather_kernel(Reps rp, const T* __restrict__ pos, const T* __restrict__ q,
+                              const uint32_t* __restrict__ perm, T* zs, T* dz, T* qs,
+                              typename PhaseT<T>::type* xh, typename PhaseT<T>::type* yh,
+                              int32_t* perm_out) {
+  const CRange ch = kchunk(rp, blockIdx.x);
+  const double Lx = rp.info[ch.r].Lx, Ly = rp.info[ch.r].Ly;
+  for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
+    const int64_t i = ch.start + t;
     const uint32_t o = perm[i];
     const T z = pos[3 * (int64_t)o + 2];
     zs[i] = z;
-    dz[i] = (i > 0) ? z - pos[3 * (int64_t)perm[i - 1] + 2] : (T)0;
+    dz[i] = (t == 0 && ch.first) ? (T)0 : z - pos[3 * (int64_t)perm[i - 1] + 2];
     qs[i] = q[o];
     xh[i] = to_fixed(pos[3 * (int64_t)o], Lx);
     yh[i] = to_fixed(pos[3 * (int64_t)o + 1], Ly);
@@ -135,15 +204,11 @@ __global__ void gather_kernel(int64_t N, const T* __restrict__ pos,
 }
 
 template <typename T>
-void launch_gather(int64_t N, const T* pos, const T* q, const uint32_t* perm,
-                   double Lx, double Ly, T* zs, T* dz, T* qs,
-                   typename PhaseT<T>::type* xh, typename PhaseT<T>::type* yh,
-                   int32_t* perm_out, cudaStream_t st) {
-  const int threads = 256;
-  int blocks = (int)((N + threads - 1) / threads);
-  if (blocks > 152 * 16) blocks = 152 * 16;
-  gather_kernel<T><<<blocks, threads, 0, st>>>(N, pos, q, perm, Lx, Ly, zs, dz,
-                                               qs, xh, yh, perm_out);
+void launch_gather(const Reps& rp, const T* pos, const T* q, const uint32_t* perm, T* zs,
+                   T* dz, T* qs, typename PhaseT<T>::type* xh,
+                   typename PhaseT<T>::type* yh, int32_t* perm_out, cudaStream_t st) {
+  gather_kernel<T><<<rp.nchunks, chunk_threads(rp.L), 0, st>>>(rp, pos, q, perm, zs, dz, qs,
+                                                                xh, yh, perm_out);
 }
 
 // ============================================================ k != 0 scans
@@ -193,7 +258,9 @@ __device__ inline ChunkSmem<T> carve(char* base, int L, int NP, int W, bool pass
 template <typename T>
 struct KParams {
   ScanPlan plan;
+  Reps rp;
   ModeTab<T> modes;
+  size_t kstride;   // R * Kpad: stride between the planes of modes.cp
   const T* zs;
   const T* dz;
   const T* qs;
@@ -213,17 +280,17 @@ struct ModeCoef {
 };
 
 template <typename T, int NP>
-__device__ __forceinline__ void load_mode(const ModeTab<T>& mt, int Kpad, int m,
+__device__ __forceinline__ void load_mode(const ModeTab<T>& mt, size_t kstride, size_t m,
                                           ModeCoef<T, NP>& c) {
   c.mx = mt.mx[m]; c.my = mt.my[m];
   c.kx = mt.kx[m]; c.ky = mt.ky[m]; c.kk = mt.kk[m];
   c.ck = mt.ck[m]; c.ckk = mt.ckk[m]; c.sY = mt.sY[m]; c.sZ = mt.sZ[m];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    c.cpr[p] = mt.cp[(0 * NP + p) * (size_t)Kpad + m];
-    c.cpi[p] = mt.cp[(1 * NP + p) * (size_t)Kpad + m];
-    c.cbr[p] = mt.cp[(2 * NP + p) * (size_t)Kpad + m];
-    c.cbi[p] = mt.cp[(3 * NP + p) * (size_t)Kpad + m];
+    c.cpr[p] = mt.cp[(0 * NP + p) * kstride + m];
+    c.cpi[p] = mt.cp[(1 * NP + p) * kstride + m];
+    c.cbr[p] = mt.cp[(2 * NP + p) * kstride + m];
+    c.cbi[p] = mt.cp[(3 * NP + p) * kstride + m];
   }
 }
 
@@ -231,7 +298,7 @@ __device__ __forceinline__ void load_mode(const ModeTab<T>& mt, int Kpad, int m,
 template <typename T>
 __device__ inline void load_chunk(const KParams<T>& P, ChunkSmem<T>& s,
                                   int64_t start, int cnt) {
-  const int64_t N = P.plan.N;
+  const int64_t N = P.rp.N;
   for (int t = threadIdx.x; t <= cnt; t += blockDim.x) {
     const int64_t i = start + t;
     Rec<T> r;
@@ -254,9 +321,11 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
   extern __shared__ __align__(32) char smem[];
   const ScanPlan& pl = P.plan;
   const int c = blockIdx.x;
-  const int64_t start = (int64_t)c * pl.L;
-  const int cnt = (int)imin64(pl.L, pl.N - start);
-  ChunkSmem<T> s = carve<T>(smem, pl.L, NP, 0, false);
+  const CRange ch = kchunk(P.rp, c);
+  const int64_t start = ch.start;
+  const int cnt = ch.cnt;
+  const int Kpad = P.rp.Kpad;
+  ChunkSmem<T> s = carve<T>(smem, P.rp.L, NP, 0, false);
   load_chunk<T>(P, s, start, cnt);
   __syncthreads();
   // E tables: [t][0][p] = e^{-a_p (z_end - z_t)}, [t][1][p] = e^{-a_p (z_t - z_start)}
@@ -270,7 +339,7 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
   __syncthreads();
   const int m = blockIdx.y * pl.KR + threadIdx.x;
   ModeCoef<T, NP> mc;
-  load_mode<T, NP>(P.modes, pl.Kpad, m, mc);
+  load_mode<T, NP>(P.modes, P.kstride, (size_t)ch.r * Kpad + m, mc);
   Cplx<T> f0 = {0, 0}, b0 = {0, 0};
   Cplx<T> fa[NP], fb[NP], ba[NP], bb[NP];
 #pragma unroll
@@ -297,17 +366,17 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
     }
   }
   const int S = pl.nstates;
-  const size_t dirstride = (size_t)pl.nchunks * S * pl.Kpad;
-  Cplx<T>* af = P.agg + ((size_t)c * S) * pl.Kpad + m;
+  const size_t dirstride = (size_t)P.rp.nchunks * S * Kpad;
+  Cplx<T>* af = P.agg + ((size_t)c * S) * Kpad + m;
   Cplx<T>* ab = af + dirstride;
   af[0] = f0;
   ab[0] = b0;
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    af[(size_t)(1 + 2 * p) * pl.Kpad] = fa[p];
-    af[(size_t)(2 + 2 * p) * pl.Kpad] = fb[p];
-    ab[(size_t)(1 + 2 * p) * pl.Kpad] = ba[p];
-    ab[(size_t)(2 + 2 * p) * pl.Kpad] = bb[p];
+    af[(size_t)(1 + 2 * p) * Kpad] = fa[p];
+    af[(size_t)(2 + 2 * p) * Kpad] = fb[p];
+    ab[(size_t)(1 + 2 * p) * Kpad] = ba[p];
+    ab[(size_t)(2 + 2 * p) * Kpad] = bb[p];
   }
 }
 
@@ -318,29 +387,31 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
 //   pair decays  pdec[dir][c][p]: forward e^{-a_p (z_end(c) - z_end(c-1))},
 //                backward e^{-a_p (z_start(c+1) - z_start(c))}
 //   mode decays  kdec[dir][c][m]: the same with beta = |k_m|
+// Both are 1 (gap 0) where the chain of a replica starts, whose carry is 0.
 template <typename T>
-__device__ inline double chunk_gap(const T* zs, int64_t N, int L, int nch, int dir, int c) {
+__device__ inline double chunk_gap(const T* zs, const CRange& ch, int dir, int L) {
   if (dir == 0) {
-    if (c == 0) return 0.0;
-    const int64_t e1 = imin64((int64_t)(c + 1) * L, N) - 1;
-    return (double)zs[e1] - (double)zs[(int64_t)c * L - 1];
+    if (ch.first) return 0.0;
+    return (double)zs[ch.start + ch.cnt - 1] - (double)zs[ch.start - 1];
   }
-  if (c >= nch - 1) return 0.0;
-  return (double)zs[(int64_t)(c + 1) * L] - (double)zs[(int64_t)c * L];
+  if (ch.last) return 0.0;
+  return (double)zs[ch.start + L] - (double)zs[ch.start];   // chunk c is full
 }
 
+// zero_chunks = 0: k-space chunks (L), 1: k = 0 chunks (L0)
 template <typename T>
-__global__ void pair_decay_kernel(int64_t N, int L, int nch, int np, const T* zs,
-                                  PairTab pairs,
+__global__ void pair_decay_kernel(Reps rp, int zero_chunks, int np, const T* zs, PairTab pairs,
                                   Cplx<typename CarryNum<T>::type>* pdec,
                                   typename CarryNum<T>::type* gaps) {
   using CN = typename CarryNum<T>::type;
+  const int nch = zero_chunks ? rp.nzchunks : rp.nchunks;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= 2 * nch * np) return;
   const int dir = e / (nch * np);
   const int r = e - dir * nch * np;
   const int c = r / np, p = r - c * np;
-  const double gap = chunk_gap(zs, N, L, nch, dir, c);
+  const CRange ch = zero_chunks ? zchunk(rp, c) : kchunk(rp, c);
+  const double gap = chunk_gap(zs, ch, dir, zero_chunks ? rp.L0 : rp.L);
   const Cplx<double> d = cexp_neg(pairs.a_re[p], pairs.a_im[p], gap);
   pdec[e] = Cplx<CN>{cn_from(d.re, (CN*)nullptr), cn_from(d.im, (CN*)nullptr)};
   if (gaps && p == 0) gaps[dir * nch + c] = cn_from(gap, (CN*)nullptr);
@@ -365,32 +436,36 @@ __device__ __forceinline__ double exp_neg_small(double x) {
 }
 
 template <typename T>
-__global__ void mode_decay_kernel(ScanPlan pl, const T* zs, const T* kk,
+__global__ void mode_decay_kernel(Reps rp, const T* zs, const T* kk,
                                   typename CarryNum<T>::type* kdec) {
   using CN = typename CarryNum<T>::type;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t tot = (int64_t)2 * pl.nchunks * pl.Kpad;
-  if (e >= tot) return;
-  const int dir = (int)(e / ((int64_t)pl.nchunks * pl.Kpad));
-  const int64_t r = e - (int64_t)dir * pl.nchunks * pl.Kpad;
-  const int c = (int)(r / pl.Kpad), m = (int)(r - (int64_t)c * pl.Kpad);
-  const double x = (double)kk[m] * chunk_gap(zs, pl.N, pl.L, pl.nchunks, dir, c);
+  const int64_t per_dir = (int64_t)rp.nchunks * rp.Kpad;
+  if (e >= 2 * per_dir) return;
+  const int dir = (int)(e / per_dir);
+  const int64_t r = e - (int64_t)dir * per_dir;
+  const int c = (int)(r / rp.Kpad), m = (int)(r - (int64_t)c * rp.Kpad);
+  const CRange ch = kchunk(rp, c);
+  const double x = (double)kk[(size_t)ch.r * rp.Kpad + m] * chunk_gap(zs, ch, dir, rp.L);
   kdec[e] = cn_from(exp_neg_small(x), (CN*)nullptr);
 }
 
 // ------------------------------------------------------------------ carries
-// carry_in[c+1] = D_c carry_in[c] + A_c over the chunks (forward; mirrored
-// backward), one chain per (direction, state, mode), in the carry type. The
-// chunks are cut into G groups of g, and the chains run in three parallel
-// phases: (1) every group composes its transfer (D_g = prod D_c, A_g = the
-// group's output from a zero input); (2) a short chain over the G groups
-// gives each group's input; (3) every group replays its chunks from that
-// input and writes the carries. Depth 2g + G instead of G g. All loads and
-// stores are coalesced across modes.
+// carry_in[c+1] = D_c carry_in[c] + A_c over the chunks of a replica
+// (forward; mirrored backward), one chain per (replica, direction, state,
+// mode), in the carry type. The chunks of a replica are cut into groups,
+// and the chains run in three parallel phases: (1) every group composes its
+// transfer (D_g = prod D_c, A_g = the group's output from a zero input);
+// (2) a short chain over the replica's groups gives each group's input;
+// (3) every group replays its chunks from that input and writes the
+// carries. Depth 2g + G instead of G g for G groups of g chunks. The last
+// group of a chain needs no transfer. Loads and stores are coalesced across
+// modes.
 
 template <typename T>
 struct CarryCtx {
-  int nc, G, g, S, Kpad, np;
+  Reps rp;
+  int S, np;
   size_t cs;        // stride between chunks in agg/carry (S * Kpad)
   size_t dirstride; // nchunks * S * Kpad
 };
@@ -402,10 +477,10 @@ __device__ __forceinline__ void chunk_decay(const CarryCtx<T>& X, const Cplx<typ
                                             typename CarryNum<T>::type& di) {
   using CN = typename CarryNum<T>::type;
   if (st == 0) {
-    dr = kdec[((size_t)dir * X.nc + c) * X.Kpad + m];
+    dr = kdec[((size_t)dir * X.rp.nchunks + c) * X.rp.Kpad + m];
     di = cn_zero((CN*)nullptr);
   } else {
-    const Cplx<CN> d = pdec[((size_t)dir * X.nc + c) * X.np + ((st - 1) >> 1)];
+    const Cplx<CN> d = pdec[((size_t)dir * X.rp.nchunks + c) * X.np + ((st - 1) >> 1)];
     dr = d.re; di = d.im;
   }
 }
@@ -418,31 +493,37 @@ __global__ void carry_group_kernel(CarryCtx<T> X, const Cplx<T>* agg, Cplx<T>* c
                                    Cplx<typename CarryNum<T>::type>* gD,
                                    Cplx<typename CarryNum<T>::type>* gA, bool replay) {
   using CN = typename CarryNum<T>::type;
+  const int Kpad = X.rp.Kpad, NG = X.rp.ngroups;
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t per_dir = (int64_t)X.S * X.G * X.Kpad;
+  const int64_t per_dir = (int64_t)X.S * NG * Kpad;
   if (e >= 2 * per_dir) return;
   const int dir = (int)(e / per_dir);
   int64_t r = e - dir * per_dir;
-  const int st = (int)(r / ((int64_t)X.G * X.Kpad));
-  r -= (int64_t)st * X.G * X.Kpad;
-  const int grp = (int)(r / X.Kpad), m = (int)(r - (int64_t)grp * X.Kpad);
-  const size_t gidx = (((size_t)dir * X.S + st) * X.G + grp) * X.Kpad + m;
+  const int st = (int)(r / ((int64_t)NG * Kpad));
+  r -= (int64_t)st * NG * Kpad;
+  const int grp = (int)(r / Kpad), m = (int)(r - (int64_t)grp * Kpad);
+  if (!replay) {
+    const RepInfo& ri = X.rp.info[X.rp.group_rep[grp]];
+    if (grp == (dir == 0 ? ri.g0 + ri.ng - 1 : ri.g0)) return;   // last in its chain
+  }
+  const size_t gidx = (((size_t)dir * X.S + st) * NG + grp) * Kpad + m;
   const CN zero = cn_zero((CN*)nullptr), one = cn_from(1.0, (CN*)nullptr);
   CN cr = zero, ci = zero, pr = one, pi = zero;
   if (replay) { cr = gA[gidx].re; ci = gA[gidx].im; }
-  const Cplx<T>* A = agg + dir * X.dirstride + (size_t)st * X.Kpad + m;
-  Cplx<T>* C = carry + dir * X.dirstride + (size_t)st * X.Kpad + m;
-  const int j0 = grp * X.g, j1 = min(X.nc, j0 + X.g);
+  const Cplx<T>* A = agg + dir * X.dirstride + (size_t)st * Kpad + m;
+  Cplx<T>* C = carry + dir * X.dirstride + (size_t)st * Kpad + m;
+  const int ca = X.rp.gstart[grp], cb = X.rp.gstart[grp + 1];
+  const int len = cb - ca;
   constexpr int B = 8;
-  for (int jb = j0; jb < j1; jb += B) {
+  for (int jb = 0; jb < len; jb += B) {
     Cplx<T> a[B];
     CN dr[B], di[B];
 #pragma unroll
     for (int u = 0; u < B; ++u) {
       const int j = jb + u;
       dr[u] = zero; di[u] = zero; a[u] = Cplx<T>{0, 0};
-      if (j < j1) {
-        const int c = dir == 0 ? j : X.nc - 1 - j;
+      if (j < len) {
+        const int c = dir == 0 ? ca + j : cb - 1 - j;
         a[u] = A[c * X.cs];
         chunk_decay<T>(X, pdec, kdec, dir, st, m, c, dr[u], di[u]);
       }
@@ -450,8 +531,8 @@ __global__ void carry_group_kernel(CarryCtx<T> X, const Cplx<T>* agg, Cplx<T>* c
 #pragma unroll
     for (int u = 0; u < B; ++u) {
       const int j = jb + u;
-      if (j < j1) {
-        const int c = dir == 0 ? j : X.nc - 1 - j;
+      if (j < len) {
+        const int c = dir == 0 ? ca + j : cb - 1 - j;
         if (replay) C[c * X.cs] = Cplx<T>{cn_to_t(cr), cn_to_t(ci)};
         const CN nr = dr[u] * cr - di[u] * ci + cn_from_t(a[u].re, (CN*)nullptr);
         const CN ni = dr[u] * ci + di[u] * cr + cn_from_t(a[u].im, (CN*)nullptr);
@@ -470,40 +551,36 @@ __global__ void carry_group_kernel(CarryCtx<T> X, const Cplx<T>* agg, Cplx<T>* c
   }
 }
 
-// phase 2: thread = (dir, state, mode); turns gA into each group's input
+// phase 2: thread = (dir, state, replica, mode); turns gA into each group's input
 template <typename T>
 __global__ void carry_chain_kernel(CarryCtx<T> X, const Cplx<typename CarryNum<T>::type>* gD,
                                    Cplx<typename CarryNum<T>::type>* gA) {
   using CN = typename CarryNum<T>::type;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 2 * X.S * X.Kpad) return;
-  const int dir = e / (X.S * X.Kpad);
-  const int r = e - dir * X.S * X.Kpad;
-  const int st = r / X.Kpad, m = r - st * X.Kpad;
+  const int Kpad = X.rp.Kpad, NG = X.rp.ngroups, R = X.rp.R;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t per_dir = (int64_t)X.S * R * Kpad;
+  if (e >= 2 * per_dir) return;
+  const int dir = (int)(e / per_dir);
+  int64_t r = e - dir * per_dir;
+  const int st = (int)(r / ((int64_t)R * Kpad));
+  r -= (int64_t)st * R * Kpad;
+  const int rep = (int)(r / Kpad), m = (int)(r - (int64_t)rep * Kpad);
+  const RepInfo& ri = X.rp.info[rep];
   const CN zero = cn_zero((CN*)nullptr);
   CN cr = zero, ci = zero;
-  for (int grp = 0; grp < X.G; ++grp) {
-    const size_t gidx = (((size_t)dir * X.S + st) * X.G + grp) * X.Kpad + m;
+  for (int j = 0; j < ri.ng; ++j) {
+    const int grp = dir == 0 ? ri.g0 + j : ri.g0 + ri.ng - 1 - j;
+    const size_t gidx = (((size_t)dir * X.S + st) * NG + grp) * Kpad + m;
+    if (j == ri.ng - 1) {
+      gA[gidx] = Cplx<CN>{cr, ci};
+      break;
+    }
     const Cplx<CN> d = gD[gidx], a = gA[gidx];
     gA[gidx] = Cplx<CN>{cr, ci};
     const CN nr = d.re * cr - d.im * ci + a.re;
     const CN ni = d.re * ci + d.im * cr + a.im;
     cr = nr; ci = ni;
   }
-}
-
-template <typename T>
-inline CarryCtx<T> carry_ctx(const ScanPlan& pl) {
-  CarryCtx<T> X;
-  X.nc = pl.nchunks;
-  X.G = pl.nchunks >= 64 ? 32 : 1;
-  X.g = (pl.nchunks + X.G - 1) / X.G;
-  X.S = pl.nstates;
-  X.Kpad = pl.Kpad;
-  X.np = pl.np;
-  X.cs = (size_t)pl.nstates * pl.Kpad;
-  X.dirstride = (size_t)pl.nchunks * pl.nstates * pl.Kpad;
-  return X;
 }
 
 // ------------------------------------------------------------------ pass B
@@ -513,9 +590,11 @@ __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
   const ScanPlan& pl = P.plan;
   const int c = blockIdx.x;
   const int W = pl.KR / kWarp;
-  const int64_t start = (int64_t)c * pl.L;
-  const int cnt = (int)imin64(pl.L, pl.N - start);
-  ChunkSmem<T> s = carve<T>(smem, pl.L, NP, W, true);
+  const int L = P.rp.L, Kpad = P.rp.Kpad;
+  const CRange ch = kchunk(P.rp, c);
+  const int64_t start = ch.start;
+  const int cnt = ch.cnt;
+  ChunkSmem<T> s = carve<T>(smem, L, NP, W, true);
   load_chunk<T>(P, s, start, cnt);
   __syncthreads();
   // per-step decays [t][p] = e^{-a_p dz_t}, t = 0..cnt (t = cnt: next chunk)
@@ -527,19 +606,19 @@ __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int m = blockIdx.y * pl.KR + threadIdx.x;
   ModeCoef<T, NP> mc;
-  load_mode<T, NP>(P.modes, pl.Kpad, m, mc);
+  load_mode<T, NP>(P.modes, P.kstride, (size_t)ch.r * Kpad + m, mc);
   const int S = pl.nstates;
-  const size_t dirstride = (size_t)pl.nchunks * S * pl.Kpad;
-  T* slot = s.slots + (size_t)w * pl.L * 4;
+  const size_t dirstride = (size_t)P.rp.nchunks * S * Kpad;
+  T* slot = s.slots + (size_t)w * L * 4;
 
   for (int dir = 0; dir < 2; ++dir) {
-    const Cplx<T>* cin = P.carry + dir * dirstride + ((size_t)c * S) * pl.Kpad + m;
+    const Cplx<T>* cin = P.carry + dir * dirstride + ((size_t)c * S) * Kpad + m;
     Cplx<T> g0 = cin[0];
     Cplx<T> ga[NP], gb[NP];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      ga[p] = cin[(size_t)(1 + 2 * p) * pl.Kpad];
-      gb[p] = cin[(size_t)(2 + 2 * p) * pl.Kpad];
+      ga[p] = cin[(size_t)(1 + 2 * p) * Kpad];
+      gb[p] = cin[(size_t)(2 + 2 * p) * Kpad];
     }
     const T zsign = dir == 0 ? (T)1 : (T)-1;
     for (int n0 = 0; n0 < cnt; n0 += 4) {
@@ -600,13 +679,26 @@ __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
   }
   __syncthreads();
   // sum the warps' slots and write this mode range's partial outputs
-  T* out = P.part + (size_t)blockIdx.y * 4 * pl.N;
+  T* out = P.part + (size_t)blockIdx.y * 4 * P.rp.N;
   for (int e = threadIdx.x; e < cnt * 4; e += blockDim.x) {
     const int t = e >> 2, qn = e & 3;
     T acc = 0;
-    for (int ww = 0; ww < W; ++ww) acc += s.slots[((size_t)ww * pl.L + t) * 4 + qn];
-    out[(size_t)qn * pl.N + start + t] = acc;
+    for (int ww = 0; ww < W; ++ww) acc += s.slots[((size_t)ww * L + t) * 4 + qn];
+    out[(size_t)qn * P.rp.N + start + t] = acc;
   }
+}
+
+template <typename T>
+inline void decay_views(const ScanPlan& pl, const Reps& rp, void* dec,
+                        Cplx<typename CarryNum<T>::type>*& pdec,
+                        typename CarryNum<T>::type*& kdec,
+                        Cplx<typename CarryNum<T>::type>*& gD,
+                        Cplx<typename CarryNum<T>::type>*& gA) {
+  using CN = typename CarryNum<T>::type;
+  pdec = static_cast<Cplx<CN>*>(dec);
+  kdec = reinterpret_cast<CN*>(pdec + (size_t)2 * rp.nchunks * pl.np);
+  gD = reinterpret_cast<Cplx<CN>*>(kdec + (size_t)2 * rp.nchunks * rp.Kpad);
+  gA = gD + (size_t)2 * pl.nstates * rp.ngroups * rp.Kpad;
 }
 
 template <typename T, int NP>
@@ -614,30 +706,33 @@ static void kspace_run(const KParams<T>& P, const PairTab& pairs, void* dec,
                        cudaStream_t st, cudaEvent_t* ev) {
   using CN = typename CarryNum<T>::type;
   const ScanPlan& pl = P.plan;
-  dim3 grid(pl.nchunks, pl.nkr);
-  const size_t smA = chunk_smem_bytes<T>(pl.L, NP, 0, false);
-  const size_t smB = chunk_smem_bytes<T>(pl.L, NP, pl.KR / kWarp, true);
+  const Reps& rp = P.rp;
+  dim3 grid(rp.nchunks, pl.nkr);
+  const size_t smA = chunk_smem_bytes<T>(rp.L, NP, 0, false);
+  const size_t smB = chunk_smem_bytes<T>(rp.L, NP, pl.KR / kWarp, true);
   cudaFuncSetAttribute(kspace_aggregate_kernel<T, NP>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
   cudaFuncSetAttribute(kspace_final_kernel<T, NP>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB);
   kspace_aggregate_kernel<T, NP><<<grid, pl.KR, smA, st>>>(P, pairs);
   if (ev) cudaEventRecord(ev[0], st);
-  Cplx<CN>* pdec = static_cast<Cplx<CN>*>(dec);
-  CN* kdec = reinterpret_cast<CN*>(pdec + (size_t)2 * pl.nchunks * pl.np);
-  const int ne = 2 * pl.nchunks * pl.np;
-  pair_decay_kernel<T><<<(ne + 255) / 256, 256, 0, st>>>(pl.N, pl.L, pl.nchunks, pl.np, P.zs,
-                                                         pairs, pdec, nullptr);
-  const int64_t nk = (int64_t)2 * pl.nchunks * pl.Kpad;
-  mode_decay_kernel<T><<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(pl, P.zs, P.modes.kk, kdec);
-  const CarryCtx<T> X = carry_ctx<T>(pl);
-  Cplx<CN>* gD = reinterpret_cast<Cplx<CN>*>(kdec + (size_t)2 * pl.nchunks * pl.Kpad);
-  Cplx<CN>* gA = gD + (size_t)2 * X.S * X.G * X.Kpad;
-  const int64_t ng = (int64_t)2 * X.S * X.G * X.Kpad;
+  Cplx<CN>* pdec; CN* kdec; Cplx<CN>* gD; Cplx<CN>* gA;
+  decay_views<T>(pl, rp, dec, pdec, kdec, gD, gA);
+  const int ne = 2 * rp.nchunks * pl.np;
+  pair_decay_kernel<T><<<(ne + 255) / 256, 256, 0, st>>>(rp, 0, pl.np, P.zs, pairs, pdec, nullptr);
+  const int64_t nk = (int64_t)2 * rp.nchunks * rp.Kpad;
+  mode_decay_kernel<T><<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(rp, P.zs, P.modes.kk, kdec);
+  CarryCtx<T> X;
+  X.rp = rp;
+  X.S = pl.nstates;
+  X.np = pl.np;
+  X.cs = (size_t)pl.nstates * rp.Kpad;
+  X.dirstride = (size_t)rp.nchunks * pl.nstates * rp.Kpad;
+  const int64_t ng = (int64_t)2 * X.S * rp.ngroups * rp.Kpad;
   carry_group_kernel<T><<<(unsigned)((ng + 127) / 128), 128, 0, st>>>(X, P.agg, P.carry, pdec, kdec,
                                                                       gD, gA, false);
-  const int nt = 2 * X.S * X.Kpad;
-  carry_chain_kernel<T><<<(nt + 127) / 128, 128, 0, st>>>(X, gD, gA);
+  const int64_t nt = (int64_t)2 * X.S * rp.R * rp.Kpad;
+  carry_chain_kernel<T><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(X, gD, gA);
   carry_group_kernel<T><<<(unsigned)((ng + 127) / 128), 128, 0, st>>>(X, P.agg, P.carry, pdec, kdec,
                                                                       gD, gA, true);
   if (ev) cudaEventRecord(ev[1], st);
@@ -645,21 +740,21 @@ static void kspace_run(const KParams<T>& P, const PairTab& pairs, void* dec,
   if (ev) cudaEventRecord(ev[2], st);
 }
 
-size_t kspace_decay_bytes(const ScanPlan& pl, int fp64) {
+size_t kspace_decay_bytes(const ScanPlan& pl, const Reps& rp, int fp64) {
   const size_t cn = fp64 ? sizeof(double) : sizeof(DF);
   // pair decays, mode decays, group transfers (D and A)
-  return 2 * cn * (size_t)2 * pl.nchunks * pl.np + cn * (size_t)2 * pl.nchunks * pl.Kpad +
-         2 * 2 * cn * (size_t)2 * pl.nstates * 32 * pl.Kpad + 1024;
+  return 2 * cn * (size_t)2 * rp.nchunks * pl.np + cn * (size_t)2 * rp.nchunks * rp.Kpad +
+         2 * 2 * cn * (size_t)2 * pl.nstates * rp.ngroups * rp.Kpad + 1024;
 }
 
 template <typename T>
-void launch_kspace(const ScanPlan& plan, const ModeTab<T>& modes,
+void launch_kspace(const ScanPlan& plan, const Reps& rp, const ModeTab<T>& modes,
                    const PairTab& pairs, const T* zs, const T* dz, const T* qs,
                    const typename PhaseT<T>::type* xh,
                    const typename PhaseT<T>::type* yh, Cplx<T>* agg,
                    Cplx<T>* carry, void* dec, T* part,
                    cudaStream_t st, cudaEvent_t* ev3) {
-  KParams<T> P{plan, modes, zs, dz, qs, xh, yh, agg, carry, part};
+  KParams<T> P{plan, rp, modes, (size_t)rp.R * rp.Kpad, zs, dz, qs, xh, yh, agg, carry, part};
   switch (plan.np) {
     case 4: kspace_run<T, 4>(P, pairs, dec, st, ev3); break;
     case 8: kspace_run<T, 8>(P, pairs, dec, st, ev3); break;
@@ -684,10 +779,9 @@ void launch_kspace(const ScanPlan& plan, const ModeTab<T>& modes,
 // in one warp and are summed by shuffles.
 
 struct K0Params {
-  int64_t N;
-  int L0, nch;
+  Reps rp;
   int npad;          // lanes per chunk (power of two >= np, at least 4)
-  double alpha, area, c1;
+  double alpha, c1;
 };
 
 // acc + a b, with the product kept exact on the double-float path
@@ -708,9 +802,10 @@ __global__ void kzero_aggregate_kernel(K0Params Q, PairTab pr, const T* zs,
   const int lanes = Q.npad;
   const int g = (blockIdx.x * blockDim.x + threadIdx.x);
   const int c = g / lanes, p = g - c * lanes;
-  if (c >= Q.nch) return;
-  const int64_t start = (int64_t)c * Q.L0;
-  const int cnt = (int)imin64(Q.L0, Q.N - start);
+  if (c >= Q.rp.nzchunks) return;
+  const CRange ch = zchunk(Q.rp, c);
+  const int64_t start = ch.start;
+  const int cnt = ch.cnt;
   const T zst = zs[start], zen = zs[start + cnt - 1];
   const bool act = p < pr.np;
   const T ar = act ? (T)pr.a_re[p] : (T)0, ai = act ? (T)pr.a_im[p] : (T)0;
@@ -735,40 +830,49 @@ __global__ void kzero_aggregate_kernel(K0Params Q, PairTab pr, const T* zs,
   if (p == 0) { csum[2 * c] = q0; csum[2 * c + 1] = q1; }
 }
 
-// One thread per (direction, pair) runs the chain over the chunks in the
-// carry type; thread 2*npad scans the chunk sums of q and q z.
+// One CTA per replica. One thread per (direction, pair) runs the chain over
+// the replica's k = 0 chunks in the carry type; thread 32k (its own warp)
+// scans the chunk sums of q and q z into per-chunk prefixes and the
+// replica's totals.
 template <typename T>
 __global__ void kzero_carry_kernel(K0Params Q, PairTab pr, const typename CarryNum<T>::type* gaps,
                                    const Cplx<T>* agg,
                                    const Cplx<typename CarryNum<T>::type>* pdec,
                                    typename CarryNum<T>::type* carry,
                                    const typename CarryNum<T>::type* csum,
-                                   typename CarryNum<T>::type* cpre) {
+                                   typename CarryNum<T>::type* cpre,
+                                   typename CarryNum<T>::type* rtot) {
   using CN = typename CarryNum<T>::type;
   const CN zero = cn_zero((CN*)nullptr);
+  const int rep = blockIdx.x;
+  const RepInfo& ri = Q.rp.info[rep];
+  const int z0 = ri.z0, nz = ri.nz;
+  const int nch = Q.rp.nzchunks;
   const int e = threadIdx.x;
-  // the prefix of the chunk sums runs in its own warp (thread 32*k), with
-  // batched loads, so it neither diverges from the chains nor waits on memory
   const int pre_thread = ((2 * Q.npad + 31) / 32) * 32;
   if (e == pre_thread) {
     CN a = zero, b = zero;
     constexpr int B = 16;
-    for (int c0 = 0; c0 < Q.nch; c0 += B) {
+    for (int j0 = 0; j0 < nz; j0 += B) {
       CN va[B], vb[B];
 #pragma unroll
       for (int u = 0; u < B; ++u) {
         va[u] = zero; vb[u] = zero;
-        if (c0 + u < Q.nch) { va[u] = csum[2 * (c0 + u)]; vb[u] = csum[2 * (c0 + u) + 1]; }
+        if (j0 + u < nz) {
+          const int c = z0 + j0 + u;
+          va[u] = csum[2 * c]; vb[u] = csum[2 * c + 1];
+        }
       }
 #pragma unroll
       for (int u = 0; u < B; ++u) {
-        if (c0 + u < Q.nch) {
-          cpre[2 * (c0 + u)] = a; cpre[2 * (c0 + u) + 1] = b;
+        if (j0 + u < nz) {
+          const int c = z0 + j0 + u;
+          cpre[2 * c] = a; cpre[2 * c + 1] = b;
           a = a + va[u]; b = b + vb[u];
         }
       }
     }
-    cpre[2 * Q.nch] = a; cpre[2 * Q.nch + 1] = b;
+    rtot[2 * rep] = a; rtot[2 * rep + 1] = b;
     return;
   }
   if (e >= 2 * Q.npad) return;
@@ -777,28 +881,28 @@ __global__ void kzero_carry_kernel(K0Params Q, PairTab pr, const typename CarryN
   const int np = pr.np;
   CN sr = zero, si = zero, hr = zero, hi = zero;
   constexpr int B = 8;
-  for (int j0 = 0; j0 < Q.nch; j0 += B) {
+  for (int j0 = 0; j0 < nz; j0 += B) {
     Cplx<T> as[B], ah[B];
     Cplx<CN> d[B];
     CN dzc[B];
 #pragma unroll
     for (int u = 0; u < B; ++u) {
       const int j = j0 + u;
-      if (j < Q.nch) {
-        const int c = dir == 0 ? j : Q.nch - 1 - j;
+      if (j < nz) {
+        const int c = dir == 0 ? z0 + j : z0 + nz - 1 - j;
         const Cplx<T>* a = agg + ((size_t)c * Q.npad + p) * 4 + 2 * dir;
         as[u] = a[0];
         ah[u] = a[1];
-        d[u] = pdec[((size_t)dir * Q.nch + c) * np + p];
-        dzc[u] = gaps[dir * Q.nch + c];
+        d[u] = pdec[((size_t)dir * nch + c) * np + p];
+        dzc[u] = gaps[dir * nch + c];
       }
     }
 #pragma unroll
     for (int u = 0; u < B; ++u) {
       const int j = j0 + u;
-      if (j < Q.nch) {
-        const int c = dir == 0 ? j : Q.nch - 1 - j;
-        CN* out = carry + (((size_t)dir * Q.nch + c) * Q.npad + p) * 4;
+      if (j < nz) {
+        const int c = dir == 0 ? z0 + j : z0 + nz - 1 - j;
+        CN* out = carry + (((size_t)dir * nch + c) * Q.npad + p) * 4;
         out[0] = sr; out[1] = si; out[2] = hr; out[3] = hi;
         // S' = d S + S_loc ; H' = d (H + dz S) + H_loc
         const CN tr = hr + dzc[u] * sr, ti = hi + dzc[u] * si;
@@ -817,19 +921,25 @@ __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
                                    const T* dz, const T* qs,
                                    const typename CarryNum<T>::type* carry,
                                    const typename CarryNum<T>::type* cpre,
+                                   const typename CarryNum<T>::type* rtot,
                                    typename CarryNum<T>::type* phi0,
                                    typename CarryNum<T>::type* fz0) {
   using CN = typename CarryNum<T>::type;
   extern __shared__ __align__(16) char ksm_raw[];   // [chunks per block][L0][2] of T
   T* ksm = reinterpret_cast<T*>(ksm_raw);
   const int lanes = Q.npad;
+  const int L0 = Q.rp.L0;
+  const int nch = Q.rp.nzchunks;
+  const int64_t N = Q.rp.N;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int c = g / lanes, p = g - c * lanes;
   const int lc = threadIdx.x / lanes;
-  T* acc = ksm + (size_t)lc * Q.L0 * 2;
-  const bool valid = c < Q.nch;
-  const int64_t start = (int64_t)c * Q.L0;
-  const int cnt = valid ? (int)imin64(Q.L0, Q.N - start) : 0;
+  T* acc = ksm + (size_t)lc * L0 * 2;
+  const bool valid = c < nch;
+  CRange ch{0, 0, 0, false, false};
+  if (valid) ch = zchunk(Q.rp, c);
+  const int64_t start = ch.start;
+  const int cnt = ch.cnt;
   const bool act = valid && p < pr.np;
   const double sq = 1.7724538509055160;   // sqrt(pi)
   T cwr = 0, cwi = 0, isr = 0, isi = 0, csr = 0, csi = 0, ar = 1, ai = 0;
@@ -843,24 +953,26 @@ __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
     ar = (T)pr.a_re[p]; ai = (T)pr.a_im[p];
   }
   const T alpha = (T)Q.alpha, ialpha = (T)(1.0 / Q.alpha);
-  for (int t = threadIdx.x % lanes; t < Q.L0; t += lanes) { acc[2 * t] = 0; acc[2 * t + 1] = 0; }
+  for (int t = threadIdx.x % lanes; t < L0; t += lanes) { acc[2 * t] = 0; acc[2 * t + 1] = 0; }
   __syncwarp();
   for (int dir = 0; dir < 2; ++dir) {
     T sr = 0, si = 0, hr = 0, hi = 0;
     if (act) {
-      const CN* in = carry + (((size_t)dir * Q.nch + c) * Q.npad + p) * 4;
+      const CN* in = carry + (((size_t)dir * nch + c) * Q.npad + p) * 4;
       sr = cn_to_t(in[0]); si = cn_to_t(in[1]); hr = cn_to_t(in[2]); hi = cn_to_t(in[3]);
     }
     // every lane runs L0 steps so that the shuffles below see the whole warp
-    for (int n = 0; n < Q.L0; ++n) {
+    for (int n = 0; n < L0; ++n) {
       const bool live = n < cnt;
       const int t = dir == 0 ? n : cnt - 1 - n;
       const int64_t i = start + t;
       T pot = 0, der = 0;
       if (act && live) {
         const T qq = qs[i];
+        // the backward step applies the next particle's dz (0 past the
+        // replica's end: its carry is 0 there)
         const int64_t id = dir == 0 ? i : i + 1;
-        const T dzi = id < Q.N ? dz[id] : (T)0;
+        const T dzi = id < N ? dz[id] : (T)0;
         const Cplx<T> d = cexp_neg(ar, ai, dzi);
         // H first (uses the previous inclusive S), then S
         const T tr = fma(dzi, sr, hr), ti = fma(dzi, si, hi);
@@ -892,9 +1004,9 @@ __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
     // the carry type (the terms cancel heavily); the result stays in the
     // carry type and the combine kernel widens it to FP64
     CN Ql = cpre[2 * c], Pl = cpre[2 * c + 1];
-    const CN Qt = cpre[2 * Q.nch], Pt = cpre[2 * Q.nch + 1];
+    const CN Qt = rtot[2 * ch.r], Pt = rtot[2 * ch.r + 1];
     const CN c1 = cn_from(Q.c1, (CN*)nullptr);
-    const CN pre = cn_from(2.0 * 3.14159265358979323846 / Q.area, (CN*)nullptr);
+    const CN pre = cn_from(2.0 * 3.14159265358979323846 / Q.rp.info[ch.r].area, (CN*)nullptr);
     for (int t = 0; t < cnt; ++t) {
       const int64_t i = start + t;
       const T zt = zs[i], qt = qs[i];
@@ -912,16 +1024,21 @@ __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
   }
 }
 
+inline int kzero_lanes(int np) {
+  int npad = 4;                 // at least 4 lanes per chunk: 8 chunks fill a warp multiple
+  while (npad < np) npad <<= 1;
+  return npad;
+}
+
 template <typename T>
-void launch_kzero(int64_t N, int L0, int nchunks0, const PairTab& pairs,
-                  double alpha, double area, const T* zs, const T* dz,
-                  const T* qs, double* work, void* phi0v, void* fz0v,
+void launch_kzero(const Reps& rp, const PairTab& pairs, double alpha, const T* zs,
+                  const T* dz, const T* qs, double* work, void* phi0v, void* fz0v,
                   cudaStream_t st) {
   using CN = typename CarryNum<T>::type;
   K0Params Q;
-  Q.N = N; Q.L0 = L0; Q.nch = nchunks0; Q.alpha = alpha; Q.area = area;
-  int npad = 4;                 // at least 4 lanes per chunk: 8 chunks fill a warp multiple
-  while (npad < pairs.np) npad <<= 1;
+  Q.rp = rp;
+  Q.alpha = alpha;
+  const int npad = kzero_lanes(pairs.np);
   Q.npad = npad;
   double c1 = 0.0;
   for (int p = 0; p < pairs.np; ++p) {
@@ -931,58 +1048,66 @@ void launch_kzero(int64_t N, int L0, int nchunks0, const PairTab& pairs,
     c1 += pairs.mult[p] * 2.0 * re / 1.7724538509055160;
   }
   Q.c1 = c1;
+  const int nch = rp.nzchunks;
   // work layout: agg [nch][npad][4] Cplx<T>, csum [nch][2] CN,
-  // pdec [2][nch][np] Cplx<CN>, carry [2][nch][npad][4] CN, cpre [nch+1][2] CN
+  // pdec [2][nch][np] Cplx<CN>, carry [2][nch][npad][4] CN, cpre [nch][2] CN,
+  // rtot [R][2] CN, gaps [2][nch] CN
   char* w = reinterpret_cast<char*>(work);
   auto take = [&w](size_t b) { char* r = w; w += (b + 255) & ~size_t(255); return r; };
-  Cplx<T>* agg = reinterpret_cast<Cplx<T>*>(take(sizeof(Cplx<T>) * (size_t)nchunks0 * npad * 4));
-  CN* csum = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)nchunks0 * 2));
-  Cplx<CN>* pdec = reinterpret_cast<Cplx<CN>*>(take(sizeof(Cplx<CN>) * (size_t)2 * nchunks0 * pairs.np));
-  CN* carry = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)2 * nchunks0 * npad * 4));
-  CN* cpre = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)(nchunks0 + 1) * 2));
-  CN* gaps = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)2 * nchunks0));
+  Cplx<T>* agg = reinterpret_cast<Cplx<T>*>(take(sizeof(Cplx<T>) * (size_t)nch * npad * 4));
+  CN* csum = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)nch * 2));
+  Cplx<CN>* pdec = reinterpret_cast<Cplx<CN>*>(take(sizeof(Cplx<CN>) * (size_t)2 * nch * pairs.np));
+  CN* carry = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)2 * nch * npad * 4));
+  CN* cpre = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)nch * 2));
+  CN* rtot = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)rp.R * 2));
+  CN* gaps = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)2 * nch));
   CN* phi0 = static_cast<CN*>(phi0v);
   CN* fz0 = static_cast<CN*>(fz0v);
-  const int tot = nchunks0 * npad;
+  const int tot = nch * npad;
   constexpr int kK0Threads = 128;
   kzero_aggregate_kernel<T><<<(tot + kK0Threads - 1) / kK0Threads, kK0Threads, 0, st>>>(
       Q, pairs, zs, qs, agg, csum);
-  const int ne = 2 * nchunks0 * pairs.np;
-  pair_decay_kernel<T><<<(ne + 255) / 256, 256, 0, st>>>(N, L0, nchunks0, pairs.np, zs, pairs, pdec,
-                                                         gaps);
-  kzero_carry_kernel<T><<<1, ((2 * npad + 31) / 32) * 32 + 32, 0, st>>>(Q, pairs, gaps, agg, pdec,
-                                                                      carry, csum, cpre);
+  const int ne = 2 * nch * pairs.np;
+  pair_decay_kernel<T><<<(ne + 255) / 256, 256, 0, st>>>(rp, 1, pairs.np, zs, pairs, pdec, gaps);
+  kzero_carry_kernel<T><<<rp.R, ((2 * npad + 31) / 32) * 32 + 32, 0, st>>>(
+      Q, pairs, gaps, agg, pdec, carry, csum, cpre, rtot);
   // 8 chunks per CTA: npad * 8 threads is a whole number of warps for npad >= 4
   const int cpb = 8;
   const int thr = npad * cpb;
-  const size_t sm = (size_t)cpb * L0 * 2 * sizeof(T);
+  const size_t sm = (size_t)cpb * rp.L0 * 2 * sizeof(T);
   cudaFuncSetAttribute(kzero_final_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   kzero_final_kernel<T><<<(tot + thr - 1) / thr, thr, sm, st>>>(
-      Q, pairs, zs, dz, qs, carry, cpre, phi0, fz0);
+      Q, pairs, zs, dz, qs, carry, cpre, rtot, phi0, fz0);
 }
 
-size_t kzero_work_doubles(int nchunks0, int np) {
-  int npad = 4;
-  while (npad < np) npad <<= 1;
-  // in 8-byte units, with room for 256-byte alignment of each of 5 arrays
-  return (size_t)nchunks0 * npad * 4 * 2 + (size_t)nchunks0 * 2 +
-         (size_t)2 * nchunks0 * kMaxPairs * 2 + (size_t)2 * nchunks0 * npad * 4 +
-         (size_t)(nchunks0 + 1) * 2 + (size_t)2 * nchunks0 + 6 * 32 + 64;
+size_t kzero_work_doubles(int nzchunks, int R, int np) {
+  const int npad = kzero_lanes(np);
+  // in 8-byte units (a double-float takes one), with room for the 256-byte
+  // alignment of each of the 7 arrays
+  return (size_t)nzchunks * npad * 4 * 2 + (size_t)nzchunks * 2 +
+         (size_t)2 * nzchunks * kMaxPairs * 2 + (size_t)2 * nzchunks * npad * 4 +
+         (size_t)nzchunks * 2 + (size_t)R * 2 + (size_t)2 * nzchunks + 7 * 32 + 64;
 }
 
 // ================================================================== combine
 
+// One CTA per k-space chunk: sums the mode ranges' partial outputs, adds the
+// k = 0 term and the j = i constant of the chunk's replica, scatters the
+// potential and force to the caller's order and writes the chunk's energy
+// 1/2 sum q_i phi_i.
 template <typename T>
-__global__ void combine_kernel(int64_t N, int nkr, const T* __restrict__ part,
+__global__ void combine_kernel(Reps rp, int nkr, const T* __restrict__ part,
                                const typename CarryNum<T>::type* __restrict__ phi0,
                                const typename CarryNum<T>::type* __restrict__ fz0,
-                               const T* __restrict__ qs,
-                               const int32_t* __restrict__ perm, double diagq,
-                               double* eblock, T* phi_out, T* force_out) {
+                               const T* __restrict__ qs, const int32_t* __restrict__ perm,
+                               double* echunk, T* phi_out, T* force_out) {
   __shared__ double red[32];
+  const CRange ch = kchunk(rp, blockIdx.x);
+  const double diagq = rp.info[ch.r].diagq;
+  const int64_t N = rp.N;
   double e = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
+    const int64_t i = ch.start + t;
     double ph = 0, fx = 0, fy = 0, fz = 0;
     for (int r = 0; r < nkr; ++r) {
       const T* b = part + (size_t)r * 4 * N;
@@ -1010,35 +1135,36 @@ __global__ void combine_kernel(int64_t N, int nkr, const T* __restrict__ part,
   if (threadIdx.x == 0) {
     double s = 0;
     for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[j];
-    eblock[blockIdx.x] = s;
+    echunk[blockIdx.x] = s;
   }
 }
 
-__global__ void energy_sum_kernel(const double* eblock, int n, double* energy) {
-  __shared__ double red[32];
+// One warp per replica: the sum of its chunks' energies in a fixed order
+// (deterministic).
+__global__ void energy_rep_kernel(Reps rp, const double* echunk, double* energies) {
+  const int rep = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (rep >= rp.R) return;   // whole warps leave together
+  const RepInfo& ri = rp.info[rep];
   double s = 0.0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) s += eblock[j];
+  for (int j = lane; j < ri.nch; j += 32) s += echunk[ri.c0 + j];
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) t += red[j];
-    *energy = t;
-  }
+  if (lane == 0) energies[rep] = s;
 }
 
 template <typename T>
-void launch_combine(int64_t N, int nkr, const T* part, const void* phi0v,
-                    const void* fz0v, const T* qs, const int32_t* perm,
-                    double diagq, double* eblock, int nblk, T* phi_out,
-                    T* force_out, double* energy, cudaStream_t st) {
+void launch_combine(const Reps& rp, int nkr, const T* part, const void* phi0v,
+                    const void* fz0v, const T* qs, const int32_t* perm, double* echunk,
+                    T* phi_out, T* force_out, double* energies, cudaStream_t st) {
   using CN = typename CarryNum<T>::type;
   const CN* phi0 = static_cast<const CN*>(phi0v);
   const CN* fz0 = static_cast<const CN*>(fz0v);
-  combine_kernel<T><<<nblk, 256, 0, st>>>(N, nkr, part, phi0, fz0, qs, perm,
-                                          diagq, eblock, phi_out, force_out);
-  if (energy) energy_sum_kernel<<<1, 256, 0, st>>>(eblock, nblk, energy);
+  combine_kernel<T><<<rp.nchunks, chunk_threads(rp.L), 0, st>>>(rp, nkr, part, phi0, fz0, qs, perm,
+                                                                 echunk, phi_out, force_out);
+  if (energies) {
+    const int64_t thr = (int64_t)rp.R * 32;
+    energy_rep_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(rp, echunk, energies);
+  }
 }
 
 // ========================================================= random-batch modes
@@ -1056,48 +1182,61 @@ __device__ __forceinline__ double uniform53(uint64_t w) {
   return (double)(w >> 11) * 1.1102230246251565e-16;   // 2^-53
 }
 
-// Fill the mode table. Full k-sum: (mx, my) from the host's half-plane list,
-// weight 2 (k and -k), gam = (pi/A) C_k 2. Random batch: (mx, my) drawn here
-// (Philox4x64-10 with counter (m, attempt, call, tag) and key (seed, 0); words
-// 0,1 then 2,3 are inverted through the per-axis cumulative tables; the origin
-// is rejected), gam = (pi/A) (H/P) 2 alpha/(sqrt(pi) k) (Eq. 4.7 with 4.9: the
-// Gaussian of C_k cancels against e^{k^2/(4 alpha^2)}).
+// Fill the mode tables; thread = (mode, replica). Full k-sum: (mx, my) from
+// the replica's half-plane list, weight 2 (k and -k), gam = (pi/A) C_k 2.
+// Random batch: (mx, my) drawn here (Philox4x64-10 with counter
+// (m, attempt, call, tag + replica * 2^32) and key (seed, 0); words 0,1 then
+// 2,3 are inverted through the replica's per-axis cumulative tables; the
+// origin is rejected), gam = (pi/A) (H/P) 2 alpha/(sqrt(pi) k) (Eq. 4.7 with
+// 4.9: the Gaussian of C_k cancels against e^{k^2/(4 alpha^2)}).
 template <typename T>
-__global__ void mode_coef_kernel(int K, int Kpad, int npc, const int32_t* list,
-                                 int rbe, uint64_t seed, uint64_t counter,
-                                 SamplerTab sp, PairTab pr, double alpha,
-                                 double Lx, double Ly, double H,
-                                 ModeTab<T> mt, int32_t* sampled) {
+__global__ void mode_coef_kernel(Reps rp, int npc, const int32_t* list, int rbe, uint64_t seed,
+                                 const uint64_t* ctr, const double* cdf, PairTab pr,
+                                 double alpha, ModeTab<T> mt, int32_t* sampled) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rep = blockIdx.y;
+  const int Kpad = rp.Kpad;
   if (m >= Kpad) return;
+  const RepInfo& ri = rp.info[rep];
+  const int K = ri.K;
+  const double Lx = ri.Lx, Ly = ri.Ly;
+  const size_t mg = (size_t)rep * Kpad + m;
+  const size_t ks = (size_t)rp.R * Kpad;
   const double pi = 3.14159265358979323846;
   const double sqpi = 1.7724538509055160;
   int mx = 0, my = 0;
   if (m < K) {
     if (!rbe) {
-      mx = list[2 * m];
-      my = list[2 * m + 1];
+      mx = list[2 * ((size_t)ri.list0 + m)];
+      my = list[2 * ((size_t)ri.list0 + m) + 1];
     } else {
+      const double* cdfx = cdf + ri.cdfx0;
+      const double* cdfy = cdf + ri.cdfy0;
+      const uint64_t counter = ctr[1];
       for (uint64_t attempt = 0; attempt < 64; ++attempt) {
         U64x4 c;
-        c.v[0] = (uint64_t)m; c.v[1] = attempt; c.v[2] = counter; c.v[3] = 0x52424531ull;
+        c.v[0] = (uint64_t)m; c.v[1] = attempt; c.v[2] = counter;
+        c.v[3] = 0x52424531ull + ((uint64_t)rep << 32);
         const U64x4 r = philox4x64_10(c, seed, 0ull);
-        const int ax = upper_index(sp.cdfx, sp.nx, uniform53(r.v[0])) - sp.mxmax;
-        const int ay = upper_index(sp.cdfy, sp.ny, uniform53(r.v[1])) - sp.mymax;
+        const int ax = upper_index(cdfx, ri.nx, uniform53(r.v[0])) - ri.mxmax;
+        const int ay = upper_index(cdfy, ri.ny, uniform53(r.v[1])) - ri.mymax;
         if (ax != 0 || ay != 0) { mx = ax; my = ay; break; }
-        const int bx = upper_index(sp.cdfx, sp.nx, uniform53(r.v[2])) - sp.mxmax;
-        const int by = upper_index(sp.cdfy, sp.ny, uniform53(r.v[3])) - sp.mymax;
+        const int bx = upper_index(cdfx, ri.nx, uniform53(r.v[2])) - ri.mxmax;
+        const int by = upper_index(cdfy, ri.ny, uniform53(r.v[3])) - ri.mymax;
         if (bx != 0 || by != 0) { mx = bx; my = by; break; }
       }
+      if (sampled) {
+        sampled[2 * ((size_t)rep * K + m)] = mx;
+        sampled[2 * ((size_t)rep * K + m) + 1] = my;
+      }
     }
-    if (sampled) { sampled[2 * m] = mx; sampled[2 * m + 1] = my; }
   }
   const bool live = (m < K) && (mx != 0 || my != 0);
   const double kx = 2 * pi * mx / Lx, ky = 2 * pi * my / Ly;
   const double k = live ? sqrt(kx * kx + ky * ky) : 1.0;
   double gam = 0.0;
   if (live) {
-    gam = rbe ? pi / (Lx * Ly) * (H / K) * 2.0 * alpha / (sqpi * k)
+    gam = rbe ? pi / (Lx * Ly) * (ri.H / K) * 2.0 * alpha / (sqpi * k)
               : pi / (Lx * Ly) * 2.0 * (2.0 * alpha * exp(-k * k / (4.0 * alpha * alpha)) / (sqpi * k));
   }
   double ckk = 0.0, sY = 0.0, sZ = 0.0;
@@ -1117,46 +1256,52 @@ __global__ void mode_coef_kernel(int K, int Kpad, int npc, const int32_t* list,
       sY += cr;
       sZ += br;
     }
-    mt.cp[((size_t)0 * npc + p) * Kpad + m] = (T)cr;
-    mt.cp[((size_t)1 * npc + p) * Kpad + m] = (T)ci;
-    mt.cp[((size_t)2 * npc + p) * Kpad + m] = (T)br;
-    mt.cp[((size_t)3 * npc + p) * Kpad + m] = (T)bi;
+    mt.cp[((size_t)0 * npc + p) * ks + mg] = (T)cr;
+    mt.cp[((size_t)1 * npc + p) * ks + mg] = (T)ci;
+    mt.cp[((size_t)2 * npc + p) * ks + mg] = (T)br;
+    mt.cp[((size_t)3 * npc + p) * ks + mg] = (T)bi;
   }
   const double ck = gam * ckk;
-  mt.mx[m] = mx;
-  mt.my[m] = my;
-  mt.kx[m] = (T)kx;
-  mt.ky[m] = (T)ky;
-  mt.kk[m] = (T)k;
-  mt.ck[m] = (T)ck;
-  mt.ckk[m] = (T)(ck * k);
-  mt.sY[m] = (T)(ck + sY);
-  mt.sZ[m] = (T)(ck * k + sZ);
+  mt.mx[mg] = mx;
+  mt.my[mg] = my;
+  mt.kx[mg] = (T)kx;
+  mt.ky[mg] = (T)ky;
+  mt.kk[mg] = (T)k;
+  mt.ck[mg] = (T)ck;
+  mt.ckk[mg] = (T)(ck * k);
+  mt.sY[mg] = (T)(ck + sY);
+  mt.sZ[mg] = (T)(ck * k + sZ);
 }
 
 template <typename T>
-void launch_mode_coef(int K, int Kpad, int npc, const int32_t* list, int rbe,
-                      uint64_t seed, uint64_t counter, const SamplerTab& sp,
-                      const PairTab& pairs, double alpha, double Lx, double Ly,
-                      double H, ModeTab<T> modes, int32_t* sampled,
-                      cudaStream_t st) {
-  mode_coef_kernel<T><<<(Kpad + 127) / 128, 128, 0, st>>>(
-      K, Kpad, npc, list, rbe, seed, counter, sp, pairs, alpha, Lx, Ly, H,
-      modes, sampled);
+void launch_mode_coef(const Reps& rp, int npc, const int32_t* list, int rbe, uint64_t seed,
+                      const uint64_t* ctr, const double* cdf, const PairTab& pairs,
+                      double alpha, ModeTab<T> modes, int32_t* sampled, cudaStream_t st) {
+  dim3 grid((rp.Kpad + 127) / 128, rp.R);
+  mode_coef_kernel<T><<<grid, 128, 0, st>>>(rp, npc, list, rbe, seed, ctr, cdf, pairs, alpha,
+                                            modes, sampled);
 }
 
 // ============================================================ instantiations
-template void launch_prepare<float>(int64_t, const float*, const float*, double, void*, uint32_t*, double*, unsigned*, cudaStream_t);
-template void launch_prepare<double>(int64_t, const double*, const double*, double, void*, uint32_t*, double*, unsigned*, cudaStream_t);
-template void launch_gather<float>(int64_t, const float*, const float*, const uint32_t*, double, double, float*, float*, float*, uint32_t*, uint32_t*, int32_t*, cudaStream_t);
-template void launch_gather<double>(int64_t, const double*, const double*, const uint32_t*, double, double, double*, double*, double*, uint64_t*, uint64_t*, int32_t*, cudaStream_t);
-template void launch_kspace<float>(const ScanPlan&, const ModeTab<float>&, const PairTab&, const float*, const float*, const float*, const uint32_t*, const uint32_t*, Cplx<float>*, Cplx<float>*, void*, float*, cudaStream_t, cudaEvent_t*);
-template void launch_kspace<double>(const ScanPlan&, const ModeTab<double>&, const PairTab&, const double*, const double*, const double*, const uint64_t*, const uint64_t*, Cplx<double>*, Cplx<double>*, void*, double*, cudaStream_t, cudaEvent_t*);
-template void launch_kzero<float>(int64_t, int, int, const PairTab&, double, double, const float*, const float*, const float*, double*, void*, void*, cudaStream_t);
-template void launch_kzero<double>(int64_t, int, int, const PairTab&, double, double, const double*, const double*, const double*, double*, void*, void*, cudaStream_t);
-template void launch_combine<float>(int64_t, int, const float*, const void*, const void*, const float*, const int32_t*, double, double*, int, float*, float*, double*, cudaStream_t);
-template void launch_combine<double>(int64_t, int, const double*, const void*, const void*, const double*, const int32_t*, double, double*, int, double*, double*, double*, cudaStream_t);
-template void launch_mode_coef<float>(int, int, int, const int32_t*, int, uint64_t, uint64_t, const SamplerTab&, const PairTab&, double, double, double, double, ModeTab<float>, int32_t*, cudaStream_t);
-template void launch_mode_coef<double>(int, int, int, const int32_t*, int, uint64_t, uint64_t, const SamplerTab&, const PairTab&, double, double, double, double, ModeTab<double>, int32_t*, cudaStream_t);
+#define QSLAB_INST(T, PH)                                                                        \
+  template void launch_prepare<T>(const Reps&, const T*, const T*, void*, uint32_t*, int32_t*,   \
+                                  double*, unsigned*, cudaStream_t);                             \
+  template void launch_gather<T>(const Reps&, const T*, const T*, const uint32_t*, T*, T*, T*,   \
+                                 PH*, PH*, int32_t*, cudaStream_t);                              \
+  template void launch_kspace<T>(const ScanPlan&, const Reps&, const ModeTab<T>&,                \
+                                 const PairTab&, const T*, const T*, const T*, const PH*,        \
+                                 const PH*, Cplx<T>*, Cplx<T>*, void*, T*, cudaStream_t,         \
+                                 cudaEvent_t*);                                                  \
+  template void launch_kzero<T>(const Reps&, const PairTab&, double, const T*, const T*,         \
+                                const T*, double*, void*, void*, cudaStream_t);                  \
+  template void launch_combine<T>(const Reps&, int, const T*, const void*, const void*,          \
+                                  const T*, const int32_t*, double*, T*, T*, double*,            \
+                                  cudaStream_t);                                                 \
+  template void launch_mode_coef<T>(const Reps&, int, const int32_t*, int, uint64_t,             \
+                                    const uint64_t*, const double*, const PairTab&, double,      \
+                                    ModeTab<T>, int32_t*, cudaStream_t);
+QSLAB_INST(float, uint32_t)
+QSLAB_INST(double, uint64_t)
+#undef QSLAB_INST
 
 }  // namespace qslab

@@ -12,6 +12,9 @@
 //   scatter stable placement: within a warp, keys are ranked in input order
 //           with __match_any_sync; warps of a tile are ordered by a per-digit
 //           prefix over their counts; tiles by the global scan.
+// Several slabs of one call are sorted by z first and then, stably, by their
+// slab index (a second LSD sort over one or two more digits), which leaves
+// every slab in its own index range and ordered by z within it.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -158,9 +161,8 @@ void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes) {
   w.totals = reinterpret_cast<uint32_t*>(p);
 }
 
-int radix_sort(SortWork& w, int64_t N, int key_bytes, cudaStream_t st) {
-  const int passes = key_bytes;  // 8-bit digits
-  int cur = 0;
+int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaStream_t st) {
+  int cur = src;
   cudaMemsetAsync(w.totals, 0, (size_t)passes * kRadix * 4, st);
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
