@@ -6,7 +6,8 @@ drawn on the device, M = 16 SOE terms (conditioned table), compensated FP32.
 One step = one qslab_compute() call: input checks, z-sort, gather, k-sampler
 and mode table, k-space chunk aggregates, carries, bidirectional recurrences
 with the fused gather, the k = 0 term, the combine and the energy reduction.
-The same step in FP64 is reported beside it.
+The same step in FP64 is reported beside it, and so is the 512-replica
+batched workload (one CUDA-graph-replayed batched call per step).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -334,6 +335,8 @@ def run_ours(args):
         "clocks": clocks,
         "gpu_launches": int(nl32),
     }
+    if not args.no_batched:
+        line["batched"] = run_batched(args, qslab, soe, dev, ws, rank, local, peak, smax)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         t, desc, cores = cpu_oracle_sample(sl, soe, P, 1000, sample_modes=8)
         line["cpu_baseline"] = {"value": N / t, "unit": "particles/s", "cores": cores,
@@ -343,6 +346,95 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def run_batched(args, qslab, soe, dev, ws, rank, local, peak, smax):
+    """The 512-replica workload (N per replica uniform in [500, 50000], number
+    density 0.05, Lz uniform in [5, 40], charges +-1, random batch P = 200,
+    M = 16, alpha = 0.25), FP32C, as one qslab_compute_batched() call
+    captured in a CUDA graph after the autotuner picked the launch shape;
+    the timed steps are graph replays (each draws a fresh sample). The
+    inputs (206 MB) and the workspace exceed L2, so no flush is needed. The
+    FP64 form of the same call is timed beside it (no graph)."""
+    import torch
+
+    import workloads
+    reps = workloads.replicas(seed=4 + rank)
+    sizes = [r.N for r in reps]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    boxes = np.array([r.box for r in reps])
+    pos = np.concatenate([r.pos for r in reps])
+    q = np.concatenate([r.q for r in reps])
+    Ntot = int(off[-1])
+    P, M = 200, 16
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": "512 independent neutral slabs, N per slab uniform in [500, 50000], "
+                       "Lx=Ly from number density 0.05, Lz uniform in [5, 40], charges +-1, "
+                       "alpha=0.25, random batch P=200 per slab, M=16, compensated FP32, "
+                       "one batched call replayed from a CUDA graph",
+           "replicas": len(reps), "N_total": Ntot, "unit": "particles/s",
+           "l2": "inputs and workspace larger than L2 (no flush)"}
+    s = qslab.QSlab(local, "fp32c").configure(reps[0].box, 0.25, soe, rbe=(P, 7000 + rank))
+    tpos = torch.tensor(pos, device=dev, dtype=torch.float32)
+    tq = torch.tensor(q, device=dev, dtype=torch.float32)
+    t0 = time.perf_counter()
+    out["tuning"] = list(s.autotune(tpos, tq, off, boxes, reps=2))
+    out["autotune_s"] = time.perf_counter() - t0
+    # one timed call outside the graph for the per-phase breakdown
+    qslab.qslab_set_timing(s.h, True)
+    s.compute_batched(tpos, tq, off, boxes)
+    ph, nl = qslab.qslab_get_timings(s.h)
+    qslab.qslab_set_timing(s.h, False)
+    g = qslab.GraphedBatch(s, tpos, tq, off, boxes)
+    for _ in range(args.warmup):
+        g.replay()
+    s.check()
+    steps = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    for i in range(steps):
+        ev0[i].record(stream)
+        g.replay()
+        ev1[i].record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    s.check()
+    ms = reduce_max(float(np.mean([a.elapsed_time(b) for a, b in zip(ev0, ev1)])), dev)
+    out.update({"value": job_throughput(Ntot, ws, ms), "ms_per_step": ms, "steps": steps,
+                "warmup": args.warmup, "graph": True, "gpu_launches_per_step": nl,
+                "phases_ms": dict(ph)})
+    rec_ms = ph["recurrence"]
+    achieved = algorithmic_instr(P, Ntot, M) / (rec_ms * 1e-3) / 1e12
+    out["roofline"] = {"bound": "alu", "kernel": "kspace_final_kernel (recurrences + gather)",
+                       "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
+                       "frac": achieved / peak, "traffic": None,
+                       "note": "recurrence phase of one timed call outside the graph"}
+    del g
+    s.close()
+    # FP64 form of the same batched call
+    s64 = qslab.QSlab(local, "fp64").configure(reps[0].box, 0.25, soe, rbe=(P, 7000 + rank))
+    tpos = torch.tensor(pos, device=dev, dtype=torch.float64)
+    tq = torch.tensor(q, device=dev, dtype=torch.float64)
+    outs = s64.compute_batched(tpos, tq, off, boxes)
+    s64.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n64 = 2
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(n64):
+        s64.compute_batched(tpos, tq, off, boxes, *outs)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    s64.check()
+    ms64 = reduce_max(e0.elapsed_time(e1) / n64, dev)
+    out["fp64"] = {"value": job_throughput(Ntot, ws, ms64), "unit": "particles/s",
+                   "ms_per_step": ms64, "steps": n64}
+    s64.close()
+    return out
 
 
 def profile_case():
@@ -370,6 +462,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 512-replica batched measurement")
     ap.add_argument("--profile-case", action="store_true",
                     help="only run two FP32 random-batch calls (for profilers)")
     args = ap.parse_args()

@@ -106,6 +106,24 @@ int qslab_set_neutrality_tol(qslab_ctx* ctx, double tol);
  * 256). Results do not depend on it beyond rounding. */
 int qslab_set_tuning(qslab_ctx* ctx, int chunk, int modes_per_cta);
 
+/* Launch-shape autotuner (the paper has no counterpart; the launch shape
+ * changes no result beyond rounding). Times qslab_compute_batched() on the
+ * given replicas (R = 1, offsets {0, N} and boxes = the context's box for a
+ * single slab) for every candidate pair (chunk length 64..512, modes per CTA
+ * 64..256 or automatic), reps timed calls each after one warm-up call, with
+ * CUDA events on `stream`, and keeps the fastest with qslab_set_tuning().
+ *   pos, q     device inputs as for qslab_compute_batched(); read only
+ *   reps       timed calls per candidate, 1..100
+ *   chunk, modes_per_cta   receive the chosen tuning (either may be NULL)
+ * The random-batch counter is restored afterwards: tuning draws no samples
+ * from the user's sequence. Synchronises the stream; allocates the largest
+ * workspace among the candidates (candidates that do not fit are skipped).
+ * Returns the status of the tuning calls (a device-side input error aborts
+ * the tuning and leaves the previous tuning in place). */
+int qslab_autotune(qslab_ctx* ctx, int R, const int64_t* offsets,
+                   const double* boxes, const void* pos, const void* q,
+                   void* stream, int reps, int* chunk, int* modes_per_cta);
+
 /* Long-range energy, potentials and forces (Algorithm 1 steps 4-5, 7-9, or
  * Algorithm 2 steps 4-7, 9; the real-space part is not included).
  *   N       number of particles, 1 <= N <= 2^31 - 1

@@ -69,6 +69,7 @@ def load(build_if_missing: bool = True):
         "qslab_compute_host": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_compute_static": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_compute_batched": ([P, I, P, P, P, P, P, P, P, P], I),
+        "qslab_autotune": ([P, I, P, P, P, P, P, I, P, P], I),
         "qslab_get_sampled_modes": ([P, P, P], I),
         "qslab_get_rng_state": ([P, P, P], I),
         "qslab_set_rng_state": ([P, ctypes.c_uint64, ctypes.c_uint64], I),
@@ -169,6 +170,22 @@ def qslab_compute_batched(h, offsets, boxes, pos_ptr, q_ptr, energies_ptr, phi_p
            "qslab_compute_batched")
 
 
+def qslab_autotune(h, offsets, boxes, pos_ptr, q_ptr, stream_ptr, reps=3):
+    """Time the candidate launch shapes on these inputs and keep the fastest;
+    returns (chunk, modes_per_cta)."""
+    off = np.ascontiguousarray(offsets, np.int64)
+    box = np.ascontiguousarray(boxes, np.float64).reshape(-1, 3)
+    R = off.shape[0] - 1
+    if box.shape[0] != R:
+        raise ValueError("boxes must have one row per replica")
+    L = ctypes.c_int()
+    kr = ctypes.c_int()
+    _check(load().qslab_autotune(h, R, off.ctypes.data, box.ctypes.data, pos_ptr, q_ptr,
+                                 stream_ptr, int(reps), ctypes.addressof(L), ctypes.addressof(kr)),
+           "qslab_autotune")
+    return L.value, kr.value
+
+
 def qslab_get_sampled_modes(h, P, R=1):
     """(mx, my, weight) of the latest random-batch call: arrays of P (R = 1)
     or R x P, and the weight H/P (a float, or R of them)."""
@@ -262,6 +279,7 @@ class QSlab:
         if isinstance(soe, int):
             soe = load_soe(soe)
         qslab_set_box(self.h, *map(float, box))
+        self.box = tuple(map(float, box))
         qslab_set_alpha(self.h, float(alpha))
         qslab_set_soe(self.h, *soe)
         if rbe is not None:
@@ -344,6 +362,19 @@ class QSlab:
         qslab_compute_host(self.h, N, pos.ctypes.data, q.ctypes.data, e.ctypes.data,
                            phi.ctypes.data, F.ctypes.data, stream)
         return float(e[0]), phi, F
+
+    def autotune(self, pos, q, offsets=None, boxes=None, reps=3):
+        """Pick the launch shape (chunk length, modes per CTA) by timing the
+        candidates on these inputs; for a single slab leave offsets and boxes
+        None. Returns the chosen (chunk, modes_per_cta)."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        N = q.shape[0]
+        if offsets is None:
+            offsets = np.array([0, N], np.int64)
+            boxes = np.array([self.box], np.float64)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        return qslab_autotune(self.h, offsets, boxes, pos.data_ptr(), q.data_ptr(), st, reps)
 
     def status(self):
         return qslab_last_status(self.h)

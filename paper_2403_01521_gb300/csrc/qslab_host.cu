@@ -284,7 +284,8 @@ bool same_key(const Tables& t, const qslab_ctx* c, int R, const int64_t* off, co
 
 // Host part of the tables of a call (no device work). Validates the replica
 // offsets and boxes.
-int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* box, Tables& t) {
+int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* box, Tables& t,
+                 const Tables* prev = nullptr) {
   if (R < 1 || R > kMaxReplicas || !off || !box) return QSLAB_ERR_INVALID_ARG;
   if (off[0] != 0) return QSLAB_ERR_INVALID_ARG;
   for (int r = 0; r < R; ++r) {
@@ -306,6 +307,15 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
   t.N = N;
   t.info.assign(R, RepInfo{});
   const double alpha = c->alpha;
+  // the per-box data of the previous tables still hold when only the
+  // offsets or the launch shape changed
+  const bool reuse = prev && prev->valid && prev->cfg_version == c->cfg_version &&
+                     prev->R == R &&
+                     std::memcmp(prev->box.data(), box, sizeof(double) * 3 * R) == 0;
+  if (reuse) {
+    t.list = prev->list;
+    t.cdf = prev->cdf;
+  }
   // modes, sampler tables and j = i constants per replica (memoised by box)
   std::map<std::pair<double, double>, int> seen;
   int Kmax = 1;
@@ -316,7 +326,12 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
     ri.Lx = box[3 * r]; ri.Ly = box[3 * r + 1]; ri.Lz = box[3 * r + 2];
     ri.area = ri.Lx * ri.Ly;
     auto it = seen.find({ri.Lx, ri.Ly});
-    if (it != seen.end()) {
+    if (reuse) {
+      const RepInfo& o = prev->info[r];
+      ri.K = o.K; ri.list0 = o.list0; ri.cdfx0 = o.cdfx0; ri.nx = o.nx;
+      ri.cdfy0 = o.cdfy0; ri.ny = o.ny; ri.mxmax = o.mxmax; ri.mymax = o.mymax;
+      ri.H = o.H; ri.diagq = o.diagq;
+    } else if (it != seen.end()) {
       const RepInfo& o = t.info[it->second];
       ri.K = o.K; ri.list0 = o.list0; ri.cdfx0 = o.cdfx0; ri.nx = o.nx;
       ri.cdfy0 = o.cdfy0; ri.ny = o.ny; ri.mxmax = o.mxmax; ri.mymax = o.mymax;
@@ -442,7 +457,7 @@ int select_tables(qslab_ctx* c, int R, const int64_t* off, const double* box) {
   if (rc) return rc;
   if (same_key(c->tab, c, R, off, box)) return QSLAB_OK;
   Tables t;
-  rc = build_tables(c, R, off, box, t);
+  rc = build_tables(c, R, off, box, t, &c->tab);
   if (rc) return rc;
   c->tab.valid = false;
   if (t.bytes > c->tab_bytes) {
@@ -907,6 +922,92 @@ int qslab_get_timings(qslab_ctx* c, double* ms8, int* launches) {
     ms8[i] = t;
   }
   if (launches) *launches = c->launches;
+  return QSLAB_OK;
+}
+
+int qslab_autotune(qslab_ctx* c, int R, const int64_t* offsets, const double* boxes,
+                   const void* pos, const void* q, void* stream, int reps, int* chunk,
+                   int* modes_per_cta) {
+  if (!c || !offsets || !boxes || !pos || !q || R < 1 || R > kMaxReplicas || reps < 1 ||
+      reps > 100)
+    return QSLAB_ERR_INVALID_ARG;
+  QS_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = ensure_config(c);
+  if (rc) return rc;
+  // the tuning calls must not consume random-batch samples: keep the counter
+  uint64_t ctr_saved = 0;
+  QS_CUDA(cudaStreamSynchronize(st));
+  QS_CUDA(cudaMemcpy(&ctr_saved, c->d_ctr, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  const int old_L = c->tune_L, old_KR = c->tune_KR;
+  const bool old_timing = c->timing;
+  c->timing = false;
+  // candidates: chunk lengths (particles per CTA along the scan) and mode
+  // ranges (threads per CTA); the largest K decides which mode widths apply
+  std::vector<int> Ls = c->prec == QSLAB_FP64 ? std::vector<int>{64, 128, 256}
+                                              : std::vector<int>{64, 128, 256, 512};
+  int Kmax = c->mode == 2 ? c->P : 1;
+  if (c->mode == 1) {
+    std::map<std::pair<double, double>, int> seen;
+    for (int r = 0; r < R; ++r) {
+      const std::pair<double, double> key(boxes[3 * r], boxes[3 * r + 1]);
+      if (seen.count(key)) continue;
+      seen[key] = 1;
+      Kmax = std::max(Kmax, (int)(half_plane(key.first, key.second, c->kc).size() / 2));
+    }
+  }
+  const int k32 = ((Kmax + 31) / 32) * 32;
+  std::vector<int> KRs;
+  for (int kr : {64, 128, 192, 256})
+    if (kr < k32) KRs.push_back(kr);
+  KRs.push_back(0);   // automatic: one range when K <= 256
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  QS_CUDA(cudaEventCreate(&e0));
+  QS_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bestL = 0, bestKR = 0;
+  rc = QSLAB_OK;
+  for (int L : Ls) {
+    for (int kr : KRs) {
+      c->tune_L = L;
+      c->tune_KR = kr;
+      Plan P;
+      rc = setup_call(c, R, offsets, boxes, false, P);
+      if (rc == QSLAB_ERR_ALLOC) { rc = QSLAB_OK; cudaGetLastError(); continue; }
+      if (rc) break;
+      rc = dispatch(c, P, pos, q, nullptr, nullptr, nullptr, st);   // warm-up
+      if (rc) break;
+      if (cudaEventRecord(e0, st) != cudaSuccess) { rc = QSLAB_ERR_CUDA; break; }
+      for (int i = 0; i < reps && !rc; ++i) rc = dispatch(c, P, pos, q, nullptr, nullptr, nullptr, st);
+      if (rc) break;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = QSLAB_ERR_CUDA;
+        break;
+      }
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bestL = L; bestKR = kr; }
+    }
+    if (rc) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->timing = old_timing;
+  c->have_sample = false;   // the tuning calls' samples are not the user's
+  if (cudaMemcpy(c->d_ctr, &ctr_saved, sizeof(uint64_t), cudaMemcpyHostToDevice) != cudaSuccess &&
+      !rc)
+    rc = QSLAB_ERR_CUDA;
+  const int st_rc = qslab_last_status(c);
+  if (!rc) rc = st_rc;
+  if (rc || best >= 1e30f) {
+    c->tune_L = old_L;
+    c->tune_KR = old_KR;
+    return rc ? rc : QSLAB_ERR_ALLOC;
+  }
+  c->tune_L = bestL;
+  c->tune_KR = bestKR;
+  if (chunk) *chunk = bestL;
+  if (modes_per_cta) *modes_per_cta = bestKR;
   return QSLAB_OK;
 }
 

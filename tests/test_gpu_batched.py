@@ -248,3 +248,22 @@ def test_replicas_workload_fp32c(qslab, replicas512, soe16):
         e_phi = 0.5 * float(got["q"][a:b] @ got["phi"][a:b])
         scale = 0.5 * float(np.abs(got["q"][a:b] * got["phi"][a:b]).sum())
         assert abs(got["E"][r] - e_phi) <= 1e-6 * scale, r
+
+
+def test_autotune(qslab, mixed, soe16):
+    """The autotuner picks a valid launch shape, keeps the random-batch
+    counter, and the tuned call equals a call with that shape set by hand."""
+    off, boxes, pos, q = _stack(mixed)
+    slab = qslab.QSlab(0, "fp32c").configure(mixed[0].box, 0.3, soe16, rbe=(64, 11))
+    tpos = torch.tensor(pos, device="cuda", dtype=torch.float32)
+    tq = torch.tensor(q, device="cuda", dtype=torch.float32)
+    L, kr = slab.autotune(tpos, tq, off, boxes, reps=2)
+    assert L in (64, 128, 256, 512) and kr in (0, 64, 128, 192, 256)
+    assert slab.rng_state() == (11, 0)
+    e1, phi1, F1 = slab.compute_batched(tpos, tq, off, boxes)
+    other = qslab.QSlab(0, "fp32c").configure(mixed[0].box, 0.3, soe16, rbe=(64, 11)).tuning(L, kr)
+    e2, phi2, F2 = other.compute_batched(tpos, tq, off, boxes)
+    assert slab.status() == 0 and other.status() == 0
+    assert torch.equal(e1, e2) and torch.equal(phi1, phi2) and torch.equal(F1, F2)
+    other.close()
+    slab.close()
