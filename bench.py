@@ -437,21 +437,37 @@ def run_batched(args, qslab, soe, dev, ws, rank, local, peak, smax):
     return out
 
 
-def profile_case():
-    """Two FP32 random-batch calls on the benchmark workload (for ncu)."""
+def profile_case(kind="single"):
+    """Two FP32 random-batch calls for profilers: 'single' = the benchmark
+    workload (N = 1e6); 'batched' = the first 128 slabs of the replica
+    workload (about 3.3e6 particles) as one batched call, launch shape fixed
+    at 512-particle chunks."""
     import torch
 
     import paper_2403_01521_gb300 as qslab
     import workloads
-    sl = workloads.rbe_large()
-    slab = qslab.QSlab(0, "fp32c").configure(sl.box, sl.alpha, qslab.load_soe(16), rbe=(200, 5))
-    pos = torch.tensor(sl.pos, device="cuda", dtype=torch.float32)
-    q = torch.tensor(sl.q, device="cuda", dtype=torch.float32)
-    for _ in range(2):
-        e, _, _ = slab.compute(pos, q)
+    soe = qslab.load_soe(16)
+    if kind == "batched":
+        reps = workloads.replicas()[:128]
+        off = np.concatenate([[0], np.cumsum([r.N for r in reps])]).astype(np.int64)
+        boxes = np.array([r.box for r in reps])
+        pos = torch.tensor(np.concatenate([r.pos for r in reps]), device="cuda", dtype=torch.float32)
+        q = torch.tensor(np.concatenate([r.q for r in reps]), device="cuda", dtype=torch.float32)
+        slab = qslab.QSlab(0, "fp32c").configure(reps[0].box, 0.25, soe, rbe=(200, 5)).tuning(512, 0)
+        for _ in range(2):
+            e, _, _ = slab.compute_batched(pos, q, off, boxes)
+        E = float(e.sum().item())
+    else:
+        sl = workloads.rbe_large()
+        slab = qslab.QSlab(0, "fp32c").configure(sl.box, sl.alpha, soe, rbe=(200, 5))
+        pos = torch.tensor(sl.pos, device="cuda", dtype=torch.float32)
+        q = torch.tensor(sl.q, device="cuda", dtype=torch.float32)
+        for _ in range(2):
+            e, _, _ = slab.compute(pos, q)
+        E = float(e.item())
     slab.check()
     torch.cuda.synchronize()
-    print("profile case done, E =", float(e.item()))
+    print("profile case", kind, "done, E =", E)
     return 0
 
 
@@ -464,11 +480,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-replica batched measurement")
-    ap.add_argument("--profile-case", action="store_true",
+    ap.add_argument("--profile-case", nargs="?", const="single", choices=["single", "batched"],
                     help="only run two FP32 random-batch calls (for profilers)")
     args = ap.parse_args()
     if args.profile_case:
-        return profile_case()
+        return profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

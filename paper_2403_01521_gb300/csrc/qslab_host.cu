@@ -43,7 +43,7 @@ struct Tables {
   std::vector<RepInfo> info;
   std::vector<int32_t> chunk_rep, zchunk_rep, gstart, group_rep, list;
   std::vector<double> cdf;
-  int Kpad = 32, KR = 32, nkr = 1, L = 32, L0 = 512;
+  int Kpad = 32, KR = 32, nkr = 1, L = 32, L0 = 128;
   int nchunks = 0, nz = 0, ngroups = 0;
   int64_t N = 0;
   // device layout of the table buffer
@@ -389,7 +389,7 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
     L = (int)(want < 32 ? 32 : (want > Lmax ? Lmax : want));
   }
   t.L = L;
-  t.L0 = 512;
+  t.L0 = 128;   // k = 0 chunks: short sequential loops, many threads
   // chunks, k = 0 chunks and carry groups per replica
   for (int r = 0; r < R; ++r) {
     RepInfo& ri = t.info[r];
@@ -632,7 +632,7 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   if (ev) cudaEventRecord(ev[2], st);
   launch_kspace<T>(P.sp, rp, modes, c->pairs, zs, dz, qs, xh, yh, agg, carry, dec, part, st,
                    ev ? ev + 3 : nullptr);
-  nl += 7;
+  nl += 8;
   QS_CUDA(cudaStreamWaitEvent(st, c->join, 0));
   if (ev) cudaEventRecord(ev[6], st);
   launch_combine<T>(rp, P.sp.nkr, part, phi0, fz0, qs, perm, echunk, phi, force, energies, st);

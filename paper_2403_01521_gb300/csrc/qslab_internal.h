@@ -125,7 +125,9 @@ void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes);
 // result.
 int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaStream_t st);
 
-// ---- kernels (qslab_kernels.cu)
+// ---- kernels (qslab_prep.cu: checks, gather, combine, mode tables;
+//      qslab_kspace.cu: k != 0 passes; qslab_carry.cu: their carries;
+//      qslab_kzero.cu: the k = 0 term)
 // Input checks and z keys, one CTA per k-space chunk; per-replica sums of q
 // and |q| (sums[2r], sums[2r+1]); rid (may be NULL) receives the replica of
 // every particle.
@@ -160,6 +162,18 @@ void launch_kspace(const ScanPlan& plan, const Reps& rp, const ModeTab<T>& modes
                    cudaStream_t st, cudaEvent_t* ev3);  // ev3: 3 events or NULL
 // bytes of the chunk-to-chunk decay tables and carry-group transfers
 size_t kspace_decay_bytes(const ScanPlan& pl, const Reps& rp, int fp64);
+// (qslab_carry.cu) the carries of every chunk from the pass-A aggregates;
+// dec: kspace_decay_bytes of scratch
+template <typename T>
+void launch_kspace_carries(const ScanPlan& pl, const Reps& rp, const PairTab& pairs, const T* zs,
+                           const T* kk, const Cplx<T>* agg, Cplx<T>* carry, void* dec,
+                           cudaStream_t st);
+// pair decays between chunk reference points (see qslab_carry.cu); pdec:
+// [2][nchunks][np] complex and gaps (may be NULL): [2][nchunks], both in the
+// carry type
+template <typename T>
+void launch_pair_decay(const Reps& rp, int zero_chunks, int np, const T* zs, const PairTab& pairs,
+                       void* pdec, void* gaps, cudaStream_t st);
 
 // phi0 / fz0: per sorted particle, in the carry type (FP64 on the FP64 path,
 // double-float on the FP32 path)

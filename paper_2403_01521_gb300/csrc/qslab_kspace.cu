@@ -1,0 +1,355 @@
+// qslab device kernels: input checks and sort keys, the sorted gather, the
+// k != 0 SOE scans (chunk aggregates, carries, bidirectional recurrences with
+// the fused potential/force gather), the k = 0 term, the final combine and
+// the random-batch k-sampler.
+//
+// Method: Gan, Gao, Liang, Xu, "Fast algorithm for quasi-2D Coulomb systems".
+// For a mode k and beta in {k, alpha s_1, ..., alpha s_M} the pair sums over
+// j < i and j > i of u_j e^{-beta |z_i - z_j|}, u_j = q_j e^{-i k.rho_j}, are
+// first-order linear recurrences over the z-sorted particles (Eqs. 3.28-3.30,
+// Remark 3.3). Forces need both directions (Appendix E). Here the sorted
+// particles are cut into chunks of L; one CTA owns one chunk and a range of
+// modes, one thread one mode:
+//   pass A   chunk aggregates sum_j u_j e^{-beta(z_end - z_j)} (forward) and
+//            sum_j u_j e^{-beta(z_j - z_start)} (backward), by dot products
+//            with k-independent exponential tables kept in shared memory;
+//   carries  an FP64 recurrence over chunks per (mode, beta, direction);
+//   pass B   the recurrences over the chunk from the carried state, with the
+//            gather of Eq. 3.21 / Appendix E fused: per particle and mode the
+//            potential and force contributions are formed, summed over the
+//            warp's 32 modes by shuffles and over warps in shared memory.
+// SOE nodes come in conjugate pairs; one representative a_p per pair drives
+// two complex states, fed by the real inputs q cos(k.rho) and q sin(k.rho),
+// whose combination 2 Re(c F(a)) - 2i Re(c F(b)) equals the pair's
+// contribution (the conjugate partner needs no scan of its own).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qslab_df.cuh"
+#include "qslab_geom.cuh"
+#include "qslab_internal.h"
+#include "qslab_math.cuh"
+
+namespace qslab {
+
+// ============================================================ k != 0 scans
+
+// Shared-memory layout of one chunk: L particle records (plus one more whose
+// dz belongs to the next chunk's first particle), the exponential tables in
+// particle-major order (all pairs of one particle are contiguous), and in
+// pass B the per-warp output slots.
+template <typename T>
+struct __align__(4 * sizeof(T)) Rec {
+  typename PhaseT<T>::type xh, yh;   // fixed-point x/Lx, y/Ly
+  T q, dz;
+};
+
+template <typename T>
+struct ChunkSmem {
+  Cplx<T>* tab;   // pass B: [L+1][NP] decays; pass A: [L][2][NP] (E_f, E_b)
+  Rec<T>* rec;    // [L+1]
+  T* zl;          // [L]
+  T* slots;       // pass B: [W][L][4]
+};
+
+__host__ __device__ inline size_t align_up(size_t x) { return (x + 31) & ~size_t(31); }
+
+template <typename T>
+__host__ __device__ inline size_t chunk_smem_bytes(int L, int NP, int W, bool passB) {
+  size_t b = 0;
+  b += align_up(sizeof(Cplx<T>) * (size_t)NP * (passB ? (L + 1) : 2 * L));
+  b += align_up(sizeof(Rec<T>) * (L + 1));
+  b += align_up(sizeof(T) * L);
+  if (passB) b += align_up(sizeof(T) * (size_t)W * L * 4);
+  return b;
+}
+
+template <typename T>
+__device__ inline ChunkSmem<T> carve(char* base, int L, int NP, int W, bool passB) {
+  ChunkSmem<T> s;
+  char* p = base;
+  s.tab = reinterpret_cast<Cplx<T>*>(p);
+  p += align_up(sizeof(Cplx<T>) * (size_t)NP * (passB ? (L + 1) : 2 * L));
+  s.rec = reinterpret_cast<Rec<T>*>(p); p += align_up(sizeof(Rec<T>) * (L + 1));
+  s.zl = reinterpret_cast<T*>(p); p += align_up(sizeof(T) * L);
+  s.slots = passB ? reinterpret_cast<T*>(p) : nullptr;
+  return s;
+}
+
+template <typename T>
+struct KParams {
+  ScanPlan plan;
+  Reps rp;
+  ModeTab<T> modes;
+  size_t kstride;   // R * Kpad: stride between the planes of modes.cp
+  const T* zs;
+  const T* dz;
+  const T* qs;
+  const typename PhaseT<T>::type* xh;
+  const typename PhaseT<T>::type* yh;
+  Cplx<T>* agg;     // [2][nchunks][nstates][Kpad]
+  Cplx<T>* carry;   // same layout
+  T* part;          // [nkr][4][N]
+};
+
+// Per-thread (per-mode) coefficients.
+template <typename T, int NP>
+struct ModeCoef {
+  int32_t mx, my;
+  T kx, ky, kk, ck, ckk, sY, sZ;
+  T cpr[NP], cpi[NP], cbr[NP], cbi[NP];
+};
+
+template <typename T, int NP>
+__device__ __forceinline__ void load_mode(const ModeTab<T>& mt, size_t kstride, size_t m,
+                                          ModeCoef<T, NP>& c) {
+  c.mx = mt.mx[m]; c.my = mt.my[m];
+  c.kx = mt.kx[m]; c.ky = mt.ky[m]; c.kk = mt.kk[m];
+  c.ck = mt.ck[m]; c.ckk = mt.ckk[m]; c.sY = mt.sY[m]; c.sZ = mt.sZ[m];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    c.cpr[p] = mt.cp[(0 * NP + p) * kstride + m];
+    c.cpi[p] = mt.cp[(1 * NP + p) * kstride + m];
+    c.cbr[p] = mt.cp[(2 * NP + p) * kstride + m];
+    c.cbi[p] = mt.cp[(3 * NP + p) * kstride + m];
+  }
+}
+
+// Load the chunk's particles into shared memory.
+template <typename T>
+__device__ inline void load_chunk(const KParams<T>& P, ChunkSmem<T>& s,
+                                  int64_t start, int cnt) {
+  const int64_t N = P.rp.N;
+  for (int t = threadIdx.x; t <= cnt; t += blockDim.x) {
+    const int64_t i = start + t;
+    Rec<T> r;
+    r.dz = (i < N) ? P.dz[i] : (T)0;
+    if (t < cnt) {
+      r.xh = P.xh[i];
+      r.yh = P.yh[i];
+      r.q = P.qs[i];
+      s.zl[t] = P.zs[i];
+    } else {
+      r.xh = 0; r.yh = 0; r.q = 0;
+    }
+    s.rec[t] = r;
+  }
+}
+
+// ------------------------------------------------------------------ pass A
+template <typename T, int NP>
+__global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
+  extern __shared__ __align__(32) char smem[];
+  const ScanPlan& pl = P.plan;
+  const int c = blockIdx.x;
+  const CRange ch = kchunk(P.rp, c);
+  const int64_t start = ch.start;
+  const int cnt = ch.cnt;
+  const int Kpad = P.rp.Kpad;
+  ChunkSmem<T> s = carve<T>(smem, P.rp.L, NP, 0, false);
+  load_chunk<T>(P, s, start, cnt);
+  __syncthreads();
+  // E tables: [t][0][p] = e^{-a_p (z_end - z_t)}, [t][1][p] = e^{-a_p (z_t - z_start)}
+  const T zend = s.zl[cnt - 1], zst = s.zl[0];
+  for (int e = threadIdx.x; e < NP * cnt; e += blockDim.x) {
+    const int t = e / NP, p = e - t * NP;
+    const T ar = (T)pairs.a_re[p], ai = (T)pairs.a_im[p];
+    s.tab[(2 * t) * NP + p] = cexp_neg(ar, ai, zend - s.zl[t]);
+    s.tab[(2 * t + 1) * NP + p] = cexp_neg(ar, ai, s.zl[t] - zst);
+  }
+  __syncthreads();
+  const int m = blockIdx.y * pl.KR + threadIdx.x;
+  ModeCoef<T, NP> mc;
+  load_mode<T, NP>(P.modes, P.kstride, (size_t)ch.r * Kpad + m, mc);
+  Cplx<T> f0 = {0, 0}, b0 = {0, 0};
+  Cplx<T> fa[NP], fb[NP], ba[NP], bb[NP];
+#pragma unroll
+  for (int p = 0; p < NP; ++p) fa[p] = fb[p] = ba[p] = bb[p] = Cplx<T>{0, 0};
+  for (int t = 0; t < cnt; ++t) {
+    const Rec<T> r = s.rec[t];
+    T cs, sn;
+    sincos_turns(phase_turns(mc.mx, mc.my, r.xh, r.yh), cs, sn);
+    const T a = r.q * cs, b = r.q * sn;   // u = a - i b
+    const T zt = s.zl[t];
+    const T ef = exp_neg(mc.kk * (zend - zt));
+    const T eb = exp_neg(mc.kk * (zt - zst));
+    f0.re = fma(ef, a, f0.re); f0.im = fma(-ef, b, f0.im);
+    b0.re = fma(eb, a, b0.re); b0.im = fma(-eb, b, b0.im);
+    const Cplx<T>* Et = s.tab + 2 * t * NP;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const Cplx<T> Ef = Et[p];
+      const Cplx<T> Eb = Et[NP + p];
+      fa[p].re = fma(Ef.re, a, fa[p].re); fa[p].im = fma(Ef.im, a, fa[p].im);
+      fb[p].re = fma(Ef.re, b, fb[p].re); fb[p].im = fma(Ef.im, b, fb[p].im);
+      ba[p].re = fma(Eb.re, a, ba[p].re); ba[p].im = fma(Eb.im, a, ba[p].im);
+      bb[p].re = fma(Eb.re, b, bb[p].re); bb[p].im = fma(Eb.im, b, bb[p].im);
+    }
+  }
+  const int S = pl.nstates;
+  const size_t dirstride = (size_t)P.rp.nchunks * S * Kpad;
+  Cplx<T>* af = P.agg + ((size_t)c * S) * Kpad + m;
+  Cplx<T>* ab = af + dirstride;
+  af[0] = f0;
+  ab[0] = b0;
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    af[(size_t)(1 + 2 * p) * Kpad] = fa[p];
+    af[(size_t)(2 + 2 * p) * Kpad] = fb[p];
+    ab[(size_t)(1 + 2 * p) * Kpad] = ba[p];
+    ab[(size_t)(2 + 2 * p) * Kpad] = bb[p];
+  }
+}
+
+// ------------------------------------------------------------------ pass B
+template <typename T, int NP>
+__global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
+  extern __shared__ __align__(32) char smem[];
+  const ScanPlan& pl = P.plan;
+  const int c = blockIdx.x;
+  const int W = pl.KR / kWarp;
+  const int L = P.rp.L, Kpad = P.rp.Kpad;
+  const CRange ch = kchunk(P.rp, c);
+  const int64_t start = ch.start;
+  const int cnt = ch.cnt;
+  ChunkSmem<T> s = carve<T>(smem, L, NP, W, true);
+  load_chunk<T>(P, s, start, cnt);
+  __syncthreads();
+  // per-step decays [t][p] = e^{-a_p dz_t}, t = 0..cnt (t = cnt: next chunk)
+  for (int e = threadIdx.x; e < NP * (cnt + 1); e += blockDim.x) {
+    const int t = e / NP, p = e - t * NP;
+    s.tab[t * NP + p] = cexp_neg((T)pairs.a_re[p], (T)pairs.a_im[p], s.rec[t].dz);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int m = blockIdx.y * pl.KR + threadIdx.x;
+  ModeCoef<T, NP> mc;
+  load_mode<T, NP>(P.modes, P.kstride, (size_t)ch.r * Kpad + m, mc);
+  const int S = pl.nstates;
+  const size_t dirstride = (size_t)P.rp.nchunks * S * Kpad;
+  T* slot = s.slots + (size_t)w * L * 4;
+
+  for (int dir = 0; dir < 2; ++dir) {
+    const Cplx<T>* cin = P.carry + dir * dirstride + ((size_t)c * S) * Kpad + m;
+    Cplx<T> g0 = cin[0];
+    Cplx<T> ga[NP], gb[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      ga[p] = cin[(size_t)(1 + 2 * p) * Kpad];
+      gb[p] = cin[(size_t)(2 + 2 * p) * Kpad];
+    }
+    const T zsign = dir == 0 ? (T)1 : (T)-1;
+    for (int n0 = 0; n0 < cnt; n0 += 4) {
+      T buf[16];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + j;
+        if (n < cnt) {
+          const int t = dir == 0 ? n : cnt - 1 - n;
+          const int td = dir == 0 ? t : t + 1;      // index of the decay to apply
+          const Rec<T> r = s.rec[t];
+          const T dzd = dir == 0 ? r.dz : s.rec[td].dz;
+          T cs, sn;
+          sincos_turns(phase_turns(mc.mx, mc.my, r.xh, r.yh), cs, sn);
+          const T a = r.q * cs, b = r.q * sn;
+          // beta = k: real decay e^{-k dz}, complex input u = a - i b, as
+          // G <- G + (u - e G) with e = 1 - e^{-k dz} (see one_minus_exp_neg)
+          const T ek = one_minus_exp_neg(mc.kk * dzd);
+          g0.re += fma(-ek, g0.re, a);
+          g0.im += fma(-ek, g0.im, -b);
+          T Yr = mc.ck * g0.re, Yi = mc.ck * g0.im;
+          T Zr = mc.ckk * g0.re, Zi = mc.ckk * g0.im;
+          const Cplx<T>* dt = s.tab + td * NP;
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            const Cplx<T> d = dt[p];
+            const T ar = fma(d.re, ga[p].re, fma(-d.im, ga[p].im, a));
+            const T ai = fma(d.re, ga[p].im, d.im * ga[p].re);
+            const T br = fma(d.re, gb[p].re, fma(-d.im, gb[p].im, b));
+            const T bi = fma(d.re, gb[p].im, d.im * gb[p].re);
+            ga[p].re = ar; ga[p].im = ai; gb[p].re = br; gb[p].im = bi;
+            Yr = fma(mc.cpr[p], ar, fma(-mc.cpi[p], ai, Yr));
+            Yi = fma(-mc.cpr[p], br, fma(mc.cpi[p], bi, Yi));
+            Zr = fma(mc.cbr[p], ar, fma(-mc.cbi[p], ai, Zr));
+            Zi = fma(-mc.cbr[p], br, fma(mc.cbi[p], bi, Zi));
+          }
+          // the sums above include j = i; remove it (coefficients sY, sZ times u_i)
+          Yr = fma(-mc.sY, a, Yr); Yi = fma(mc.sY, b, Yi);
+          Zr = fma(-mc.sZ, a, Zr); Zi = fma(mc.sZ, b, Zi);
+          const T W2 = cs * Yi + sn * Yr;         // Im e^{i k.rho} Y
+          buf[4 * j + 0] = cs * Yr - sn * Yi;     // Re e^{i k.rho} Y
+          buf[4 * j + 1] = mc.kx * W2;
+          buf[4 * j + 2] = mc.ky * W2;
+          buf[4 * j + 3] = zsign * (cs * Zr - sn * Zi);   // Re e^{i k.rho} Z
+        } else {
+          buf[4 * j + 0] = buf[4 * j + 1] = buf[4 * j + 2] = buf[4 * j + 3] = (T)0;
+        }
+      }
+      const T v = warp_reduce16<T>(buf, lane);
+      const int idx = lane >> 1, g = idx >> 2, qn = idx & 3;
+      if (!(lane & 1) && n0 + g < cnt) {
+        const int tt = dir == 0 ? n0 + g : cnt - 1 - (n0 + g);
+        if (dir == 0) slot[tt * 4 + qn] = v;
+        else slot[tt * 4 + qn] += v;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // sum the warps' slots and write this mode range's partial outputs
+  T* out = P.part + (size_t)blockIdx.y * 4 * P.rp.N;
+  for (int e = threadIdx.x; e < cnt * 4; e += blockDim.x) {
+    const int t = e >> 2, qn = e & 3;
+    T acc = 0;
+    for (int ww = 0; ww < W; ++ww) acc += s.slots[((size_t)ww * L + t) * 4 + qn];
+    out[(size_t)qn * P.rp.N + start + t] = acc;
+  }
+}
+
+template <typename T, int NP>
+static void kspace_run(const KParams<T>& P, const PairTab& pairs, void* dec,
+                       cudaStream_t st, cudaEvent_t* ev) {
+  const ScanPlan& pl = P.plan;
+  const Reps& rp = P.rp;
+  dim3 grid(rp.nchunks, pl.nkr);
+  const size_t smA = chunk_smem_bytes<T>(rp.L, NP, 0, false);
+  const size_t smB = chunk_smem_bytes<T>(rp.L, NP, pl.KR / kWarp, true);
+  cudaFuncSetAttribute(kspace_aggregate_kernel<T, NP>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
+  cudaFuncSetAttribute(kspace_final_kernel<T, NP>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB);
+  kspace_aggregate_kernel<T, NP><<<grid, pl.KR, smA, st>>>(P, pairs);
+  if (ev) cudaEventRecord(ev[0], st);
+  launch_kspace_carries<T>(pl, rp, pairs, P.zs, P.modes.kk, P.agg, P.carry, dec, st);
+  if (ev) cudaEventRecord(ev[1], st);
+  kspace_final_kernel<T, NP><<<grid, pl.KR, smB, st>>>(P, pairs);
+  if (ev) cudaEventRecord(ev[2], st);
+}
+
+template <typename T>
+void launch_kspace(const ScanPlan& plan, const Reps& rp, const ModeTab<T>& modes,
+                   const PairTab& pairs, const T* zs, const T* dz, const T* qs,
+                   const typename PhaseT<T>::type* xh,
+                   const typename PhaseT<T>::type* yh, Cplx<T>* agg,
+                   Cplx<T>* carry, void* dec, T* part,
+                   cudaStream_t st, cudaEvent_t* ev3) {
+  KParams<T> P{plan, rp, modes, (size_t)rp.R * rp.Kpad, zs, dz, qs, xh, yh, agg, carry, part};
+  switch (plan.np) {
+    case 4: kspace_run<T, 4>(P, pairs, dec, st, ev3); break;
+    case 8: kspace_run<T, 8>(P, pairs, dec, st, ev3); break;
+    case 12: kspace_run<T, 12>(P, pairs, dec, st, ev3); break;
+    default: kspace_run<T, 16>(P, pairs, dec, st, ev3); break;
+  }
+}
+
+// ============================================================ instantiations
+template void launch_kspace<float>(const ScanPlan&, const Reps&, const ModeTab<float>&,
+                                   const PairTab&, const float*, const float*, const float*,
+                                   const uint32_t*, const uint32_t*, Cplx<float>*, Cplx<float>*,
+                                   void*, float*, cudaStream_t, cudaEvent_t*);
+template void launch_kspace<double>(const ScanPlan&, const Reps&, const ModeTab<double>&,
+                                    const PairTab&, const double*, const double*, const double*,
+                                    const uint64_t*, const uint64_t*, Cplx<double>*,
+                                    Cplx<double>*, void*, double*, cudaStream_t, cudaEvent_t*);
+
+}  // namespace qslab

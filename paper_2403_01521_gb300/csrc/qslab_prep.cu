@@ -1,0 +1,359 @@
+// qslab device kernels around the scans: input checks and sort keys, the
+// sorted gather, the final combine with the energy reduction, and the mode
+// tables (full k-sum list or the random-batch k-sampler).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qslab_df.cuh"
+#include "qslab_geom.cuh"
+#include "qslab_internal.h"
+#include "qslab_math.cuh"
+
+namespace qslab {
+
+// ====================================================================== prep
+
+template <typename T> struct KeyOf;
+template <> struct KeyOf<float> {
+  using type = uint32_t;
+  __device__ static type key(float z) { return __float_as_uint(z == 0.0f ? 0.0f : z); }
+};
+template <> struct KeyOf<double> {
+  using type = uint64_t;
+  __device__ static type key(double z) {
+    return (uint64_t)__double_as_longlong(z == 0.0 ? 0.0 : z);
+  }
+};
+
+// One CTA per k-space chunk (chunks are contiguous in the caller's order as
+// well): finiteness and z-range checks, the z keys, the replica index and
+// the replica's sums of q and |q|.
+template <typename T>
+__global__ void prepare_kernel(Reps rp, const T* __restrict__ pos, const T* __restrict__ q,
+                               typename KeyOf<T>::type* keys, uint32_t* vals, int32_t* rid,
+                               double* sums, unsigned* status) {
+  __shared__ double red[2][32];
+  const CRange ch = kchunk(rp, blockIdx.x);
+  const double Lz = rp.info[ch.r].Lz;
+  double sq = 0.0, sa = 0.0;
+  unsigned flags = 0;
+  for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
+    const int64_t i = ch.start + t;
+    const T x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2], qi = q[i];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) flags |= kStNonfinite;
+    else if (!(z >= (T)0) || !((double)z <= Lz)) flags |= kStZRange;
+    keys[i] = KeyOf<T>::key(z);
+    vals[i] = (uint32_t)i;
+    if (rid) rid[i] = ch.r;
+    sq += (double)qi;
+    sa += fabs((double)qi);
+  }
+  if (flags) atomicOr(status, flags);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 16; o; o >>= 1) {
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+  }
+  if (lane == 0) { red[0][w] = sq; red[1][w] = sa; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { a += red[0][j]; b += red[1][j]; }
+    atomicAdd(&sums[2 * ch.r], a);
+    atomicAdd(&sums[2 * ch.r + 1], b);
+  }
+}
+
+template <typename T>
+void launch_prepare(const Reps& rp, const T* pos, const T* q, void* keys, uint32_t* vals,
+                    int32_t* rid, double* sums, unsigned* status, cudaStream_t st) {
+  prepare_kernel<T><<<rp.nchunks, chunk_threads(rp.L), 0, st>>>(
+      rp, pos, q, static_cast<typename KeyOf<T>::type*>(keys), vals, rid, sums, status);
+}
+
+__global__ void check_neutral_kernel(int R, const double* sums, double tol, unsigned* status,
+                                     uint64_t* ctr) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < R && tol >= 0.0 && fabs(sums[2 * r]) > tol * sums[2 * r + 1])
+    atomicOr(status, kStNonneutral);
+  if (ctr && r == 0) {
+    const uint64_t c = ctr[0];
+    ctr[1] = c;
+    ctr[0] = c + 1;
+  }
+}
+
+void launch_check_neutral(const Reps& rp, const double* sums, double tol, unsigned* status,
+                          uint64_t* ctr, cudaStream_t st) {
+  check_neutral_kernel<<<(rp.R + 255) / 256, 256, 0, st>>>(rp.R, sums, tol, status, ctr);
+}
+
+__global__ void rep_keys_kernel(int64_t N, const uint32_t* __restrict__ perm,
+                                const int32_t* __restrict__ rid, uint32_t* keys) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    keys[i] = (uint32_t)rid[perm[i]];
+}
+
+void launch_rep_keys(int64_t N, const uint32_t* perm, const int32_t* rid, uint32_t* keys,
+                     cudaStream_t st) {
+  int blocks = (int)((N + 255) / 256);
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  rep_keys_kernel<<<blocks, 256, 0, st>>>(N, perm, rid, keys);
+}
+
+// ==================================================================== gather
+
+__device__ __forceinline__ uint32_t to_fixed(float x, double L) {
+  double f = (double)x / L;
+  f -= floor(f);
+  if (!(f < 1.0)) f = 0.0;
+  return (uint32_t)(uint64_t)(f * 4294967296.0);
+}
+__device__ __forceinline__ uint64_t to_fixed(double x, double L) {
+  double f = x / L;
+  f -= floor(f);
+  if (!(f < 1.0)) f = 0.0;
+  return (uint64_t)(f * 18446744073709551616.0);
+}
+
+// One CTA per k-space chunk: the sorted SoA arrays, with dz = 0 at the first
+// particle of every replica.
+template <typename T>
+__global__ void gather_kernel(Reps rp, const T* __restrict__ pos, const T* __restrict__ q,
+                              const uint32_t* __restrict__ perm, T* zs, T* dz, T* qs,
+                              typename PhaseT<T>::type* xh, typename PhaseT<T>::type* yh,
+                              int32_t* perm_out) {
+  const CRange ch = kchunk(rp, blockIdx.x);
+  const double Lx = rp.info[ch.r].Lx, Ly = rp.info[ch.r].Ly;
+  for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
+    const int64_t i = ch.start + t;
+    const uint32_t o = perm[i];
+    const T z = pos[3 * (int64_t)o + 2];
+    zs[i] = z;
+    dz[i] = (t == 0 && ch.first) ? (T)0 : z - pos[3 * (int64_t)perm[i - 1] + 2];
+    qs[i] = q[o];
+    xh[i] = to_fixed(pos[3 * (int64_t)o], Lx);
+    yh[i] = to_fixed(pos[3 * (int64_t)o + 1], Ly);
+    perm_out[i] = (int32_t)o;
+  }
+}
+
+template <typename T>
+void launch_gather(const Reps& rp, const T* pos, const T* q, const uint32_t* perm, T* zs,
+                   T* dz, T* qs, typename PhaseT<T>::type* xh,
+                   typename PhaseT<T>::type* yh, int32_t* perm_out, cudaStream_t st) {
+  gather_kernel<T><<<rp.nchunks, chunk_threads(rp.L), 0, st>>>(rp, pos, q, perm, zs, dz, qs,
+                                                                xh, yh, perm_out);
+}
+
+// ================================================================== combine
+
+// One CTA per k-space chunk: sums the mode ranges' partial outputs, adds the
+// k = 0 term and the j = i constant of the chunk's replica, scatters the
+// potential and force to the caller's order and writes the chunk's energy
+// 1/2 sum q_i phi_i.
+template <typename T>
+__global__ void combine_kernel(Reps rp, int nkr, const T* __restrict__ part,
+                               const typename CarryNum<T>::type* __restrict__ phi0,
+                               const typename CarryNum<T>::type* __restrict__ fz0,
+                               const T* __restrict__ qs, const int32_t* __restrict__ perm,
+                               double* echunk, T* phi_out, T* force_out) {
+  __shared__ double red[32];
+  const CRange ch = kchunk(rp, blockIdx.x);
+  const double diagq = rp.info[ch.r].diagq;
+  const int64_t N = rp.N;
+  double e = 0.0;
+  for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
+    const int64_t i = ch.start + t;
+    double ph = 0, fx = 0, fy = 0, fz = 0;
+    for (int r = 0; r < nkr; ++r) {
+      const T* b = part + (size_t)r * 4 * N;
+      ph += (double)b[i];
+      fx += (double)b[N + i];
+      fy += (double)b[2 * N + i];
+      fz += (double)b[3 * N + i];
+    }
+    const double qq = (double)qs[i];
+    ph += cn_to_double(phi0[i]) + qq * diagq;
+    fx *= qq; fy *= qq;
+    fz = fz * qq + cn_to_double(fz0[i]);
+    const int32_t o = perm[i];
+    if (phi_out) phi_out[o] = (T)ph;
+    if (force_out) {
+      force_out[3 * (int64_t)o] = (T)fx;
+      force_out[3 * (int64_t)o + 1] = (T)fy;
+      force_out[3 * (int64_t)o + 2] = (T)fz;
+    }
+    e += 0.5 * qq * ph;
+  }
+  for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[j];
+    echunk[blockIdx.x] = s;
+  }
+}
+
+// One warp per replica: the sum of its chunks' energies in a fixed order
+// (deterministic).
+__global__ void energy_rep_kernel(Reps rp, const double* echunk, double* energies) {
+  const int rep = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (rep >= rp.R) return;   // whole warps leave together
+  const RepInfo& ri = rp.info[rep];
+  double s = 0.0;
+  for (int j = lane; j < ri.nch; j += 32) s += echunk[ri.c0 + j];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) energies[rep] = s;
+}
+
+template <typename T>
+void launch_combine(const Reps& rp, int nkr, const T* part, const void* phi0v,
+                    const void* fz0v, const T* qs, const int32_t* perm, double* echunk,
+                    T* phi_out, T* force_out, double* energies, cudaStream_t st) {
+  using CN = typename CarryNum<T>::type;
+  const CN* phi0 = static_cast<const CN*>(phi0v);
+  const CN* fz0 = static_cast<const CN*>(fz0v);
+  combine_kernel<T><<<rp.nchunks, chunk_threads(rp.L), 0, st>>>(rp, nkr, part, phi0, fz0, qs, perm,
+                                                                 echunk, phi_out, force_out);
+  if (energies) {
+    const int64_t thr = (int64_t)rp.R * 32;
+    energy_rep_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(rp, echunk, energies);
+  }
+}
+
+// ========================================================= random-batch modes
+
+__device__ int upper_index(const double* cdf, int n, double u) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (u < cdf[mid]) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double uniform53(uint64_t w) {
+  return (double)(w >> 11) * 1.1102230246251565e-16;   // 2^-53
+}
+
+// Fill the mode tables; thread = (mode, replica). Full k-sum: (mx, my) from
+// the replica's half-plane list, weight 2 (k and -k), gam = (pi/A) C_k 2.
+// Random batch: (mx, my) drawn here (Philox4x64-10 with counter
+// (m, attempt, call, tag + replica * 2^32) and key (seed, 0); words 0,1 then
+// 2,3 are inverted through the replica's per-axis cumulative tables; the
+// origin is rejected), gam = (pi/A) (H/P) 2 alpha/(sqrt(pi) k) (Eq. 4.7 with
+// 4.9: the Gaussian of C_k cancels against e^{k^2/(4 alpha^2)}).
+template <typename T>
+__global__ void mode_coef_kernel(Reps rp, int npc, const int32_t* list, int rbe, uint64_t seed,
+                                 const uint64_t* ctr, const double* cdf, PairTab pr,
+                                 double alpha, ModeTab<T> mt, int32_t* sampled) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rep = blockIdx.y;
+  const int Kpad = rp.Kpad;
+  if (m >= Kpad) return;
+  const RepInfo& ri = rp.info[rep];
+  const int K = ri.K;
+  const double Lx = ri.Lx, Ly = ri.Ly;
+  const size_t mg = (size_t)rep * Kpad + m;
+  const size_t ks = (size_t)rp.R * Kpad;
+  const double pi = 3.14159265358979323846;
+  const double sqpi = 1.7724538509055160;
+  int mx = 0, my = 0;
+  if (m < K) {
+    if (!rbe) {
+      mx = list[2 * ((size_t)ri.list0 + m)];
+      my = list[2 * ((size_t)ri.list0 + m) + 1];
+    } else {
+      const double* cdfx = cdf + ri.cdfx0;
+      const double* cdfy = cdf + ri.cdfy0;
+      const uint64_t counter = ctr[1];
+      for (uint64_t attempt = 0; attempt < 64; ++attempt) {
+        U64x4 c;
+        c.v[0] = (uint64_t)m; c.v[1] = attempt; c.v[2] = counter;
+        c.v[3] = 0x52424531ull + ((uint64_t)rep << 32);
+        const U64x4 r = philox4x64_10(c, seed, 0ull);
+        const int ax = upper_index(cdfx, ri.nx, uniform53(r.v[0])) - ri.mxmax;
+        const int ay = upper_index(cdfy, ri.ny, uniform53(r.v[1])) - ri.mymax;
+        if (ax != 0 || ay != 0) { mx = ax; my = ay; break; }
+        const int bx = upper_index(cdfx, ri.nx, uniform53(r.v[2])) - ri.mxmax;
+        const int by = upper_index(cdfy, ri.ny, uniform53(r.v[3])) - ri.mymax;
+        if (bx != 0 || by != 0) { mx = bx; my = by; break; }
+      }
+      if (sampled) {
+        sampled[2 * ((size_t)rep * K + m)] = mx;
+        sampled[2 * ((size_t)rep * K + m) + 1] = my;
+      }
+    }
+  }
+  const bool live = (m < K) && (mx != 0 || my != 0);
+  const double kx = 2 * pi * mx / Lx, ky = 2 * pi * my / Ly;
+  const double k = live ? sqrt(kx * kx + ky * ky) : 1.0;
+  double gam = 0.0;
+  if (live) {
+    gam = rbe ? pi / (Lx * Ly) * (ri.H / K) * 2.0 * alpha / (sqpi * k)
+              : pi / (Lx * Ly) * 2.0 * (2.0 * alpha * exp(-k * k / (4.0 * alpha * alpha)) / (sqpi * k));
+  }
+  double ckk = 0.0, sY = 0.0, sZ = 0.0;
+  for (int p = 0; p < npc; ++p) {
+    double cr = 0, ci = 0, br = 0, bi = 0;
+    if (p < pr.np) {
+      const double ar = pr.a_re[p], ai = pr.a_im[p];
+      const double wr = pr.w_re[p], wi = pr.w_im[p];
+      const double dr = ar * ar - ai * ai - k * k, di = 2 * ar * ai;   // a^2 - k^2
+      const double dd = dr * dr + di * di;
+      const double qr = (wr * dr + wi * di) / dd, qi = (wi * dr - wr * di) / dd;  // w/(a^2-k^2)
+      ckk += pr.mult[p] * 2.0 * (ar * qr - ai * qi);     // sum over both nodes of 2 a w/(a^2-k^2)
+      cr = -2.0 * k * qr * pr.mult[p] * gam;             // m_p gam c_{k,p}
+      ci = -2.0 * k * qi * pr.mult[p] * gam;
+      br = cr * ar - ci * ai;                            // times a_p
+      bi = cr * ai + ci * ar;
+      sY += cr;
+      sZ += br;
+    }
+    mt.cp[((size_t)0 * npc + p) * ks + mg] = (T)cr;
+    mt.cp[((size_t)1 * npc + p) * ks + mg] = (T)ci;
+    mt.cp[((size_t)2 * npc + p) * ks + mg] = (T)br;
+    mt.cp[((size_t)3 * npc + p) * ks + mg] = (T)bi;
+  }
+  const double ck = gam * ckk;
+  mt.mx[mg] = mx;
+  mt.my[mg] = my;
+  mt.kx[mg] = (T)kx;
+  mt.ky[mg] = (T)ky;
+  mt.kk[mg] = (T)k;
+  mt.ck[mg] = (T)ck;
+  mt.ckk[mg] = (T)(ck * k);
+  mt.sY[mg] = (T)(ck + sY);
+  mt.sZ[mg] = (T)(ck * k + sZ);
+}
+
+template <typename T>
+void launch_mode_coef(const Reps& rp, int npc, const int32_t* list, int rbe, uint64_t seed,
+                      const uint64_t* ctr, const double* cdf, const PairTab& pairs,
+                      double alpha, ModeTab<T> modes, int32_t* sampled, cudaStream_t st) {
+  dim3 grid((rp.Kpad + 127) / 128, rp.R);
+  mode_coef_kernel<T><<<grid, 128, 0, st>>>(rp, npc, list, rbe, seed, ctr, cdf, pairs, alpha,
+                                            modes, sampled);
+}
+
+// ============================================================ instantiations
+#define QSLAB_INST(T, PH)                                                                        \
+  template void launch_prepare<T>(const Reps&, const T*, const T*, void*, uint32_t*, int32_t*,   \
+                                  double*, unsigned*, cudaStream_t);                             \
+  template void launch_gather<T>(const Reps&, const T*, const T*, const uint32_t*, T*, T*, T*,   \
+                                 PH*, PH*, int32_t*, cudaStream_t);                              \
+  template void launch_combine<T>(const Reps&, int, const T*, const void*, const void*,          \
+                                  const T*, const int32_t*, double*, T*, T*, double*,            \
+                                  cudaStream_t);                                                 \
+  template void launch_mode_coef<T>(const Reps&, int, const int32_t*, int, uint64_t,             \
+                                    const uint64_t*, const double*, const PairTab&, double,      \
+                                    ModeTab<T>, int32_t*, cudaStream_t);
+QSLAB_INST(float, uint32_t)
+QSLAB_INST(double, uint64_t)
+#undef QSLAB_INST
+
+}  // namespace qslab
