@@ -54,6 +54,21 @@ def algorithmic_instr(K, N, M):
     return float(K) * N * (24 * (M + 1) + 20)
 
 
+def kernel_sources_sha256(names):
+    """sha256 over the listed CUDA source files (in order): the traffic figure
+    recorded in profiles/traffic.json holds only while they are unchanged."""
+    import hashlib
+
+    from paper_2403_01521_gb300 import build as _b
+    if not names:
+        return None
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(_b.CSRC, n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples during the timed region."""
 
@@ -299,10 +314,7 @@ def run_ours(args):
         try:
             with open(tpath) as fh:
                 tj = json.load(fh)
-            from paper_2403_01521_gb300 import build as _b
-            import hashlib
-            h = hashlib.sha256(open(os.path.join(_b.CSRC, "qslab_kernels.cu"), "rb").read()).hexdigest()
-            if tj.get("kernels_sha256") == h:
+            if tj.get("sources_sha256") == kernel_sources_sha256(tj.get("sources", [])):
                 traffic = tj.get("recurrence_bytes_per_launch")
         except (OSError, ValueError):
             traffic = None

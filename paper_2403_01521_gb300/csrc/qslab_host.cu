@@ -41,13 +41,14 @@ struct Tables {
   int tune_L = 0, tune_KR = 0;
   // derived
   std::vector<RepInfo> info;
-  std::vector<int32_t> chunk_rep, zchunk_rep, gstart, group_rep, list;
+  std::vector<int32_t> chunk_rep, zchunk_rep, gstart, group_rep, zgstart, zgroup_rep, list;
   std::vector<double> cdf;
   int Kpad = 32, KR = 32, nkr = 1, L = 32, L0 = 128;
-  int nchunks = 0, nz = 0, ngroups = 0;
+  int nchunks = 0, nz = 0, ngroups = 0, nzgroups = 0;
   int64_t N = 0;
   // device layout of the table buffer
-  size_t o_info = 0, o_crep = 0, o_zrep = 0, o_gstart = 0, o_grep = 0, o_list = 0, o_cdf = 0,
+  size_t o_info = 0, o_crep = 0, o_zrep = 0, o_gstart = 0, o_grep = 0, o_zgstart = 0, o_zgrep = 0,
+         o_list = 0, o_cdf = 0,
          o_sampled = 0, o_modes = 0, bytes = 0;
 };
 
@@ -399,6 +400,18 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
     ri.z0 = (int32_t)t.zchunk_rep.size();
     ri.nz = (int32_t)((ri.n + (int64_t)t.L0 - 1) / t.L0);
     t.zchunk_rep.insert(t.zchunk_rep.end(), ri.nz, r);
+    // k = 0 carry groups: about sqrt(nz) groups of about sqrt(nz) chunks
+    ri.zg0 = (int32_t)t.zgroup_rep.size();
+    ri.nzg = 0;
+    if (ri.nz > 0) {
+      const int G = std::max(1, (int)std::lround(std::sqrt((double)ri.nz)));
+      const int g = (ri.nz + G - 1) / G;
+      for (int a = 0; a < ri.nz; a += g) {
+        t.zgstart.push_back(ri.z0 + a);
+        t.zgroup_rep.push_back(r);
+        ++ri.nzg;
+      }
+    }
     // groups: 32 groups when the chain has 64 chunks or more, else one
     ri.g0 = (int32_t)t.group_rep.size();
     ri.ng = 0;
@@ -416,6 +429,8 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
   t.nz = (int)t.zchunk_rep.size();
   t.ngroups = (int)t.group_rep.size();
   t.gstart.push_back(t.nchunks);
+  t.nzgroups = (int)t.zgroup_rep.size();
+  t.zgstart.push_back(t.nz);
   // device layout
   const size_t tsz = dp ? sizeof(double) : sizeof(float);
   size_t o = 0;
@@ -425,6 +440,8 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
   t.o_zrep = take(sizeof(int32_t) * t.nz);
   t.o_gstart = take(sizeof(int32_t) * t.gstart.size());
   t.o_grep = take(sizeof(int32_t) * std::max(t.ngroups, 1));
+  t.o_zgstart = take(sizeof(int32_t) * t.zgstart.size());
+  t.o_zgrep = take(sizeof(int32_t) * std::max(t.nzgroups, 1));
   t.o_list = take(sizeof(int32_t) * std::max<size_t>(t.list.size(), 2));
   t.o_cdf = take(sizeof(double) * std::max<size_t>(t.cdf.size(), 1));
   t.o_sampled = take(sizeof(int32_t) * 2 * (size_t)R * t.Kpad);
@@ -445,6 +462,8 @@ int upload_tables(const Tables& t, void* dst) {
   put(t.o_zrep, t.zchunk_rep.data(), sizeof(int32_t) * t.zchunk_rep.size());
   put(t.o_gstart, t.gstart.data(), sizeof(int32_t) * t.gstart.size());
   put(t.o_grep, t.group_rep.data(), sizeof(int32_t) * t.group_rep.size());
+  put(t.o_zgstart, t.zgstart.data(), sizeof(int32_t) * t.zgstart.size());
+  put(t.o_zgrep, t.zgroup_rep.data(), sizeof(int32_t) * t.zgroup_rep.size());
   put(t.o_list, t.list.data(), sizeof(int32_t) * t.list.size());
   put(t.o_cdf, t.cdf.data(), sizeof(double) * t.cdf.size());
   QS_CUDA(cudaMemcpy(dst, stage.data(), stage.size(), cudaMemcpyHostToDevice));
@@ -495,6 +514,9 @@ Reps reps_view(const qslab_ctx* c) {
   rp.zchunk_rep = reinterpret_cast<const int32_t*>(b + t.o_zrep);
   rp.gstart = reinterpret_cast<const int32_t*>(b + t.o_gstart);
   rp.group_rep = reinterpret_cast<const int32_t*>(b + t.o_grep);
+  rp.zgstart = reinterpret_cast<const int32_t*>(b + t.o_zgstart);
+  rp.zgroup_rep = reinterpret_cast<const int32_t*>(b + t.o_zgrep);
+  rp.nzgroups = t.nzgroups;
   return rp;
 }
 
@@ -533,7 +555,7 @@ Plan make_plan(const qslab_ctx* c, bool host_io) {
   P.off_carry = take(2 * tsz * aggn);
   P.off_dec = take(kspace_decay_bytes(s, rp, dp ? 1 : 0));
   P.off_part = take(tsz * 4 * (size_t)s.nkr * N);
-  P.off_k0 = take(8 * kzero_work_doubles(t.nz, t.R, c->pairs.np));
+  P.off_k0 = take(8 * kzero_work_doubles(t.nz, t.nzgroups, t.R, c->pairs.np));
   P.off_phi0 = take(8 * (size_t)N);
   P.off_fz0 = take(8 * (size_t)N);
   P.off_echunk = take(8 * (size_t)t.nchunks);
@@ -616,7 +638,7 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   QS_CUDA(cudaEventRecord(c->fork, st));
   QS_CUDA(cudaStreamWaitEvent(c->side, c->fork, 0));
   launch_kzero<T>(rp, c->pairs, c->alpha, zs, dz, qs, k0w, phi0, fz0, c->side);
-  nl += 4;
+  nl += 6;
   if (ev) cudaEventRecord(ev[8], c->side);
   QS_CUDA(cudaEventRecord(c->join, c->side));
   // mode tables: once per configuration for the full k-sum, every call for RBE

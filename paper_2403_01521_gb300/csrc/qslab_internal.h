@@ -80,6 +80,7 @@ struct RepInfo {
   int32_t c0, nch;        // k-space chunks [c0, c0 + nch)
   int32_t z0, nz;         // k = 0 chunks [z0, z0 + nz)
   int32_t g0, ng;         // carry groups [g0, g0 + ng)
+  int32_t zg0, nzg;       // k = 0 carry groups [zg0, zg0 + nzg)
   int32_t K;              // modes (half-plane list length, or P)
   int32_t list0;          // offset (in modes) into the concatenated full-k lists
   int32_t cdfx0, nx;      // sampler tables: offsets into the concatenated
@@ -92,7 +93,7 @@ struct RepInfo {
 struct Reps {
   int R;
   int L, L0;              // particles per k-space / k = 0 chunk
-  int nchunks, nzchunks, ngroups;
+  int nchunks, nzchunks, ngroups, nzgroups;
   int Kpad;               // modes per replica (multiple of 32)
   int64_t N;              // particles in all replicas
   const RepInfo* info;        // [R]
@@ -100,6 +101,8 @@ struct Reps {
   const int32_t* zchunk_rep;  // [nzchunks]
   const int32_t* gstart;      // [ngroups + 1] first k-space chunk of each carry group
   const int32_t* group_rep;   // [ngroups]
+  const int32_t* zgstart;     // [nzgroups + 1] first k = 0 chunk of each k = 0 carry group
+  const int32_t* zgroup_rep;  // [nzgroups]
 };
 
 // Status flags set by kernels (bitwise OR into a device word).
@@ -181,7 +184,7 @@ template <typename T>
 void launch_kzero(const Reps& rp, const PairTab& pairs, double alpha, const T* zs,
                   const T* dz, const T* qs, double* work, void* phi0, void* fz0,
                   cudaStream_t st);
-size_t kzero_work_doubles(int nzchunks, int R, int np);
+size_t kzero_work_doubles(int nzchunks, int nzgroups, int R, int np);
 
 // Potential, forces and per-chunk energies (echunk[nchunks]) back in the
 // caller's order; energies[r] (if not NULL) = the sum over replica r's chunks.

@@ -110,18 +110,19 @@ __global__ void kzero_aggregate_kernel(K0Params Q, PairTab pr, const T* zs,
   if (valid && p == 0) { csum[2 * c] = q0; csum[2 * c + 1] = q1; }
 }
 
-// Carries of the k = 0 scans, one CTA per replica. The per-chunk update of
-// a pair's state (S, H) is affine, S' = d S + S_c, H' = d (H + g S) + H_c
-// (d the chunk's decay, g its gap), and so is any run of chunks:
-// (S, H) -> (D S + A_S, D (H + G S) + A_H). The replica's chunks are cut
-// into kK0Group groups per (direction, pair) chain; (1) every thread
-// composes its group's transfer (D, G, A_S, A_H) from the chunk aggregates,
-// (2) one thread per chain runs the short chain over the groups in shared
-// memory, (3) every thread replays its group from its input and writes the
-// carry entering each chunk. The last warp does the same for the chunk sums
-// of q and q z (per-chunk prefixes and the replica's totals).
-constexpr int kK0Chains = 512;   // (direction, pair, group) threads per CTA
-
+// Carries of the k = 0 scans. The per-chunk update of a pair's state
+// (S, H) is affine, S' = d S + S_c, H' = d (H + g S) + H_c (d the chunk's
+// decay, g its gap), and so is any run of chunks:
+// (S, H) -> (D S + A_S, D (H + G S) + A_H). A slab's k = 0 chunks are cut
+// into about sqrt(nz) groups of about sqrt(nz) chunks, and the chains run in
+// three parallel phases as the k-space carries do: (1) every (direction,
+// group, pair) composes its group's transfer (D, G, A_S, A_H) from the chunk
+// aggregates (kzero_group_kernel), (2) one thread per (direction, slab,
+// pair) chains the groups (kzero_chain_kernel), (3) every group replays its
+// chunks from its input and writes the carry entering each chunk. The chunk
+// sums of q and q z go through the same three phases (per-chunk prefixes
+// and the slab's totals). Lanes run over the pairs of one group, so that
+// their loads are contiguous.
 template <typename CN>
 struct K0Transfer {
   CN Dr, Di, G, Sr, Si, Hr, Hi;
@@ -131,160 +132,166 @@ struct K0State {
   CN Sr, Si, Hr, Hi;
 };
 
-__host__ __device__ inline int kzero_groups(int npad) { return kK0Chains / (2 * npad); }
-
 template <typename T>
-__global__ void __launch_bounds__(kK0Chains + 32) kzero_carry_kernel(K0Params Q, PairTab pr, const typename CarryNum<T>::type* gaps,
-                                   const Cplx<T>* agg,
-                                   const Cplx<typename CarryNum<T>::type>* pdec,
-                                   typename CarryNum<T>::type* carry,
-                                   const typename CarryNum<T>::type* csum,
-                                   typename CarryNum<T>::type* cpre,
-                                   typename CarryNum<T>::type* rtot) {
+struct K0Carry {
   using CN = typename CarryNum<T>::type;
-  extern __shared__ __align__(16) char k0c_raw[];
-  const int G = kzero_groups(Q.npad);
-  K0Transfer<CN>* tr = reinterpret_cast<K0Transfer<CN>*>(k0c_raw);          // [2 npad G]
-  K0State<CN>* in = reinterpret_cast<K0State<CN>*>(tr + kK0Chains);         // [2 npad G]
-  CN* qsum = reinterpret_cast<CN*>(in + kK0Chains);                         // [32][2]
-  const CN zero = cn_zero((CN*)nullptr), one = cn_from(1.0, (CN*)nullptr);
-  const int rep = blockIdx.x;
-  const int z0 = Q.rp.info[rep].z0, nz = Q.rp.info[rep].nz;
-  const int nch = Q.rp.nzchunks;
-  const int np = pr.np;
-  const int e = threadIdx.x;
-  const int g = (nz + G - 1) / G;            // chunks per chain group
-  const int gq = (nz + 31) / 32;             // chunks per prefix group
-  // chain threads: e = (dir * npad + p) * G + grp
-  const bool chain = e < kK0Chains;
-  const int dir = chain ? e / (Q.npad * G) : 0;
-  const int p = chain ? (e / G) % Q.npad : 0;
-  const int grp = chain ? e % G : 0;
-  const bool act = chain && p < np;
-  // the group's chunks in chain order: forward ascending, backward descending
-  const int gpos = dir == 0 ? grp : G - 1 - grp;          // position along the chain
-  const int ja = gpos * g, jb = min(nz, ja + g);          // replica-local chunk range
-  const int q = e - kK0Chains;                            // prefix lane (0..31)
-  const int qa = q * gq, qb = min(nz, qa + gq);
+  const CN* gaps;              // [2][nch]
+  const Cplx<T>* agg;          // [nch][npad][4]
+  const Cplx<CN>* pdec;        // [2][nch][np]
+  const CN* csum;              // [nch][2]
+  K0Transfer<CN>* ztr;         // [2][NZG][npad]
+  K0State<CN>* zin;            // [2][NZG][npad]
+  CN* zq;                      // [NZG][2] group sums, then group inputs
+  CN* carry;                   // [2][nch][npad][4]
+  CN* cpre;                    // [nch][2]
+  CN* rtot;                    // [R][2]
+};
 
-  // the chunk aggregates, decay and gap of chunk c for this chain
-  auto load_step = [&](int c, Cplx<T>& as, Cplx<T>& ah, Cplx<CN>& d, CN& dz) {
-    const Cplx<T>* a = agg + ((size_t)c * Q.npad + p) * 4 + 2 * dir;
-    as = a[0];
-    ah = a[1];
-    d = pdec[((size_t)dir * nch + c) * np + p];
-    dz = gaps[dir * nch + c];
-  };
-  constexpr int B = 4;   // loads in flight per thread (bounded by 96 registers)
-  // ---- phase 1: compose the group's transfer from a zero input
-  if (act) {
-    CN Dr = one, Di = zero, Gs = zero, sr = zero, si = zero, hr = zero, hi = zero;
-    for (int j0 = ja; j0 < jb; j0 += B) {
+// one chunk of a pair chain: S' = d S + S_c, H' = d (H + g S) + H_c
+template <typename CN, typename T>
+__device__ __forceinline__ void k0_step(CN& sr, CN& si, CN& hr, CN& hi, const Cplx<CN>& d,
+                                        const CN& g, const Cplx<T>& as, const Cplx<T>& ah) {
+  const CN tr = hr + g * sr, ti = hi + g * si;
+  const CN nhr = d.re * tr - d.im * ti + cn_from_t(ah.re, (CN*)nullptr);
+  const CN nhi = d.re * ti + d.im * tr + cn_from_t(ah.im, (CN*)nullptr);
+  const CN nsr = d.re * sr - d.im * si + cn_from_t(as.re, (CN*)nullptr);
+  const CN nsi = d.re * si + d.im * sr + cn_from_t(as.im, (CN*)nullptr);
+  sr = nsr; si = nsi; hr = nhr; hi = nhi;
+}
+
+// phases 1 (replay = false) and 3 (replay = true)
+template <typename T>
+__global__ void kzero_group_kernel(K0Params Q, PairTab pr, K0Carry<T> W, bool replay) {
+  using CN = typename CarryNum<T>::type;
+  const CN zero = cn_zero((CN*)nullptr), one = cn_from(1.0, (CN*)nullptr);
+  const int NZG = Q.rp.nzgroups, npad = Q.npad, np = pr.np;
+  const int nch = Q.rp.nzchunks;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int npair = 2 * NZG * npad;
+  if (e < npair) {
+    const int p = e % npad, rest = e / npad;
+    const int grp = rest % NZG, dir = rest / NZG;
+    if (p >= np) return;
+    if (!replay) {
+      const RepInfo& ri = Q.rp.info[Q.rp.zgroup_rep[grp]];
+      if (grp == (dir == 0 ? ri.zg0 + ri.nzg - 1 : ri.zg0)) return;   // last in its chain
+    }
+    const int ca = Q.rp.zgstart[grp], cb = Q.rp.zgstart[grp + 1], len = cb - ca;
+    const size_t ti = ((size_t)dir * NZG + grp) * npad + p;
+    CN sr = zero, si = zero, hr = zero, hi = zero, Dr = one, Di = zero, Gs = zero;
+    if (replay) { const K0State<CN> x = W.zin[ti]; sr = x.Sr; si = x.Si; hr = x.Hr; hi = x.Hi; }
+    constexpr int B = 4;
+    for (int j0 = 0; j0 < len; j0 += B) {
       Cplx<T> as[B], ah[B];
       Cplx<CN> d[B];
       CN dz[B];
 #pragma unroll
       for (int u = 0; u < B; ++u) {
-        const int j = j0 + u;
-        if (j < jb) load_step(dir == 0 ? z0 + j : z0 + nz - 1 - j, as[u], ah[u], d[u], dz[u]);
+        if (j0 + u < len) {
+          const int c = dir == 0 ? ca + j0 + u : cb - 1 - (j0 + u);
+          const Cplx<T>* a = W.agg + ((size_t)c * npad + p) * 4 + 2 * dir;
+          as[u] = a[0];
+          ah[u] = a[1];
+          d[u] = W.pdec[((size_t)dir * nch + c) * np + p];
+          dz[u] = W.gaps[dir * nch + c];
+        }
       }
 #pragma unroll
       for (int u = 0; u < B; ++u) {
-        if (j0 + u < jb) {
-          const CN tr_ = hr + dz[u] * sr, ti_ = hi + dz[u] * si;
-          const CN nhr = d[u].re * tr_ - d[u].im * ti_ + cn_from_t(ah[u].re, (CN*)nullptr);
-          const CN nhi = d[u].re * ti_ + d[u].im * tr_ + cn_from_t(ah[u].im, (CN*)nullptr);
-          const CN nsr = d[u].re * sr - d[u].im * si + cn_from_t(as[u].re, (CN*)nullptr);
-          const CN nsi = d[u].re * si + d[u].im * sr + cn_from_t(as[u].im, (CN*)nullptr);
-          sr = nsr; si = nsi; hr = nhr; hi = nhi;
-          const CN nDr = d[u].re * Dr - d[u].im * Di;
-          const CN nDi = d[u].re * Di + d[u].im * Dr;
-          Dr = nDr; Di = nDi;
-          Gs = Gs + dz[u];
+        if (j0 + u < len) {
+          if (replay) {
+            const int c = dir == 0 ? ca + j0 + u : cb - 1 - (j0 + u);
+            CN* out = W.carry + (((size_t)dir * nch + c) * npad + p) * 4;
+            out[0] = sr; out[1] = si; out[2] = hr; out[3] = hi;
+          }
+          k0_step(sr, si, hr, hi, d[u], dz[u], as[u], ah[u]);
+          if (!replay) {
+            const CN nDr = d[u].re * Dr - d[u].im * Di;
+            const CN nDi = d[u].re * Di + d[u].im * Dr;
+            Dr = nDr; Di = nDi;
+            Gs = Gs + dz[u];
+          }
         }
       }
     }
-    tr[e] = K0Transfer<CN>{Dr, Di, Gs, sr, si, hr, hi};
-  } else if (!chain && q < 32) {
-    CN a = zero, b = zero;
-    for (int j = qa; j < qb; ++j) { a = a + csum[2 * (z0 + j)]; b = b + csum[2 * (z0 + j) + 1]; }
-    qsum[2 * q] = a;
-    qsum[2 * q + 1] = b;
-  }
-  __syncthreads();
-  // ---- phase 2: chain over the groups (thread of group 0 of each chain)
-  if (act && grp == 0) {
-    CN sr = zero, si = zero, hr = zero, hi = zero;
-    for (int gg = 0; gg < G; ++gg) {
-      // group at chain position gg is thread index with grp' such that
-      // gpos(grp') = gg
-      const int gidx = dir == 0 ? gg : G - 1 - gg;
-      const int t = (dir * Q.npad + p) * G + gidx;
-      in[t] = K0State<CN>{sr, si, hr, hi};
-      const K0Transfer<CN> x = tr[t];
-      const CN tr_ = hr + x.G * sr, ti_ = hi + x.G * si;
-      const CN nhr = x.Dr * tr_ - x.Di * ti_ + x.Hr;
-      const CN nhi = x.Dr * ti_ + x.Di * tr_ + x.Hi;
-      const CN nsr = x.Dr * sr - x.Di * si + x.Sr;
-      const CN nsi = x.Dr * si + x.Di * sr + x.Si;
-      sr = nsr; si = nsi; hr = nhr; hi = nhi;
-    }
-  } else if (!chain && q == 0) {
-    CN a = zero, b = zero;
-    for (int j = 0; j < 32; ++j) {
-      const CN na = a + qsum[2 * j], nb = b + qsum[2 * j + 1];
-      qsum[2 * j] = a;
-      qsum[2 * j + 1] = b;
-      a = na; b = nb;
-    }
-    rtot[2 * rep] = a;
-    rtot[2 * rep + 1] = b;
-  }
-  __syncthreads();
-  // ---- phase 3: replay every group from its input, writing the carries
-  if (act) {
-    const K0State<CN> s0 = in[e];
-    CN sr = s0.Sr, si = s0.Si, hr = s0.Hr, hi = s0.Hi;
-    for (int j0 = ja; j0 < jb; j0 += B) {
-      Cplx<T> as[B], ah[B];
-      Cplx<CN> d[B];
-      CN dz[B];
-#pragma unroll
-      for (int u = 0; u < B; ++u) {
-        const int j = j0 + u;
-        if (j < jb) load_step(dir == 0 ? z0 + j : z0 + nz - 1 - j, as[u], ah[u], d[u], dz[u]);
+    if (!replay) W.ztr[ti] = K0Transfer<CN>{Dr, Di, Gs, sr, si, hr, hi};
+  } else if (e < npair + NZG) {
+    const int grp = e - npair;
+    const int ca = Q.rp.zgstart[grp], cb = Q.rp.zgstart[grp + 1];
+    if (!replay) {
+      CN a = zero, b = zero;
+      for (int c = ca; c < cb; ++c) { a = a + W.csum[2 * c]; b = b + W.csum[2 * c + 1]; }
+      W.zq[2 * grp] = a;
+      W.zq[2 * grp + 1] = b;
+    } else {
+      CN a = W.zq[2 * grp], b = W.zq[2 * grp + 1];
+      for (int c = ca; c < cb; ++c) {
+        W.cpre[2 * c] = a;
+        W.cpre[2 * c + 1] = b;
+        a = a + W.csum[2 * c];
+        b = b + W.csum[2 * c + 1];
       }
-#pragma unroll
-      for (int u = 0; u < B; ++u) {
-        const int j = j0 + u;
-        if (j < jb) {
-          const int c = dir == 0 ? z0 + j : z0 + nz - 1 - j;
-          CN* out = carry + (((size_t)dir * nch + c) * Q.npad + p) * 4;
-          out[0] = sr; out[1] = si; out[2] = hr; out[3] = hi;
-          const CN tr_ = hr + dz[u] * sr, ti_ = hi + dz[u] * si;
-          const CN nhr = d[u].re * tr_ - d[u].im * ti_ + cn_from_t(ah[u].re, (CN*)nullptr);
-          const CN nhi = d[u].re * ti_ + d[u].im * tr_ + cn_from_t(ah[u].im, (CN*)nullptr);
-          const CN nsr = d[u].re * sr - d[u].im * si + cn_from_t(as[u].re, (CN*)nullptr);
-          const CN nsi = d[u].re * si + d[u].im * sr + cn_from_t(as[u].im, (CN*)nullptr);
-          sr = nsr; si = nsi; hr = nhr; hi = nhi;
-        }
-      }
-    }
-  } else if (!chain && q < 32) {
-    CN a = qsum[2 * q], b = qsum[2 * q + 1];
-    for (int j = qa; j < qb; ++j) {
-      const int c = z0 + j;
-      cpre[2 * c] = a;
-      cpre[2 * c + 1] = b;
-      a = a + csum[2 * c];
-      b = b + csum[2 * c + 1];
     }
   }
 }
 
-inline size_t kzero_carry_smem(int fp64) {
-  const size_t cn = fp64 ? sizeof(double) : sizeof(DF);
-  return (size_t)kK0Chains * (7 + 4) * cn + 64 * cn;
+// phase 2: thread = (direction, slab, pair), plus one thread per slab for
+// the sums of q and q z
+template <typename T>
+__global__ void kzero_chain_kernel(K0Params Q, PairTab pr, K0Carry<T> W) {
+  using CN = typename CarryNum<T>::type;
+  const CN zero = cn_zero((CN*)nullptr);
+  const int NZG = Q.rp.nzgroups, npad = Q.npad, R = Q.rp.R;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int npair = 2 * R * npad;
+  if (e < npair) {
+    const int p = e % npad, rest = e / npad;
+    const int rep = rest % R, dir = rest / R;
+    if (p >= pr.np) return;
+    const int g0 = Q.rp.info[rep].zg0, ng = Q.rp.info[rep].nzg;
+    CN sr = zero, si = zero, hr = zero, hi = zero;
+    constexpr int B = 4;
+    for (int j0 = 0; j0 < ng; j0 += B) {
+      K0Transfer<CN> x[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const int j = j0 + u;
+        if (j < ng - 1) {
+          const int grp = dir == 0 ? g0 + j : g0 + ng - 1 - j;
+          x[u] = W.ztr[((size_t)dir * NZG + grp) * npad + p];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        const int j = j0 + u;
+        if (j < ng) {
+          const int grp = dir == 0 ? g0 + j : g0 + ng - 1 - j;
+          W.zin[((size_t)dir * NZG + grp) * npad + p] = K0State<CN>{sr, si, hr, hi};
+          if (j < ng - 1) {
+            const CN tr = hr + x[u].G * sr, ti = hi + x[u].G * si;
+            const CN nhr = x[u].Dr * tr - x[u].Di * ti + x[u].Hr;
+            const CN nhi = x[u].Dr * ti + x[u].Di * tr + x[u].Hi;
+            const CN nsr = x[u].Dr * sr - x[u].Di * si + x[u].Sr;
+            const CN nsi = x[u].Dr * si + x[u].Di * sr + x[u].Si;
+            sr = nsr; si = nsi; hr = nhr; hi = nhi;
+          }
+        }
+      }
+    }
+  } else if (e < npair + R) {
+    const int rep = e - npair;
+    const int g0 = Q.rp.info[rep].zg0, ng = Q.rp.info[rep].nzg;
+    CN a = zero, b = zero;
+    for (int j = 0; j < ng; ++j) {
+      const int grp = g0 + j;
+      const CN na = a + W.zq[2 * grp], nb = b + W.zq[2 * grp + 1];
+      W.zq[2 * grp] = a;
+      W.zq[2 * grp + 1] = b;
+      a = na; b = nb;
+    }
+    W.rtot[2 * rep] = a;
+    W.rtot[2 * rep + 1] = b;
+  }
 }
 
 template <typename T>
@@ -437,9 +444,11 @@ void launch_kzero(const Reps& rp, const PairTab& pairs, double alpha, const T* z
   }
   Q.c1 = c1;
   const int nch = rp.nzchunks;
+  const int NZG = rp.nzgroups;
   // work layout: agg [nch][npad][4] Cplx<T>, csum [nch][2] CN,
   // pdec [2][nch][np] Cplx<CN>, carry [2][nch][npad][4] CN, cpre [nch][2] CN,
-  // rtot [R][2] CN, gaps [2][nch] CN
+  // rtot [R][2] CN, gaps [2][nch] CN, ztr [2][NZG][npad] K0Transfer,
+  // zin [2][NZG][npad] K0State, zq [NZG][2] CN
   char* w = reinterpret_cast<char*>(work);
   auto take = [&w](size_t b) { char* r = w; w += (b + 255) & ~size_t(255); return r; };
   Cplx<T>* agg = reinterpret_cast<Cplx<T>*>(take(sizeof(Cplx<T>) * (size_t)nch * npad * 4));
@@ -449,6 +458,17 @@ void launch_kzero(const Reps& rp, const PairTab& pairs, double alpha, const T* z
   CN* cpre = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)nch * 2));
   CN* rtot = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)rp.R * 2));
   CN* gaps = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)2 * nch));
+  K0Carry<T> W;
+  W.gaps = gaps;
+  W.agg = agg;
+  W.pdec = pdec;
+  W.csum = csum;
+  W.ztr = reinterpret_cast<K0Transfer<CN>*>(take(sizeof(K0Transfer<CN>) * (size_t)2 * NZG * npad));
+  W.zin = reinterpret_cast<K0State<CN>*>(take(sizeof(K0State<CN>) * (size_t)2 * NZG * npad));
+  W.zq = reinterpret_cast<CN*>(take(sizeof(CN) * (size_t)NZG * 2));
+  W.carry = carry;
+  W.cpre = cpre;
+  W.rtot = rtot;
   CN* phi0 = static_cast<CN*>(phi0v);
   CN* fz0 = static_cast<CN*>(fz0v);
   const int nblk = (nch + kK0Cpb - 1) / kK0Cpb;
@@ -458,23 +478,25 @@ void launch_kzero(const Reps& rp, const PairTab& pairs, double alpha, const T* z
                        (int)sma);
   kzero_aggregate_kernel<T><<<nblk, thr, sma, st>>>(Q, pairs, zs, qs, agg, csum);
   launch_pair_decay<T>(rp, 1, pairs.np, zs, pairs, pdec, gaps, st);
-  const size_t smc = kzero_carry_smem(sizeof(T) == 8);
-  cudaFuncSetAttribute(kzero_carry_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
-  kzero_carry_kernel<T><<<rp.R, kK0Chains + 32, smc, st>>>(Q, pairs, gaps, agg, pdec, carry, csum,
-                                                           cpre, rtot);
+  const int ng1 = 2 * NZG * npad + NZG;
+  kzero_group_kernel<T><<<(ng1 + 127) / 128, 128, 0, st>>>(Q, pairs, W, false);
+  const int ng2 = 2 * rp.R * npad + rp.R;
+  kzero_chain_kernel<T><<<(ng2 + 127) / 128, 128, 0, st>>>(Q, pairs, W);
+  kzero_group_kernel<T><<<(ng1 + 127) / 128, 128, 0, st>>>(Q, pairs, W, true);
   const size_t smf = (size_t)kK0Cpb * (5 * rp.L0 + 3) * sizeof(T);
   cudaFuncSetAttribute(kzero_final_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
   kzero_final_kernel<T><<<nblk, thr, smf, st>>>(Q, pairs, zs, dz, qs, carry, cpre, rtot, phi0,
                                                 fz0);
 }
 
-size_t kzero_work_doubles(int nzchunks, int R, int np) {
+size_t kzero_work_doubles(int nzchunks, int nzgroups, int R, int np) {
   const int npad = kzero_lanes(np);
   // in 8-byte units (a double-float takes one), with room for the 256-byte
-  // alignment of each of the 7 arrays
+  // alignment of each of the 10 arrays
   return (size_t)nzchunks * npad * 4 * 2 + (size_t)nzchunks * 2 +
          (size_t)2 * nzchunks * kMaxPairs * 2 + (size_t)2 * nzchunks * npad * 4 +
-         (size_t)nzchunks * 2 + (size_t)R * 2 + (size_t)2 * nzchunks + 7 * 32 + 64;
+         (size_t)nzchunks * 2 + (size_t)R * 2 + (size_t)2 * nzchunks +
+         (size_t)2 * nzgroups * npad * (7 + 4) + (size_t)nzgroups * 2 + 10 * 32 + 64;
 }
 
 // ============================================================ instantiations
