@@ -48,7 +48,7 @@ struct Tables {
   int64_t N = 0;
   // device layout of the table buffer
   size_t o_info = 0, o_crep = 0, o_zrep = 0, o_gstart = 0, o_grep = 0, o_zgstart = 0, o_zgrep = 0,
-         o_list = 0, o_cdf = 0,
+         o_list = 0, o_cdf = 0, o_trig = 0,
          o_sampled = 0, o_modes = 0, bytes = 0;
 };
 
@@ -444,6 +444,7 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
   t.o_zgrep = take(sizeof(int32_t) * std::max(t.nzgroups, 1));
   t.o_list = take(sizeof(int32_t) * std::max<size_t>(t.list.size(), 2));
   t.o_cdf = take(sizeof(double) * std::max<size_t>(t.cdf.size(), 1));
+  t.o_trig = take(sizeof(float) * 2 * 256);
   t.o_sampled = take(sizeof(int32_t) * 2 * (size_t)R * t.Kpad);
   t.o_modes = take(mode_bytes((size_t)R * t.Kpad, c->npc, tsz));
   t.bytes = o;
@@ -466,6 +467,13 @@ int upload_tables(const Tables& t, void* dst) {
   put(t.o_zgrep, t.zgroup_rep.data(), sizeof(int32_t) * t.zgroup_rep.size());
   put(t.o_list, t.list.data(), sizeof(int32_t) * t.list.size());
   put(t.o_cdf, t.cdf.data(), sizeof(double) * t.cdf.size());
+  // (cos, sin) of the turns j/256 for the FP32 phases, rounded from FP64
+  float trig[512];
+  for (int j = 0; j < 256; ++j) {
+    trig[2 * j] = (float)std::cos(2.0 * kPi * j / 256.0);
+    trig[2 * j + 1] = (float)std::sin(2.0 * kPi * j / 256.0);
+  }
+  put(t.o_trig, trig, sizeof(trig));
   QS_CUDA(cudaMemcpy(dst, stage.data(), stage.size(), cudaMemcpyHostToDevice));
   return QSLAB_OK;
 }
@@ -652,8 +660,9 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
     else c->coef_ready = true;
   }
   if (ev) cudaEventRecord(ev[2], st);
-  launch_kspace<T>(P.sp, rp, modes, c->pairs, zs, dz, qs, xh, yh, agg, carry, dec, part, st,
-                   ev ? ev + 3 : nullptr);
+  launch_kspace<T>(P.sp, rp, modes, c->pairs, zs, dz, qs, xh, yh,
+                   sizeof(T) == 4 ? reinterpret_cast<const float2*>(tab + tb.o_trig) : nullptr,
+                   agg, carry, dec, part, st, ev ? ev + 3 : nullptr);
   nl += 8;
   QS_CUDA(cudaStreamWaitEvent(st, c->join, 0));
   if (ev) cudaEventRecord(ev[6], st);

@@ -160,8 +160,9 @@ template <typename T>
 void launch_kspace(const ScanPlan& plan, const Reps& rp, const ModeTab<T>& modes,
                    const PairTab& pairs, const T* zs, const T* dz, const T* qs,
                    const typename PhaseT<T>::type* xh,
-                   const typename PhaseT<T>::type* yh, Cplx<T>* agg,
-                   Cplx<T>* carry, void* dec, T* part,
+                   const typename PhaseT<T>::type* yh,
+                   const float2* trig,   // FP32: [256] (cos, sin) of j/256 turns
+                   Cplx<T>* agg, Cplx<T>* carry, void* dec, T* part,
                    cudaStream_t st, cudaEvent_t* ev3);  // ev3: 3 events or NULL
 // bytes of the chunk-to-chunk decay tables and carry-group transfers
 size_t kspace_decay_bytes(const ScanPlan& pl, const Reps& rp, int fp64);

@@ -49,8 +49,10 @@ struct ChunkSmem {
   Cplx<T>* tab;   // pass B: [L+1][NP] decays; pass A: [L][2][NP] (E_f, E_b)
   Rec<T>* rec;    // [L+1]
   T* zl;          // [L]
+  float2* trig;   // FP32 path: [256] (cos, sin) of j/256 turns
   T* slots;       // pass B: [W][L][4]
 };
+constexpr int kTrig = 256;
 
 __host__ __device__ inline size_t align_up(size_t x) { return (x + 31) & ~size_t(31); }
 
@@ -60,6 +62,7 @@ __host__ __device__ inline size_t chunk_smem_bytes(int L, int NP, int W, bool pa
   b += align_up(sizeof(Cplx<T>) * (size_t)NP * (passB ? (L + 1) : 2 * L));
   b += align_up(sizeof(Rec<T>) * (L + 1));
   b += align_up(sizeof(T) * L);
+  b += align_up(sizeof(float2) * kTrig);
   if (passB) b += align_up(sizeof(T) * (size_t)W * L * 4);
   return b;
 }
@@ -72,6 +75,7 @@ __device__ inline ChunkSmem<T> carve(char* base, int L, int NP, int W, bool pass
   p += align_up(sizeof(Cplx<T>) * (size_t)NP * (passB ? (L + 1) : 2 * L));
   s.rec = reinterpret_cast<Rec<T>*>(p); p += align_up(sizeof(Rec<T>) * (L + 1));
   s.zl = reinterpret_cast<T*>(p); p += align_up(sizeof(T) * L);
+  s.trig = reinterpret_cast<float2*>(p); p += align_up(sizeof(float2) * kTrig);
   s.slots = passB ? reinterpret_cast<T*>(p) : nullptr;
   return s;
 }
@@ -87,6 +91,7 @@ struct KParams {
   const T* qs;
   const typename PhaseT<T>::type* xh;
   const typename PhaseT<T>::type* yh;
+  const float2* trig;  // [256] (cos, sin) of j/256 turns (FP32 path)
   Cplx<T>* agg;     // [2][nchunks][nstates][Kpad]
   Cplx<T>* carry;   // same layout
   T* part;          // [nkr][4][N]
@@ -134,6 +139,8 @@ __device__ inline void load_chunk(const KParams<T>& P, ChunkSmem<T>& s,
     }
     s.rec[t] = r;
   }
+  if (P.trig)
+    for (int t = threadIdx.x; t < kTrig; t += blockDim.x) s.trig[t] = P.trig[t];
 }
 
 // ------------------------------------------------------------------ pass A
@@ -168,11 +175,11 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
   for (int t = 0; t < cnt; ++t) {
     const Rec<T> r = s.rec[t];
     T cs, sn;
-    sincos_turns(phase_turns(mc.mx, mc.my, r.xh, r.yh), cs, sn);
+    phase_cs(phase_turns(mc.mx, mc.my, r.xh, r.yh), s.trig, cs, sn);
     const T a = r.q * cs, b = r.q * sn;   // u = a - i b
     const T zt = s.zl[t];
-    const T ef = exp_neg(mc.kk * (zend - zt));
-    const T eb = exp_neg(mc.kk * (zt - zst));
+    const T ef = exp_neg_term(mc.kk * (zend - zt));
+    const T eb = exp_neg_term(mc.kk * (zt - zst));
     f0.re = fma(ef, a, f0.re); f0.im = fma(-ef, b, f0.im);
     b0.re = fma(eb, a, b0.re); b0.im = fma(-eb, b, b0.im);
     const Cplx<T>* Et = s.tab + 2 * t * NP;
@@ -250,7 +257,7 @@ __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
           const Rec<T> r = s.rec[t];
           const T dzd = dir == 0 ? r.dz : s.rec[td].dz;
           T cs, sn;
-          sincos_turns(phase_turns(mc.mx, mc.my, r.xh, r.yh), cs, sn);
+          phase_cs(phase_turns(mc.mx, mc.my, r.xh, r.yh), s.trig, cs, sn);
           const T a = r.q * cs, b = r.q * sn;
           // beta = k: real decay e^{-k dz}, complex input u = a - i b, as
           // G <- G + (u - e G) with e = 1 - e^{-k dz} (see one_minus_exp_neg)
@@ -330,10 +337,11 @@ template <typename T>
 void launch_kspace(const ScanPlan& plan, const Reps& rp, const ModeTab<T>& modes,
                    const PairTab& pairs, const T* zs, const T* dz, const T* qs,
                    const typename PhaseT<T>::type* xh,
-                   const typename PhaseT<T>::type* yh, Cplx<T>* agg,
-                   Cplx<T>* carry, void* dec, T* part,
+                   const typename PhaseT<T>::type* yh, const float2* trig,
+                   Cplx<T>* agg, Cplx<T>* carry, void* dec, T* part,
                    cudaStream_t st, cudaEvent_t* ev3) {
-  KParams<T> P{plan, rp, modes, (size_t)rp.R * rp.Kpad, zs, dz, qs, xh, yh, agg, carry, part};
+  KParams<T> P{plan, rp, modes, (size_t)rp.R * rp.Kpad, zs, dz, qs, xh, yh, trig, agg, carry,
+               part};
   switch (plan.np) {
     case 4: kspace_run<T, 4>(P, pairs, dec, st, ev3); break;
     case 8: kspace_run<T, 8>(P, pairs, dec, st, ev3); break;
@@ -345,11 +353,12 @@ void launch_kspace(const ScanPlan& plan, const Reps& rp, const ModeTab<T>& modes
 // ============================================================ instantiations
 template void launch_kspace<float>(const ScanPlan&, const Reps&, const ModeTab<float>&,
                                    const PairTab&, const float*, const float*, const float*,
-                                   const uint32_t*, const uint32_t*, Cplx<float>*, Cplx<float>*,
-                                   void*, float*, cudaStream_t, cudaEvent_t*);
+                                   const uint32_t*, const uint32_t*, const float2*, Cplx<float>*,
+                                   Cplx<float>*, void*, float*, cudaStream_t, cudaEvent_t*);
 template void launch_kspace<double>(const ScanPlan&, const Reps&, const ModeTab<double>&,
                                     const PairTab&, const double*, const double*, const double*,
-                                    const uint64_t*, const uint64_t*, Cplx<double>*,
-                                    Cplx<double>*, void*, double*, cudaStream_t, cudaEvent_t*);
+                                    const uint64_t*, const uint64_t*, const float2*,
+                                    Cplx<double>*, Cplx<double>*, void*, double*, cudaStream_t,
+                                    cudaEvent_t*);
 
 }  // namespace qslab

@@ -51,26 +51,54 @@ __device__ __forceinline__ void sincos_turns(uint32_t ph, float& c, float& s) {
   s = (qd & 2u) ? -s0 : s0;          // qd = 2, 3 negate sin
 }
 
+// cos and sin of 2 pi ph / 2^32 from a table of the 256 turns j/256 (in
+// shared memory, tab[j] = (cos, sin)(2 pi j/256), rounded from FP64 on the
+// host) and the remainder x, |x| <= pi/256: sin x = x - x^3/6 (truncation
+// below 3e-12), cos x = 1 - x^2/2 (below 1e-9), combined by the angle-sum
+// formulas. About half the instructions of the series above; the error is
+// about one unit in the last place.
+__device__ __forceinline__ void sincos_table(uint32_t ph, const float2* tab, float& c, float& s) {
+  const uint32_t j = (ph + 0x800000u) >> 24;            // nearest 1/256 turn
+  const int32_t r = (int32_t)(ph << 8) >> 8;            // ph - j 2^24, in [-2^23, 2^23)
+  const float x = (float)r * 1.4629180792671596e-9f;    // 2 pi / 2^32
+  const float x2 = x * x;
+  const float sx = fmaf(x * x2, -0.16666666666666666f, x);
+  const float2 t = tab[j & 255u];
+  c = fmaf(-t.y, sx, fmaf(t.x * x2, -0.5f, t.x));
+  s = fmaf(t.x, sx, fmaf(t.y * x2, -0.5f, t.y));
+}
+
 // cos and sin of 2 pi ph / 2^64 in FP64.
 __device__ __forceinline__ void sincos_turns(uint64_t ph, double& c, double& s) {
   const double t = (double)(int64_t)ph * 1.0842021724855044e-19;  // 2^-63
   sincospi(t, &s, &c);
 }
 
+// phase factors of a mode: FP32 from the shared-memory table, FP64 exact
+__device__ __forceinline__ void phase_cs(uint32_t ph, const float2* tab, float& c, float& s) {
+  sincos_table(ph, tab, c, s);
+}
+__device__ __forceinline__ void phase_cs(uint64_t ph, const float2*, double& c, double& s) {
+  sincos_turns(ph, c, s);
+}
+
 // --------------------------------------------------------------- decays
 __device__ __forceinline__ float exp_neg(float x) { return expf(-x); }
 __device__ __forceinline__ double exp_neg(double x) { return exp(-x); }
+// e^{-x} for terms that enter a sum once (not a product along a scan): the
+// fast FP32 exponential (a few ulp) is enough there
+__device__ __forceinline__ float exp_neg_term(float x) { return __expf(-x); }
+__device__ __forceinline__ double exp_neg_term(double x) { return exp(-x); }
 
 // 1 - e^{-x} for x >= 0, accurate relative to itself. A decay e^{-x} close
 // to 1 cannot be stored in FP32 to better than about 6e-8 absolute, which for
 // the x ~ 1e-6 of neighbouring particles is a relative error of several
 // percent in 1 - e^{-x}; carrying e = 1 - e^{-x} instead keeps it exact to
-// rounding. Taylor series to x^6 below 1/16 (truncation < 3e-13 relative).
+// rounding. Taylor series to x^5 below 1/16 (truncation < 2e-9 relative).
 __device__ __forceinline__ float one_minus_exp_neg(float x) {
   // branch-free: for x >= 1/16, 1 - e^{-x} >= 0.06 and the plain form is exact enough
   const float big = 1.0f - __expf(-x);
-  float r = fmaf(x, -1.0f / 720.0f, 1.0f / 120.0f);
-  r = fmaf(x, r, -1.0f / 24.0f);
+  float r = fmaf(x, 1.0f / 120.0f, -1.0f / 24.0f);
   r = fmaf(x, r, 1.0f / 6.0f);
   r = fmaf(x, r, -0.5f);
   r = fmaf(x, r, 1.0f);
