@@ -51,6 +51,7 @@ struct ChunkSmem {
   T* zl;          // [L]
   float2* trig;   // FP32 path: [256] (cos, sin) of j/256 turns
   T* slots;       // pass B: [W][L][4]
+  T* idle;        // pass B: [W][32] write targets of lanes that hold no output
 };
 constexpr int kTrig = 256;
 
@@ -63,7 +64,7 @@ __host__ __device__ inline size_t chunk_smem_bytes(int L, int NP, int W, bool pa
   b += align_up(sizeof(Rec<T>) * (L + 1));
   b += align_up(sizeof(T) * L);
   b += align_up(sizeof(float2) * kTrig);
-  if (passB) b += align_up(sizeof(T) * (size_t)W * L * 4);
+  if (passB) b += align_up(sizeof(T) * (size_t)W * L * 4) + align_up(sizeof(T) * (size_t)W * kWarp);
   return b;
 }
 
@@ -77,6 +78,8 @@ __device__ inline ChunkSmem<T> carve(char* base, int L, int NP, int W, bool pass
   s.zl = reinterpret_cast<T*>(p); p += align_up(sizeof(T) * L);
   s.trig = reinterpret_cast<float2*>(p); p += align_up(sizeof(float2) * kTrig);
   s.slots = passB ? reinterpret_cast<T*>(p) : nullptr;
+  if (passB) p += align_up(sizeof(T) * (size_t)W * L * 4);
+  s.idle = passB ? reinterpret_cast<T*>(p) : nullptr;
   return s;
 }
 
@@ -293,12 +296,13 @@ __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
         }
       }
       const T v = warp_reduce16<T>(buf, lane);
+      // every even lane now holds one (particle, quantity) total; all lanes
+      // store (the others into an idle row) so that the warp does not diverge
       const int idx = lane >> 1, g = idx >> 2, qn = idx & 3;
-      if (!(lane & 1) && n0 + g < cnt) {
-        const int tt = dir == 0 ? n0 + g : cnt - 1 - (n0 + g);
-        if (dir == 0) slot[tt * 4 + qn] = v;
-        else slot[tt * 4 + qn] += v;
-      }
+      const bool own = !(lane & 1) && n0 + g < cnt;
+      const int tt = dir == 0 ? n0 + g : cnt - 1 - (n0 + g);
+      T* dst = own ? slot + tt * 4 + qn : s.idle + w * kWarp + lane;
+      *dst = (dir == 0 ? (T)0 : *dst) + v;
     }
     __syncwarp();
   }
@@ -313,6 +317,177 @@ __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
   }
 }
 
+// ------------------------------------------------ pass B, packed FP32 form
+// The same recurrences and gather on the FP32 path with two SOE pairs per
+// 64-bit register: the sm_100-family packed FP32 instructions (__ffma2_rn,
+// __fmul2_rn: two IEEE FMAs / products in one instruction) run the 16
+// operations per pair and step as 8, which halves the issue slots of the
+// arithmetic core. The pair (p, p+1) states sit in the two lanes of a float2;
+// the decay table is stored re/im-split per particle so that the decays of
+// two pairs load as one float2; the potential and force sums keep one
+// partial sum per lane, added at the end of the step.
+template <int NP>
+struct ModeCoefF2 {
+  int32_t mx, my;
+  float kx, ky, kk, ck, ckk, sY, sZ;
+  float2 cpr[NP / 2], ncpi[NP / 2], cbr[NP / 2], ncbi[NP / 2];   // ncpi = -cpi, ncbi = -cbi
+};
+
+template <int NP>
+__device__ __forceinline__ void load_mode_f2(const ModeTab<float>& mt, size_t kstride, size_t m,
+                                             ModeCoefF2<NP>& c) {
+  c.mx = mt.mx[m]; c.my = mt.my[m];
+  c.kx = mt.kx[m]; c.ky = mt.ky[m]; c.kk = mt.kk[m];
+  c.ck = mt.ck[m]; c.ckk = mt.ckk[m]; c.sY = mt.sY[m]; c.sZ = mt.sZ[m];
+#pragma unroll
+  for (int q = 0; q < NP / 2; ++q) {
+    const int p0 = 2 * q, p1 = 2 * q + 1;
+    c.cpr[q] = make_float2(mt.cp[(0 * NP + p0) * kstride + m], mt.cp[(0 * NP + p1) * kstride + m]);
+    c.ncpi[q] = make_float2(-mt.cp[(1 * NP + p0) * kstride + m], -mt.cp[(1 * NP + p1) * kstride + m]);
+    c.cbr[q] = make_float2(mt.cp[(2 * NP + p0) * kstride + m], mt.cp[(2 * NP + p1) * kstride + m]);
+    c.ncbi[q] = make_float2(-mt.cp[(3 * NP + p0) * kstride + m], -mt.cp[(3 * NP + p1) * kstride + m]);
+  }
+}
+
+template <int NP>
+__global__ void kspace_final_f2_kernel(KParams<float> P, PairTab pairs) {
+  extern __shared__ __align__(32) char smem[];
+  const ScanPlan& pl = P.plan;
+  const int c = blockIdx.x;
+  const int W = pl.KR / kWarp;
+  const int L = P.rp.L, Kpad = P.rp.Kpad;
+  const CRange ch = kchunk(P.rp, c);
+  const int64_t start = ch.start;
+  const int cnt = ch.cnt;
+  ChunkSmem<float> s = carve<float>(smem, L, NP, W, true);
+  load_chunk<float>(P, s, start, cnt);
+  __syncthreads();
+  // per-step decays of particle t: tabf[t][0][p] = Re, tabf[t][1][p] = Im of
+  // e^{-a_p dz_t}, t = 0..cnt (t = cnt: next chunk)
+  float* tabf = reinterpret_cast<float*>(s.tab);
+  for (int e = threadIdx.x; e < NP * (cnt + 1); e += blockDim.x) {
+    const int t = e / NP, p = e - t * NP;
+    const Cplx<float> d = cexp_neg((float)pairs.a_re[p], (float)pairs.a_im[p], s.rec[t].dz);
+    tabf[t * 2 * NP + p] = d.re;
+    tabf[t * 2 * NP + NP + p] = d.im;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int m = blockIdx.y * pl.KR + threadIdx.x;
+  ModeCoefF2<NP> mc;
+  load_mode_f2<NP>(P.modes, P.kstride, (size_t)ch.r * Kpad + m, mc);
+  const int S = pl.nstates;
+  const size_t dirstride = (size_t)P.rp.nchunks * S * Kpad;
+  float* slot = s.slots + (size_t)w * L * 4;
+  const float2 minus1 = make_float2(-1.0f, -1.0f);
+
+  for (int dir = 0; dir < 2; ++dir) {
+    const Cplx<float>* cin = P.carry + dir * dirstride + ((size_t)c * S) * Kpad + m;
+    Cplx<float> g0 = cin[0];
+    float2 Ra[NP / 2], Ia[NP / 2], Rb[NP / 2], Ib[NP / 2];
+#pragma unroll
+    for (int q = 0; q < NP / 2; ++q) {
+      const Cplx<float> a0 = cin[(size_t)(1 + 4 * q) * Kpad], b0 = cin[(size_t)(2 + 4 * q) * Kpad];
+      const Cplx<float> a1 = cin[(size_t)(3 + 4 * q) * Kpad], b1 = cin[(size_t)(4 + 4 * q) * Kpad];
+      Ra[q] = make_float2(a0.re, a1.re); Ia[q] = make_float2(a0.im, a1.im);
+      Rb[q] = make_float2(b0.re, b1.re); Ib[q] = make_float2(b0.im, b1.im);
+    }
+    const float zsign = dir == 0 ? 1.0f : -1.0f;
+    for (int n0 = 0; n0 < cnt; n0 += 4) {
+      float buf[16];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + j;
+        if (n < cnt) {
+          const int t = dir == 0 ? n : cnt - 1 - n;
+          const int td = dir == 0 ? t : t + 1;      // index of the decay to apply
+          const Rec<float> r = s.rec[t];
+          const float dzd = dir == 0 ? r.dz : s.rec[td].dz;
+          float cs, sn;
+          phase_cs(phase_turns(mc.mx, mc.my, r.xh, r.yh), s.trig, cs, sn);
+          const float a = r.q * cs, b = r.q * sn;
+          // beta = k: as in the scalar kernel
+          const float ek = one_minus_exp_neg(mc.kk * dzd);
+          g0.re += fmaf(-ek, g0.re, a);
+          g0.im += fmaf(-ek, g0.im, -b);
+          const float2 Ua = make_float2(a, a), Ub = make_float2(b, b);
+          float2 Ya = make_float2(0.0f, 0.0f), Yb = Ya, Za = Ya, Zb = Ya;
+          const float2* dre = reinterpret_cast<const float2*>(tabf + td * 2 * NP);
+          const float2* dim = reinterpret_cast<const float2*>(tabf + td * 2 * NP + NP);
+#pragma unroll
+          for (int q = 0; q < NP / 2; ++q) {
+            const float2 Dr = dre[q], Di = dim[q];
+            const float2 nDi = __fmul2_rn(Di, minus1);
+            // a-state: (R + iI) <- D (R + iI) + a ; b-state likewise with b
+            const float2 ra = __ffma2_rn(Dr, Ra[q], __ffma2_rn(nDi, Ia[q], Ua));
+            const float2 ia = __ffma2_rn(Dr, Ia[q], __fmul2_rn(Di, Ra[q]));
+            const float2 rb = __ffma2_rn(Dr, Rb[q], __ffma2_rn(nDi, Ib[q], Ub));
+            const float2 ib = __ffma2_rn(Dr, Ib[q], __fmul2_rn(Di, Rb[q]));
+            Ra[q] = ra; Ia[q] = ia; Rb[q] = rb; Ib[q] = ib;
+            Ya = __ffma2_rn(mc.cpr[q], ra, __ffma2_rn(mc.ncpi[q], ia, Ya));
+            Yb = __ffma2_rn(mc.cpr[q], rb, __ffma2_rn(mc.ncpi[q], ib, Yb));
+            Za = __ffma2_rn(mc.cbr[q], ra, __ffma2_rn(mc.ncbi[q], ia, Za));
+            Zb = __ffma2_rn(mc.cbr[q], rb, __ffma2_rn(mc.ncbi[q], ib, Zb));
+          }
+          // Y = ck G0 + sum_p Re(cp Ga) - i sum_p Re(cp Gb), Z likewise with cbp
+          float Yr = fmaf(mc.ck, g0.re, Ya.x + Ya.y);
+          float Yi = fmaf(mc.ck, g0.im, -(Yb.x + Yb.y));
+          float Zr = fmaf(mc.ckk, g0.re, Za.x + Za.y);
+          float Zi = fmaf(mc.ckk, g0.im, -(Zb.x + Zb.y));
+          // the sums above include j = i; remove it (coefficients sY, sZ times u_i)
+          Yr = fmaf(-mc.sY, a, Yr); Yi = fmaf(mc.sY, b, Yi);
+          Zr = fmaf(-mc.sZ, a, Zr); Zi = fmaf(mc.sZ, b, Zi);
+          const float W2 = cs * Yi + sn * Yr;         // Im e^{i k.rho} Y
+          buf[4 * j + 0] = cs * Yr - sn * Yi;         // Re e^{i k.rho} Y
+          buf[4 * j + 1] = mc.kx * W2;
+          buf[4 * j + 2] = mc.ky * W2;
+          buf[4 * j + 3] = zsign * (cs * Zr - sn * Zi);   // Re e^{i k.rho} Z
+        } else {
+          buf[4 * j + 0] = buf[4 * j + 1] = buf[4 * j + 2] = buf[4 * j + 3] = 0.0f;
+        }
+      }
+      const float v = warp_reduce16<float>(buf, lane);
+      // every even lane now holds one (particle, quantity) total; all lanes
+      // store (the others into an idle row) so that the warp does not diverge
+      const int idx = lane >> 1, g = idx >> 2, qn = idx & 3;
+      const bool own = !(lane & 1) && n0 + g < cnt;
+      const int tt = dir == 0 ? n0 + g : cnt - 1 - (n0 + g);
+      float* dst = own ? slot + tt * 4 + qn : s.idle + w * kWarp + lane;
+      *dst = (dir == 0 ? 0.0f : *dst) + v;
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // sum the warps' slots and write this mode range's partial outputs
+  float* out = P.part + (size_t)blockIdx.y * 4 * P.rp.N;
+  for (int e = threadIdx.x; e < cnt * 4; e += blockDim.x) {
+    const int t = e >> 2, qn = e & 3;
+    float acc = 0;
+    for (int ww = 0; ww < W; ++ww) acc += s.slots[((size_t)ww * L + t) * 4 + qn];
+    out[(size_t)qn * P.rp.N + start + t] = acc;
+  }
+}
+
+// pass B launcher: the packed kernel on the FP32 path, the scalar one on FP64
+template <typename T, int NP>
+struct FinalKernel {
+  static void run(const KParams<T>& P, const PairTab& pairs, dim3 grid, int threads, size_t sm,
+                  cudaStream_t st) {
+    cudaFuncSetAttribute(kspace_final_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    kspace_final_kernel<T, NP><<<grid, threads, sm, st>>>(P, pairs);
+  }
+};
+template <int NP>
+struct FinalKernel<float, NP> {
+  static void run(const KParams<float>& P, const PairTab& pairs, dim3 grid, int threads, size_t sm,
+                  cudaStream_t st) {
+    cudaFuncSetAttribute(kspace_final_f2_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    kspace_final_f2_kernel<NP><<<grid, threads, sm, st>>>(P, pairs);
+  }
+};
+
 template <typename T, int NP>
 static void kspace_run(const KParams<T>& P, const PairTab& pairs, void* dec,
                        cudaStream_t st, cudaEvent_t* ev) {
@@ -323,13 +498,11 @@ static void kspace_run(const KParams<T>& P, const PairTab& pairs, void* dec,
   const size_t smB = chunk_smem_bytes<T>(rp.L, NP, pl.KR / kWarp, true);
   cudaFuncSetAttribute(kspace_aggregate_kernel<T, NP>,
                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
-  cudaFuncSetAttribute(kspace_final_kernel<T, NP>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smB);
   kspace_aggregate_kernel<T, NP><<<grid, pl.KR, smA, st>>>(P, pairs);
   if (ev) cudaEventRecord(ev[0], st);
   launch_kspace_carries<T>(pl, rp, pairs, P.zs, P.modes.kk, P.agg, P.carry, dec, st);
   if (ev) cudaEventRecord(ev[1], st);
-  kspace_final_kernel<T, NP><<<grid, pl.KR, smB, st>>>(P, pairs);
+  FinalKernel<T, NP>::run(P, pairs, grid, pl.KR, smB, st);
   if (ev) cudaEventRecord(ev[2], st);
 }
 
