@@ -206,6 +206,32 @@ int qslab_compute_host(qslab_ctx* ctx, int64_t N, const void* pos_host,
 int qslab_compute_static(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
                          double* energy, void* phi, void* force, void* stream);
 
+/* Real-space cut-off rc for qslab_compute_realspace() (Section 2.3:
+ * pairs with |r_ij + M| > rc are dropped; the truncation error is of order
+ * erfc(alpha rc)). */
+int qslab_set_rcut(qslab_ctx* ctx, double rc);
+
+/* The real-space part of the Ewald2D splitting (Eq. 2.10): per particle
+ *   phi_s,i = sum_{j, M} q_j erfc(alpha |r_ij + M|)/|r_ij + M|   (j != i when M = 0)
+ * over the images M = (mx Lx, my Ly, 0) with |r_ij + M| <= rc, its forces
+ * F_i = -dE_s/dr_i and E_s = 1/2 sum_i q_i phi_s,i. Adding it to
+ * qslab_compute()'s long-range part gives the total Coulomb energy, potential
+ * and forces of the slab (Eq. 2.9). Uses the context's box, alpha, rc and
+ * precision (not the k-set).
+ *   N, pos, q, energy, phi, force, stream: as for qslab_compute(); the outputs
+ *   are written, not added to. energy (device double), phi and force may be
+ *   NULL.
+ * Needs rc <= min(Lx, Ly)/3 (QSLAB_ERR_INVALID_ARG otherwise) and rc set
+ * (QSLAB_ERR_NOT_CONFIGURED). Device-side input errors (non-finite values,
+ * z outside [0, Lz]) go to the status word as for qslab_compute(). Cell list
+ * with cells of edge >= rc; every pair is evaluated from both ends, in a
+ * fixed order (bitwise reproducible). Own workspace: it may run on another
+ * stream than the long-range call of the same context. The paper evaluates
+ * this part with a cell or Verlet list (Section 2.3); not part of Algorithms
+ * 1 and 2's long-range path. */
+int qslab_compute_realspace(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
+                            double* energy, void* phi, void* force, void* stream);
+
 /* Random-batch mode: copy the lattice vectors used by the latest
  * qslab_compute() or qslab_compute_batched() into mxy (host, 2*P*R int32:
  * (m_x, m_y) pairs, replica by replica; R = 1 after qslab_compute()) and, if

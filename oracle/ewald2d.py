@@ -142,6 +142,39 @@ def realspace(pos, q, box, alpha, rc):
     return {"E": 0.5 * float(q @ phi), "phi": phi, "F": F}
 
 
+def realspace_at(pos, q, box, alpha, rc, idx):
+    """phi_s and F_s (Eq. 2.10, |r_ij + M| <= rc, images in x,y) of the
+    particles idx only, each summed over every j: the same sum as realspace()
+    restricted to a sample of targets, for systems too large for all pairs."""
+    pos = np.asarray(pos, float)
+    q = np.asarray(q, float)
+    Lx, Ly, _ = box
+    idx = np.asarray(idx, int)
+    nx = int(math.ceil(rc / Lx)) + 1
+    ny = int(math.ceil(rc / Ly)) + 1
+    phi = np.zeros(idx.size)
+    F = np.zeros((idx.size, 3))
+    for a, i in enumerate(idx):
+        d0 = pos[i][None, :] - pos
+        for ix in range(-nx, nx + 1):
+            for iy in range(-ny, ny + 1):
+                d = d0.copy()
+                d[:, 0] += ix * Lx
+                d[:, 1] += iy * Ly
+                r = np.sqrt((d * d).sum(-1))
+                mask = r <= rc
+                if ix == 0 and iy == 0:
+                    mask[i] = False
+                if not mask.any():
+                    continue
+                rr = r[mask]
+                e = erfc(alpha * rr) / rr
+                phi[a] += e @ q[mask]
+                fr = (e + 2 * alpha / SQPI * np.exp(-(alpha * rr) ** 2)) / (rr * rr)
+                F[a] += q[i] * ((fr * q[mask])[:, None] * d[mask]).sum(0)
+    return {"phi": phi, "F": F}
+
+
 def image_sum_energy(pos, q, box, R, chunk=200_000):
     """U(R) = 1/2 sum_{|M| <= R} sum'_{i,j} q_i q_j/|r_ij + M| (Eq. 2.8) with the
     images M = (mx Lx, my Ly, 0) inside the disc of radius R."""

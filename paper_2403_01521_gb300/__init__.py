@@ -70,6 +70,8 @@ def load(build_if_missing: bool = True):
         "qslab_compute_static": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_compute_batched": ([P, I, P, P, P, P, P, P, P, P], I),
         "qslab_autotune": ([P, I, P, P, P, P, P, I, P, P], I),
+        "qslab_set_rcut": ([P, D], I),
+        "qslab_compute_realspace": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_get_sampled_modes": ([P, P, P], I),
         "qslab_get_rng_state": ([P, P, P], I),
         "qslab_set_rng_state": ([P, ctypes.c_uint64, ctypes.c_uint64], I),
@@ -186,6 +188,16 @@ def qslab_autotune(h, offsets, boxes, pos_ptr, q_ptr, stream_ptr, reps=3):
     return L.value, kr.value
 
 
+def qslab_set_rcut(h, rc):
+    _check(load().qslab_set_rcut(h, float(rc)), "qslab_set_rcut")
+
+
+def qslab_compute_realspace(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr, stream_ptr):
+    """Real-space part (Eq. 2.10) within the cut-off set by qslab_set_rcut."""
+    _check(load().qslab_compute_realspace(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr,
+                                          stream_ptr), "qslab_compute_realspace")
+
+
 def qslab_get_sampled_modes(h, P, R=1):
     """(mx, my, weight) of the latest random-batch call: arrays of P (R = 1)
     or R x P, and the weight H/P (a float, or R of them)."""
@@ -274,8 +286,9 @@ class QSlab:
         except Exception:
             pass
 
-    def configure(self, box, alpha, soe, kcut=None, rbe=None, tail=1e-8):
-        """box=(Lx,Ly,Lz); soe=(s,w) or M; kcut (full k-sum) or rbe=(P, seed)."""
+    def configure(self, box, alpha, soe, kcut=None, rbe=None, tail=1e-8, rcut=None):
+        """box=(Lx,Ly,Lz); soe=(s,w) or M; kcut (full k-sum) or rbe=(P, seed);
+        rcut: the real-space cut-off for compute_realspace (optional)."""
         if isinstance(soe, int):
             soe = load_soe(soe)
         qslab_set_box(self.h, *map(float, box))
@@ -287,6 +300,8 @@ class QSlab:
             qslab_set_rbe(self.h, self.P, int(rbe[1]))
         else:
             qslab_set_kcut(self.h, float(kcut if kcut is not None else kcut_for_tail(alpha, tail)))
+        if rcut is not None:
+            qslab_set_rcut(self.h, float(rcut))
         return self
 
     def tuning(self, chunk=0, modes_per_cta=0):
@@ -350,6 +365,28 @@ class QSlab:
                               force.data_ptr() if force is not None else None, st)
         self.last_R = R
         return energies, phi, force
+
+    def compute_realspace(self, pos, q, energy=None, phi=None, force=None, want_phi=True,
+                          want_force=True):
+        """Real-space part: (energy[1] float64, phi[N], force[N,3]) as CUDA tensors."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        if pos.device != dev or q.device != dev:
+            raise ValueError("pos and q must be CUDA tensors on the context's device")
+        pos = pos.to(self.dtype).contiguous()
+        q = q.to(self.dtype).contiguous()
+        N = q.shape[0]
+        if energy is None:
+            energy = torch.empty(1, dtype=torch.float64, device=dev)
+        if phi is None and want_phi:
+            phi = torch.empty(N, dtype=self.dtype, device=dev)
+        if force is None and want_force:
+            force = torch.empty((N, 3), dtype=self.dtype, device=dev)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        qslab_compute_realspace(self.h, N, pos.data_ptr(), q.data_ptr(), energy.data_ptr(),
+                                phi.data_ptr() if phi is not None else None,
+                                force.data_ptr() if force is not None else None, st)
+        return energy, phi, force
 
     def compute_host(self, pos, q, stream=None):
         """Host numpy in, host numpy out, through qslab_compute_host."""

@@ -66,6 +66,7 @@ struct qslab_ctx {
   double neutral_tol = -2.0;    // < -1: default for the precision
   int tune_L = 0, tune_KR = 0;
   bool timing = false;
+  double rc = 0;                // real-space cut-off (0: not set)
   // derived configuration
   bool cfg_dirty = true;
   uint64_t cfg_version = 0;
@@ -84,6 +85,8 @@ struct qslab_ctx {
   // per-call workspace
   void* d_ws = nullptr;
   size_t ws_bytes = 0;
+  void* d_rs_ws = nullptr;      // real-space workspace
+  size_t rs_ws_bytes = 0;
   cudaStream_t last_stream = nullptr;
   bool have_sample = false;
   int last_R = 1;
@@ -749,6 +752,7 @@ void qslab_destroy(qslab_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   if (c->d_ws) cudaFree(c->d_ws);
+  if (c->d_rs_ws) cudaFree(c->d_rs_ws);
   if (c->d_tab) cudaFree(c->d_tab);
   if (c->d_status) cudaFree(c->d_status);
   for (auto& ev : c->ev)
@@ -881,6 +885,53 @@ int qslab_compute_host(qslab_ctx* c, int64_t N, const void* pos_host, const void
   if (phi_host) QS_CUDA(cudaMemcpyAsync(phi_host, dphi, tsz * N, cudaMemcpyDeviceToHost, st));
   if (force_host) QS_CUDA(cudaMemcpyAsync(force_host, df, 3 * tsz * N, cudaMemcpyDeviceToHost, st));
   return qslab_last_status(c);
+}
+
+int qslab_set_rcut(qslab_ctx* c, double rc) {
+  if (!c || !finite_pos(rc)) return QSLAB_ERR_INVALID_ARG;
+  c->rc = rc;
+  return QSLAB_OK;
+}
+
+int qslab_compute_realspace(qslab_ctx* c, int64_t N, const void* pos, const void* q,
+                            double* energy, void* phi, void* force, void* stream) {
+  if (!c || !pos || !q || N < 1 || N > 2147483647LL) return QSLAB_ERR_INVALID_ARG;
+  if (!c->has_box || !c->has_alpha || c->rc <= 0) return QSLAB_ERR_NOT_CONFIGURED;
+  RsGrid g;
+  g.N = N;
+  g.Lx = c->Lx; g.Ly = c->Ly; g.Lz = c->Lz;
+  g.alpha = c->alpha;
+  g.rc = c->rc;
+  const double fx = std::floor(c->Lx / c->rc), fy = std::floor(c->Ly / c->rc);
+  if (fx < 3 || fy < 3) return QSLAB_ERR_INVALID_ARG;   // needs rc <= min(Lx, Ly)/3
+  const double fz = std::max(1.0, std::floor(c->Lz / c->rc));
+  if (fx * fy * fz > 1.0e8) return QSLAB_ERR_INVALID_ARG;
+  g.ncx = (int)fx; g.ncy = (int)fy; g.ncz = (int)fz;
+  g.hz = c->Lz / g.ncz;
+  QS_CUDA(cudaSetDevice(c->device));
+  const size_t need = rs_workspace_bytes(g);
+  if (need > c->rs_ws_bytes) {
+    if (c->d_rs_ws) {
+      cudaDeviceSynchronize();
+      cudaFree(c->d_rs_ws);
+    }
+    c->d_rs_ws = nullptr;
+    c->rs_ws_bytes = 0;
+    QS_CUDA(cudaMalloc(&c->d_rs_ws, need));
+    c->rs_ws_bytes = need;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->prec == QSLAB_FP64)
+    launch_realspace<double>(g, static_cast<const double*>(pos), static_cast<const double*>(q),
+                             c->d_rs_ws, c->d_status, energy, static_cast<double*>(phi),
+                             static_cast<double*>(force), st);
+  else
+    launch_realspace<float>(g, static_cast<const float*>(pos), static_cast<const float*>(q),
+                            c->d_rs_ws, c->d_status, energy, static_cast<float*>(phi),
+                            static_cast<float*>(force), st);
+  QS_CUDA(cudaGetLastError());
+  c->last_stream = st;
+  return QSLAB_OK;
 }
 
 int qslab_get_sampled_modes(qslab_ctx* c, int32_t* mxy, double* weight) {

@@ -231,3 +231,13 @@ def test_small_full_workload_soe_vs_exact(soe16):
     assert abs(so["E"] - ex["E"]) < 1e-11 * abs(ex["E"])
     assert _rel(so["phi"], ex["phi"]) < 1e-10
     assert _rel(so["F"], ex["F"]) < 1e-9
+
+
+def test_realspace_at_equals_all_pairs():
+    """The sampled real-space sum is the all-pairs one restricted to targets."""
+    sl = workloads.uniform_slab(300, (15.0, 12.0, 6.0), 77, alpha=0.5)
+    full = ewald2d.realspace(sl.pos, sl.q, sl.box, 0.5, 5.5)
+    idx = np.array([0, 17, 150, 299])
+    some = ewald2d.realspace_at(sl.pos, sl.q, sl.box, 0.5, 5.5, idx)
+    assert np.allclose(some["phi"], full["phi"][idx], rtol=1e-13, atol=1e-15)
+    assert np.allclose(some["F"], full["F"][idx], rtol=1e-12, atol=1e-14)
