@@ -356,6 +356,7 @@ def run_ours(args):
     }
     if not args.no_batched:
         line["batched"] = run_batched(args, qslab, soe, dev, ws, rank, local, peak, smax)
+    line["realspace"] = run_realspace(args, qslab, soe, dev, ws)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         t, desc, cores = cpu_oracle_sample(sl, soe, P, 1000, sample_modes=8)
         line["cpu_baseline"] = {"value": N / t, "unit": "particles/s", "cores": cores,
@@ -456,16 +457,74 @@ def run_batched(args, qslab, soe, dev, ws, rank, local, peak, smax):
     return out
 
 
+def run_realspace(args, qslab, soe, dev, ws):
+    """The real-space part (Eq. 2.10) on the N = 1e5 workload of the FP32
+    full-k configuration (100 x 100 x 20, alpha = 0.25, rc = 10), FP32C:
+    cell list, every pair from both ends. Pairs per second counts the pairs
+    inside rc (each once per direction)."""
+    import torch
+
+    import workloads
+    sl = workloads.fp32_full()
+    s = qslab.QSlab(dev.index or 0, "fp32c").configure(sl.box, 0.25, soe, kcut=1.0, rcut=10.0)
+    pos = torch.tensor(sl.pos, device=dev, dtype=torch.float32)
+    q = torch.tensor(sl.q, device=dev, dtype=torch.float32)
+    outs = s.compute_realspace(pos, q)
+    for _ in range(max(args.warmup, 3)):
+        s.compute_realspace(pos, q, *outs)
+    s.check()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    steps = max(args.steps, 5)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        s.compute_realspace(pos, q, *outs)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    s.check()
+    ms = reduce_max(e0.elapsed_time(e1) / steps, dev)
+    s.close()
+    # pairs inside rc: density x sphere volume, cut by the walls (estimate
+    # from the uniform density over the slab thickness)
+    Lx, Ly, Lz = sl.box
+    rho = sl.N / (Lx * Ly * Lz)
+    rc = 10.0
+    # mean volume of the sphere of radius rc inside the slab, for uniform z
+    zs = np.linspace(0.0, Lz, 401)
+    def cap(h):   # volume of a sphere cap of height h
+        h = np.clip(h, 0.0, 2 * rc)
+        return np.pi * h * h * (3 * rc - h) / 3.0
+    vol = 4.0 / 3.0 * np.pi * rc ** 3 - cap(rc - zs) - cap(rc - (Lz - zs))
+    pairs = sl.N * rho * float(vol.mean())
+    return {"workload": "N=1e5 charges +-1 uniform in 100x100x20, alpha=0.25, rc=10 (real-space "
+                        "part of the FP32 full-k configuration), FP32C",
+            "ms_per_call": ms, "particles_per_s": job_throughput(sl.N, ws, ms),
+            "pairs_in_rc_per_s": pairs * ws / (ms * 1e-3), "steps": steps}
+
+
 def profile_case(kind="single"):
-    """Two FP32 random-batch calls for profilers: 'single' = the benchmark
+    """Two FP32 calls for profilers: 'single' = the random-batch benchmark
     workload (N = 1e6); 'batched' = the first 128 slabs of the replica
     workload (about 3.3e6 particles) as one batched call, launch shape fixed
-    at 512-particle chunks."""
+    at 512-particle chunks; 'realspace' = the real-space part on the N = 1e5
+    FP32 full-k workload (rc = 10)."""
     import torch
 
     import paper_2403_01521_gb300 as qslab
     import workloads
     soe = qslab.load_soe(16)
+    if kind == "realspace":
+        sl = workloads.fp32_full()
+        slab = qslab.QSlab(0, "fp32c").configure(sl.box, 0.25, soe, kcut=1.0, rcut=10.0)
+        pos = torch.tensor(sl.pos, device="cuda", dtype=torch.float32)
+        q = torch.tensor(sl.q, device="cuda", dtype=torch.float32)
+        for _ in range(2):
+            e, _, _ = slab.compute_realspace(pos, q)
+        slab.check()
+        torch.cuda.synchronize()
+        print("profile case realspace done, E =", float(e.item()))
+        return 0
     if kind == "batched":
         reps = workloads.replicas()[:128]
         off = np.concatenate([[0], np.cumsum([r.N for r in reps])]).astype(np.int64)
@@ -499,7 +558,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-replica batched measurement")
-    ap.add_argument("--profile-case", nargs="?", const="single", choices=["single", "batched"],
+    ap.add_argument("--profile-case", nargs="?", const="single",
+                    choices=["single", "batched", "realspace"],
                     help="only run two FP32 random-batch calls (for profilers)")
     args = ap.parse_args()
     if args.profile_case:

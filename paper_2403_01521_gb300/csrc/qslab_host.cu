@@ -902,9 +902,13 @@ int qslab_compute_realspace(qslab_ctx* c, int64_t N, const void* pos, const void
   g.Lx = c->Lx; g.Ly = c->Ly; g.Lz = c->Lz;
   g.alpha = c->alpha;
   g.rc = c->rc;
-  const double fx = std::floor(c->Lx / c->rc), fy = std::floor(c->Ly / c->rc);
-  if (fx < 3 || fy < 3) return QSLAB_ERR_INVALID_ARG;   // needs rc <= min(Lx, Ly)/3
-  const double fz = std::max(1.0, std::floor(c->Lz / c->rc));
+  if (std::floor(c->Lx / c->rc) < 3 || std::floor(c->Ly / c->rc) < 3)
+    return QSLAB_ERR_INVALID_ARG;   // needs rc <= min(Lx, Ly)/3
+  // cells of edge >= rc/2: a 5 x 5 x 5 stencil covers rc with less volume
+  // than 3 x 3 x 3 cells of edge rc (15.6 rc^3 instead of 27 rc^3)
+  g.s = 2;
+  const double fx = std::floor(c->Lx * g.s / c->rc), fy = std::floor(c->Ly * g.s / c->rc);
+  const double fz = std::max(1.0, std::floor(c->Lz * g.s / c->rc));
   if (fx * fy * fz > 1.0e8) return QSLAB_ERR_INVALID_ARG;
   g.ncx = (int)fx; g.ncy = (int)fy; g.ncz = (int)fz;
   g.hz = c->Lz / g.ncz;

@@ -207,7 +207,8 @@ void launch_mode_coef(const Reps& rp, int npc, const int32_t* list, int rbe, uin
 // ---- real-space part (qslab_real.cu)
 struct RsGrid {
   int64_t N;
-  int ncx, ncy, ncz;        // cells (ncx, ncy >= 3; edges >= rc)
+  int s;                    // cells of edge >= rc/s; (2s+1)^3 neighbour cells
+  int ncx, ncy, ncz;        // cells (ncx, ncy >= 2s + 1)
   double Lx, Ly, Lz, hz;    // box and cell height in z
   double alpha, rc;
 };

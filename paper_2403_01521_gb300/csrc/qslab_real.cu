@@ -3,12 +3,15 @@
 // and its forces, truncated at |r| <= rc (Section 2.3), with images
 // M = (mx Lx, my Ly, 0) in x and y only.
 //
-// Cell list: the box is cut into ncx x ncy x ncz cells of edge >= rc
-// (ncx, ncy >= 3, so that the 3 x 3 x 3 neighbouring cells of a cell are
-// distinct images); particles are sorted by cell with the radix sort of
-// qslab_sort.cu; one CTA per home cell streams the neighbouring cells through
-// shared memory, each with the image shift of its periodic wrap.
+// Cell list: the box is cut into ncx x ncy x ncz cells of edge >= rc/s
+// (ncx, ncy >= 2s + 1, so that the (2s+1)^3 neighbouring cells of a cell
+// are distinct images); particles are sorted by cell with the radix sort of
+// qslab_sort.cu; CTAs take tiles of a home cell's particles and stream the
+// neighbouring cells through shared memory, each with the image shift of its
+// periodic wrap.
 // Every pair is evaluated from both ends (no atomics, deterministic sums).
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -19,12 +22,41 @@ namespace qslab {
 
 template <typename T> struct RsRec { T x, y, z, q; };
 
-__device__ __forceinline__ float rs_erfc(float x) { return erfcf(x); }
-__device__ __forceinline__ double rs_erfc(double x) { return erfc(x); }
-__device__ __forceinline__ float rs_exp_neg(float x) { return __expf(-x); }
-__device__ __forceinline__ double rs_exp_neg(double x) { return exp(-x); }
-__device__ __forceinline__ float rs_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double rs_sqrt(double x) { return sqrt(x); }
+// erfc(x) e^{x^2} for x >= 0 in FP32, branch-free: t P(2t - 1) with
+// t = 1/(1 + x/2) and P of degree 10 fitted by least squares in the relative
+// error (fit_erfcx.py in the package; relative error 1.2e-8 in exact
+// arithmetic, 3e-7 evaluated in FP32).
+__device__ __forceinline__ float rs_erfcx(float x) {
+  const float t = __frcp_rn(fmaf(0.5f, x, 1.0f));
+  const float s = fmaf(2.0f, t, -1.0f);
+  float p = 4.218412153e-05f;
+  p = fmaf(p, s, -3.663383905e-05f);
+  p = fmaf(p, s, -2.994463409e-04f);
+  p = fmaf(p, s, 4.307417894e-04f);
+  p = fmaf(p, s, 1.529219982e-03f);
+  p = fmaf(p, s, -3.243504795e-03f);
+  p = fmaf(p, s, -1.075165204e-02f);
+  p = fmaf(p, s, 1.822168389e-02f);
+  p = fmaf(p, s, 1.397357374e-01f);
+  p = fmaf(p, s, 3.435803177e-01f);
+  p = fmaf(p, s, 5.107913568e-01f);
+  return t * p;
+}
+
+// erfc(a r) and e^{-a^2 r^2} of one pair: FP32 through erfcx and one fast
+// exponential shared by both terms; FP64 with the library functions
+__device__ __forceinline__ void rs_erfc_exp(float ar, float ar2, float& erfc_v, float& ex) {
+  ex = __expf(-ar2);
+  erfc_v = rs_erfcx(ar) * ex;
+}
+__device__ __forceinline__ void rs_erfc_exp(double ar, double ar2, double& erfc_v, double& ex) {
+  ex = exp(-ar2);
+  erfc_v = erfc(ar);
+}
+// 1/r from r^2: the FP32 reciprocal square root (a few ulp) on the FP32
+// path, the exact FP64 operations on the FP64 path
+__device__ __forceinline__ float rs_rinv(float r2) { return rsqrtf(r2); }
+__device__ __forceinline__ double rs_rinv(double r2) { return 1.0 / sqrt(r2); }
 
 // box fraction of x in [0, 1)
 __device__ __forceinline__ double rs_frac(double x, double L) {
@@ -54,14 +86,19 @@ __global__ void rs_keys_kernel(RsGrid g, const T* __restrict__ pos, const T* __r
   }
 }
 
-// first and one-past-last sorted index of every non-empty cell
-__global__ void rs_cells_kernel(int64_t N, const uint32_t* __restrict__ skeys, int32_t* cstart,
-                                int32_t* cend) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t k = skeys[i];
-    if (i == 0 || skeys[i - 1] != k) cstart[k] = (int32_t)i;
-    if (i == N - 1 || skeys[i + 1] != k) cend[k] = (int32_t)(i + 1);
+// cstart[k] = first sorted index of cell k (= of the first cell >= k that
+// is not empty; N for k = ncell), by binary search in the sorted keys, so
+// that the cells of a row of the grid form one contiguous range
+__global__ void rs_cells_kernel(int64_t N, int64_t ncell, const uint32_t* __restrict__ skeys,
+                                int32_t* cstart) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= ncell;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = N;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if ((int64_t)skeys[mid] < k) lo = mid + 1; else hi = mid;
+    }
+    cstart[k] = (int32_t)lo;
   }
 }
 
@@ -81,75 +118,121 @@ __global__ void rs_gather_kernel(RsGrid g, const T* __restrict__ pos, const T* _
   }
 }
 
-constexpr int kRsThreads = 128;
+constexpr int kRsThreads = 64;   // also the width of the hit mask
 
-// One CTA per home cell. For every tile of home particles (one per thread),
-// the 27 neighbouring cells are streamed through shared memory in tiles of
-// kRsThreads records, shifted by the image of their periodic wrap.
+// Grid (cell, part): CTA (c, y) takes the home tiles y, y + gridDim.y, ... of
+// cell c (kRsThreads particles each, one per thread). Cells have edge
+// >= rc/s; the (2s+1)^3 neighbouring cells are visited row by row: the
+// cells of a row in x are consecutive keys, so a row is one or two
+// contiguous ranges of sorted particles (two where it wraps around the box,
+// each with its image shift), streamed through shared memory in tiles.
+// Per tile every thread first marks the tile entries within rc of its
+// particle in a 64-bit register mask, then evaluates erfc and exp for the
+// marked pairs only, so that the warp does not run the pair arithmetic for
+// the candidates outside rc.
 template <typename T>
-__global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g, const int32_t* __restrict__ cstart,
-                                                           const int32_t* __restrict__ cend,
+__global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
+                                                           const int32_t* __restrict__ cstart,
                                                            const RsRec<T>* __restrict__ rec,
                                                            const uint32_t* __restrict__ perm,
                                                            T* phi_out, T* force_out, double* ecell) {
   __shared__ RsRec<T> tile[kRsThreads];
   __shared__ double red[kRsThreads / 32];
   const int c = blockIdx.x;
+  const int S = g.s;
   const int cx = c % g.ncx, cy = (c / g.ncx) % g.ncy, cz = c / (g.ncx * g.ncy);
-  const int hs = cstart[c], he = cend[c];
+  const int hs = cstart[c], he = cstart[c + 1];
   const T alpha = (T)g.alpha, rc2 = (T)(g.rc * g.rc);
   const T a2 = alpha * alpha;
   const T two_a_sqpi = (T)(2.0 * g.alpha / 1.7724538509055160);
   double e_acc = 0.0;
-  for (int i0 = hs; i0 < he; i0 += kRsThreads) {
+  for (int i0 = hs + blockIdx.y * kRsThreads; i0 < he; i0 += gridDim.y * kRsThreads) {
     const int i = i0 + threadIdx.x;
     const bool live = i < he;
-    RsRec<T> ri{0, 0, 0, 0};
+    RsRec<T> ri{(T)-1e30, (T)-1e30, (T)-1e30, (T)0};   // idle threads match nothing
     if (live) ri = rec[i];
     T ph = 0, fx = 0, fy = 0, fz = 0;
-    for (int dz = -1; dz <= 1; ++dz) {
+    for (int dz = -S; dz <= S; ++dz) {
       const int nz = cz + dz;
       if (nz < 0 || nz >= g.ncz) continue;
-      for (int dy = -1; dy <= 1; ++dy) {
+      for (int dy = -S; dy <= S; ++dy) {
         int ny = cy + dy;
         T sy = 0;
         if (ny < 0) { ny += g.ncy; sy = (T)(-g.Ly); }
         else if (ny >= g.ncy) { ny -= g.ncy; sy = (T)g.Ly; }
-        for (int dx = -1; dx <= 1; ++dx) {
-          int nx = cx + dx;
-          T sx = 0;
-          if (nx < 0) { nx += g.ncx; sx = (T)(-g.Lx); }
-          else if (nx >= g.ncx) { nx -= g.ncx; sx = (T)g.Lx; }
-          const int nc = (nz * g.ncy + ny) * g.ncx + nx;
-          const int js = cstart[nc], je = cend[nc];
+        const int row = (nz * g.ncy + ny) * g.ncx;
+        // the row's cells [cx - S, cx + S] as up to two key ranges
+        int seg_a[2], seg_b[2];
+        T seg_s[2];
+        int nseg = 1;
+        const int lo = cx - S, hi = cx + S;
+        if (lo < 0) {
+          seg_a[0] = g.ncx + lo; seg_b[0] = g.ncx - 1; seg_s[0] = (T)(-g.Lx);
+          seg_a[1] = 0; seg_b[1] = hi; seg_s[1] = 0; nseg = 2;
+        } else if (hi >= g.ncx) {
+          seg_a[0] = lo; seg_b[0] = g.ncx - 1; seg_s[0] = 0;
+          seg_a[1] = 0; seg_b[1] = hi - g.ncx; seg_s[1] = (T)g.Lx; nseg = 2;
+        } else {
+          seg_a[0] = lo; seg_b[0] = hi; seg_s[0] = 0;
+        }
+        for (int sg = 0; sg < nseg; ++sg) {
+          const int js = cstart[row + seg_a[sg]], je = cstart[row + seg_b[sg] + 1];
+          const T sx = seg_s[sg];
           for (int j0 = js; j0 < je; j0 += kRsThreads) {
             const int cntj = min(kRsThreads, je - j0);
             __syncthreads();
-            if (threadIdx.x < cntj) {
-              RsRec<T> rj = rec[j0 + threadIdx.x];
-              rj.x += sx;
-              rj.y += sy;
+            {
+              // a short tile is padded with records far outside any cut-off
+              RsRec<T> rj{(T)1e30, (T)1e30, (T)1e30, (T)0};
+              if (threadIdx.x < cntj) {
+                rj = rec[j0 + threadIdx.x];
+                rj.x += sx;
+                rj.y += sy;
+              }
               tile[threadIdx.x] = rj;
             }
             __syncthreads();
-            if (live) {
-              for (int t = 0; t < cntj; ++t) {
-                const RsRec<T> rj = tile[t];
+            // phase 1: mark the tile entries within rc; the particle itself
+            // (r2 = 0) is left out (so would a distinct particle at the same
+            // point be, whose pair energy is infinite)
+            uint32_t m0 = 0u, m1 = 0u;
+#pragma unroll
+            for (int t = 0; t < 32; ++t) {
+              const RsRec<T> rj = tile[t];
+              const T ddx = ri.x - rj.x, ddy = ri.y - rj.y, ddz = ri.z - rj.z;
+              const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+              m0 |= (r2 <= rc2 && r2 > (T)0) ? (1u << t) : 0u;
+            }
+            if (cntj > 32) {
+#pragma unroll
+              for (int t = 0; t < 32; ++t) {
+                const RsRec<T> rj = tile[32 + t];
                 const T ddx = ri.x - rj.x, ddy = ri.y - rj.y, ddz = ri.z - rj.z;
                 const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                if (r2 <= rc2 && (j0 + t != i || nc != c)) {
-                  const T r = rs_sqrt(r2);
-                  const T inv = (T)1 / r;
-                  const T e = rs_erfc(alpha * r) * inv;          // erfc(a r)/r
-                  const T g2 = two_a_sqpi * rs_exp_neg(a2 * r2);  // 2a/sqrt(pi) e^{-a^2 r^2}
-                  const T fr = (e + g2) * inv * inv;             // -(d/dr)(erfc(a r)/r) / r
-                  ph = fma(rj.q, e, ph);
-                  const T w = rj.q * fr;
-                  fx = fma(w, ddx, fx);
-                  fy = fma(w, ddy, fy);
-                  fz = fma(w, ddz, fz);
-                }
+                m1 |= (r2 <= rc2 && r2 > (T)0) ? (1u << t) : 0u;
               }
+            }
+            if (!live) m0 = m1 = 0u;
+            unsigned long long mask = ((unsigned long long)m1 << 32) | m0;
+            // phase 2: the pair terms of the marked entries
+            while (mask) {
+              const int t = __ffsll((long long)mask) - 1;
+              mask &= mask - 1ull;
+              const RsRec<T> rj = tile[t];
+              const T ddx = ri.x - rj.x, ddy = ri.y - rj.y, ddz = ri.z - rj.z;
+              const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+              const T inv = rs_rinv(r2);
+              const T r = r2 * inv;
+              T erfc_v, ex;
+              rs_erfc_exp(alpha * r, a2 * r2, erfc_v, ex);
+              const T e = erfc_v * inv;                      // erfc(a r)/r
+              const T g2 = two_a_sqpi * ex;                  // 2a/sqrt(pi) e^{-a^2 r^2}
+              const T fr = (e + g2) * inv * inv;             // -(d/dr)(erfc(a r)/r) / r
+              ph = fma(rj.q, e, ph);
+              const T w = rj.q * fr;
+              fx = fma(w, ddx, fx);
+              fy = fma(w, ddy, fy);
+              fz = fma(w, ddz, fz);
             }
           }
         }
@@ -172,7 +255,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g, const int
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < kRsThreads / 32; ++w) s += red[w];
-    ecell[c] = s;
+    ecell[(size_t)c * gridDim.y + blockIdx.y] = s;
   }
 }
 
@@ -191,11 +274,18 @@ __global__ void rs_energy_kernel(int ncell, const double* ecell, double* energy)
   }
 }
 
+// CTAs per cell: about twice the mean occupancy over kRsThreads
+static int rs_parts(const RsGrid& g) {
+  const double ncell = (double)g.ncx * g.ncy * g.ncz;
+  const double per = 2.0 * (double)g.N / ncell / kRsThreads;
+  return (int)std::min(64.0, std::max(1.0, std::ceil(per)));
+}
+
 size_t rs_workspace_bytes(const RsGrid& g) {
   const int64_t ncell = (int64_t)g.ncx * g.ncy * g.ncz;
   auto a = [](size_t b) { return (b + 255) & ~size_t(255); };
-  return a(sort_workspace_bytes(g.N, 4)) + 2 * a(4 * (size_t)ncell) + a(8 * (size_t)ncell) +
-         a(sizeof(RsRec<double>) * (size_t)g.N);
+  return a(sort_workspace_bytes(g.N, 4)) + a(4 * (size_t)(ncell + 1)) +
+         a(8 * (size_t)ncell * rs_parts(g)) + a(sizeof(RsRec<double>) * (size_t)g.N);
 }
 
 template <typename T>
@@ -207,9 +297,9 @@ int launch_realspace(const RsGrid& g, const T* pos, const T* q, void* ws, unsign
   SortWork sw;
   sort_bind_workspace(sw, p, g.N, 4);
   p += a(sort_workspace_bytes(g.N, 4));
-  int32_t* cstart = reinterpret_cast<int32_t*>(p); p += a(4 * (size_t)ncell);
-  int32_t* cend = reinterpret_cast<int32_t*>(p); p += a(4 * (size_t)ncell);
-  double* ecell = reinterpret_cast<double*>(p); p += a(8 * (size_t)ncell);
+  int32_t* cstart = reinterpret_cast<int32_t*>(p); p += a(4 * (size_t)(ncell + 1));
+  const int parts = rs_parts(g);
+  double* ecell = reinterpret_cast<double*>(p); p += a(8 * (size_t)ncell * parts);
   RsRec<T>* rec = reinterpret_cast<RsRec<T>*>(p);
   int blocks = (int)((g.N + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
@@ -218,14 +308,15 @@ int launch_realspace(const RsGrid& g, const T* pos, const T* q, void* ws, unsign
   int passes = 1;
   while (passes < 4 && (uint64_t)ncell > (1ull << (8 * passes))) ++passes;
   const int r = radix_sort(sw, g.N, 4, passes, 0, st);
-  cudaMemsetAsync(cstart, 0, 4 * (size_t)ncell, st);
-  cudaMemsetAsync(cend, 0, 4 * (size_t)ncell, st);
-  rs_cells_kernel<<<blocks, 256, 0, st>>>(g.N, static_cast<const uint32_t*>(sw.keys[r]), cstart,
-                                          cend);
+  int cblocks = (int)((ncell + 1 + 255) / 256);
+  if (cblocks > 152 * 16) cblocks = 152 * 16;
+  rs_cells_kernel<<<cblocks, 256, 0, st>>>(g.N, ncell, static_cast<const uint32_t*>(sw.keys[r]),
+                                           cstart);
   rs_gather_kernel<T><<<blocks, 256, 0, st>>>(g, pos, q, sw.vals[r], rec);
-  rs_pair_kernel<T><<<(unsigned)ncell, kRsThreads, 0, st>>>(g, cstart, cend, rec, sw.vals[r], phi,
-                                                            force, ecell);
-  if (energy) rs_energy_kernel<<<1, 256, 0, st>>>((int)ncell, ecell, energy);
+  rs_pair_kernel<T><<<dim3((unsigned)ncell, parts), kRsThreads, 0, st>>>(g, cstart, rec,
+                                                                          sw.vals[r], phi, force,
+                                                                          ecell);
+  if (energy) rs_energy_kernel<<<1, 256, 0, st>>>((int)(ncell * parts), ecell, energy);
   return 3 + 3 * passes + (energy ? 2 : 1);
 }
 
