@@ -16,6 +16,7 @@
 
 #include "qslab.h"
 #include "qslab_internal.h"
+#include "qslab_real.h"
 
 using namespace qslab;
 

@@ -204,19 +204,4 @@ void launch_mode_coef(const Reps& rp, int npc, const int32_t* list, int rbe, uin
                       const uint64_t* ctr, const double* cdf, const PairTab& pairs,
                       double alpha, ModeTab<T> modes, int32_t* sampled, cudaStream_t st);
 
-// ---- real-space part (qslab_real.cu)
-struct RsGrid {
-  int64_t N;
-  int s;                    // cells of edge >= rc/s; (2s+1)^3 neighbour cells
-  int ncx, ncy, ncz;        // cells (ncx, ncy >= 2s + 1)
-  double Lx, Ly, Lz, hz;    // box and cell height in z
-  double alpha, rc;
-};
-size_t rs_workspace_bytes(const RsGrid& g);
-// phi, force (caller's order; may be NULL) and energy (device scalar, may be
-// NULL) of the real-space sum; returns the number of kernels launched
-template <typename T>
-int launch_realspace(const RsGrid& g, const T* pos, const T* q, void* ws, unsigned* status,
-                     double* energy, T* phi, T* force, cudaStream_t st);
-
 }  // namespace qslab

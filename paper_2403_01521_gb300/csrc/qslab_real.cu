@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include "qslab_internal.h"
+#include "qslab_real.h"
 #include "qslab_math.cuh"
 
 namespace qslab {
