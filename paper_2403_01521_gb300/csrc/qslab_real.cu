@@ -24,11 +24,12 @@ namespace qslab {
 template <typename T> struct RsRec { T x, y, z, q; };
 
 // erfc(x) e^{x^2} for x >= 0 in FP32, branch-free: t P(2t - 1) with
-// t = 1/(1 + x/2) and P of degree 10 fitted by least squares in the relative
-// error (fit_erfcx.py in the package; relative error 1.2e-8 in exact
-// arithmetic, 3e-7 evaluated in FP32).
+// t = 1/(1 + x/2) (the approximate reciprocal, within 2 ulp) and P of degree
+// 10 fitted by least squares in the relative error (fit_erfcx.py in the
+// package; relative error 1.2e-8 in exact arithmetic, below 7e-7 evaluated
+// in FP32).
 __device__ __forceinline__ float rs_erfcx(float x) {
-  const float t = __frcp_rn(fmaf(0.5f, x, 1.0f));
+  const float t = __fdividef(1.0f, fmaf(0.5f, x, 1.0f));
   const float s = fmaf(2.0f, t, -1.0f);
   float p = 4.218412153e-05f;
   p = fmaf(p, s, -3.663383905e-05f);
@@ -119,25 +120,28 @@ __global__ void rs_gather_kernel(RsGrid g, const T* __restrict__ pos, const T* _
   }
 }
 
-constexpr int kRsThreads = 64;   // also the width of the hit mask
+constexpr int kRsThreads = 64;   // home particles per CTA, one per thread
+constexpr int kRsRow = 512;      // neighbour records staged in shared memory at once
 
 // Grid (cell, part): CTA (c, y) takes the home tiles y, y + gridDim.y, ... of
 // cell c (kRsThreads particles each, one per thread). Cells have edge
 // >= rc/s; the (2s+1)^3 neighbouring cells are visited row by row: the
 // cells of a row in x are consecutive keys, so a row is one or two
 // contiguous ranges of sorted particles (two where it wraps around the box,
-// each with its image shift), streamed through shared memory in tiles.
-// Per tile every thread first marks the tile entries within rc of its
-// particle in a 64-bit register mask, then evaluates erfc and exp for the
-// marked pairs only, so that the warp does not run the pair arithmetic for
-// the candidates outside rc.
+// each with its image shift). A row is staged in shared memory in one piece
+// (kRsRow records at a time), padded to a multiple of 32 with records far
+// outside any cut-off. Per group of 32 staged records every thread first
+// marks those within rc of its particle in a 32-bit mask, then evaluates
+// erfc and exp for the marked pairs only, so that the warp does not run the
+// pair arithmetic for the candidates outside rc. A warp without a home
+// particle only helps to stage the rows.
 template <typename T>
 __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
                                                            const int32_t* __restrict__ cstart,
                                                            const RsRec<T>* __restrict__ rec,
                                                            const uint32_t* __restrict__ perm,
                                                            T* phi_out, T* force_out, double* ecell) {
-  __shared__ RsRec<T> tile[kRsThreads];
+  __shared__ RsRec<T> buf[kRsRow];
   __shared__ double red[kRsThreads / 32];
   const int c = blockIdx.x;
   const int S = g.s;
@@ -146,10 +150,12 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
   const T alpha = (T)g.alpha, rc2 = (T)(g.rc * g.rc);
   const T a2 = alpha * alpha;
   const T two_a_sqpi = (T)(2.0 * g.alpha / 1.7724538509055160);
+  const RsRec<T> far{(T)1e30, (T)1e30, (T)1e30, (T)0};
   double e_acc = 0.0;
   for (int i0 = hs + blockIdx.y * kRsThreads; i0 < he; i0 += gridDim.y * kRsThreads) {
     const int i = i0 + threadIdx.x;
     const bool live = i < he;
+    const bool wlive = __ballot_sync(0xffffffffu, live) != 0u;   // warp-uniform
     RsRec<T> ri{(T)-1e30, (T)-1e30, (T)-1e30, (T)0};   // idle threads match nothing
     if (live) ri = rec[i];
     T ph = 0, fx = 0, fy = 0, fz = 0;
@@ -162,64 +168,54 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
         if (ny < 0) { ny += g.ncy; sy = (T)(-g.Ly); }
         else if (ny >= g.ncy) { ny -= g.ncy; sy = (T)g.Ly; }
         const int row = (nz * g.ncy + ny) * g.ncx;
-        // the row's cells [cx - S, cx + S] as up to two key ranges
-        int seg_a[2], seg_b[2];
-        T seg_s[2];
-        int nseg = 1;
+        // the row's cells [cx - S, cx + S] as up to two key ranges: records
+        // [a0, a0 + n0) shifted by s0, then [a1, a1 + n1) shifted by s1
         const int lo = cx - S, hi = cx + S;
+        int a0, n0, a1 = 0, n1 = 0;
+        T s0 = 0, s1 = 0;
         if (lo < 0) {
-          seg_a[0] = g.ncx + lo; seg_b[0] = g.ncx - 1; seg_s[0] = (T)(-g.Lx);
-          seg_a[1] = 0; seg_b[1] = hi; seg_s[1] = 0; nseg = 2;
+          a0 = cstart[row + g.ncx + lo]; n0 = cstart[row + g.ncx] - a0; s0 = (T)(-g.Lx);
+          a1 = cstart[row]; n1 = cstart[row + hi + 1] - a1;
         } else if (hi >= g.ncx) {
-          seg_a[0] = lo; seg_b[0] = g.ncx - 1; seg_s[0] = 0;
-          seg_a[1] = 0; seg_b[1] = hi - g.ncx; seg_s[1] = (T)g.Lx; nseg = 2;
+          a0 = cstart[row + lo]; n0 = cstart[row + g.ncx] - a0;
+          a1 = cstart[row]; n1 = cstart[row + hi - g.ncx + 1] - a1; s1 = (T)g.Lx;
         } else {
-          seg_a[0] = lo; seg_b[0] = hi; seg_s[0] = 0;
+          a0 = cstart[row + lo]; n0 = cstart[row + hi + 1] - a0;
         }
-        for (int sg = 0; sg < nseg; ++sg) {
-          const int js = cstart[row + seg_a[sg]], je = cstart[row + seg_b[sg] + 1];
-          const T sx = seg_s[sg];
-          for (int j0 = js; j0 < je; j0 += kRsThreads) {
-            const int cntj = min(kRsThreads, je - j0);
-            __syncthreads();
-            {
-              // a short tile is padded with records far outside any cut-off
-              RsRec<T> rj{(T)1e30, (T)1e30, (T)1e30, (T)0};
-              if (threadIdx.x < cntj) {
-                rj = rec[j0 + threadIdx.x];
-                rj.x += sx;
-                rj.y += sy;
-              }
-              tile[threadIdx.x] = rj;
+        const int nrow = n0 + n1;
+        for (int b0 = 0; b0 < nrow; b0 += kRsRow) {
+          const int cnt = min(kRsRow, nrow - b0);
+          const int cpad = (cnt + 31) & ~31;
+          __syncthreads();   // the previous records are no longer read
+          for (int t = threadIdx.x; t < cpad; t += kRsThreads) {
+            const int e = b0 + t;
+            RsRec<T> rj = far;
+            if (t < cnt) {
+              if (e < n0) { rj = rec[a0 + e]; rj.x += s0; }
+              else { rj = rec[a1 + (e - n0)]; rj.x += s1; }
+              rj.y += sy;
             }
-            __syncthreads();
-            // phase 1: mark the tile entries within rc; the particle itself
-            // (r2 = 0) is left out (so would a distinct particle at the same
-            // point be, whose pair energy is infinite)
-            uint32_t m0 = 0u, m1 = 0u;
+            buf[t] = rj;
+          }
+          __syncthreads();
+          if (!wlive) continue;
+          for (int t0 = 0; t0 < cpad; t0 += 32) {
+            // phase 1: mark the records within rc; the particle itself
+            // (r2 = 0) is left out (so would a distinct particle at the
+            // same point be, whose pair energy is infinite)
+            uint32_t m = 0u;
 #pragma unroll
             for (int t = 0; t < 32; ++t) {
-              const RsRec<T> rj = tile[t];
+              const RsRec<T> rj = buf[t0 + t];
               const T ddx = ri.x - rj.x, ddy = ri.y - rj.y, ddz = ri.z - rj.z;
               const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-              m0 |= (r2 <= rc2 && r2 > (T)0) ? (1u << t) : 0u;
+              m |= (r2 <= rc2 && r2 > (T)0) ? (1u << t) : 0u;
             }
-            if (cntj > 32) {
-#pragma unroll
-              for (int t = 0; t < 32; ++t) {
-                const RsRec<T> rj = tile[32 + t];
-                const T ddx = ri.x - rj.x, ddy = ri.y - rj.y, ddz = ri.z - rj.z;
-                const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                m1 |= (r2 <= rc2 && r2 > (T)0) ? (1u << t) : 0u;
-              }
-            }
-            if (!live) m0 = m1 = 0u;
-            unsigned long long mask = ((unsigned long long)m1 << 32) | m0;
-            // phase 2: the pair terms of the marked entries
-            while (mask) {
-              const int t = __ffsll((long long)mask) - 1;
-              mask &= mask - 1ull;
-              const RsRec<T> rj = tile[t];
+            // phase 2: the pair terms of the marked records
+            while (m) {
+              const int t = __ffs(m) - 1;
+              m &= m - 1u;
+              const RsRec<T> rj = buf[t0 + t];
               const T ddx = ri.x - rj.x, ddy = ri.y - rj.y, ddz = ri.z - rj.z;
               const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
               const T inv = rs_rinv(r2);

@@ -8,7 +8,7 @@ Chebyshev nodes in t, with erfcx from scipy in FP64.
 
 Run: python paper_2403_01521_gb300/fit_erfcx.py   (prints the coefficients
 of P, constant term first, and the maximum relative error on x in [0, 12]
-in FP64 and in an FP32 Horner evaluation)
+in FP64 and in an FP32 Horner evaluation with t within 2 ulp)
 """
 import numpy as np
 from scipy.special import erfcx
@@ -28,23 +28,31 @@ def fit(degree=DEGREE, nodes=6000):
     return coef
 
 
-def check(coef):
+def check(coef, t_ulps=0):
+    """Maximum relative error of t P(2t - 1) against erfcx on x in [0, 12]:
+    in FP64, and in an FP32 Horner evaluation whose t = 1/(1 + x/2) is off
+    by -t_ulps, 0 and +t_ulps units in the last place (the worst of the
+    three; the kernel's approximate reciprocal is within 2 ulp)."""
     x = np.linspace(0, 12, 400001)
     t = 1 / (1 + P_SCALE * x)
     rel64 = np.abs(np.polyval(coef[::-1], 2 * t - 1) * t / erfcx(x) - 1).max()
     x32 = x.astype(np.float32)
     t32 = (np.float32(1) / (np.float32(1) + np.float32(P_SCALE) * x32)).astype(np.float32)
-    s32 = (np.float32(2) * t32 - np.float32(1)).astype(np.float32)
     c32 = coef.astype(np.float32)
-    acc = c32[-1]
-    for c in c32[::-1][1:]:
-        acc = (acc * s32 + c).astype(np.float32)
-    rel32 = np.abs((acc * t32).astype(np.float64) / erfcx(x32.astype(np.float64)) - 1).max()
+    rel32 = 0.0
+    for u in sorted({-t_ulps, 0, t_ulps}):
+        tu = (t32 + np.float32(u) * np.spacing(t32)).astype(np.float32)
+        s32 = (np.float32(2) * tu - np.float32(1)).astype(np.float32)
+        acc = c32[-1]
+        for c in c32[::-1][1:]:
+            acc = (acc * s32 + c).astype(np.float32)
+        ref = erfcx(x32.astype(np.float64))
+        rel32 = max(rel32, np.abs((acc * tu).astype(np.float64) / ref - 1).max())
     return rel64, rel32
 
 
 if __name__ == "__main__":
     c = fit()
-    r64, r32 = check(c)
+    r64, r32 = check(c, t_ulps=2)
     print("coefficients:", ", ".join("%.9e" % v for v in c))
-    print("max relative error: FP64 %.2e, FP32 %.2e" % (r64, r32))
+    print("max relative error: FP64 %.2e, FP32 (t within 2 ulp) %.2e" % (r64, r32))

@@ -1,6 +1,7 @@
 """The FP32 erfc of the real-space kernel: its coefficients are the ones the
 committed fit produces, and the fit meets its stated error bound against
-scipy's erfcx (FP64) and evaluated in FP32 arithmetic."""
+scipy's erfcx, in FP64 and in FP32 arithmetic with the reciprocal
+t = 1/(1 + x/2) off by up to 2 units in the last place."""
 import os
 import re
 
@@ -24,6 +25,6 @@ def test_erfc_fit_matches_kernel_and_bound():
     ker = _kernel_coefficients()
     assert ker.shape == coef.shape
     assert np.allclose(ker, coef, rtol=1e-8, atol=1e-12)
-    rel64, rel32 = fit_erfcx.check(ker)
+    rel64, rel32 = fit_erfcx.check(ker, t_ulps=2)
     assert rel64 < 2e-8
-    assert rel32 < 5e-7
+    assert rel32 < 7e-7
