@@ -98,7 +98,10 @@ int qslab_set_soe(qslab_ctx* ctx, int M, const double* s_re, const double* s_im,
 
 /* Neutrality tolerance: compute() flags QSLAB_ERR_NONNEUTRAL when
  * |sum q| > tol * sum |q|. Default 64 x the unit roundoff of the precision.
- * A negative tol disables the check. */
+ * A negative tol disables the check. With charged walls
+ * (qslab_set_walls) the check covers particles and walls together:
+ * |sum q + A (sigma_bot + sigma_top)| > tol (sum |q| + A (|sigma_bot| + |sigma_top|)),
+ * A = Lx Ly of the slab. */
 int qslab_set_neutrality_tol(qslab_ctx* ctx, double tol);
 
 /* Launch shape: particles per chunk (0 = automatic; at most 512 for FP32C,
@@ -157,7 +160,7 @@ int qslab_compute(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
  * and are shared by all replicas; the full k-sum uses each replica's own
  * half-plane lattice, the random batch draws P vectors per replica from the
  * replica's own h(k), with the stream index r in the generator's counter.
- * Every replica must be charge neutral on its own.
+ * Every replica must be charge neutral on its own (with the walls, if set).
  * Tables derived from offsets and boxes are cached in the context: calls
  * that repeat them do no host-side set-up and no synchronous transfer. Such a
  * repeat call (after one ordinary call with the same arguments and buffers
@@ -206,6 +209,32 @@ int qslab_compute_host(qslab_ctx* ctx, int64_t N, const void* pos_host,
 int qslab_compute_static(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
                          double* energy, void* phi, void* force, void* stream);
 
+/* Charged walls at z = 0 (bottom) and z = Lz (top), Section 2.4. The walls
+ * carry doubly periodic surface charge densities (charge per unit area)
+ *   sigma_bot(rho) = sigma_bot + sum_w 2 Re[(bot[2w] + i bot[2w+1]) e^{i k_w.rho}]
+ *   sigma_top(rho) = sigma_top + sum_w 2 Re[(top[2w] + i top[2w+1]) e^{i k_w.rho}]
+ * with k_w = (2 pi mxy[2w]/Lx, 2 pi mxy[2w+1]/Ly), w < nw. After this call
+ * qslab_compute() and qslab_compute_batched() (every replica, each with its
+ * own box) add the particle-slab potential of Thm 2.4,
+ *   phi_p-s(r) = -2 pi [sigma_bot z + sigma_top (Lz - z)]
+ *                + sum_w Re[e^{i k_w.rho} (4 pi / |k_w|)
+ *                       ((bot_w) e^{-|k_w| z} + (top_w) e^{-|k_w| (Lz - z)})],
+ * to phi, its force -q grad phi_p-s to force, and sum_i q_i phi_p-s(r_i) to
+ * the energy (each particle-wall pair counted once, so that F = -grad E and
+ * phi = dE/dq still hold). The particles then need not be neutral; the
+ * neutrality check covers particles and walls together.
+ *   sigma_bot, sigma_top: uniform parts (finite).
+ *   nw: 0 (uniform walls, the special case after Thm 2.4) to 64 Fourier modes.
+ *   mxy: host int32 [nw][2], (mx, my) != (0, 0), |mx|, |my| <= 2^20, each
+ *        pair (m, -m) listed at most once; bot, top: host double [nw][2]
+ *        (real, imaginary part). Copied; may be NULL when nw = 0.
+ * QSLAB_ERR_INVALID_ARG on any violation (the walls are then unchanged).
+ * qslab_clear_walls() removes them. The real-space part does not involve
+ * the walls. */
+int qslab_set_walls(qslab_ctx* ctx, double sigma_bot, double sigma_top, int nw,
+                    const int32_t* mxy, const double* bot, const double* top);
+int qslab_clear_walls(qslab_ctx* ctx);
+
 /* Real-space cut-off rc for qslab_compute_realspace() (Section 2.3:
  * pairs with |r_ij + M| > rc are dropped; the truncation error is of order
  * erfc(alpha rc)). */
@@ -224,7 +253,7 @@ int qslab_set_rcut(qslab_ctx* ctx, double rc);
  * Needs rc <= min(Lx, Ly)/3 (QSLAB_ERR_INVALID_ARG otherwise) and rc set
  * (QSLAB_ERR_NOT_CONFIGURED). Device-side input errors (non-finite values,
  * z outside [0, Lz]) go to the status word as for qslab_compute(). Cell list
- * with cells of edge >= rc; every pair is evaluated from both ends, in a
+ * with cells of edge >= rc/2; every pair is evaluated from both ends, in a
  * fixed order (bitwise reproducible). Own workspace: it may run on another
  * stream than the long-range call of the same context. The paper evaluates
  * this part with a cell or Verlet list (Section 2.3); not part of Algorithms

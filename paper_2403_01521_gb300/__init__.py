@@ -24,6 +24,17 @@ from .soe import load_soe  # noqa: F401  (tables are method parameters)
 
 QSLAB_FP64 = 0
 QSLAB_FP32C = 1
+# status codes (include/qslab.h)
+QSLAB_OK = 0
+QSLAB_ERR_INVALID_ARG = -1
+QSLAB_ERR_NOT_CONFIGURED = -2
+QSLAB_ERR_NONFINITE = -3
+QSLAB_ERR_Z_OUT_OF_RANGE = -4
+QSLAB_ERR_NONNEUTRAL = -5
+QSLAB_ERR_ALLOC = -6
+QSLAB_ERR_CUDA = -7
+QSLAB_ERR_TIMEOUT = -8
+QSLAB_ERR_TOO_LARGE = -9
 _PREC = {"fp64": QSLAB_FP64, "fp32c": QSLAB_FP32C}
 
 _lib = None
@@ -71,6 +82,8 @@ def load(build_if_missing: bool = True):
         "qslab_compute_batched": ([P, I, P, P, P, P, P, P, P, P], I),
         "qslab_autotune": ([P, I, P, P, P, P, P, I, P, P], I),
         "qslab_set_rcut": ([P, D], I),
+        "qslab_set_walls": ([P, D, D, I, P, P, P], I),
+        "qslab_clear_walls": ([P], I),
         "qslab_compute_realspace": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_get_sampled_modes": ([P, P, P], I),
         "qslab_get_rng_state": ([P, P, P], I),
@@ -192,6 +205,28 @@ def qslab_set_rcut(h, rc):
     _check(load().qslab_set_rcut(h, float(rc)), "qslab_set_rcut")
 
 
+def qslab_set_walls(h, sigma_bot, sigma_top, modes=None, bot=None, top=None):
+    """Charged walls (Section 2.4, Thm 2.4): uniform densities sigma_bot at
+    z = 0 and sigma_top at z = Lz, plus Fourier modes: modes = [(mx, my), ...]
+    (each pair (m, -m) once), bot/top = complex coefficients c_w of
+    sigma(rho) = sigma0 + sum_w 2 Re[c_w e^{i k_w.rho}]."""
+    modes = np.ascontiguousarray(np.zeros((0, 2)) if modes is None else modes, dtype=np.int32).reshape(-1, 2)
+    nw = modes.shape[0]
+    b = np.asarray([] if bot is None else bot, dtype=complex).reshape(-1)
+    t = np.asarray([] if top is None else top, dtype=complex).reshape(-1)
+    if b.size != nw or t.size != nw:
+        raise ValueError("bot and top need one coefficient per mode")
+    bb = np.ascontiguousarray(np.stack([b.real, b.imag], axis=1).reshape(-1))
+    tt = np.ascontiguousarray(np.stack([t.real, t.imag], axis=1).reshape(-1))
+    _check(load().qslab_set_walls(h, float(sigma_bot), float(sigma_top), nw,
+                                  modes.ctypes.data if nw else None, bb.ctypes.data if nw else None,
+                                  tt.ctypes.data if nw else None), "qslab_set_walls")
+
+
+def qslab_clear_walls(h):
+    _check(load().qslab_clear_walls(h), "qslab_clear_walls")
+
+
 def qslab_compute_realspace(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr, stream_ptr):
     """Real-space part (Eq. 2.10) within the cut-off set by qslab_set_rcut."""
     _check(load().qslab_compute_realspace(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr,
@@ -302,6 +337,14 @@ class QSlab:
             qslab_set_kcut(self.h, float(kcut if kcut is not None else kcut_for_tail(alpha, tail)))
         if rcut is not None:
             qslab_set_rcut(self.h, float(rcut))
+        return self
+
+    def set_walls(self, sigma_bot, sigma_top, modes=None, bot=None, top=None):
+        """Charged walls at z = 0 and z = Lz (see qslab_set_walls); None clears them."""
+        if sigma_bot is None:
+            qslab_clear_walls(self.h)
+        else:
+            qslab_set_walls(self.h, sigma_bot, sigma_top, modes, bot, top)
         return self
 
     def tuning(self, chunk=0, modes_per_cta=0):
@@ -415,6 +458,11 @@ class QSlab:
 
     def status(self):
         return qslab_last_status(self.h)
+
+    def set_neutrality_tol(self, tol):
+        """Relative neutrality tolerance; a negative value turns the check off."""
+        qslab_set_neutrality_tol(self.h, float(tol))
+        return self
 
     def check(self):
         rc = qslab_last_status(self.h)

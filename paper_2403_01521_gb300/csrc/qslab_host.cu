@@ -68,6 +68,7 @@ struct qslab_ctx {
   int tune_L = 0, tune_KR = 0;
   bool timing = false;
   double rc = 0;                // real-space cut-off (0: not set)
+  WallTab walls{};              // charged walls (walls.on = 0: none)
   // derived configuration
   bool cfg_dirty = true;
   uint64_t cfg_version = 0;
@@ -633,7 +634,8 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
                     c->d_status, st);
   double tol = c->neutral_tol;
   if (tol < -1.0) tol = 64.0 * (sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
-  launch_check_neutral(rp, sums, tol, c->d_status, rbe ? c->d_ctr : nullptr, st);
+  launch_check_neutral(rp, sums, tol, c->walls.on ? c->walls.sb0 : 0.0,
+                       c->walls.on ? c->walls.st0 : 0.0, c->d_status, rbe ? c->d_ctr : nullptr, st);
   int r = radix_sort(sw, N, (int)sizeof(T), (int)sizeof(T), 0, st);
   nl += 2 + 3 * (int)sizeof(T);   // prepare, check + 3 kernels per sort pass
   if (R > 1) {
@@ -670,7 +672,8 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   nl += 8;
   QS_CUDA(cudaStreamWaitEvent(st, c->join, 0));
   if (ev) cudaEventRecord(ev[6], st);
-  launch_combine<T>(rp, P.sp.nkr, part, phi0, fz0, qs, perm, echunk, phi, force, energies, st);
+  launch_combine<T>(rp, P.sp.nkr, part, phi0, fz0, qs, zs, xh, yh, c->walls, perm, echunk, phi,
+                    force, energies, st);
   nl += energies ? 2 : 1;
   if (ev) cudaEventRecord(ev[7], st);
   c->launches = nl;
@@ -886,6 +889,45 @@ int qslab_compute_host(qslab_ctx* c, int64_t N, const void* pos_host, const void
   if (phi_host) QS_CUDA(cudaMemcpyAsync(phi_host, dphi, tsz * N, cudaMemcpyDeviceToHost, st));
   if (force_host) QS_CUDA(cudaMemcpyAsync(force_host, df, 3 * tsz * N, cudaMemcpyDeviceToHost, st));
   return qslab_last_status(c);
+}
+
+int qslab_set_walls(qslab_ctx* c, double sigma_bot, double sigma_top, int nw,
+                    const int32_t* mxy, const double* bot, const double* top) {
+  if (!c || !std::isfinite(sigma_bot) || !std::isfinite(sigma_top) || nw < 0 ||
+      nw > kMaxWallModes || (nw > 0 && (!mxy || !bot || !top)))
+    return QSLAB_ERR_INVALID_ARG;
+  WallTab w{};
+  w.on = 1;
+  w.nw = nw;
+  w.sb0 = sigma_bot;
+  w.st0 = sigma_top;
+  for (int i = 0; i < nw; ++i) {
+    const int32_t mx = mxy[2 * i], my = mxy[2 * i + 1];
+    if (mx == 0 && my == 0) return QSLAB_ERR_INVALID_ARG;
+    if (mx < -(1 << 20) || mx > (1 << 20) || my < -(1 << 20) || my > (1 << 20))
+      return QSLAB_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j) {   // each pair (m, -m) at most once
+      const int32_t ax = mxy[2 * j], ay = mxy[2 * j + 1];
+      if ((ax == mx && ay == my) || (ax == -mx && ay == -my)) return QSLAB_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < 2; ++k)
+      if (!std::isfinite(bot[2 * i + k]) || !std::isfinite(top[2 * i + k]))
+        return QSLAB_ERR_INVALID_ARG;
+    w.m[i][0] = mx;
+    w.m[i][1] = my;
+    w.c[i][0] = bot[2 * i];
+    w.c[i][1] = bot[2 * i + 1];
+    w.c[i][2] = top[2 * i];
+    w.c[i][3] = top[2 * i + 1];
+  }
+  c->walls = w;
+  return QSLAB_OK;
+}
+
+int qslab_clear_walls(qslab_ctx* c) {
+  if (!c) return QSLAB_ERR_INVALID_ARG;
+  c->walls = WallTab{};
+  return QSLAB_OK;
 }
 
 int qslab_set_rcut(qslab_ctx* c, double rc) {

@@ -105,6 +105,19 @@ struct Reps {
   const int32_t* zgroup_rep;  // [nzgroups]
 };
 
+// Charged walls at z = 0 (bottom) and z = Lz (top), the same for every
+// replica (Section 2.4, Thm 2.4): surface charge densities per unit area
+// sigma(rho) = s0 + sum_w 2 Re[c_w e^{i k_w.rho}], k_w = 2 pi (mx/Lx, my/Ly).
+// Passed to kernels by value (__grid_constant__).
+constexpr int kMaxWallModes = 64;
+struct WallTab {
+  int on;                          // walls set (else the particles must be neutral)
+  int nw;                          // Fourier modes, each pair (m, -m) once
+  double sb0, st0;                 // uniform parts of sigma_bot, sigma_top
+  int32_t m[kMaxWallModes][2];     // (mx, my)
+  double c[kMaxWallModes][4];      // c_bot re, im, c_top re, im
+};
+
 // Status flags set by kernels (bitwise OR into a device word).
 enum StatusBits : unsigned {
   kStNonfinite = 1u,
@@ -137,10 +150,12 @@ int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaS
 template <typename T>
 void launch_prepare(const Reps& rp, const T* pos, const T* q, void* keys, uint32_t* vals,
                     int32_t* rid, double* sums, unsigned* status, cudaStream_t st);
-// Per-replica neutrality check; when ctr is not NULL also advances the
+// Per-replica neutrality check of particles and walls together:
+// |sum q + area (sb0 + st0)| <= tol (sum |q| + area (|sb0| + |st0|)), with
+// sb0 = st0 = 0 without walls; when ctr is not NULL also advances the
 // random-batch counter: ctr[1] = ctr[0]++ (the counter this call uses).
-void launch_check_neutral(const Reps& rp, const double* sums, double tol, unsigned* status,
-                          uint64_t* ctr, cudaStream_t st);
+void launch_check_neutral(const Reps& rp, const double* sums, double tol, double sb0,
+                          double st0, unsigned* status, uint64_t* ctr, cudaStream_t st);
 // Second sort key: keys[i] = rid[perm[i]].
 void launch_rep_keys(int64_t N, const uint32_t* perm, const int32_t* rid, uint32_t* keys,
                      cudaStream_t st);
@@ -189,9 +204,13 @@ size_t kzero_work_doubles(int nzchunks, int nzgroups, int R, int np);
 
 // Potential, forces and per-chunk energies (echunk[nchunks]) back in the
 // caller's order; energies[r] (if not NULL) = the sum over replica r's chunks.
+// With walls (W.on) the particle-slab potential and its forces are added,
+// and the energy gains sum_i q_i phi_p-s,i (zs, xh, yh: sorted z and phases).
 template <typename T>
 void launch_combine(const Reps& rp, int nkr, const T* part, const void* phi0,
-                    const void* fz0, const T* qs, const int32_t* perm, double* echunk,
+                    const void* fz0, const T* qs, const T* zs,
+                    const typename PhaseT<T>::type* xh, const typename PhaseT<T>::type* yh,
+                    const WallTab& W, const int32_t* perm, double* echunk,
                     T* phi_out, T* force_out, double* energies, cudaStream_t st);
 
 // Mode tables of all replicas. rbe = 0: modes from `list` (the replicas'

@@ -71,11 +71,16 @@ void launch_prepare(const Reps& rp, const T* pos, const T* q, void* keys, uint32
       rp, pos, q, static_cast<typename KeyOf<T>::type*>(keys), vals, rid, sums, status);
 }
 
-__global__ void check_neutral_kernel(int R, const double* sums, double tol, unsigned* status,
-                                     uint64_t* ctr) {
+__global__ void check_neutral_kernel(Reps rp, const double* sums, double tol, double sb0,
+                                     double st0, unsigned* status, uint64_t* ctr) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < R && tol >= 0.0 && fabs(sums[2 * r]) > tol * sums[2 * r + 1])
-    atomicOr(status, kStNonneutral);
+  if (r < rp.R && tol >= 0.0) {
+    // particles and walls together (the neutrality condition of Section 2.4)
+    const double a = rp.info[r].area;
+    const double net = sums[2 * r] + a * (sb0 + st0);
+    const double mag = sums[2 * r + 1] + a * (fabs(sb0) + fabs(st0));
+    if (fabs(net) > tol * mag) atomicOr(status, kStNonneutral);
+  }
   if (ctr && r == 0) {
     const uint64_t c = ctr[0];
     ctr[1] = c;
@@ -83,9 +88,9 @@ __global__ void check_neutral_kernel(int R, const double* sums, double tol, unsi
   }
 }
 
-void launch_check_neutral(const Reps& rp, const double* sums, double tol, unsigned* status,
-                          uint64_t* ctr, cudaStream_t st) {
-  check_neutral_kernel<<<(rp.R + 255) / 256, 256, 0, st>>>(rp.R, sums, tol, status, ctr);
+void launch_check_neutral(const Reps& rp, const double* sums, double tol, double sb0,
+                          double st0, unsigned* status, uint64_t* ctr, cudaStream_t st) {
+  check_neutral_kernel<<<(rp.R + 255) / 256, 256, 0, st>>>(rp, sums, tol, sb0, st0, status, ctr);
 }
 
 __global__ void rep_keys_kernel(int64_t N, const uint32_t* __restrict__ perm,
@@ -150,18 +155,44 @@ void launch_gather(const Reps& rp, const T* pos, const T* q, const uint32_t* per
 // ================================================================== combine
 
 // One CTA per k-space chunk: sums the mode ranges' partial outputs, adds the
-// k = 0 term and the j = i constant of the chunk's replica, scatters the
-// potential and force to the caller's order and writes the chunk's energy
-// 1/2 sum q_i phi_i.
+// k = 0 term and the j = i constant of the chunk's replica, and with walls
+// the particle-slab potential (Thm 2.4); scatters the potential and force to
+// the caller's order and writes the chunk's energy
+// sum_i q_i (phi_p-p,i / 2 + phi_p-s,i).
+//
+// Walls: phi_p-s = -2 pi [sb0 z + st0 (Lz - z)]
+//                  + sum_w Re[e^{i k_w.rho} (Cb_w e^{-k z} + Ct_w e^{-k (Lz - z)})]
+// with Cb_w = 4 pi c_bot,w / k (the 2 pi/(A k) of Thm 2.4, times A c_w for
+// the cell integral, times 2 for the pair (m, -m)); F = -q grad phi_p-s.
 template <typename T>
 __global__ void combine_kernel(Reps rp, int nkr, const T* __restrict__ part,
                                const typename CarryNum<T>::type* __restrict__ phi0,
                                const typename CarryNum<T>::type* __restrict__ fz0,
-                               const T* __restrict__ qs, const int32_t* __restrict__ perm,
+                               const T* __restrict__ qs, const T* __restrict__ zs,
+                               const typename PhaseT<T>::type* __restrict__ xh,
+                               const typename PhaseT<T>::type* __restrict__ yh,
+                               const __grid_constant__ WallTab W,
+                               const int32_t* __restrict__ perm,
                                double* echunk, T* phi_out, T* force_out) {
+  using PH = typename PhaseT<T>::type;
   __shared__ double red[32];
+  // per-mode constants of this chunk's box: kx, ky, k, Cb (re, im), Ct (re, im)
+  __shared__ T wk[kMaxWallModes][7];
   const CRange ch = kchunk(rp, blockIdx.x);
-  const double diagq = rp.info[ch.r].diagq;
+  const RepInfo& ri = rp.info[ch.r];
+  const double diagq = ri.diagq;
+  const double Lz = ri.Lz;
+  const int nw = W.on ? W.nw : 0;
+  for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+    const double kx = 6.283185307179586 * W.m[w][0] / ri.Lx;
+    const double ky = 6.283185307179586 * W.m[w][1] / ri.Ly;
+    const double k = sqrt(kx * kx + ky * ky);
+    const double f = 12.566370614359172 / k;   // 4 pi / k
+    wk[w][0] = (T)kx; wk[w][1] = (T)ky; wk[w][2] = (T)k;
+    wk[w][3] = (T)(f * W.c[w][0]); wk[w][4] = (T)(f * W.c[w][1]);
+    wk[w][5] = (T)(f * W.c[w][2]); wk[w][6] = (T)(f * W.c[w][3]);
+  }
+  __syncthreads();
   const int64_t N = rp.N;
   double e = 0.0;
   for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
@@ -178,14 +209,45 @@ __global__ void combine_kernel(Reps rp, int nkr, const T* __restrict__ part,
     ph += cn_to_double(phi0[i]) + qq * diagq;
     fx *= qq; fy *= qq;
     fz = fz * qq + cn_to_double(fz0[i]);
+    double pw = 0.0;
+    if (W.on) {
+      const double z = (double)zs[i];
+      pw = -6.283185307179586 * (W.sb0 * z + W.st0 * (Lz - z));
+      double gz = 6.283185307179586 * (W.sb0 - W.st0);   // field along z
+      T pm = 0, gx = 0, gy = 0, gzm = 0;
+      if (nw) {
+        const T zb = (T)z, zt = (T)(Lz - z);
+        const PH px = xh[i], py = yh[i];
+        for (int w = 0; w < nw; ++w) {
+          T cs, sn;
+          sincos_turns((PH)((PH)(int64_t)W.m[w][0] * px + (PH)(int64_t)W.m[w][1] * py), cs, sn);
+          const T k = wk[w][2];
+          const T eb = exp_neg(k * zb), et = exp_neg(k * zt);
+          const T ar = wk[w][3] * eb + wk[w][5] * et;    // Cb e^{-k z} + Ct e^{-k (Lz - z)}
+          const T ai = wk[w][4] * eb + wk[w][6] * et;
+          const T br = k * (wk[w][5] * et - wk[w][3] * eb);   // its z-derivative
+          const T bi = k * (wk[w][6] * et - wk[w][4] * eb);
+          pm += cs * ar - sn * ai;                        // Re[e^{i k.rho} a]
+          const T im = sn * ar + cs * ai;                 // Im[e^{i k.rho} a]
+          gx += wk[w][0] * im;                            // -d/dx of Re[...]
+          gy += wk[w][1] * im;
+          gzm -= cs * br - sn * bi;                       // -d/dz of Re[...]
+        }
+      }
+      pw += (double)pm;
+      gz += (double)gzm;
+      fx += qq * (double)gx;
+      fy += qq * (double)gy;
+      fz += qq * gz;
+    }
     const int32_t o = perm[i];
-    if (phi_out) phi_out[o] = (T)ph;
+    if (phi_out) phi_out[o] = (T)(ph + pw);
     if (force_out) {
       force_out[3 * (int64_t)o] = (T)fx;
       force_out[3 * (int64_t)o + 1] = (T)fy;
       force_out[3 * (int64_t)o + 2] = (T)fz;
     }
-    e += 0.5 * qq * ph;
+    e += qq * (0.5 * ph + pw);
   }
   for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
@@ -212,13 +274,15 @@ __global__ void energy_rep_kernel(Reps rp, const double* echunk, double* energie
 
 template <typename T>
 void launch_combine(const Reps& rp, int nkr, const T* part, const void* phi0v,
-                    const void* fz0v, const T* qs, const int32_t* perm, double* echunk,
+                    const void* fz0v, const T* qs, const T* zs,
+                    const typename PhaseT<T>::type* xh, const typename PhaseT<T>::type* yh,
+                    const WallTab& W, const int32_t* perm, double* echunk,
                     T* phi_out, T* force_out, double* energies, cudaStream_t st) {
   using CN = typename CarryNum<T>::type;
   const CN* phi0 = static_cast<const CN*>(phi0v);
   const CN* fz0 = static_cast<const CN*>(fz0v);
-  combine_kernel<T><<<rp.nchunks, chunk_threads(rp.L), 0, st>>>(rp, nkr, part, phi0, fz0, qs, perm,
-                                                                 echunk, phi_out, force_out);
+  combine_kernel<T><<<rp.nchunks, chunk_threads(rp.L), 0, st>>>(
+      rp, nkr, part, phi0, fz0, qs, zs, xh, yh, W, perm, echunk, phi_out, force_out);
   if (energies) {
     const int64_t thr = (int64_t)rp.R * 32;
     energy_rep_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(rp, echunk, energies);
@@ -347,8 +411,8 @@ void launch_mode_coef(const Reps& rp, int npc, const int32_t* list, int rbe, uin
   template void launch_gather<T>(const Reps&, const T*, const T*, const uint32_t*, T*, T*, T*,   \
                                  PH*, PH*, int32_t*, cudaStream_t);                              \
   template void launch_combine<T>(const Reps&, int, const T*, const void*, const void*,          \
-                                  const T*, const int32_t*, double*, T*, T*, double*,            \
-                                  cudaStream_t);                                                 \
+                                  const T*, const T*, const PH*, const PH*, const WallTab&,       \
+                                  const int32_t*, double*, T*, T*, double*, cudaStream_t);       \
   template void launch_mode_coef<T>(const Reps&, int, const int32_t*, int, uint64_t,             \
                                     const uint64_t*, const double*, const PairTab&, double,      \
                                     ModeTab<T>, int32_t*, cudaStream_t);

@@ -53,3 +53,17 @@ def test_library_is_in_tree():
     path = qslab.library_path()
     assert path.startswith(os.path.join(ROOT, "paper_2403_01521_gb300"))
     assert os.path.exists(path)
+
+
+def test_status_codes_match_header():
+    import paper_2403_01521_gb300 as qslab
+    src = open(os.path.join(ROOT, "include", "qslab.h")).read()
+    codes = dict((k, int(v)) for k, v in re.findall(r"#define (QSLAB_(?:OK|ERR_[A-Z_]+))\s+\(?(-?\d+)\)?", src))
+    assert len(codes) >= 10
+    for name, value in codes.items():
+        assert getattr(qslab, name) == value, name
+
+
+def test_walls_null_context_is_rejected(lib):
+    assert lib.qslab_set_walls(None, 0.0, 0.0, 0, None, None, None) == -1
+    assert lib.qslab_clear_walls(None) == -1

@@ -23,6 +23,13 @@ workloads, scaled to the sizes this library is measured at:
   confined     N=2e5 in 200 x 200 x 2, z exponential from a randomly chosen
                wall with decay length 0.2 (redrawn above Lz), charges
                N(0,1) minus their mean, alpha=0.2, M=24, full k-sum
+  cations_walls  n cations (+1) uniform in L x L x 30 between an uncharged
+               bottom wall and a top wall of density -n/L^2 (Section 5.2's
+               cation-only system: n = 436, L = 100, sigma_top = -0.0436),
+               alpha=0.1, full k-sum
+  electrolyte_walls  n/2 cations and n/2 anions uniform in L x L x 30
+               between walls of density +-n/(2 L^2) (Section 5.2's 1:1
+               electrolyte: n = 436, L = 100, sigma = +-0.0218), alpha=0.1
 
 Every generator takes a seed and returns float64 numpy arrays; callers that
 test a float32 path round them to float32 and feed the same rounded values to
@@ -42,13 +49,14 @@ class Slab:
 
     name: str
     pos: np.ndarray          # (N, 3) float64, x,y in [0,L), z in [0,Lz]
-    q: np.ndarray            # (N,) float64, sums to zero
+    q: np.ndarray            # (N,) float64, sums to zero unless walls are set
     box: tuple               # (Lx, Ly, Lz)
     alpha: float
     M: int                   # number of SOE terms
     tail: float = 1e-8       # Gaussian tail that sets the k cutoff (full k-sum)
     P: int = 0               # RBE batch size (0 = full k-sum)
     rc: float = 10.0         # real-space cutoff (used only for totals)
+    walls: tuple = None      # (sigma_bot, sigma_top) uniform wall charge densities
 
     @property
     def N(self) -> int:
@@ -138,3 +146,22 @@ def replicas(seed: int = 4, R: int = 512, nmin: int = 500, nmax: int = 50_000,
 def tiny_neutral(n: int, box, seed: int) -> Slab:
     """A handful of +-1 charges, for brute-force checks."""
     return uniform_slab(n, box, seed, "tiny", alpha=0.5, M=16)
+
+
+def cations_walls(seed: int = 6, n: int = 436, L: float = 100.0) -> Slab:
+    """Cations only, neutralised by the top wall's charge."""
+    rng = np.random.default_rng(seed)
+    Lz = 30.0
+    pos = np.column_stack([rng.random(n) * L, rng.random(n) * L, rng.random(n) * Lz])
+    return Slab("cations_walls", pos, np.ones(n), (L, L, Lz), 0.1, 16,
+                walls=(0.0, -n / (L * L)))
+
+
+def electrolyte_walls(seed: int = 7, n: int = 436, L: float = 100.0) -> Slab:
+    """1:1 electrolyte between oppositely charged walls."""
+    rng = np.random.default_rng(seed)
+    Lz = 30.0
+    pos = np.column_stack([rng.random(n) * L, rng.random(n) * L, rng.random(n) * Lz])
+    sig = n / (2 * L * L)
+    return Slab("electrolyte_walls", pos, _pm_charges(rng, n), (L, L, Lz), 0.1, 16,
+                walls=(sig, -sig))
