@@ -211,25 +211,36 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
               const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
               m |= (r2 <= rc2 && r2 > (T)0) ? (1u << t) : 0u;
             }
-            // phase 2: the pair terms of the marked records
+            // phase 2: the pair terms of the marked records, two per step
+            // (two independent dependency chains); an odd last record is
+            // paired with itself at charge 0, which adds exact zeros
             while (m) {
-              const int t = __ffs(m) - 1;
+              const int t1 = __ffs(m) - 1;
               m &= m - 1u;
-              const RsRec<T> rj = buf[t0 + t];
-              const T ddx = ri.x - rj.x, ddy = ri.y - rj.y, ddz = ri.z - rj.z;
-              const T r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-              const T inv = rs_rinv(r2);
-              const T r = r2 * inv;
-              T erfc_v, ex;
-              rs_erfc_exp(alpha * r, a2 * r2, erfc_v, ex);
-              const T e = erfc_v * inv;                      // erfc(a r)/r
-              const T g2 = two_a_sqpi * ex;                  // 2a/sqrt(pi) e^{-a^2 r^2}
-              const T fr = (e + g2) * inv * inv;             // -(d/dr)(erfc(a r)/r) / r
-              ph = fma(rj.q, e, ph);
-              const T w = rj.q * fr;
-              fx = fma(w, ddx, fx);
-              fy = fma(w, ddy, fy);
-              fz = fma(w, ddz, fz);
+              int t2 = t1;
+              T qmul = (T)0;
+              if (m) { t2 = __ffs(m) - 1; m &= m - 1u; qmul = (T)1; }
+              const RsRec<T> rj1 = buf[t0 + t1];
+              const RsRec<T> rj2 = buf[t0 + t2];
+              const T dx1 = ri.x - rj1.x, dy1 = ri.y - rj1.y, dz1 = ri.z - rj1.z;
+              const T dx2 = ri.x - rj2.x, dy2 = ri.y - rj2.y, dz2 = ri.z - rj2.z;
+              const T r21 = dx1 * dx1 + dy1 * dy1 + dz1 * dz1;
+              const T r22 = dx2 * dx2 + dy2 * dy2 + dz2 * dz2;
+              const T inv1 = rs_rinv(r21), inv2 = rs_rinv(r22);
+              const T r1 = r21 * inv1, r2b = r22 * inv2;
+              T ec1, ex1, ec2, ex2;
+              rs_erfc_exp(alpha * r1, a2 * r21, ec1, ex1);
+              rs_erfc_exp(alpha * r2b, a2 * r22, ec2, ex2);
+              const T e1 = ec1 * inv1, e2 = ec2 * inv2;
+              const T fr1 = (e1 + two_a_sqpi * ex1) * inv1 * inv1;
+              const T fr2 = (e2 + two_a_sqpi * ex2) * inv2 * inv2;
+              const T q1 = rj1.q, q2 = rj2.q * qmul;
+              ph = fma(q1, e1, ph);
+              ph = fma(q2, e2, ph);
+              const T w1 = q1 * fr1, w2 = q2 * fr2;
+              fx = fma(w2, dx2, fma(w1, dx1, fx));
+              fy = fma(w2, dy2, fma(w1, dy1, fy));
+              fz = fma(w2, dz2, fma(w1, dz1, fz));
             }
           }
         }
