@@ -15,7 +15,9 @@ Paper references (Gan, Gao, Liang, Xu, arXiv 2403.01521):
 The k-sampler draws i.i.d. lattice vectors from h. Because h factorises into
 two one-dimensional discrete Gaussians p(m) ~ e^{-pi^2 m^2/(alpha L)^2}, each
 component is drawn by inversion of its cumulative table and the origin is
-rejected. Random words come from the counter-based generator Philox4x64-10
+rejected. The paper's own sampler, the independence Metropolis chain of
+App. G (rounded-normal proposals, optional downsampling), is
+metropolis_modes. Random words come from the counter-based generator Philox4x64-10
 (Salmon, Moraes, Dror, Shaw, SC'11), written here from its definition.
 """
 from __future__ import annotations
@@ -23,6 +25,7 @@ from __future__ import annotations
 import math
 
 import numpy as np
+from scipy.special import erf, erfc
 
 PI = math.pi
 
@@ -226,6 +229,108 @@ def sample_modes(P: int, seed: int, call: int, alpha: float, Lx: float, Ly: floa
             done |= ok
         todo = todo[~done]
         attempt += 1
+    return out_x, out_y
+
+
+MH_TAG = 0x4D484731               # fourth counter word of the Metropolis draws
+
+
+def round_half_away(x):
+    """Nearest integer, halves away from zero (C's round())."""
+    x = np.asarray(x, float)
+    return (np.sign(x) * np.floor(np.abs(x) + 0.5)).astype(np.int64)
+
+
+def proposal_pmf(m, alpha: float, L: float):
+    """q(m) of App. G: the probability that a normal of mean 0 and variance
+    (alpha L)^2/(2 pi^2) rounds to the integer m; erf(pi/(2 alpha L)) at
+    m = 0, else half the difference of erf at pi(2|m| +- 1)/(2 alpha L),
+    written with erfc so that the far tail keeps its relative accuracy."""
+    a = PI / (2.0 * alpha * L)
+    m = np.abs(np.asarray(m, float))
+    return np.where(m == 0, erf(a), 0.5 * (erfc(a * (2 * m - 1)) - erfc(a * (2 * m + 1))))
+
+
+def mh_log_weight(mx, my, alpha: float, Lx: float, Ly: float):
+    """log[H(m)/q(m)] up to a constant (H(m) = h(k) of Eq. 4.5 unnormalised):
+    the acceptance ratio of App. G is exp of the difference of two of these."""
+    return (-(PI * np.asarray(mx, float) / (alpha * Lx)) ** 2 - np.log(proposal_pmf(mx, alpha, Lx))
+            - (PI * np.asarray(my, float) / (alpha * Ly)) ** 2 - np.log(proposal_pmf(my, alpha, Ly)))
+
+
+def mh_proposal(w0, w1, alpha: float, Lx: float, Ly: float):
+    """Proposals of App. G from pairs of 64-bit words (arrays): a pair of
+    normals by the Box-Muller transform (u1 = 1 - uniform53(w0) in (0, 1],
+    u2 = uniform53(w1)), scaled to the standard deviations
+    alpha L/(sqrt(2) pi), rounded to the nearest integers."""
+    u1 = 1.0 - uniform53(w0)
+    u2 = uniform53(w1)
+    r = np.sqrt(-2.0 * np.log(u1))
+    th = 2.0 * PI * u2
+    sx = alpha * Lx / (math.sqrt(2.0) * PI)
+    sy = alpha * Ly / (math.sqrt(2.0) * PI)
+    return round_half_away(sx * r * np.cos(th)), round_half_away(sy * r * np.sin(th))
+
+
+def _mh_words(i0, i1, call, seed, stream):
+    i0 = np.atleast_1d(np.asarray(i0, np.uint64))
+    ctr = np.zeros((i0.size, 4), np.uint64)
+    ctr[:, 0] = i0
+    ctr[:, 1] = np.uint64(i1)
+    ctr[:, 2] = np.uint64(call)
+    ctr[:, 3] = np.uint64(MH_TAG + (int(stream) << 32))
+    key = np.zeros((i0.size, 2), np.uint64)
+    key[:, 0] = np.uint64(seed)
+    return philox4x64_10(ctr, key)
+
+
+def metropolis_modes(P: int, seed: int, call: int, alpha: float, Lx: float, Ly: float,
+                     stream: int = 0, thin: int = 1, return_rate: bool = False):
+    """P lattice vectors from h(k) by the independence Metropolis chain of
+    App. G, keeping every thin-th state (the downsampling rate).
+
+    Start: attempt a = 0, 1, ... (Philox counter (a, 1, call, MH_TAG +
+    stream 2^32), key (seed, 0)) gives two proposals, from words (0, 1) and
+    (2, 3); the first that is not the origin is the initial state; after 64
+    attempts the state is (1, 0). Step eta = 1 .. P thin uses counter
+    (eta - 1, 0, call, MH_TAG + stream 2^32): words 0, 1 give the proposal,
+    word 2 the uniform u; the origin is rejected (h = 0 there), any other
+    proposal is accepted when u < H(new) q(old) / (H(old) q(new)). The
+    sample after step j thin is the j-th output. The proposals do not depend
+    on the state (App. G), so they are drawn for all steps first; the chain
+    itself runs step by step."""
+    state = (1, 0)
+    w = _mh_words(np.arange(64), 1, call, seed, stream)
+    ax, ay = mh_proposal(w[:, 0], w[:, 1], alpha, Lx, Ly)
+    bx, by = mh_proposal(w[:, 2], w[:, 3], alpha, Lx, Ly)
+    for a in range(64):
+        if ax[a] != 0 or ay[a] != 0:
+            state = (int(ax[a]), int(ay[a]))
+            break
+        if bx[a] != 0 or by[a] != 0:
+            state = (int(bx[a]), int(by[a]))
+            break
+    n = P * thin
+    w = _mh_words(np.arange(n), 0, call, seed, stream)
+    px, py = mh_proposal(w[:, 0], w[:, 1], alpha, Lx, Ly)
+    u = uniform53(w[:, 2])
+    origin = (px == 0) & (py == 0)
+    lwp = mh_log_weight(px, py, alpha, Lx, Ly)    # not used at the origin
+    lw = float(mh_log_weight(state[0], state[1], alpha, Lx, Ly))
+    out_x = np.zeros(P, np.int64)
+    out_y = np.zeros(P, np.int64)
+    accepted = 0
+    for eta in range(1, n + 1):
+        t = eta - 1
+        if not origin[t]:
+            d = float(lwp[t]) - lw
+            if d >= 0.0 or float(u[t]) < math.exp(d):
+                state, lw = (int(px[t]), int(py[t])), float(lwp[t])
+                accepted += 1
+        if eta % thin == 0:
+            out_x[eta // thin - 1], out_y[eta // thin - 1] = state
+    if return_rate:
+        return out_x, out_y, accepted / n
     return out_x, out_y
 
 

@@ -154,3 +154,104 @@ def test_rbe_unbiased_and_variance(rbe_system, soe16):
     ratio = sd ** 2 / var_exact
     # sample variance of 400 draws: relative sd ~ sqrt(2/399) ~ 7%
     assert 0.7 < ratio < 1.4
+
+
+# ------------------------------------------------ Metropolis sampler (App. G)
+
+
+@pytest.mark.parametrize("aL", [1.5, 7.0, 30.0])
+def test_mh_proposal_pmf_is_the_rounded_normal(aL):
+    """q(m) of App. G is the mass of N(0, (alpha L)^2/(2 pi^2)) on
+    [m - 1/2, m + 1/2]: numerical quadrature of the normal density."""
+    from scipy.integrate import quad
+    sig = aL / (math.sqrt(2.0) * math.pi)
+    dens = lambda t: math.exp(-0.5 * (t / sig) ** 2) / (sig * math.sqrt(2 * math.pi))
+    ms = np.arange(0, int(6 * sig) + 3)
+    q = lattice.proposal_pmf(ms, aL, 1.0)
+    for m, qm in zip(ms, q):
+        ref = quad(dens, m - 0.5, m + 0.5, epsabs=0, epsrel=1e-13)[0]
+        assert abs(qm - ref) <= 1e-11 * ref + 1e-300
+    qall = lattice.proposal_pmf(np.arange(0, int(10 * sig) + 3), aL, 1.0)
+    assert abs(qall[0] + 2 * qall[1:].sum() - 1.0) < 1e-12
+
+
+def test_mh_proposals_follow_q():
+    """The Box-Muller proposals, rounded, follow q(mx) q(my): chi-square."""
+    alpha, Lx, Ly = 0.3, 10.0, 15.0
+    n = 100_000
+    w = lattice._mh_words(np.arange(n), 0, 5, 99, 0)
+    mx, my = lattice.mh_proposal(w[:, 0], w[:, 1], alpha, Lx, Ly)
+    for m, L in ((mx, Lx), (my, Ly)):
+        vals, cnt = np.unique(m, return_counts=True)
+        exp_ = n * lattice.proposal_pmf(vals, alpha, L)
+        big = exp_ >= 10
+        chi2 = float((((cnt - exp_) ** 2 / exp_)[big]).sum())
+        dof = int(big.sum()) - 1
+        assert abs(chi2 - dof) < 5 * math.sqrt(2 * dof)
+
+
+def test_mh_chain_targets_h():
+    """The chain's states follow h(k) (origin excluded): chi-square on a long
+    thinned chain of a small box (alpha L = 3, acceptance ~0.67, where a
+    wrong acceptance ratio shows), with the variance allowance of a
+    correlated chain."""
+    alpha, Lx, Ly = 0.25, 12.0, 12.0
+    n = 40_000
+    mx, my, rate = lattice.metropolis_modes(n, 3, 1, alpha, Lx, Ly, thin=4, return_rate=True)
+    assert 0.5 < rate < 0.8
+    assert not ((mx == 0) & (my == 0)).any()
+    keys, counts = np.unique(np.stack([mx, my], 1), axis=0, return_counts=True)
+    cnt = dict(zip(map(tuple, keys.tolist()), counts.tolist()))
+    R = lattice.axis_mmax(alpha, Lx)
+    gx, gy = np.meshgrid(np.arange(-R, R + 1), np.arange(-R, R + 1), indexing="ij")
+    gx, gy = gx.ravel(), gy.ravel()
+    nz = ~((gx == 0) & (gy == 0))
+    gx, gy = gx[nz], gy[nz]
+    exp_ = n * lattice.h_pmf(alpha, Lx, Ly, gx, gy)
+    obs = np.array([cnt.get((a, b), 0) for a, b in zip(gx.tolist(), gy.tolist())])
+    big = exp_ >= 10
+    chi2 = float((((obs - exp_) ** 2 / exp_)[big]).sum())
+    dof = int(big.sum()) - 1
+    assert chi2 < 1.6 * dof + 5 * math.sqrt(2 * dof)
+    # the proposal alone (no acceptance step) is far from h here
+    w = lattice._mh_words(np.arange(n), 0, 1, 3, 0)
+    px, py = lattice.mh_proposal(w[:, 0], w[:, 1], alpha, Lx, Ly)
+    keep = ~((px == 0) & (py == 0))
+    kp, cp = np.unique(np.stack([px[keep], py[keep]], 1), axis=0, return_counts=True)
+    cntp = dict(zip(map(tuple, kp.tolist()), cp.tolist()))
+    obsp = np.array([cntp.get((a, b), 0) for a, b in zip(gx.tolist(), gy.tolist())]) * n / keep.sum()
+    chi2p = float((((obsp - exp_) ** 2 / exp_)[big]).sum())
+    assert chi2p > 10 * chi2
+
+
+@pytest.mark.parametrize("alpha,L", [(0.1, 400.0), (0.3, 100.0), (0.25, 40.0)])
+def test_mh_acceptance_above_90_percent(alpha, L):
+    """App. G reports acceptance rates above 90% on its workloads."""
+    _, _, rate = lattice.metropolis_modes(2000, 5, 0, alpha, L, L, return_rate=True)
+    assert rate > 0.9
+
+
+def test_mh_thinning_and_counter():
+    a = lattice.metropolis_modes(50, 7, 3, 0.25, 20.0, 20.0, thin=3)
+    b = lattice.metropolis_modes(150, 7, 3, 0.25, 20.0, 20.0, thin=1)
+    assert (a[0] == b[0][2::3]).all() and (a[1] == b[1][2::3]).all()
+    c = lattice.metropolis_modes(50, 7, 4, 0.25, 20.0, 20.0, thin=3)
+    d = lattice.metropolis_modes(50, 7, 3, 0.25, 20.0, 20.0, thin=3, stream=1)
+    for e in (c, d):
+        assert not ((a[0] == e[0]).all() and (a[1] == e[1]).all())
+
+
+def test_rbe_with_mh_samples_is_unbiased(rbe_system, soe16):
+    """The random-batch energy with Metropolis samples averages to the
+    full-k energy (over 300 calls of one seed)."""
+    s, w = soe16
+    sl = rbe_system
+    Lx, Ly, _ = sl.box
+    kc = lattice.kcut_for_tail(sl.alpha, 1e-14)
+    full = soe_ewald2d.soe_full(sl.pos, sl.q, sl.box, sl.alpha, s, w, kc=kc)["E"]
+    es = []
+    for call in range(300):
+        mx, my = lattice.metropolis_modes(20, 13, call, sl.alpha, Lx, Ly, thin=2)
+        es.append(soe_ewald2d.soe_rbe(sl.pos, sl.q, sl.box, sl.alpha, s, w, mx, my)["E"])
+    es = np.array(es)
+    assert abs(es.mean() - full) < 5 * es.std() / math.sqrt(es.size)
