@@ -209,6 +209,23 @@ int qslab_compute_host(qslab_ctx* ctx, int64_t N, const void* pos_host,
 int qslab_compute_static(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
                          double* energy, void* phi, void* force, void* stream);
 
+/* Random-batch k-sampler (Section 4, App. G). QSLAB_SAMPLER_IID (default):
+ * P independent draws from h(k) by inversion of its two one-dimensional
+ * factors. QSLAB_SAMPLER_METROPOLIS: the independence Metropolis chain of
+ * App. G: proposals are rounded normals of variance (alpha L)^2/(2 pi^2)
+ * per axis (Box-Muller from Philox4x64-10 words), the origin is rejected,
+ * other proposals are accepted with probability
+ * min{1, H(new) q(old)/(H(old) q(new))}; each call runs a fresh chain of
+ * P * thin steps per slab (started at the first proposal that is not the
+ * origin) and keeps every thin-th state (the downsampling rate, 1..4096).
+ * Both samplers weight every sample by H/P (Eq. 4.7) and draw from the
+ * counter of the call, so CUDA-graph replays draw fresh samples. Takes
+ * effect at the next random-batch call; QSLAB_ERR_INVALID_ARG for another
+ * kind or thin. */
+#define QSLAB_SAMPLER_IID 0
+#define QSLAB_SAMPLER_METROPOLIS 1
+int qslab_set_rbe_sampler(qslab_ctx* ctx, int kind, int thin);
+
 /* Charged walls at z = 0 (bottom) and z = Lz (top), Section 2.4. The walls
  * carry doubly periodic surface charge densities (charge per unit area)
  *   sigma_bot(rho) = sigma_bot + sum_w 2 Re[(bot[2w] + i bot[2w+1]) e^{i k_w.rho}]

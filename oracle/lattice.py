@@ -253,9 +253,11 @@ def proposal_pmf(m, alpha: float, L: float):
 
 def mh_log_weight(mx, my, alpha: float, Lx: float, Ly: float):
     """log[H(m)/q(m)] up to a constant (H(m) = h(k) of Eq. 4.5 unnormalised):
-    the acceptance ratio of App. G is exp of the difference of two of these."""
-    return (-(PI * np.asarray(mx, float) / (alpha * Lx)) ** 2 - np.log(proposal_pmf(mx, alpha, Lx))
-            - (PI * np.asarray(my, float) / (alpha * Ly)) ** 2 - np.log(proposal_pmf(my, alpha, Ly)))
+    the acceptance ratio of App. G is exp of the difference of two of these.
+    Both factorise over the axes: the x part plus the y part."""
+    def axis(m, L):
+        return -(PI * np.asarray(m, float) / (alpha * L)) ** 2 - np.log(proposal_pmf(m, alpha, L))
+    return axis(mx, Lx) + axis(my, Ly)
 
 
 def mh_proposal(w0, w1, alpha: float, Lx: float, Ly: float):
@@ -295,10 +297,11 @@ def metropolis_modes(P: int, seed: int, call: int, alpha: float, Lx: float, Ly: 
     attempts the state is (1, 0). Step eta = 1 .. P thin uses counter
     (eta - 1, 0, call, MH_TAG + stream 2^32): words 0, 1 give the proposal,
     word 2 the uniform u; the origin is rejected (h = 0 there), any other
-    proposal is accepted when u < H(new) q(old) / (H(old) q(new)). The
-    sample after step j thin is the j-th output. The proposals do not depend
-    on the state (App. G), so they are drawn for all steps first; the chain
-    itself runs step by step."""
+    proposal is accepted when u < H(new) q(old) / (H(old) q(new)), tested
+    as d >= 0 or log u < d with d the log of that ratio. The sample after
+    step j thin is the j-th output. The proposals do not depend on the state
+    (App. G), so they are drawn for all steps first; the chain itself runs
+    step by step."""
     state = (1, 0)
     w = _mh_words(np.arange(64), 1, call, seed, stream)
     ax, ay = mh_proposal(w[:, 0], w[:, 1], alpha, Lx, Ly)
@@ -313,7 +316,8 @@ def metropolis_modes(P: int, seed: int, call: int, alpha: float, Lx: float, Ly: 
     n = P * thin
     w = _mh_words(np.arange(n), 0, call, seed, stream)
     px, py = mh_proposal(w[:, 0], w[:, 1], alpha, Lx, Ly)
-    u = uniform53(w[:, 2])
+    with np.errstate(divide="ignore"):
+        logu = np.log(uniform53(w[:, 2]))          # -inf for u = 0
     origin = (px == 0) & (py == 0)
     lwp = mh_log_weight(px, py, alpha, Lx, Ly)    # not used at the origin
     lw = float(mh_log_weight(state[0], state[1], alpha, Lx, Ly))
@@ -324,7 +328,7 @@ def metropolis_modes(P: int, seed: int, call: int, alpha: float, Lx: float, Ly: 
         t = eta - 1
         if not origin[t]:
             d = float(lwp[t]) - lw
-            if d >= 0.0 or float(u[t]) < math.exp(d):
+            if d >= 0.0 or float(logu[t]) < d:
                 state, lw = (int(px[t]), int(py[t])), float(lwp[t])
                 accepted += 1
         if eta % thin == 0:

@@ -24,6 +24,8 @@ from .soe import load_soe  # noqa: F401  (tables are method parameters)
 
 QSLAB_FP64 = 0
 QSLAB_FP32C = 1
+QSLAB_SAMPLER_IID = 0
+QSLAB_SAMPLER_METROPOLIS = 1
 # status codes (include/qslab.h)
 QSLAB_OK = 0
 QSLAB_ERR_INVALID_ARG = -1
@@ -83,6 +85,7 @@ def load(build_if_missing: bool = True):
         "qslab_autotune": ([P, I, P, P, P, P, P, I, P, P], I),
         "qslab_set_rcut": ([P, D], I),
         "qslab_set_walls": ([P, D, D, I, P, P, P], I),
+        "qslab_set_rbe_sampler": ([P, I, I], I),
         "qslab_clear_walls": ([P], I),
         "qslab_compute_realspace": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_get_sampled_modes": ([P, P, P], I),
@@ -223,6 +226,12 @@ def qslab_set_walls(h, sigma_bot, sigma_top, modes=None, bot=None, top=None):
                                   tt.ctypes.data if nw else None), "qslab_set_walls")
 
 
+def qslab_set_rbe_sampler(h, kind, thin=1):
+    """Random-batch k-sampler: QSLAB_SAMPLER_IID or QSLAB_SAMPLER_METROPOLIS
+    (App. G) with downsampling rate thin."""
+    _check(load().qslab_set_rbe_sampler(h, int(kind), int(thin)), "qslab_set_rbe_sampler")
+
+
 def qslab_clear_walls(h):
     _check(load().qslab_clear_walls(h), "qslab_clear_walls")
 
@@ -345,6 +354,13 @@ class QSlab:
             qslab_clear_walls(self.h)
         else:
             qslab_set_walls(self.h, sigma_bot, sigma_top, modes, bot, top)
+        return self
+
+    def sampler(self, kind="iid", thin=1):
+        """Random-batch k-sampler: "iid" (exact independent draws) or
+        "metropolis" (the chain of App. G, keeping every thin-th state)."""
+        k = {"iid": QSLAB_SAMPLER_IID, "metropolis": QSLAB_SAMPLER_METROPOLIS}[kind]
+        qslab_set_rbe_sampler(self.h, k, thin)
         return self
 
     def tuning(self, chunk=0, modes_per_cta=0):

@@ -69,6 +69,8 @@ struct qslab_ctx {
   bool timing = false;
   double rc = 0;                // real-space cut-off (0: not set)
   WallTab walls{};              // charged walls (walls.on = 0: none)
+  int sampler = QSLAB_SAMPLER_IID;   // random-batch k-sampler
+  int mh_thin = 1;              // Metropolis downsampling rate
   // derived configuration
   bool cfg_dirty = true;
   uint64_t cfg_version = 0;
@@ -263,6 +265,24 @@ std::vector<double> axis_cdf(double alpha, double L, int* mmax_out) {
   return c;
 }
 
+// Metropolis log-weights of one axis (App. G): -(pi m/(alpha L))^2 - log q(m)
+// for m = -mmax..mmax, with q(m) the probability that the proposal normal of
+// variance (alpha L)^2/(2 pi^2) rounds to m (the erf difference of App. G,
+// written with erfc so that the tail keeps its relative accuracy).
+std::vector<double> axis_mh_logw(double alpha, double L, int mmax) {
+  std::vector<double> v(2 * mmax + 1);
+  const double a = kPi / (2.0 * alpha * L);
+  for (int j = 0; j <= 2 * mmax; ++j) {
+    const int m = j - mmax;
+    const double am = std::fabs((double)m);
+    const double q = m == 0 ? std::erf(a)
+                            : 0.5 * (std::erfc(a * (2.0 * am - 1.0)) - std::erfc(a * (2.0 * am + 1.0)));
+    const double t = kPi * m / (alpha * L);
+    v[j] = -(t * t) - std::log(q);
+  }
+  return v;
+}
+
 template <typename T>
 ModeTab<T> mode_views(void* base, size_t n, int npc) {
   ModeTab<T> m;
@@ -363,6 +383,10 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
         t.cdf.insert(t.cdf.end(), cx.begin(), cx.end());
         ri.cdfy0 = (int32_t)t.cdf.size(); ri.ny = (int32_t)cy.size(); ri.mymax = my;
         t.cdf.insert(t.cdf.end(), cy.begin(), cy.end());
+        const std::vector<double> lx = axis_mh_logw(alpha, ri.Lx, mx);
+        const std::vector<double> ly = axis_mh_logw(alpha, ri.Ly, my);
+        t.cdf.insert(t.cdf.end(), lx.begin(), lx.end());
+        t.cdf.insert(t.cdf.end(), ly.begin(), ly.end());
         if (t.cdf.size() > (size_t)1 << 28) return QSLAB_ERR_INVALID_ARG;
       }
       // j = i constant per unit q_i^2 of the potential: k != 0 (Eq. 3.20),
@@ -657,10 +681,16 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   QS_CUDA(cudaEventRecord(c->join, c->side));
   // mode tables: once per configuration for the full k-sum, every call for RBE
   if (rbe || !c->coef_ready) {
-    launch_mode_coef<T>(rp, c->npc, reinterpret_cast<const int32_t*>(tab + tb.o_list), rbe ? 1 : 0,
-                        c->seed, c->d_ctr, reinterpret_cast<const double*>(tab + tb.o_cdf),
-                        c->pairs, c->alpha, modes,
-                        rbe ? reinterpret_cast<int32_t*>(tab + tb.o_sampled) : nullptr, st);
+    const double* cdf = reinterpret_cast<const double*>(tab + tb.o_cdf);
+    int32_t* sampled = rbe ? reinterpret_cast<int32_t*>(tab + tb.o_sampled) : nullptr;
+    const bool mh = rbe && c->sampler == QSLAB_SAMPLER_METROPOLIS;
+    if (mh) {
+      launch_mh_chain(rp, c->P, c->mh_thin, c->seed, c->d_ctr, cdf, c->alpha, sampled, st);
+      ++nl;
+    }
+    launch_mode_coef<T>(rp, c->npc, reinterpret_cast<const int32_t*>(tab + tb.o_list),
+                        rbe ? (mh ? 2 : 1) : 0, c->seed, c->d_ctr, cdf, c->pairs, c->alpha, modes,
+                        sampled, st);
     ++nl;
     if (rbe) c->have_sample = true;
     else c->coef_ready = true;
@@ -921,6 +951,16 @@ int qslab_set_walls(qslab_ctx* c, double sigma_bot, double sigma_top, int nw,
     w.c[i][3] = top[2 * i + 1];
   }
   c->walls = w;
+  return QSLAB_OK;
+}
+
+int qslab_set_rbe_sampler(qslab_ctx* c, int kind, int thin) {
+  if (!c || (kind != QSLAB_SAMPLER_IID && kind != QSLAB_SAMPLER_METROPOLIS) || thin < 1 ||
+      thin > 4096)
+    return QSLAB_ERR_INVALID_ARG;
+  c->sampler = kind;
+  c->mh_thin = kind == QSLAB_SAMPLER_METROPOLIS ? thin : 1;
+  c->have_sample = false;
   return QSLAB_OK;
 }
 

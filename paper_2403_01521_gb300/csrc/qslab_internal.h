@@ -217,10 +217,22 @@ void launch_combine(const Reps& rp, int nkr, const T* part, const void* phi0,
 // half-plane lists, concatenated). rbe = 1: K_r = P modes per replica drawn
 // on the device from the replica's sampler tables, with the counter ctr[1];
 // the drawn (mx, my) go to `sampled` ([R][P] pairs) if it is not NULL.
-// npc = pair count the table is laid out for (compiled NP).
+// rbe = 2: random-batch weights for the modes already in `sampled` (the
+// Metropolis chain's). npc = pair count the table is laid out for (compiled
+// NP).
+//
+// Sampler tables per replica (in `cdf`, from cdfx0): the cumulative tables
+// of x (nx entries, m = -mxmax..mxmax) and y (ny entries), then the
+// Metropolis log-weights -(pi m/(alpha L))^2 - log q(m) of x and y on the
+// same ranges (App. G), at cdfx0 + nx + ny and cdfy0 + nx + ny.
 template <typename T>
 void launch_mode_coef(const Reps& rp, int npc, const int32_t* list, int rbe, uint64_t seed,
                       const uint64_t* ctr, const double* cdf, const PairTab& pairs,
                       double alpha, ModeTab<T> modes, int32_t* sampled, cudaStream_t st);
+// The independence Metropolis chain of App. G, one CTA per replica: P
+// samples (every thin-th state of P * thin steps) per replica into
+// `sampled` ([R][P] pairs), with the counter ctr[1].
+void launch_mh_chain(const Reps& rp, int P, int thin, uint64_t seed, const uint64_t* ctr,
+                     const double* cdf, double alpha, int32_t* sampled, cudaStream_t st);
 
 }  // namespace qslab

@@ -328,9 +328,12 @@ __global__ void mode_coef_kernel(Reps rp, int npc, const int32_t* list, int rbe,
   const double sqpi = 1.7724538509055160;
   int mx = 0, my = 0;
   if (m < K) {
-    if (!rbe) {
+    if (rbe == 0) {
       mx = list[2 * ((size_t)ri.list0 + m)];
       my = list[2 * ((size_t)ri.list0 + m) + 1];
+    } else if (rbe == 2) {
+      mx = sampled[2 * ((size_t)rep * K + m)];
+      my = sampled[2 * ((size_t)rep * K + m) + 1];
     } else {
       const double* cdfx = cdf + ri.cdfx0;
       const double* cdfy = cdf + ri.cdfy0;
@@ -393,6 +396,110 @@ __global__ void mode_coef_kernel(Reps rp, int npc, const int32_t* list, int rbe,
   mt.ckk[mg] = (T)(ck * k);
   mt.sY[mg] = (T)(ck + sY);
   mt.sZ[mg] = (T)(ck * k + sZ);
+}
+
+// ================================================= Metropolis k-sampler
+
+constexpr int kMhBlock = 1024;          // chain steps prepared per round
+constexpr uint64_t kMhTag = 0x4D484731ull;
+
+// One proposal of App. G from two words: Box-Muller normals (u1 = 1 -
+// uniform53(w0) in (0, 1], u2 = uniform53(w1)) scaled by the standard
+// deviations alpha L/(sqrt(2) pi), rounded half away from zero.
+__device__ __forceinline__ void mh_propose(uint64_t w0, uint64_t w1, double sdx, double sdy,
+                                           int& mx, int& my) {
+  const double u1 = 1.0 - uniform53(w0);
+  const double u2 = uniform53(w1);
+  const double r = sqrt(-2.0 * log(u1));
+  const double th = 2.0 * 3.14159265358979323846 * u2;
+  mx = (int)round(sdx * r * cos(th));
+  my = (int)round(sdy * r * sin(th));
+}
+
+// log[H(m)/q(m)] from the replica's per-axis tables. A Box-Muller normal is
+// at most sqrt(2 * 53 ln 2) < 8.58 standard deviations from 0, so |m| stays
+// within the tables' range 6.438 alpha L / pi + 1; the clamp only guards
+// the memory access.
+__device__ __forceinline__ double mh_log_weight(const double* lwx, const double* lwy,
+                                                int mxmax, int mymax, int mx, int my) {
+  const int ix = min(max(mx, -mxmax), mxmax) + mxmax;
+  const int iy = min(max(my, -mymax), mymax) + mymax;
+  return lwx[ix] + lwy[iy];
+}
+
+// One CTA per replica. The proposals do not depend on the chain's state
+// (App. G), so the CTA's threads draw kMhBlock of them at a time (proposal,
+// its log-weight and log u) into shared memory; thread 0 then runs the
+// chain through them: the origin is rejected (h = 0 there), any other
+// proposal accepted when d >= 0 or log u < d, d the log acceptance ratio.
+// Counters: start attempts (a, 1, ctr[1], tag + rep 2^32), steps
+// (eta - 1, 0, ctr[1], tag + rep 2^32), key (seed, 0).
+__global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin, uint64_t seed,
+                                                       const uint64_t* ctr, const double* cdf,
+                                                       double alpha, int32_t* sampled) {
+  __shared__ int32_t spx[kMhBlock], spy[kMhBlock];
+  __shared__ double slw[kMhBlock], slu[kMhBlock];
+  const int rep = blockIdx.x;
+  const RepInfo& ri = rp.info[rep];
+  const double pi = 3.14159265358979323846;
+  const double sdx = alpha * ri.Lx / (sqrt(2.0) * pi);
+  const double sdy = alpha * ri.Ly / (sqrt(2.0) * pi);
+  const double* lwx = cdf + ri.cdfx0 + ri.nx + ri.ny;
+  const double* lwy = cdf + ri.cdfy0 + ri.nx + ri.ny;
+  const uint64_t counter = ctr[1];
+  const uint64_t tag = kMhTag + ((uint64_t)rep << 32);
+  int cx = 1, cy = 0;         // chain state (thread 0)
+  double lw = 0.0;
+  if (threadIdx.x == 0) {
+    for (uint64_t a = 0; a < 64; ++a) {
+      U64x4 c;
+      c.v[0] = a; c.v[1] = 1; c.v[2] = counter; c.v[3] = tag;
+      const U64x4 w = philox4x64_10(c, seed, 0ull);
+      int px, py;
+      mh_propose(w.v[0], w.v[1], sdx, sdy, px, py);
+      if (px != 0 || py != 0) { cx = px; cy = py; break; }
+      mh_propose(w.v[2], w.v[3], sdx, sdy, px, py);
+      if (px != 0 || py != 0) { cx = px; cy = py; break; }
+    }
+    lw = mh_log_weight(lwx, lwy, ri.mxmax, ri.mymax, cx, cy);
+  }
+  const int64_t n = (int64_t)P * thin;
+  for (int64_t b0 = 0; b0 < n; b0 += kMhBlock) {
+    const int cnt = (int)min((int64_t)kMhBlock, n - b0);
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+      U64x4 c;
+      c.v[0] = (uint64_t)(b0 + t); c.v[1] = 0; c.v[2] = counter; c.v[3] = tag;
+      const U64x4 w = philox4x64_10(c, seed, 0ull);
+      int px, py;
+      mh_propose(w.v[0], w.v[1], sdx, sdy, px, py);
+      spx[t] = px;
+      spy[t] = py;
+      slw[t] = mh_log_weight(lwx, lwy, ri.mxmax, ri.mymax, px, py);
+      slu[t] = log(uniform53(w.v[2]));      // -inf for u = 0
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int t = 0; t < cnt; ++t) {
+        const int px = spx[t], py = spy[t];
+        if (px != 0 || py != 0) {
+          const double d = slw[t] - lw;
+          if (d >= 0.0 || slu[t] < d) { cx = px; cy = py; lw = slw[t]; }
+        }
+        const int64_t eta = b0 + t + 1;
+        if (eta % thin == 0) {
+          const size_t j = (size_t)rep * P + (size_t)(eta / thin - 1);
+          sampled[2 * j] = cx;
+          sampled[2 * j + 1] = cy;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_mh_chain(const Reps& rp, int P, int thin, uint64_t seed, const uint64_t* ctr,
+                     const double* cdf, double alpha, int32_t* sampled, cudaStream_t st) {
+  mh_chain_kernel<<<rp.R, 256, 0, st>>>(rp, P, thin, seed, ctr, cdf, alpha, sampled);
 }
 
 template <typename T>
