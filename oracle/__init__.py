@@ -19,11 +19,14 @@ Modules:
   soe_check     SOE table checks (Eq. 3.1, Thm 3.2, Eq. 3.24)
   walls         charged walls at z = 0 and z = Lz: the particle-slab
                 potential, forces and energy (Section 2.4, Thm 2.4)
+  md            Langevin dynamics (Section 4.3) with the short-range model of
+                Section 5.2 (shifted-truncated LJ between particles and at
+                the walls), BAOAB steps, Philox normal noise
   soe_recursion.c   the recursion itself, plain C99 + OpenMP
 
 Every function is pinned by tests under tests/ against closed forms,
 invariants, brute force or the paper's error bounds (see the test files).
 """
-from . import ewald2d, lattice, soe_check, soe_ewald2d, walls  # noqa: F401
+from . import ewald2d, lattice, md, soe_check, soe_ewald2d, walls  # noqa: F401
 from .ewald2d import ewald2d_longrange, image_sum_extrapolated, realspace, soe_pair_direct  # noqa: F401
 from .soe_ewald2d import soe_full, soe_rbe, soe_rbe_seeded  # noqa: F401
