@@ -278,6 +278,43 @@ int qslab_set_rcut(qslab_ctx* ctx, double rc);
 int qslab_compute_realspace(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
                             double* energy, void* phi, void* force, void* stream);
 
+/* Langevin dynamics of one slab (Section 4.3) with the forces of this
+ * library: the long-range part as configured (full k-sum or random batch,
+ * either sampler, charged walls if set), the real-space part within rc, and
+ * the short-range model of Section 5.2: a shifted-truncated Lennard-Jones
+ * repulsion 4 eps [(s/r)^12 - (s/r)^6 + 1/4] for r < 2^(1/6) s between
+ * particles (lj_eps, lj_sigma; 2^(1/6) lj_sigma <= rc) and in the distance
+ * to each wall (wall_eps, wall_sigma). lj_eps = 0 or wall_eps = 0 turns a
+ * term off. Time stepping is BAOAB (Leimkuhler and Matthews 2013) in
+ * velocities: v += dt/2 F/m; x += dt/2 v; v <- c1 v + c2 xi with
+ * c1 = e^{-gamma dt/m}, c2 = sqrt((1 - c1^2) kT/m); x += dt/2 v; new F;
+ * v += dt/2 F/m. x and y are wrapped into [0, L). The noise xi of particle
+ * i at step n comes from Philox4x64-10 with counter (i, n, 0, 0x4D445331)
+ * and key (seed, 0) through the Box-Muller transform; n is a device counter
+ * advanced by every step (so CUDA-graph replays continue the noise), read
+ * and set with qslab_md_get_step / qslab_md_set_step. */
+int qslab_md_configure(qslab_ctx* ctx, double dt, double mass, double gamma, double kT,
+                       double lj_eps, double lj_sigma, double wall_eps, double wall_sigma,
+                       uint64_t seed);
+/* The total force at pos into force (device, 3N of the context's
+ * precision), and if energies (device double[4]) is not NULL: the
+ * long-range energy (walls included), the real-space energy with the LJ
+ * pairs, the LJ wall energy and the kinetic energy of vel (vel may be
+ * NULL: 0). Needs qslab_md_configure, the box and rc
+ * (QSLAB_ERR_NOT_CONFIGURED). Stream-ordered. */
+int qslab_md_forces(qslab_ctx* ctx, int64_t N, const void* pos, const void* q, void* vel,
+                    void* force, double* energies, void* stream);
+/* nsteps >= 1 BAOAB steps in place: pos, vel (device, 3N) and force (the
+ * total force at pos on entry, as left by qslab_md_forces or the previous
+ * step; updated). energies as for qslab_md_forces, after the last step.
+ * No allocation once the buffers for N exist (first call), so a call can be
+ * captured in a CUDA graph. Device-side input errors go to the status word;
+ * a particle leaving [0, Lz] sets QSLAB_ERR_Z_OUT_OF_RANGE. */
+int qslab_md_step(qslab_ctx* ctx, int64_t N, void* pos, void* vel, const void* q, void* force,
+                  int nsteps, double* energies, void* stream);
+int qslab_md_set_step(qslab_ctx* ctx, uint64_t step);
+int qslab_md_get_step(qslab_ctx* ctx, uint64_t* step);
+
 /* Random-batch mode: copy the lattice vectors used by the latest
  * qslab_compute() or qslab_compute_batched() into mxy (host, 2*P*R int32:
  * (m_x, m_y) pairs, replica by replica; R = 1 after qslab_compute()) and, if

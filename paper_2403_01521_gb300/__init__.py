@@ -86,6 +86,11 @@ def load(build_if_missing: bool = True):
         "qslab_set_rcut": ([P, D], I),
         "qslab_set_walls": ([P, D, D, I, P, P, P], I),
         "qslab_set_rbe_sampler": ([P, I, I], I),
+        "qslab_md_configure": ([P, D, D, D, D, D, D, D, D, ctypes.c_uint64], I),
+        "qslab_md_forces": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
+        "qslab_md_step": ([P, ctypes.c_int64, P, P, P, P, I, P, P], I),
+        "qslab_md_set_step": ([P, ctypes.c_uint64], I),
+        "qslab_md_get_step": ([P, P], I),
         "qslab_clear_walls": ([P], I),
         "qslab_compute_realspace": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_get_sampled_modes": ([P, P, P], I),
@@ -230,6 +235,32 @@ def qslab_set_rbe_sampler(h, kind, thin=1):
     """Random-batch k-sampler: QSLAB_SAMPLER_IID or QSLAB_SAMPLER_METROPOLIS
     (App. G) with downsampling rate thin."""
     _check(load().qslab_set_rbe_sampler(h, int(kind), int(thin)), "qslab_set_rbe_sampler")
+
+
+def qslab_md_configure(h, dt, mass, gamma, kT, lj_eps, lj_sigma, wall_eps, wall_sigma, seed):
+    _check(load().qslab_md_configure(h, float(dt), float(mass), float(gamma), float(kT),
+                                     float(lj_eps), float(lj_sigma), float(wall_eps),
+                                     float(wall_sigma), int(seed)), "qslab_md_configure")
+
+
+def qslab_md_forces(h, N, pos_ptr, q_ptr, vel_ptr, force_ptr, energies_ptr, stream_ptr):
+    _check(load().qslab_md_forces(h, N, pos_ptr, q_ptr, vel_ptr, force_ptr, energies_ptr,
+                                  stream_ptr), "qslab_md_forces")
+
+
+def qslab_md_step(h, N, pos_ptr, vel_ptr, q_ptr, force_ptr, nsteps, energies_ptr, stream_ptr):
+    _check(load().qslab_md_step(h, N, pos_ptr, vel_ptr, q_ptr, force_ptr, int(nsteps),
+                                energies_ptr, stream_ptr), "qslab_md_step")
+
+
+def qslab_md_set_step(h, step):
+    _check(load().qslab_md_set_step(h, int(step)), "qslab_md_set_step")
+
+
+def qslab_md_get_step(h):
+    v = ctypes.c_uint64(0)
+    _check(load().qslab_md_get_step(h, ctypes.byref(v)), "qslab_md_get_step")
+    return v.value
 
 
 def qslab_clear_walls(h):
@@ -447,6 +478,50 @@ class QSlab:
                                 force.data_ptr() if force is not None else None, st)
         return energy, phi, force
 
+    def md_configure(self, dt, mass=1.0, gamma=1.0, kT=1.0, lj=(1.0, 1.0), wall=(1.0, 0.5),
+                     seed=0):
+        """Langevin dynamics (BAOAB): lj=(eps, sigma) between particles and
+        wall=(eps, sigma) at both walls, or None to leave a term out."""
+        lj = lj or (0.0, 0.0)
+        wall = wall or (0.0, 0.0)
+        qslab_md_configure(self.h, dt, mass, gamma, kT, lj[0], lj[1], wall[0], wall[1], seed)
+        return self
+
+    def _md_check(self, *ts):
+        dev = self.torch.device("cuda", self.device)
+        for t in ts:
+            if t is not None and (t.device != dev or t.dtype != self.dtype or not t.is_contiguous()):
+                raise ValueError("MD arrays must be contiguous CUDA tensors of the context's dtype")
+
+    def md_forces(self, pos, q, vel=None, force=None, energies=None):
+        """Total force at pos; returns (force[N,3], energies[4]): long range,
+        real space + LJ pairs, LJ walls, kinetic."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        N = q.shape[0]
+        if force is None:
+            force = torch.empty((N, 3), dtype=self.dtype, device=dev)
+        if energies is None:
+            energies = torch.empty(4, dtype=torch.float64, device=dev)
+        self._md_check(pos, q, vel, force)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        qslab_md_forces(self.h, N, pos.data_ptr(), q.data_ptr(),
+                        vel.data_ptr() if vel is not None else None, force.data_ptr(),
+                        energies.data_ptr(), st)
+        return force, energies
+
+    def md_step(self, pos, vel, q, force, nsteps=1, energies=None):
+        """nsteps BAOAB steps in place (pos, vel, force); returns energies[4]."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        if energies is None:
+            energies = torch.empty(4, dtype=torch.float64, device=dev)
+        self._md_check(pos, vel, q, force)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        qslab_md_step(self.h, q.shape[0], pos.data_ptr(), vel.data_ptr(), q.data_ptr(),
+                      force.data_ptr(), nsteps, energies.data_ptr(), st)
+        return energies
+
     def compute_host(self, pos, q, stream=None):
         """Host numpy in, host numpy out, through qslab_compute_host."""
         pos = np.ascontiguousarray(pos, self.np_dtype)
@@ -531,6 +606,34 @@ class GraphedBatch:
     def replay(self):
         self.graph.replay()
         return self.energies, self.phi, self.force
+
+
+class GraphedMD:
+    """nsteps of qslab_md_step captured once in a CUDA graph. pos, vel and
+    force are updated in place at every replay; the noise and random-batch
+    counters live on the device, so replays continue the trajectory."""
+
+    def __init__(self, slab: QSlab, pos, vel, q, force, nsteps: int = 1):
+        import torch
+        self.slab, self.pos, self.vel, self.q, self.force = slab, pos, vel, q, force
+        self.nsteps = int(nsteps)
+        dev = pos.device
+        self.energies = torch.empty(4, dtype=torch.float64, device=dev)
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            # sizes every buffer, so that the captured call only issues
+            # stream-ordered work (this warm-up advances the trajectory)
+            slab.md_step(pos, vel, q, force, self.nsteps, self.energies)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            slab.md_step(pos, vel, q, force, self.nsteps, self.energies)
+
+    def replay(self):
+        self.graph.replay()
+        return self.energies
 
 
 def _autograd():

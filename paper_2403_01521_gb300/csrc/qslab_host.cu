@@ -17,6 +17,7 @@
 #include "qslab.h"
 #include "qslab_internal.h"
 #include "qslab_real.h"
+#include "qslab_md.h"
 
 using namespace qslab;
 
@@ -71,6 +72,13 @@ struct qslab_ctx {
   WallTab walls{};              // charged walls (walls.on = 0: none)
   int sampler = QSLAB_SAMPLER_IID;   // random-batch k-sampler
   int mh_thin = 1;              // Metropolis downsampling rate
+  // Langevin dynamics driver
+  bool md_on = false;
+  MDDev md{};
+  double lj_eps = 0, lj_sigma = 0;
+  void* d_md = nullptr;         // F_lr, F_rs (3N each), partial sums, e_lr, e_rs
+  size_t md_bytes = 0;
+  uint64_t* d_md_ctr = nullptr; // step counter of the noise (device)
   // derived configuration
   bool cfg_dirty = true;
   uint64_t cfg_version = 0;
@@ -765,6 +773,7 @@ int qslab_create(qslab_ctx** out, int cuda_device, int prec) {
   c->d_status = static_cast<unsigned*>(small);
   c->d_energy = reinterpret_cast<double*>(static_cast<char*>(small) + 128);
   c->d_ctr = reinterpret_cast<uint64_t*>(static_cast<char*>(small) + 192);
+  c->d_md_ctr = reinterpret_cast<uint64_t*>(static_cast<char*>(small) + 224);
   if (cudaMemset(small, 0, 256) != cudaSuccess) {
     cudaFree(small);
     delete c;
@@ -787,6 +796,7 @@ void qslab_destroy(qslab_ctx* c) {
   cudaDeviceSynchronize();
   if (c->d_ws) cudaFree(c->d_ws);
   if (c->d_rs_ws) cudaFree(c->d_rs_ws);
+  if (c->d_md) cudaFree(c->d_md);
   if (c->d_tab) cudaFree(c->d_tab);
   if (c->d_status) cudaFree(c->d_status);
   for (auto& ev : c->ev)
@@ -976,8 +986,13 @@ int qslab_set_rcut(qslab_ctx* c, double rc) {
   return QSLAB_OK;
 }
 
-int qslab_compute_realspace(qslab_ctx* c, int64_t N, const void* pos, const void* q,
-                            double* energy, void* phi, void* force, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// The real-space sum (with the LJ pairs when lj_eps > 0) on stream st.
+int realspace_call(qslab_ctx* c, int64_t N, const void* pos, const void* q, double* energy,
+                   void* phi, void* force, cudaStream_t st, double lj_eps, double lj_sigma) {
   if (!c || !pos || !q || N < 1 || N > 2147483647LL) return QSLAB_ERR_INVALID_ARG;
   if (!c->has_box || !c->has_alpha || c->rc <= 0) return QSLAB_ERR_NOT_CONFIGURED;
   RsGrid g;
@@ -985,6 +1000,9 @@ int qslab_compute_realspace(qslab_ctx* c, int64_t N, const void* pos, const void
   g.Lx = c->Lx; g.Ly = c->Ly; g.Lz = c->Lz;
   g.alpha = c->alpha;
   g.rc = c->rc;
+  g.lj_eps = lj_eps;
+  g.lj_sigma = lj_sigma;
+  if (lj_eps > 0.0 && 1.122462048309373 * lj_sigma > c->rc) return QSLAB_ERR_INVALID_ARG;
   if (std::floor(c->Lx / c->rc) < 3 || std::floor(c->Ly / c->rc) < 3)
     return QSLAB_ERR_INVALID_ARG;   // needs rc <= min(Lx, Ly)/3
   // cells of edge >= rc/2: a 5 x 5 x 5 stencil covers rc with less volume
@@ -1007,7 +1025,6 @@ int qslab_compute_realspace(qslab_ctx* c, int64_t N, const void* pos, const void
     QS_CUDA(cudaMalloc(&c->d_rs_ws, need));
     c->rs_ws_bytes = need;
   }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (c->prec == QSLAB_FP64)
     launch_realspace<double>(g, static_cast<const double*>(pos), static_cast<const double*>(q),
                              c->d_rs_ws, c->d_status, energy, static_cast<double*>(phi),
@@ -1019,6 +1036,160 @@ int qslab_compute_realspace(qslab_ctx* c, int64_t N, const void* pos, const void
   QS_CUDA(cudaGetLastError());
   c->last_stream = st;
   return QSLAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qslab_compute_realspace(qslab_ctx* c, int64_t N, const void* pos, const void* q,
+                            double* energy, void* phi, void* force, void* stream) {
+  return realspace_call(c, N, pos, q, energy, phi, force, static_cast<cudaStream_t>(stream), 0.0,
+                        0.0);
+}
+
+int qslab_md_configure(qslab_ctx* c, double dt, double mass, double gamma, double kT,
+                       double lj_eps, double lj_sigma, double wall_eps, double wall_sigma,
+                       uint64_t seed) {
+  if (!c || !finite_pos(dt) || !finite_pos(mass) || !std::isfinite(gamma) || gamma < 0 ||
+      !std::isfinite(kT) || kT < 0 || !std::isfinite(lj_eps) || lj_eps < 0 ||
+      !std::isfinite(wall_eps) || wall_eps < 0 || (lj_eps > 0 && !finite_pos(lj_sigma)) ||
+      (wall_eps > 0 && !finite_pos(wall_sigma)))
+    return QSLAB_ERR_INVALID_ARG;
+  MDDev m{};
+  m.dt = dt;
+  m.mass = mass;
+  m.c1 = std::exp(-gamma * dt / mass);
+  m.c2 = std::sqrt((1.0 - m.c1 * m.c1) * kT / mass);
+  m.wall_eps = wall_eps;
+  m.wall_sigma = wall_eps > 0 ? wall_sigma : 1.0;
+  m.seed = seed;
+  c->md = m;
+  c->lj_eps = lj_eps;
+  c->lj_sigma = lj_eps > 0 ? lj_sigma : 0.0;
+  c->md_on = true;
+  return QSLAB_OK;
+}
+
+int qslab_md_set_step(qslab_ctx* c, uint64_t step) {
+  if (!c) return QSLAB_ERR_INVALID_ARG;
+  QS_CUDA(cudaSetDevice(c->device));
+  QS_CUDA(cudaStreamSynchronize(c->last_stream));
+  QS_CUDA(cudaMemcpy(c->d_md_ctr, &step, sizeof(uint64_t), cudaMemcpyHostToDevice));
+  return QSLAB_OK;
+}
+
+int qslab_md_get_step(qslab_ctx* c, uint64_t* step) {
+  if (!c || !step) return QSLAB_ERR_INVALID_ARG;
+  QS_CUDA(cudaSetDevice(c->device));
+  QS_CUDA(cudaStreamSynchronize(c->last_stream));
+  QS_CUDA(cudaMemcpy(step, c->d_md_ctr, sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  return QSLAB_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct MDBufs {
+  void* flr;
+  void* frs;
+  double* part;
+  double* e_lr;
+  double* e_rs;
+};
+
+int md_buffers(qslab_ctx* c, int64_t N, MDBufs& b) {
+  const size_t tsz = c->prec == QSLAB_FP64 ? 8 : 4;
+  const size_t f = a256(3 * tsz * (size_t)N);
+  const size_t need = 2 * f + a256(16 * (size_t)md_blocks(N)) + 256;
+  if (need > c->md_bytes) {
+    if (c->d_md) {
+      cudaDeviceSynchronize();
+      cudaFree(c->d_md);
+    }
+    c->d_md = nullptr;
+    c->md_bytes = 0;
+    QS_CUDA(cudaMalloc(&c->d_md, need));
+    c->md_bytes = need;
+  }
+  char* p = static_cast<char*>(c->d_md);
+  b.flr = p;
+  b.frs = p + f;
+  b.part = reinterpret_cast<double*>(p + 2 * f);
+  b.e_lr = reinterpret_cast<double*>(p + 2 * f + a256(16 * (size_t)md_blocks(N)));
+  b.e_rs = b.e_lr + 1;
+  return QSLAB_OK;
+}
+
+// Forces at pos (long range, real space with LJ pairs, LJ walls) into
+// `force`; with kick, the closing half kick of a step.
+template <typename T>
+int md_force_pass(qslab_ctx* c, const Plan& P, int64_t N, const MDBufs& b, const void* pos,
+                  const void* q, void* vel, void* force, bool kick, cudaStream_t st) {
+  int rc = dispatch(c, P, pos, q, b.e_lr, nullptr, b.flr, st);
+  if (rc) return rc;
+  rc = realspace_call(c, N, pos, q, b.e_rs, nullptr, b.frs, st, c->lj_eps, c->lj_sigma);
+  if (rc) return rc;
+  launch_md_end<T>(N, c->md, static_cast<const T*>(pos), static_cast<T*>(vel),
+                   static_cast<const T*>(b.flr), static_cast<const T*>(b.frs),
+                   static_cast<T*>(force), b.part, c->d_md_ctr, kick, st);
+  return QSLAB_OK;
+}
+
+template <typename T>
+int md_run(qslab_ctx* c, int64_t N, void* pos, void* vel, const void* q, void* force, int nsteps,
+           double* energies, cudaStream_t st) {
+  const int64_t off[2] = {0, N};
+  const double box[3] = {c->Lx, c->Ly, c->Lz};
+  Plan P;
+  int rc = setup_call(c, 1, off, box, false, P);
+  if (rc) return rc;
+  MDBufs b;
+  rc = md_buffers(c, N, b);
+  if (rc) return rc;
+  c->md.Lx = c->Lx; c->md.Ly = c->Ly; c->md.Lz = c->Lz;
+  if (nsteps == 0) {
+    rc = md_force_pass<T>(c, P, N, b, pos, q, vel, force, false, st);
+    if (rc) return rc;
+  }
+  for (int n = 0; n < nsteps; ++n) {
+    launch_md_begin<T>(N, c->md, static_cast<T*>(pos), static_cast<T*>(vel),
+                       static_cast<const T*>(force), c->d_md_ctr, st);
+    rc = md_force_pass<T>(c, P, N, b, pos, q, vel, force, true, st);
+    if (rc) return rc;
+  }
+  if (energies) launch_md_energies(N, b.part, b.e_lr, b.e_rs, energies, st);
+  QS_CUDA(cudaGetLastError());
+  c->last_stream = st;
+  return QSLAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qslab_md_forces(qslab_ctx* c, int64_t N, const void* pos, const void* q, void* vel,
+                    void* force, double* energies, void* stream) {
+  if (!c || !pos || !q || !force || N < 1 || N > 2147483647LL) return QSLAB_ERR_INVALID_ARG;
+  if (!c->md_on || !c->has_box || c->rc <= 0) return QSLAB_ERR_NOT_CONFIGURED;
+  QS_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->prec == QSLAB_FP64)
+    return md_run<double>(c, N, const_cast<void*>(pos), vel, q, force, 0, energies, st);
+  return md_run<float>(c, N, const_cast<void*>(pos), vel, q, force, 0, energies, st);
+}
+
+int qslab_md_step(qslab_ctx* c, int64_t N, void* pos, void* vel, const void* q, void* force,
+                  int nsteps, double* energies, void* stream) {
+  if (!c || !pos || !vel || !q || !force || N < 1 || N > 2147483647LL || nsteps < 1)
+    return QSLAB_ERR_INVALID_ARG;
+  if (!c->md_on || !c->has_box || c->rc <= 0) return QSLAB_ERR_NOT_CONFIGURED;
+  QS_CUDA(cudaSetDevice(c->device));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->prec == QSLAB_FP64)
+    return md_run<double>(c, N, pos, vel, q, force, nsteps, energies, st);
+  return md_run<float>(c, N, pos, vel, q, force, nsteps, energies, st);
 }
 
 int qslab_get_sampled_modes(qslab_ctx* c, int32_t* mxy, double* weight) {

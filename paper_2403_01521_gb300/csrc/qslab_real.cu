@@ -135,7 +135,7 @@ constexpr int kRsRow = 512;      // neighbour records staged in shared memory at
 // erfc and exp for the marked pairs only, so that the warp does not run the
 // pair arithmetic for the candidates outside rc. A warp without a home
 // particle only helps to stage the rows.
-template <typename T>
+template <typename T, bool LJ>
 __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
                                                            const int32_t* __restrict__ cstart,
                                                            const RsRec<T>* __restrict__ rec,
@@ -150,6 +150,10 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
   const T alpha = (T)g.alpha, rc2 = (T)(g.rc * g.rc);
   const T a2 = alpha * alpha;
   const T two_a_sqpi = (T)(2.0 * g.alpha / 1.7724538509055160);
+  // shifted-truncated LJ (the short-range model of Section 5.2), optional
+  const T lj_s2 = (T)(g.lj_sigma * g.lj_sigma);
+  const T lj_rc2 = (T)(1.2599210498948732 * g.lj_sigma * g.lj_sigma);   // (2^(1/6) sigma)^2
+  const T lj_24e = (T)(24.0 * g.lj_eps), lj_4e = (T)(4.0 * g.lj_eps);
   const RsRec<T> far{(T)1e30, (T)1e30, (T)1e30, (T)0};
   double e_acc = 0.0;
   for (int i0 = hs + blockIdx.y * kRsThreads; i0 < he; i0 += gridDim.y * kRsThreads) {
@@ -159,6 +163,7 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
     RsRec<T> ri{(T)-1e30, (T)-1e30, (T)-1e30, (T)0};   // idle threads match nothing
     if (live) ri = rec[i];
     T ph = 0, fx = 0, fy = 0, fz = 0;
+    T lx = 0, ly = 0, lz = 0, le = 0;       // LJ force and twice its energy share
     for (int dz = -S; dz <= S; ++dz) {
       const int nz = cz + dz;
       if (nz < 0 || nz >= g.ncz) continue;
@@ -241,6 +246,20 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
               fx = fma(w2, dx2, fma(w1, dx1, fx));
               fy = fma(w2, dy2, fma(w1, dy1, fy));
               fz = fma(w2, dz2, fma(w1, dz1, fz));
+              if (LJ) {
+                if (r21 < lj_rc2) {
+                  const T s2 = lj_s2 / r21, s6 = s2 * s2 * s2;
+                  const T f = lj_24e * (2 * s6 * s6 - s6) / r21;   // -(dU/dr)/r
+                  lx = fma(f, dx1, lx); ly = fma(f, dy1, ly); lz = fma(f, dz1, lz);
+                  le += lj_4e * (s6 * s6 - s6 + (T)0.25);
+                }
+                if (qmul != (T)0 && r22 < lj_rc2) {
+                  const T s2 = lj_s2 / r22, s6 = s2 * s2 * s2;
+                  const T f = lj_24e * (2 * s6 * s6 - s6) / r22;
+                  lx = fma(f, dx2, lx); ly = fma(f, dy2, ly); lz = fma(f, dz2, lz);
+                  le += lj_4e * (s6 * s6 - s6 + (T)0.25);
+                }
+              }
             }
           }
         }
@@ -250,11 +269,11 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
       const uint32_t o = perm[i];
       if (phi_out) phi_out[o] = ph;
       if (force_out) {
-        force_out[3 * (int64_t)o] = ri.q * fx;
-        force_out[3 * (int64_t)o + 1] = ri.q * fy;
-        force_out[3 * (int64_t)o + 2] = ri.q * fz;
+        force_out[3 * (int64_t)o] = fma(ri.q, fx, lx);
+        force_out[3 * (int64_t)o + 1] = fma(ri.q, fy, ly);
+        force_out[3 * (int64_t)o + 2] = fma(ri.q, fz, lz);
       }
-      e_acc += 0.5 * (double)ri.q * (double)ph;
+      e_acc += 0.5 * (double)ri.q * (double)ph + 0.5 * (double)le;
     }
   }
   for (int o = 16; o; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
@@ -321,9 +340,12 @@ int launch_realspace(const RsGrid& g, const T* pos, const T* q, void* ws, unsign
   rs_cells_kernel<<<cblocks, 256, 0, st>>>(g.N, ncell, static_cast<const uint32_t*>(sw.keys[r]),
                                            cstart);
   rs_gather_kernel<T><<<blocks, 256, 0, st>>>(g, pos, q, sw.vals[r], rec);
-  rs_pair_kernel<T><<<dim3((unsigned)ncell, parts), kRsThreads, 0, st>>>(g, cstart, rec,
-                                                                          sw.vals[r], phi, force,
-                                                                          ecell);
+  if (g.lj_eps > 0.0)
+    rs_pair_kernel<T, true><<<dim3((unsigned)ncell, parts), kRsThreads, 0, st>>>(
+        g, cstart, rec, sw.vals[r], phi, force, ecell);
+  else
+    rs_pair_kernel<T, false><<<dim3((unsigned)ncell, parts), kRsThreads, 0, st>>>(
+        g, cstart, rec, sw.vals[r], phi, force, ecell);
   if (energy) rs_energy_kernel<<<1, 256, 0, st>>>((int)(ncell * parts), ecell, energy);
   return 3 + 3 * passes + (energy ? 2 : 1);
 }

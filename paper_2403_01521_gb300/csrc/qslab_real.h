@@ -13,10 +13,13 @@ struct RsGrid {
   int ncx, ncy, ncz;        // cells (ncx, ncy >= 2s + 1)
   double Lx, Ly, Lz, hz;    // box and cell height in z
   double alpha, rc;
+  double lj_eps, lj_sigma;  // shifted-truncated LJ between particles (eps = 0: none)
 };
 size_t rs_workspace_bytes(const RsGrid& g);
 // phi, force (caller's order; may be NULL) and energy (device scalar, may be
-// NULL) of the real-space sum; returns the number of kernels launched
+// NULL) of the real-space sum; with lj_eps > 0 the force and energy include
+// the LJ pairs (r < 2^(1/6) lj_sigma <= rc), phi does not. Returns the number
+// of kernels launched.
 template <typename T>
 int launch_realspace(const RsGrid& g, const T* pos, const T* q, void* ws, unsigned* status,
                      double* energy, T* phi, T* force, cudaStream_t st);
