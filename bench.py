@@ -357,6 +357,7 @@ def run_ours(args):
     if not args.no_batched:
         line["batched"] = run_batched(args, qslab, soe, dev, ws, rank, local, peak, smax)
     line["realspace"] = run_realspace(args, qslab, soe, dev, ws)
+    line["md"] = run_md(args, qslab, soe, dev, ws)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         t, desc, cores = cpu_oracle_sample(sl, soe, P, 1000, sample_modes=8)
         line["cpu_baseline"] = {"value": N / t, "unit": "particles/s", "cores": cores,
@@ -457,6 +458,49 @@ def run_batched(args, qslab, soe, dev, ws, rank, local, peak, smax):
     return out
 
 
+def run_md(args, qslab, soe, dev, ws):
+    """Langevin steps of Section 5.2's cation-only system (436 cations in
+    100 x 100 x 30 between an uncharged wall and one at -0.0436, LJ
+    particles and walls, alpha = 0.3, rc = 4/alpha), FP32C, random batch
+    P = 100 with the Metropolis sampler, 100 steps per CUDA-graph replay.
+    Each step: one long-range call, one real-space call, two MD kernels."""
+    import torch
+
+    import workloads
+    sl = workloads.cations_walls()
+    rng = np.random.default_rng(1)
+    g = (np.arange(8) + 0.5) * 12.5
+    gx, gy, gz = np.meshgrid(g, g, 2.0 + np.arange(7) * 4.3, indexing="ij")
+    pos0 = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], 1)[:sl.N] + rng.uniform(-1, 1, (sl.N, 3))
+    s = qslab.QSlab(dev.index or 0, "fp32c").configure(sl.box, 0.3, soe, rbe=(100, 7), rcut=4 / 0.3)
+    s.sampler("metropolis", 1)
+    s.set_walls(*sl.walls)
+    s.md_configure(0.005, 1.0, 1.0, 1.0, (1.0, 1.0), (1.0, 0.5), 3)
+    pos = torch.tensor(pos0, device=dev, dtype=torch.float32)
+    vel = torch.tensor(rng.normal(size=(sl.N, 3)), device=dev, dtype=torch.float32)
+    q = torch.tensor(sl.q, device=dev, dtype=torch.float32)
+    F, _ = s.md_forces(pos, q, vel)
+    chunk = 100
+    gr = qslab.GraphedMD(s, pos, vel, q, F, chunk)
+    for _ in range(3):
+        gr.replay()
+    reps = max(5, args.steps // 5)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(reps):
+        gr.replay()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    s.check()
+    ms = reduce_max(e0.elapsed_time(e1) / (reps * chunk), dev)
+    s.close()
+    return {"workload": "436 cations in 100x100x30, top wall -0.0436, LJ, alpha=0.3, rc=4/alpha, "
+                        "RBE P=100 (Metropolis), BAOAB dt=0.005, FP32C",
+            "us_per_step": 1e3 * ms, "steps_per_s": ws / (ms * 1e-3), "steps": reps * chunk}
+
+
 def run_realspace(args, qslab, soe, dev, ws):
     """The real-space part (Eq. 2.10) on the N = 1e5 workload of the FP32
     full-k configuration (100 x 100 x 20, alpha = 0.25, rc = 10), FP32C:
@@ -508,12 +552,16 @@ def profile_case(kind="single"):
     workload (N = 1e6); 'batched' = the first 128 slabs of the replica
     workload (about 3.3e6 particles) as one batched call, launch shape fixed
     at 512-particle chunks; 'realspace' = the real-space part on the N = 1e5
-    FP32 full-k workload (rc = 10)."""
+    FP32 full-k workload (rc = 10); 'single+realspace' = both, one after
+    the other."""
     import torch
 
     import paper_2403_01521_gb300 as qslab
     import workloads
     soe = qslab.load_soe(16)
+    if kind == "single+realspace":
+        profile_case("single")
+        return profile_case("realspace")
     if kind == "realspace":
         sl = workloads.fp32_full()
         slab = qslab.QSlab(0, "fp32c").configure(sl.box, 0.25, soe, kcut=1.0, rcut=10.0)
@@ -559,7 +607,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-replica batched measurement")
     ap.add_argument("--profile-case", nargs="?", const="single",
-                    choices=["single", "batched", "realspace"],
+                    choices=["single", "batched", "realspace", "single+realspace"],
                     help="only run two FP32 random-batch calls (for profilers)")
     args = ap.parse_args()
     if args.profile_case:

@@ -184,3 +184,51 @@ def test_md_input_errors(qslab, soe16):
         slab.md_forces(pos, q)
     assert e.value.code == qslab.QSLAB_ERR_INVALID_ARG
     slab.close()
+
+
+def _cation_profile(qslab, soe, rbe, nsteps, seed):
+    """z-histogram (1-wide bins) of Section 5.2's cation-only system: 436
+    cations in 100 x 100 x 30, top wall at -0.0436 (neutralising), LJ
+    particles and walls, alpha = 0.3, rc = 4/alpha, Langevin at kT = 1,
+    dt = 0.005; averaged over the last two thirds of the run."""
+    import workloads
+    sl = workloads.cations_walls()
+    rng = np.random.default_rng(seed)
+    g = (np.arange(8) + 0.5) * 12.5
+    gx, gy, gz = np.meshgrid(g, g, 2.0 + np.arange(7) * 4.3, indexing="ij")
+    pos0 = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], 1)[:sl.N] + rng.uniform(-1, 1, (sl.N, 3))
+    slab = qslab.QSlab(0, "fp32c").configure(sl.box, 0.3, soe, rbe=rbe, rcut=4 / 0.3)
+    if rbe is not None:
+        slab.sampler("metropolis", 1)
+    slab.set_walls(*sl.walls)
+    slab.md_configure(0.005, 1.0, 1.0, 1.0, (1.0, 1.0), (1.0, 0.5), seed)
+    pos = torch.tensor(pos0, device="cuda", dtype=torch.float32)
+    vel = torch.tensor(rng.normal(size=(sl.N, 3)), device="cuda", dtype=torch.float32)
+    q = torch.tensor(sl.q, device="cuda", dtype=torch.float32)
+    F, _ = slab.md_forces(pos, q, vel)
+    chunk = 100
+    gr = qslab.GraphedMD(slab, pos, vel, q, F, chunk)
+    hist = np.zeros(30)
+    nchunks = nsteps // chunk
+    for k in range(nchunks):
+        gr.replay()
+        if k >= nchunks // 3:
+            hist += np.histogram(pos[:, 2].cpu().numpy(), bins=30, range=(0.0, 30.0))[0]
+    assert slab.status() == 0
+    slab.close()
+    return hist / hist.sum()
+
+
+def test_md_cation_layer_rbe_matches_full_k(qslab, soe16):
+    """Section 5.2, cation-only system (the concentration profile of its
+    Fig. 5(b), qualitatively): the cations gather in a layer at the
+    neutralising wall, and the random-batch run (P = 100, Metropolis
+    sampler) gives the same profile as the full k-sum."""
+    rb = _cation_profile(qslab, soe16, (100, 7), 30_000, 3)
+    fk = _cation_profile(qslab, soe16, None, 30_000, 4)
+    for p in (rb, fk):
+        assert p[25:].sum() > 0.4            # most cations within 5 of the top wall
+        assert p[:15].sum() < 0.25           # a dilute bulk at the uncharged wall's side
+        assert (np.diff(p[15:29]) > -0.01).all()   # rising towards the charged wall
+    assert abs(rb[25:].sum() - fk[25:].sum()) < 0.03
+    assert abs((rb * np.arange(30)).sum() - (fk * np.arange(30)).sum()) < 0.5
