@@ -19,6 +19,11 @@ Modules:
   soe_check     SOE table checks (Eq. 3.1, Thm 3.2, Eq. 3.24)
   walls         charged walls at z = 0 and z = Lz: the particle-slab
                 potential, forces and energy (Section 2.4, Thm 2.4)
+  virial        the virial tensor W_ab = -dE/d eps_ab of the long-range
+                energy (exact and SOE, full k-sum and random batch), of the
+                particle-slab energy and of the real-space sum (pressure for
+                the NPT ensemble, Section 4.3; the L_z-dependent constant of
+                Thm 2.4's uniform-density case)
   md            Langevin dynamics (Section 4.3) with the short-range model of
                 Section 5.2 (shifted-truncated LJ between particles and at
                 the walls), BAOAB steps, Philox normal noise
@@ -27,6 +32,6 @@ Modules:
 Every function is pinned by tests under tests/ against closed forms,
 invariants, brute force or the paper's error bounds (see the test files).
 """
-from . import ewald2d, lattice, md, soe_check, soe_ewald2d, walls  # noqa: F401
+from . import ewald2d, lattice, md, soe_check, soe_ewald2d, virial, walls  # noqa: F401
 from .ewald2d import ewald2d_longrange, image_sum_extrapolated, realspace, soe_pair_direct  # noqa: F401
 from .soe_ewald2d import soe_full, soe_rbe, soe_rbe_seeded  # noqa: F401

@@ -123,12 +123,16 @@ def _assemble(q, box, alpha, phik, Fk, phi0, fz0, Dk):
     return {"E": 0.5 * float(q @ phi), "phi": phi, "F": F}
 
 
-def soe_full(pos, q, box, alpha, s, w, kc=None, tail=1e-8):
-    """SOEwald2D long-range part, full k-sum over 0 < |k| <= kc."""
+def soe_full(pos, q, box, alpha, s, w, kc=None, tail=1e-8, modes=None):
+    """SOEwald2D long-range part, full k-sum over 0 < |k| <= kc (or over the
+    given integer modes (mx, my), which must be closed under k -> -k)."""
     Lx, Ly, _ = box
-    if kc is None:
-        kc = kcut_for_tail(alpha, tail)
-    mx, my = full_modes(Lx, Ly, kc)
+    if modes is not None:
+        mx, my = (np.asarray(v, dtype=np.int64) for v in modes)
+    else:
+        if kc is None:
+            kc = kcut_for_tail(alpha, tail)
+        mx, my = full_modes(Lx, Ly, kc)
     gam = mode_prefactor(alpha, Lx, Ly, mx, my, 1.0)
     phik, Fk = kspace_pairs(pos, q, box, alpha, s, w, mx, my, gam)
     phi0, fz0 = kzero_pairs(pos, q, box, alpha, s, w)

@@ -39,6 +39,20 @@
  *     The |z| parts use sorted prefix sums of q and q z; the exponential parts
  *     use the same A_i recursion with inputs q_j and q_j z_j.
  *
+ *   k-derivative of the k != 0 pair sums (the lateral virial, oracle/virial.py):
+ *     R_k = sum_{i != j} q_i q_j cos(k.rho_ij) d/dk G_SOE(k, |z_ij|),
+ *     G_SOE(k, z) = C_k sum_beta c_beta e^{-beta z}.
+ *     Only C_k, the coefficients c_beta and the node beta = k depend on k
+ *     (a_l = alpha s_l does not), so
+ *       dG_SOE/dk = sum_beta (C_k c_beta)' e^{-beta z} - C_k c_k z e^{-k z},
+ *     C_k' = C_k (-k/(2 alpha^2) - 1/k),
+ *     c_k' = sum_l 4 k a_l w_l/(a_l^2-k^2)^2,
+ *     c_l' = -2 w_l (a_l^2+k^2)/(a_l^2-k^2)^2.
+ *     The pair sums are sum_i conj(u_i) (F_i + B_i) (their sin part cancels
+ *     between (i,j) and (j,i)); the z-weighted sum for beta = k is
+ *     sum_{j<i} u_j (z_i - z_j) e^{-k(z_i-z_j)} = z_i F_i(u) - F_i(u z) and
+ *     its mirror B_i(u z) - z_i B_i(u).
+ *
  * The diagonal (j = i) constants, the self term and the energy are added by
  * the Python wrapper.
  */
@@ -260,4 +274,87 @@ void oracle_kzero_soe(int64_t N, const double* z, const double* q, double area,
     free(pot); free(der); free(uq); free(uqz); free(dec);
     free(Sf); free(Sb); free(Zf); free(Zb);
     free(Qlt); free(Qgt); free(Plt); free(Pgt); free(zs); free(qs); free(ord);
+}
+
+/*
+ * R[m] = sum_{i != j} q_i q_j cos(k.rho_ij) dG_SOE/dk(k, |z_ij|) for each
+ * mode (kx[m], ky[m]); see the header comment. Inputs in any order.
+ */
+void oracle_kspace_soe_dk(int64_t N, const double* x, const double* y,
+                          const double* z, const double* q, int64_t K,
+                          const double* kx, const double* ky, double alpha,
+                          int M, const double* s_re, const double* s_im,
+                          const double* w_re, const double* w_im, double* R) {
+    const double pi = 3.14159265358979323846;
+    int64_t* ord = sort_by_z(N, z);
+    double *xs = malloc(sizeof(double) * N), *ys = malloc(sizeof(double) * N);
+    double *zs = malloc(sizeof(double) * N), *qs = malloc(sizeof(double) * N);
+    for (int64_t i = 0; i < N; ++i) {
+        xs[i] = x[ord[i]]; ys[i] = y[ord[i]]; zs[i] = z[ord[i]]; qs[i] = q[ord[i]];
+    }
+    cplx* a = malloc(sizeof(cplx) * (M > 0 ? M : 1));
+    cplx* wl = malloc(sizeof(cplx) * (M > 0 ? M : 1));
+    for (int l = 0; l < M; ++l) {
+        a[l] = alpha * (s_re[l] + I * s_im[l]);
+        wl[l] = w_re[l] + I * w_im[l];
+    }
+    cplx* decl = malloc(sizeof(cplx) * (size_t)(M > 0 ? M : 1) * (size_t)(N > 0 ? N : 1));
+    for (int l = 0; l < M; ++l) {
+        decl[(size_t)l * N] = 1.0;
+        for (int64_t i = 1; i < N; ++i)
+            decl[(size_t)l * N + i] = cexp(-a[l] * (zs[i] - zs[i - 1]));
+    }
+#pragma omp parallel
+    {
+        cplx* u = malloc(sizeof(cplx) * N);
+        cplx* uz = malloc(sizeof(cplx) * N);
+        cplx* deck = malloc(sizeof(cplx) * N);
+        cplx *F = malloc(sizeof(cplx) * N), *B = malloc(sizeof(cplx) * N);
+        cplx *Fz = malloc(sizeof(cplx) * N), *Bz = malloc(sizeof(cplx) * N);
+#pragma omp for schedule(static)
+        for (int64_t m = 0; m < K; ++m) {
+            double k = sqrt(kx[m] * kx[m] + ky[m] * ky[m]);
+            double Ck = 2.0 * alpha * exp(-k * k / (4.0 * alpha * alpha)) / (sqrt(pi) * k);
+            double g = -k / (2.0 * alpha * alpha) - 1.0 / k;     /* C_k'/C_k */
+            for (int64_t i = 0; i < N; ++i) {
+                u[i] = qs[i] * cexp(-I * (kx[m] * xs[i] + ky[m] * ys[i]));
+                uz[i] = u[i] * zs[i];
+            }
+            cplx ck = 0.0, dck = 0.0;
+            for (int l = 0; l < M; ++l) {
+                cplx den = a[l] * a[l] - k * k;
+                ck += 2.0 * a[l] * wl[l] / den;
+                dck += 4.0 * k * a[l] * wl[l] / (den * den);
+            }
+            /* beta = k: plain and z-weighted sums */
+            deck[0] = 1.0;
+            for (int64_t i = 1; i < N; ++i) deck[i] = exp(-k * (zs[i] - zs[i - 1]));
+            forward_sum(N, u, deck, F);
+            backward_sum(N, u, deck, B);
+            forward_sum(N, uz, deck, Fz);
+            backward_sum(N, uz, deck, Bz);
+            cplx Pk = 0.0, Pz = 0.0;
+            for (int64_t i = 0; i < N; ++i) {
+                cplx cu = conj(u[i]);
+                Pk += cu * (F[i] + B[i]);
+                Pz += cu * ((zs[i] * F[i] - Fz[i]) + (Bz[i] - zs[i] * B[i]));
+            }
+            cplx acc = Ck * (ck * g + dck) * Pk - Ck * ck * Pz;
+            /* beta = a_l */
+            for (int l = 0; l < M; ++l) {
+                cplx den = a[l] * a[l] - k * k;
+                cplx cl = -2.0 * k * wl[l] / den;
+                cplx dcl = -2.0 * wl[l] * (a[l] * a[l] + k * k) / (den * den);
+                forward_sum(N, u, decl + (size_t)l * N, F);
+                backward_sum(N, u, decl + (size_t)l * N, B);
+                cplx Pl = 0.0;
+                for (int64_t i = 0; i < N; ++i) Pl += conj(u[i]) * (F[i] + B[i]);
+                acc += Ck * (cl * g + dcl) * Pl;
+            }
+            R[m] = creal(acc);
+        }
+        free(u); free(uz); free(deck); free(F); free(B); free(Fz); free(Bz);
+    }
+    free(decl); free(a); free(wl);
+    free(xs); free(ys); free(zs); free(qs); free(ord);
 }
