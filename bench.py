@@ -357,6 +357,7 @@ def run_ours(args):
     if not args.no_batched:
         line["batched"] = run_batched(args, qslab, soe, dev, ws, rank, local, peak, smax)
     line["realspace"] = run_realspace(args, qslab, soe, dev, ws)
+    line["virial"] = run_virial(args, qslab, soe, dev, ws, sl, P, ms32_max)
     line["md"] = run_md(args, qslab, soe, dev, ws)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         t, desc, cores = cpu_oracle_sample(sl, soe, P, 1000, sample_modes=8)
@@ -499,6 +500,69 @@ def run_md(args, qslab, soe, dev, ws):
     return {"workload": "436 cations in 100x100x30, top wall -0.0436, LJ, alpha=0.3, rc=4/alpha, "
                         "RBE P=100 (Metropolis), BAOAB dt=0.005, FP32C",
             "us_per_step": 1e3 * ms, "steps_per_s": ws / (ms * 1e-3), "steps": reps * chunk}
+
+
+def run_virial(args, qslab, soe, dev, ws, sl, P, ms_plain):
+    """The long-range call with the virial tensor (qslab_compute_virial) on
+    the headline workload (N = 1e6, P = 200, FP32C), L2 flushed between calls
+    as for the headline; and the real-space pair virial on the N = 1e5 case."""
+    import torch
+
+    import workloads
+    N = sl.N
+    s = qslab.QSlab(dev.index or 0, "fp32c").configure(sl.box, sl.alpha, soe, rbe=(P, 77))
+    pos = torch.tensor(sl.pos, device=dev, dtype=torch.float32)
+    q = torch.tensor(sl.q, device=dev, dtype=torch.float32)
+    e = torch.empty(1, dtype=torch.float64, device=dev)
+    phi = torch.empty(N, dtype=torch.float32, device=dev)
+    F = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    W = torch.empty(6, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def call():
+        qslab.qslab_compute_virial(s.h, N, pos.data_ptr(), q.data_ptr(), e.data_ptr(),
+                                   phi.data_ptr(), F.data_ptr(), W.data_ptr(), stream.cuda_stream)
+    for _ in range(max(args.warmup, 3)):
+        call()
+    s.check()
+    steps = max(args.steps, 5)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize(dev)
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        call()
+        b.record(stream)
+    torch.cuda.synchronize(dev)
+    s.check()
+    ms = reduce_max(float(np.mean([a.elapsed_time(b) for a, b in ev])), dev)
+    s.close()
+    # real-space pair virial, N = 1e5 case of run_realspace
+    rs = workloads.fp32_full()
+    t = qslab.QSlab(dev.index or 0, "fp32c").configure(rs.box, 0.25, soe, kcut=1.0, rcut=10.0)
+    rpos = torch.tensor(rs.pos, device=dev, dtype=torch.float32)
+    rq = torch.tensor(rs.q, device=dev, dtype=torch.float32)
+    for _ in range(3):
+        t.compute_realspace_virial(rpos, rq)
+    t.check()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        t.compute_realspace_virial(rpos, rq)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t.check()
+    rs_ms = reduce_max(e0.elapsed_time(e1) / steps, dev)
+    t.close()
+    return {"workload": "long-range energy, forces and virial tensor (qslab_compute_virial), "
+                        "same workload as the headline (N=1e6, P=200, FP32C)",
+            "ms_per_call": ms, "particles_per_s": job_throughput(N, ws, ms),
+            "overhead_vs_plain": ms / ms_plain - 1.0, "steps": steps,
+            "realspace_virial_ms_per_call": rs_ms,
+            "realspace_workload": "N=1e5, 100x100x20, alpha=0.25, rc=10, FP32C, pair virial"}
 
 
 def run_realspace(args, qslab, soe, dev, ws):

@@ -173,6 +173,41 @@ int qslab_compute_batched(qslab_ctx* ctx, int R, const int64_t* offsets,
                           double* energies, void* phi, void* force,
                           void* stream);
 
+/* Virial tensor of the long-range energy, for pressures in the NPT ensemble
+ * (Section 4.3: the random-batch dynamics extends to NPT through the virial;
+ * Section 2.4: the L_z-dependent constant of the particle-slab potential of
+ * Thm 2.4 is what the walls' part needs). The same call as qslab_compute()
+ * (energy, phi, force as there) that also returns
+ *   W_ab = -dE_long/d eps_ab,   virial = (W_xx, W_yy, W_zz, W_xy, W_xz, W_yz),
+ * for the strain r -> (I + eps) r applied to the particles, to the lateral
+ * lattice vectors and to the charged walls (which keep their charge per cell,
+ * so sigma scales as 1/A; the top wall at z = L_z moves with the box).
+ * eps_zx = eps_zy = 0 keeps the lattice in the plane z = 0, and W_yx = W_xy
+ * (rotation invariance in the plane). In detail:
+ *   lateral: W_ab = delta_ab (E + U_self) + sum_k (k_a k_b/|k|) dU^k/d|k|,
+ *            U^k of the SOE kernel (Eq. 3.21) over the k-set of the call
+ *            (random batch: each sample weighted as in Eq. 4.7, an unbiased
+ *            estimate of the full sum), plus the walls' modes;
+ *   zz, xz, yz: sum_i F_i,a z_i plus the top wall's explicit terms.
+ * The pressure tensor is P_ab = (sum_i m v_a v_b + W_ab)/(Lx Ly Lz) once
+ * the real-space virial (qslab_compute_realspace_virial) is added.
+ *   energy, force  required (device; the z-components are formed from force)
+ *   phi            device or NULL
+ *   virial         device, 6 doubles (FP64)
+ * Needs more workspace than qslab_compute() (about 40 bytes per chunk and
+ * mode); errors as for qslab_compute(). */
+int qslab_compute_virial(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
+                         double* energy, void* phi, void* force, double* virial,
+                         void* stream);
+
+/* qslab_compute_batched() with the virial of every replica:
+ *   energies, force  required (device)
+ *   virial           device, R x 6 doubles, the order of qslab_compute_virial() */
+int qslab_compute_batched_virial(qslab_ctx* ctx, int R, const int64_t* offsets,
+                                 const double* boxes, const void* pos, const void* q,
+                                 double* energies, void* phi, void* force,
+                                 double* virial, void* stream);
+
 /* The same computation from host buffers: copies pos and q (host, layout as
  * above; pinned memory makes the copies asynchronous) to the device, runs,
  * copies energy/phi/force back to host buffers (any may be NULL) and waits
@@ -277,6 +312,19 @@ int qslab_set_rcut(qslab_ctx* ctx, double rc);
  * 1 and 2's long-range path. */
 int qslab_compute_realspace(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
                             double* energy, void* phi, void* force, void* stream);
+
+/* qslab_compute_realspace() that also returns the pair virial of the
+ * real-space sum (Eq. 2.10 within rc), for pressures (Section 4.3):
+ *   W_ab = 1/2 sum_{i, j, M} (F_ij)_a (r_ij + M)_b,
+ * F_ij the force on i from the pair term of j, as
+ * virial = (W_xx, W_yy, W_zz, W_xy, W_xz, W_yz) (device, 6 doubles, FP64
+ * sums). With qslab_compute_virial() it gives the virial of the whole
+ * Ewald2D energy, whose trace equals that energy (the Coulomb energy is
+ * homogeneous of degree -1 in all lengths). Other arguments and errors as for
+ * qslab_compute_realspace(); virial must not be NULL. */
+int qslab_compute_realspace_virial(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
+                                   double* energy, void* phi, void* force, double* virial,
+                                   void* stream);
 
 /* Langevin dynamics of one slab (Section 4.3) with the forces of this
  * library: the long-range part as configured (full k-sum or random batch,

@@ -82,6 +82,9 @@ def load(build_if_missing: bool = True):
         "qslab_compute_host": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_compute_static": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_compute_batched": ([P, I, P, P, P, P, P, P, P, P], I),
+        "qslab_compute_virial": ([P, ctypes.c_int64, P, P, P, P, P, P, P], I),
+        "qslab_compute_batched_virial": ([P, I, P, P, P, P, P, P, P, P, P], I),
+        "qslab_compute_realspace_virial": ([P, ctypes.c_int64, P, P, P, P, P, P, P], I),
         "qslab_autotune": ([P, I, P, P, P, P, P, I, P, P], I),
         "qslab_set_rcut": ([P, D], I),
         "qslab_set_walls": ([P, D, D, I, P, P, P], I),
@@ -191,6 +194,32 @@ def qslab_compute_batched(h, offsets, boxes, pos_ptr, q_ptr, energies_ptr, phi_p
     _check(load().qslab_compute_batched(h, R, off.ctypes.data, box.ctypes.data, pos_ptr, q_ptr,
                                         energies_ptr, phi_ptr, force_ptr, stream_ptr),
            "qslab_compute_batched")
+
+
+def qslab_compute_virial(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr, virial_ptr,
+                         stream_ptr):
+    _check(load().qslab_compute_virial(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr,
+                                       virial_ptr, stream_ptr), "qslab_compute_virial")
+
+
+def qslab_compute_batched_virial(h, offsets, boxes, pos_ptr, q_ptr, energies_ptr, phi_ptr,
+                                 force_ptr, virial_ptr, stream_ptr):
+    off = np.ascontiguousarray(offsets, np.int64)
+    box = np.ascontiguousarray(boxes, np.float64).reshape(-1, 3)
+    R = off.shape[0] - 1
+    if box.shape[0] != R:
+        raise ValueError("boxes must have one row per replica")
+    _check(load().qslab_compute_batched_virial(h, R, off.ctypes.data, box.ctypes.data, pos_ptr,
+                                               q_ptr, energies_ptr, phi_ptr, force_ptr,
+                                               virial_ptr, stream_ptr),
+           "qslab_compute_batched_virial")
+
+
+def qslab_compute_realspace_virial(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr,
+                                   virial_ptr, stream_ptr):
+    _check(load().qslab_compute_realspace_virial(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr,
+                                                 force_ptr, virial_ptr, stream_ptr),
+           "qslab_compute_realspace_virial")
 
 
 def qslab_autotune(h, offsets, boxes, pos_ptr, q_ptr, stream_ptr, reps=3):
@@ -455,6 +484,71 @@ class QSlab:
                               force.data_ptr() if force is not None else None, st)
         self.last_R = R
         return energies, phi, force
+
+    def compute_virial(self, pos, q, want_phi=True):
+        """Long-range energy, potentials, forces and the virial tensor
+        W = (xx, yy, zz, xy, xz, yz) of the long-range energy (float64[6]), as
+        CUDA tensors: (energy[1], phi[N] or None, force[N,3], virial[6])."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        if pos.device != dev or q.device != dev:
+            raise ValueError("pos and q must be CUDA tensors on the context's device")
+        pos = pos.to(self.dtype).contiguous()
+        q = q.to(self.dtype).contiguous()
+        N = q.shape[0]
+        energy = torch.empty(1, dtype=torch.float64, device=dev)
+        phi = torch.empty(N, dtype=self.dtype, device=dev) if want_phi else None
+        force = torch.empty((N, 3), dtype=self.dtype, device=dev)
+        virial = torch.empty(6, dtype=torch.float64, device=dev)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        qslab_compute_virial(self.h, N, pos.data_ptr(), q.data_ptr(), energy.data_ptr(),
+                             phi.data_ptr() if phi is not None else None, force.data_ptr(),
+                             virial.data_ptr(), st)
+        self.last_R = 1
+        return energy, phi, force, virial
+
+    def compute_batched_virial(self, pos, q, offsets, boxes):
+        """compute_batched() plus each replica's virial: returns (energies[R],
+        phi[N], force[N,3], virial[R,6]) as CUDA tensors."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        if pos.dtype != self.dtype or q.dtype != self.dtype or not pos.is_contiguous() \
+                or not q.is_contiguous() or pos.device != dev or q.device != dev:
+            raise ValueError("pos and q must be contiguous CUDA tensors of the context's precision")
+        off = np.ascontiguousarray(offsets, np.int64)
+        R = off.shape[0] - 1
+        N = q.shape[0]
+        if int(off[-1]) != N:
+            raise ValueError("offsets[-1] must equal the number of particles")
+        energies = torch.empty(R, dtype=torch.float64, device=dev)
+        phi = torch.empty(N, dtype=self.dtype, device=dev)
+        force = torch.empty((N, 3), dtype=self.dtype, device=dev)
+        virial = torch.empty((R, 6), dtype=torch.float64, device=dev)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        qslab_compute_batched_virial(self.h, off, boxes, pos.data_ptr(), q.data_ptr(),
+                                     energies.data_ptr(), phi.data_ptr(), force.data_ptr(),
+                                     virial.data_ptr(), st)
+        self.last_R = R
+        return energies, phi, force, virial
+
+    def compute_realspace_virial(self, pos, q):
+        """Real-space part and its pair virial: (energy[1], phi[N], force[N,3],
+        virial[6]) as CUDA tensors."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        if pos.device != dev or q.device != dev:
+            raise ValueError("pos and q must be CUDA tensors on the context's device")
+        pos = pos.to(self.dtype).contiguous()
+        q = q.to(self.dtype).contiguous()
+        N = q.shape[0]
+        energy = torch.empty(1, dtype=torch.float64, device=dev)
+        phi = torch.empty(N, dtype=self.dtype, device=dev)
+        force = torch.empty((N, 3), dtype=self.dtype, device=dev)
+        virial = torch.empty(6, dtype=torch.float64, device=dev)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        qslab_compute_realspace_virial(self.h, N, pos.data_ptr(), q.data_ptr(), energy.data_ptr(),
+                                       phi.data_ptr(), force.data_ptr(), virial.data_ptr(), st)
+        return energy, phi, force, virial
 
     def compute_realspace(self, pos, q, energy=None, phi=None, force=None, want_phi=True,
                           want_force=True):

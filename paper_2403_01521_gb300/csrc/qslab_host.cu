@@ -17,6 +17,7 @@
 #include "qslab.h"
 #include "qslab_internal.h"
 #include "qslab_real.h"
+#include "qslab_virial.h"
 #include "qslab_md.h"
 
 using namespace qslab;
@@ -45,12 +46,13 @@ struct Tables {
   std::vector<RepInfo> info;
   std::vector<int32_t> chunk_rep, zchunk_rep, gstart, group_rep, zgstart, zgroup_rep, list;
   std::vector<double> cdf;
+  std::vector<double> vdiag;    // 3 R: j = i lateral virial per unit sum q^2 (xx, yy, xy)
   int Kpad = 32, KR = 32, nkr = 1, L = 32, L0 = 128;
   int nchunks = 0, nz = 0, ngroups = 0, nzgroups = 0;
   int64_t N = 0;
   // device layout of the table buffer
   size_t o_info = 0, o_crep = 0, o_zrep = 0, o_gstart = 0, o_grep = 0, o_zgstart = 0, o_zgrep = 0,
-         o_list = 0, o_cdf = 0, o_trig = 0,
+         o_list = 0, o_cdf = 0, o_trig = 0, o_vdiag = 0,
          o_sampled = 0, o_modes = 0, bytes = 0;
 };
 
@@ -189,8 +191,23 @@ int ensure_config(qslab_ctx* c) {
   return QSLAB_OK;
 }
 
+// The k-derivative of the j = i term of a mode, (pi/(2A)) d/dk [2 erfc(k/(2 alpha))/k],
+// weighted by k_a k_b/k, added to vd[3] (xx, yy, xy) with multiplicity w: the
+// j = i part of the lateral virial per unit sum q^2.
+void add_vdiag(double alpha, double A, double kx, double ky, double w, double* vd) {
+  const double k = std::sqrt(kx * kx + ky * ky);
+  const double dG = -2.0 * std::erfc(k / (2 * alpha)) / (k * k) -
+                    2.0 * std::exp(-k * k / (4 * alpha * alpha)) / (alpha * kSqrtPi * k);
+  const double t = w * kPi / (2 * A) * dG / k;
+  vd[0] += t * kx * kx;
+  vd[1] += t * ky * ky;
+  vd[2] += t * kx * ky;
+}
+
 // (pi/A) erfc(k/(2 alpha))/k summed over the listed (half-plane) modes, times 2
-double diag_half(double alpha, double Lx, double Ly, const int32_t* list, size_t K) {
+// (k and -k); vd (may be NULL) receives the lateral virial constants
+double diag_half(double alpha, double Lx, double Ly, const int32_t* list, size_t K,
+                 double* vd = nullptr) {
   double s = 0.0;
   const double A = Lx * Ly;
   for (size_t m = 0; m < K; ++m) {
@@ -198,6 +215,7 @@ double diag_half(double alpha, double Lx, double Ly, const int32_t* list, size_t
     const double ky = 2 * kPi * list[2 * m + 1] / Ly;
     const double k = std::sqrt(kx * kx + ky * ky);
     s += kPi / A * std::erfc(k / (2 * alpha)) / k;
+    if (vd) add_vdiag(alpha, A, kx, ky, 2.0, vd);
   }
   return 2.0 * s;
 }
@@ -205,7 +223,7 @@ double diag_half(double alpha, double Lx, double Ly, const int32_t* list, size_t
 // The same over every k != 0 (the random batch samples the whole lattice);
 // erfc(k/(2 alpha)) < 1e-21 beyond |k| = 14 alpha. The terms of (mx, my) and
 // (mx, -my) are equal and are summed once.
-double diag_all(double alpha, double Lx, double Ly) {
+double diag_all(double alpha, double Lx, double Ly, double* vd = nullptr) {
   const double kc = 14.0 * alpha;
   const int mxm = (int)std::floor(kc * Lx / (2 * kPi)) + 1;
   const int mym = (int)std::floor(kc * Ly / (2 * kPi)) + 1;
@@ -219,9 +237,13 @@ double diag_all(double alpha, double Lx, double Ly) {
       if (k2 > kc * kc) break;
       const double k = std::sqrt(k2);
       const double t = kPi / A * std::erfc(k / (2 * alpha)) / k;
-      s += (mx > 0 && my > 0) ? 2.0 * t : t;
+      const double mult = (mx > 0 && my > 0) ? 2.0 : 1.0;
+      s += mult * t;
+      // xx, yy are even in mx and in my; xy cancels over the lattice
+      if (vd) add_vdiag(alpha, A, kx, ky, 2.0 * mult, vd);
     }
   }
+  if (vd) vd[2] = 0.0;
   return 2.0 * s;
 }
 
@@ -340,6 +362,7 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
   t.tune_KR = c->tune_KR;
   t.N = N;
   t.info.assign(R, RepInfo{});
+  t.vdiag.assign(3 * (size_t)R, 0.0);
   const double alpha = c->alpha;
   // the per-box data of the previous tables still hold when only the
   // offsets or the launch shape changed
@@ -365,11 +388,14 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
       ri.K = o.K; ri.list0 = o.list0; ri.cdfx0 = o.cdfx0; ri.nx = o.nx;
       ri.cdfy0 = o.cdfy0; ri.ny = o.ny; ri.mxmax = o.mxmax; ri.mymax = o.mymax;
       ri.H = o.H; ri.diagq = o.diagq;
+      std::copy(prev->vdiag.begin() + 3 * r, prev->vdiag.begin() + 3 * r + 3, t.vdiag.begin() + 3 * r);
     } else if (it != seen.end()) {
       const RepInfo& o = t.info[it->second];
       ri.K = o.K; ri.list0 = o.list0; ri.cdfx0 = o.cdfx0; ri.nx = o.nx;
       ri.cdfy0 = o.cdfy0; ri.ny = o.ny; ri.mxmax = o.mxmax; ri.mymax = o.mymax;
       ri.H = o.H; ri.diagq = o.diagq;
+      std::copy(t.vdiag.begin() + 3 * it->second, t.vdiag.begin() + 3 * it->second + 3,
+                t.vdiag.begin() + 3 * r);
     } else {
       seen[{ri.Lx, ri.Ly}] = r;
       double dk = 0.0;
@@ -377,13 +403,13 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
         const std::vector<int32_t> l = half_plane(ri.Lx, ri.Ly, c->kc);
         ri.K = (int32_t)(l.size() / 2);
         ri.list0 = (int32_t)(t.list.size() / 2);
-        dk = diag_half(alpha, ri.Lx, ri.Ly, l.data(), l.size() / 2);
+        dk = diag_half(alpha, ri.Lx, ri.Ly, l.data(), l.size() / 2, &t.vdiag[3 * (size_t)r]);
         t.list.insert(t.list.end(), l.begin(), l.end());
         if (t.list.size() > (size_t)1 << 30) return QSLAB_ERR_INVALID_ARG;
       } else {
         ri.K = c->P;
         ri.H = H_direct(alpha, ri.Lx, ri.Ly);
-        dk = diag_all(alpha, ri.Lx, ri.Ly);
+        dk = diag_all(alpha, ri.Lx, ri.Ly, &t.vdiag[3 * (size_t)r]);
         int mx = 0, my = 0;
         const std::vector<double> cx = axis_cdf(alpha, ri.Lx, &mx);
         const std::vector<double> cy = axis_cdf(alpha, ri.Ly, &my);
@@ -482,6 +508,7 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
   t.o_list = take(sizeof(int32_t) * std::max<size_t>(t.list.size(), 2));
   t.o_cdf = take(sizeof(double) * std::max<size_t>(t.cdf.size(), 1));
   t.o_trig = take(sizeof(float) * 2 * 256);
+  t.o_vdiag = take(sizeof(double) * 3 * (size_t)R);
   t.o_sampled = take(sizeof(int32_t) * 2 * (size_t)R * t.Kpad);
   t.o_modes = take(mode_bytes((size_t)R * t.Kpad, c->npc, tsz));
   t.bytes = o;
@@ -511,6 +538,7 @@ int upload_tables(const Tables& t, void* dst) {
     trig[2 * j + 1] = (float)std::sin(2.0 * kPi * j / 256.0);
   }
   put(t.o_trig, trig, sizeof(trig));
+  put(t.o_vdiag, t.vdiag.data(), sizeof(double) * t.vdiag.size());
   QS_CUDA(cudaMemcpy(dst, stage.data(), stage.size(), cudaMemcpyHostToDevice));
   return QSLAB_OK;
 }
@@ -569,10 +597,10 @@ struct Plan {
   ScanPlan sp;
   size_t off_sort, off_rid, off_sums, off_zs, off_dz, off_qs, off_xh, off_yh, off_perm,
       off_agg, off_carry, off_dec, off_part, off_k0, off_phi0, off_fz0, off_echunk, off_in_pos,
-      off_in_q, off_out_phi, off_out_f, total;
+      off_in_q, off_out_phi, off_out_f, off_vir, total;
 };
 
-Plan make_plan(const qslab_ctx* c, bool host_io) {
+Plan make_plan(const qslab_ctx* c, bool host_io, bool virial = false) {
   Plan P{};
   const Tables& t = c->tab;
   const bool dp = c->prec == QSLAB_FP64;
@@ -610,6 +638,7 @@ Plan make_plan(const qslab_ctx* c, bool host_io) {
     P.off_out_phi = take(tsz * N);
     P.off_out_f = take(3 * tsz * N);
   }
+  if (virial) P.off_vir = take(virial_workspace_bytes(s, rp));
   P.total = o;
   return P;
 }
@@ -629,7 +658,7 @@ int ensure_ws(qslab_ctx* c, size_t bytes) {
 
 template <typename T>
 int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies, T* phi,
-        T* force, cudaStream_t st) {
+        T* force, cudaStream_t st, double* virial = nullptr) {
   using PH = typename PhaseT<T>::type;
   const Tables& tb = c->tab;
   const int64_t N = tb.N;
@@ -713,6 +742,15 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   launch_combine<T>(rp, P.sp.nkr, part, phi0, fz0, qs, zs, xh, yh, c->walls, perm, echunk, phi,
                     force, energies, st);
   nl += energies ? 2 : 1;
+  if (virial) {
+    // the virial of the same energy, from this call's sorted data, mode
+    // tables, forward carries, forces and energies
+    VirArgs<T> va{P.sp, rp, modes, c->pairs, c->alpha, rbe ? 1 : 0, zs, dz, qs, xh, yh,
+                  sizeof(T) == 4 ? reinterpret_cast<const float2*>(tab + tb.o_trig) : nullptr,
+                  carry, pos, q, force, energies,
+                  reinterpret_cast<const double*>(tab + tb.o_vdiag), c->walls, virial};
+    nl += launch_virial<T>(va, ws + P.off_vir, st);
+  }
   if (ev) cudaEventRecord(ev[7], st);
   c->launches = nl;
   c->last_R = R;
@@ -731,21 +769,22 @@ int status_code(unsigned f) {
 
 // Tables and workspace for one call; on success P describes the workspace.
 int setup_call(qslab_ctx* c, int R, const int64_t* off, const double* box, bool host_io,
-               Plan& P) {
+               Plan& P, bool virial = false) {
   QS_CUDA(cudaSetDevice(c->device));
   int rc = select_tables(c, R, off, box);
   if (rc) return rc;
-  P = make_plan(c, host_io);
+  P = make_plan(c, host_io, virial);
   return ensure_ws(c, P.total);
 }
 
 int dispatch(qslab_ctx* c, const Plan& P, const void* pos, const void* q, double* energies,
-             void* phi, void* force, cudaStream_t st) {
+             void* phi, void* force, cudaStream_t st, double* virial = nullptr) {
   if (c->prec == QSLAB_FP64)
     return run<double>(c, P, static_cast<const double*>(pos), static_cast<const double*>(q),
-                       energies, static_cast<double*>(phi), static_cast<double*>(force), st);
+                       energies, static_cast<double*>(phi), static_cast<double*>(force), st,
+                       virial);
   return run<float>(c, P, static_cast<const float*>(pos), static_cast<const float*>(q), energies,
-                    static_cast<float*>(phi), static_cast<float*>(force), st);
+                    static_cast<float*>(phi), static_cast<float*>(force), st, virial);
 }
 
 }  // namespace
@@ -904,6 +943,32 @@ int qslab_compute_batched(qslab_ctx* c, int R, const int64_t* offsets, const dou
   return dispatch(c, P, pos, q, energies, phi, force, static_cast<cudaStream_t>(stream));
 }
 
+int qslab_compute_virial(qslab_ctx* c, int64_t N, const void* pos, const void* q,
+                         double* energy, void* phi, void* force, double* virial, void* stream) {
+  if (!c || !pos || !q || !energy || !force || !virial || N < 1 || N > 2147483647LL)
+    return QSLAB_ERR_INVALID_ARG;
+  if (!c->has_box) return QSLAB_ERR_NOT_CONFIGURED;
+  const int64_t off[2] = {0, N};
+  const double box[3] = {c->Lx, c->Ly, c->Lz};
+  Plan P;
+  const int rc = setup_call(c, 1, off, box, false, P, true);
+  if (rc) return rc;
+  return dispatch(c, P, pos, q, energy, phi, force, static_cast<cudaStream_t>(stream), virial);
+}
+
+int qslab_compute_batched_virial(qslab_ctx* c, int R, const int64_t* offsets,
+                                 const double* boxes, const void* pos, const void* q,
+                                 double* energies, void* phi, void* force, double* virial,
+                                 void* stream) {
+  if (!c || !pos || !q || !offsets || !boxes || !energies || !force || !virial || R < 1 ||
+      R > kMaxReplicas)
+    return QSLAB_ERR_INVALID_ARG;
+  Plan P;
+  const int rc = setup_call(c, R, offsets, boxes, false, P, true);
+  if (rc) return rc;
+  return dispatch(c, P, pos, q, energies, phi, force, static_cast<cudaStream_t>(stream), virial);
+}
+
 int qslab_compute_host(qslab_ctx* c, int64_t N, const void* pos_host, const void* q_host,
                        double* energy_host, void* phi_host, void* force_host, void* stream) {
   if (!c || !pos_host || !q_host || N < 1 || N > 2147483647LL) return QSLAB_ERR_INVALID_ARG;
@@ -992,7 +1057,8 @@ namespace {
 
 // The real-space sum (with the LJ pairs when lj_eps > 0) on stream st.
 int realspace_call(qslab_ctx* c, int64_t N, const void* pos, const void* q, double* energy,
-                   void* phi, void* force, cudaStream_t st, double lj_eps, double lj_sigma) {
+                   void* phi, void* force, cudaStream_t st, double lj_eps, double lj_sigma,
+                   double* virial = nullptr) {
   if (!c || !pos || !q || N < 1 || N > 2147483647LL) return QSLAB_ERR_INVALID_ARG;
   if (!c->has_box || !c->has_alpha || c->rc <= 0) return QSLAB_ERR_NOT_CONFIGURED;
   RsGrid g;
@@ -1028,11 +1094,11 @@ int realspace_call(qslab_ctx* c, int64_t N, const void* pos, const void* q, doub
   if (c->prec == QSLAB_FP64)
     launch_realspace<double>(g, static_cast<const double*>(pos), static_cast<const double*>(q),
                              c->d_rs_ws, c->d_status, energy, static_cast<double*>(phi),
-                             static_cast<double*>(force), st);
+                             static_cast<double*>(force), st, virial);
   else
     launch_realspace<float>(g, static_cast<const float*>(pos), static_cast<const float*>(q),
                             c->d_rs_ws, c->d_status, energy, static_cast<float*>(phi),
-                            static_cast<float*>(force), st);
+                            static_cast<float*>(force), st, virial);
   QS_CUDA(cudaGetLastError());
   c->last_stream = st;
   return QSLAB_OK;
@@ -1046,6 +1112,14 @@ int qslab_compute_realspace(qslab_ctx* c, int64_t N, const void* pos, const void
                             double* energy, void* phi, void* force, void* stream) {
   return realspace_call(c, N, pos, q, energy, phi, force, static_cast<cudaStream_t>(stream), 0.0,
                         0.0);
+}
+
+int qslab_compute_realspace_virial(qslab_ctx* c, int64_t N, const void* pos, const void* q,
+                                   double* energy, void* phi, void* force, double* virial,
+                                   void* stream) {
+  if (!virial) return QSLAB_ERR_INVALID_ARG;
+  return realspace_call(c, N, pos, q, energy, phi, force, static_cast<cudaStream_t>(stream), 0.0,
+                        0.0, virial);
 }
 
 int qslab_md_configure(qslab_ctx* c, double dt, double mass, double gamma, double kT,

@@ -135,14 +135,19 @@ constexpr int kRsRow = 512;      // neighbour records staged in shared memory at
 // erfc and exp for the marked pairs only, so that the warp does not run the
 // pair arithmetic for the candidates outside rc. A warp without a home
 // particle only helps to stage the rows.
-template <typename T, bool LJ>
+// VIR: also the pair virial (1/2) sum_{i,j} (F_ij)_a (r_ij)_b of the CTA's
+// particles (Coulomb and LJ pairs) into vcell[cta][6] (xx, yy, zz, xy, xz, yz).
+template <typename T, bool LJ, bool VIR>
 __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
                                                            const int32_t* __restrict__ cstart,
                                                            const RsRec<T>* __restrict__ rec,
                                                            const uint32_t* __restrict__ perm,
-                                                           T* phi_out, T* force_out, double* ecell) {
+                                                           T* phi_out, T* force_out, double* ecell,
+                                                           double* vcell) {
   __shared__ RsRec<T> buf[kRsRow];
   __shared__ double red[kRsThreads / 32];
+  __shared__ double vred[VIR ? 6 : 1][kRsThreads / 32];
+  double v_acc[6] = {0, 0, 0, 0, 0, 0};
   const int c = blockIdx.x;
   const int S = g.s;
   const int cx = c % g.ncx, cy = (c / g.ncx) % g.ncy, cz = c / (g.ncx * g.ncy);
@@ -164,6 +169,8 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
     if (live) ri = rec[i];
     T ph = 0, fx = 0, fy = 0, fz = 0;
     T lx = 0, ly = 0, lz = 0, le = 0;       // LJ force and twice its energy share
+    T vc[6] = {0, 0, 0, 0, 0, 0};           // sum_j q_j fr d_a d_b (VIR)
+    T vl[6] = {0, 0, 0, 0, 0, 0};           // the same for the LJ pairs (VIR && LJ)
     for (int dz = -S; dz <= S; ++dz) {
       const int nz = cz + dz;
       if (nz < 0 || nz >= g.ncz) continue;
@@ -246,18 +253,38 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
               fx = fma(w2, dx2, fma(w1, dx1, fx));
               fy = fma(w2, dy2, fma(w1, dy1, fy));
               fz = fma(w2, dz2, fma(w1, dz1, fz));
+              if (VIR) {
+                const T tx1 = w1 * dx1, ty1 = w1 * dy1, tz1 = w1 * dz1;
+                const T tx2 = w2 * dx2, ty2 = w2 * dy2, tz2 = w2 * dz2;
+                vc[0] = fma(tx2, dx2, fma(tx1, dx1, vc[0]));
+                vc[1] = fma(ty2, dy2, fma(ty1, dy1, vc[1]));
+                vc[2] = fma(tz2, dz2, fma(tz1, dz1, vc[2]));
+                vc[3] = fma(tx2, dy2, fma(tx1, dy1, vc[3]));
+                vc[4] = fma(tx2, dz2, fma(tx1, dz1, vc[4]));
+                vc[5] = fma(ty2, dz2, fma(ty1, dz1, vc[5]));
+              }
               if (LJ) {
                 if (r21 < lj_rc2) {
                   const T s2 = lj_s2 / r21, s6 = s2 * s2 * s2;
                   const T f = lj_24e * (2 * s6 * s6 - s6) / r21;   // -(dU/dr)/r
                   lx = fma(f, dx1, lx); ly = fma(f, dy1, ly); lz = fma(f, dz1, lz);
                   le += lj_4e * (s6 * s6 - s6 + (T)0.25);
+                  if (VIR) {
+                    vl[0] = fma(f * dx1, dx1, vl[0]); vl[1] = fma(f * dy1, dy1, vl[1]);
+                    vl[2] = fma(f * dz1, dz1, vl[2]); vl[3] = fma(f * dx1, dy1, vl[3]);
+                    vl[4] = fma(f * dx1, dz1, vl[4]); vl[5] = fma(f * dy1, dz1, vl[5]);
+                  }
                 }
                 if (qmul != (T)0 && r22 < lj_rc2) {
                   const T s2 = lj_s2 / r22, s6 = s2 * s2 * s2;
                   const T f = lj_24e * (2 * s6 * s6 - s6) / r22;
                   lx = fma(f, dx2, lx); ly = fma(f, dy2, ly); lz = fma(f, dz2, lz);
                   le += lj_4e * (s6 * s6 - s6 + (T)0.25);
+                  if (VIR) {
+                    vl[0] = fma(f * dx2, dx2, vl[0]); vl[1] = fma(f * dy2, dy2, vl[1]);
+                    vl[2] = fma(f * dz2, dz2, vl[2]); vl[3] = fma(f * dx2, dy2, vl[3]);
+                    vl[4] = fma(f * dx2, dz2, vl[4]); vl[5] = fma(f * dy2, dz2, vl[5]);
+                  }
                 }
               }
             }
@@ -274,6 +301,15 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
         force_out[3 * (int64_t)o + 2] = fma(ri.q, fz, lz);
       }
       e_acc += 0.5 * (double)ri.q * (double)ph + 0.5 * (double)le;
+      if (VIR)
+        for (int k = 0; k < 6; ++k) v_acc[k] += 0.5 * ((double)ri.q * (double)vc[k] + (double)vl[k]);
+    }
+  }
+  if (VIR) {
+    for (int k = 0; k < 6; ++k) {
+      double v = v_acc[k];
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) vred[k][threadIdx.x >> 5] = v;
     }
   }
   for (int o = 16; o; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
@@ -283,6 +319,33 @@ __global__ void __launch_bounds__(kRsThreads) rs_pair_kernel(RsGrid g,
     double s = 0.0;
     for (int w = 0; w < kRsThreads / 32; ++w) s += red[w];
     ecell[(size_t)c * gridDim.y + blockIdx.y] = s;
+    if (VIR) {
+      // stored as xx, yy, zz, xy, xz, yz
+      for (int k = 0; k < 6; ++k) {
+        double t = 0.0;
+        for (int w = 0; w < kRsThreads / 32; ++w) t += vred[k][w];
+        vcell[((size_t)c * gridDim.y + blockIdx.y) * 6 + k] = t;
+      }
+    }
+  }
+}
+
+// sum of the CTAs' virials in a fixed order (one CTA)
+__global__ void rs_virial_kernel(int ncta, const double* vcell, double* virial) {
+  __shared__ double red[6][32];
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int j = threadIdx.x; j < ncta; j += blockDim.x)
+    for (int k = 0; k < 6; ++k) s[k] += vcell[(size_t)j * 6 + k];
+  for (int k = 0; k < 6; ++k) {
+    double v = s[k];
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+    virial[threadIdx.x] = t;
   }
 }
 
@@ -312,12 +375,13 @@ size_t rs_workspace_bytes(const RsGrid& g) {
   const int64_t ncell = (int64_t)g.ncx * g.ncy * g.ncz;
   auto a = [](size_t b) { return (b + 255) & ~size_t(255); };
   return a(sort_workspace_bytes(g.N, 4)) + a(4 * (size_t)(ncell + 1)) +
-         a(8 * (size_t)ncell * rs_parts(g)) + a(sizeof(RsRec<double>) * (size_t)g.N);
+         a(8 * (size_t)ncell * rs_parts(g)) + a(sizeof(RsRec<double>) * (size_t)g.N) +
+         a(6 * 8 * (size_t)ncell * rs_parts(g));
 }
 
 template <typename T>
 int launch_realspace(const RsGrid& g, const T* pos, const T* q, void* ws, unsigned* status,
-                     double* energy, T* phi, T* force, cudaStream_t st) {
+                     double* energy, T* phi, T* force, cudaStream_t st, double* virial) {
   const int64_t ncell = (int64_t)g.ncx * g.ncy * g.ncz;
   auto a = [](size_t b) { return (b + 255) & ~size_t(255); };
   char* p = static_cast<char*>(ws);
@@ -328,6 +392,8 @@ int launch_realspace(const RsGrid& g, const T* pos, const T* q, void* ws, unsign
   const int parts = rs_parts(g);
   double* ecell = reinterpret_cast<double*>(p); p += a(8 * (size_t)ncell * parts);
   RsRec<T>* rec = reinterpret_cast<RsRec<T>*>(p);
+  p += a(sizeof(RsRec<double>) * (size_t)g.N);
+  double* vcell = reinterpret_cast<double*>(p);
   int blocks = (int)((g.N + 255) / 256);
   if (blocks > 152 * 16) blocks = 152 * 16;
   rs_keys_kernel<T><<<blocks, 256, 0, st>>>(g, pos, q, static_cast<uint32_t*>(sw.keys[0]),
@@ -340,19 +406,29 @@ int launch_realspace(const RsGrid& g, const T* pos, const T* q, void* ws, unsign
   rs_cells_kernel<<<cblocks, 256, 0, st>>>(g.N, ncell, static_cast<const uint32_t*>(sw.keys[r]),
                                            cstart);
   rs_gather_kernel<T><<<blocks, 256, 0, st>>>(g, pos, q, sw.vals[r], rec);
-  if (g.lj_eps > 0.0)
-    rs_pair_kernel<T, true><<<dim3((unsigned)ncell, parts), kRsThreads, 0, st>>>(
-        g, cstart, rec, sw.vals[r], phi, force, ecell);
-  else
-    rs_pair_kernel<T, false><<<dim3((unsigned)ncell, parts), kRsThreads, 0, st>>>(
-        g, cstart, rec, sw.vals[r], phi, force, ecell);
+  const dim3 grid((unsigned)ncell, parts);
+  if (virial) {
+    if (g.lj_eps > 0.0)
+      rs_pair_kernel<T, true, true><<<grid, kRsThreads, 0, st>>>(g, cstart, rec, sw.vals[r], phi,
+                                                                 force, ecell, vcell);
+    else
+      rs_pair_kernel<T, false, true><<<grid, kRsThreads, 0, st>>>(g, cstart, rec, sw.vals[r], phi,
+                                                                  force, ecell, vcell);
+    rs_virial_kernel<<<1, 256, 0, st>>>((int)(ncell * parts), vcell, virial);
+  } else if (g.lj_eps > 0.0) {
+    rs_pair_kernel<T, true, false><<<grid, kRsThreads, 0, st>>>(g, cstart, rec, sw.vals[r], phi,
+                                                                force, ecell, nullptr);
+  } else {
+    rs_pair_kernel<T, false, false><<<grid, kRsThreads, 0, st>>>(g, cstart, rec, sw.vals[r], phi,
+                                                                 force, ecell, nullptr);
+  }
   if (energy) rs_energy_kernel<<<1, 256, 0, st>>>((int)(ncell * parts), ecell, energy);
-  return 3 + 3 * passes + (energy ? 2 : 1);
+  return 3 + 3 * passes + (energy ? 2 : 1) + (virial ? 1 : 0);
 }
 
 template int launch_realspace<float>(const RsGrid&, const float*, const float*, void*, unsigned*,
-                                     double*, float*, float*, cudaStream_t);
+                                     double*, float*, float*, cudaStream_t, double*);
 template int launch_realspace<double>(const RsGrid&, const double*, const double*, void*,
-                                      unsigned*, double*, double*, double*, cudaStream_t);
+                                      unsigned*, double*, double*, double*, cudaStream_t, double*);
 
 }  // namespace qslab
