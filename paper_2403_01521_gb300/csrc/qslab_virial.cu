@@ -175,7 +175,7 @@ __global__ void vir_zagg_kernel(VirArgs<T> a, Cplx<double>* az) {
 // exclusive scan over the threads gives each segment its input, and each
 // thread replays its segment. The maps compose as
 // (e2, B2) o (e1, B1) = (e2 e1, e2 B1 + B2).
-constexpr int kChainT = 64;
+constexpr int kChainT = 128;
 
 template <typename T>
 __device__ __forceinline__ void chain_map(const VirArgs<T>& a, const Cplx<double>* az, int c,
@@ -320,6 +320,89 @@ __global__ void vir_pass_kernel(VirArgs<T> a, const double* vc, const Cplx<T>* g
   dpart[(size_t)c * Kpad + m] = D;
 }
 
+// The same pass on the FP32 path with two SOE pairs per 64-bit register
+// (packed FP32 FMAs, __ffma2_rn / __fmul2_rn): the decay table is stored
+// re/im-split per particle so that two pairs' decays load as one float2.
+template <int NP>
+__global__ void vir_pass_f2_kernel(VirArgs<float> a, const double* vc, const Cplx<float>* gzc,
+                                   double* dpart) {
+  extern __shared__ __align__(32) char smem[];
+  const int c = blockIdx.x;
+  const CRange ch = kchunk(a.rp, c);
+  const int L = a.rp.L, Kpad = a.rp.Kpad;
+  const int cnt = ch.cnt;
+  VRec<float>* rec = reinterpret_cast<VRec<float>*>(smem);
+  float2* trig = reinterpret_cast<float2*>(smem + ((sizeof(VRec<float>) * (size_t)L + 31) & ~size_t(31)));
+  float* tabf = reinterpret_cast<float*>(smem + rec_bytes<float>(L));
+  load_recs<float>(a, rec, trig, ch.start, cnt, true);
+  for (int e = threadIdx.x; e < NP * cnt; e += blockDim.x) {
+    const int t = e / NP, p = e - t * NP;
+    const Cplx<float> d = cexp_neg((float)a.pairs.a_re[p], (float)a.pairs.a_im[p], a.dz[ch.start + t]);
+    tabf[t * 2 * NP + p] = d.re;
+    tabf[t * 2 * NP + NP + p] = d.im;
+  }
+  __syncthreads();
+  const int m = blockIdx.y * a.plan.KR + threadIdx.x;
+  const size_t mg = (size_t)ch.r * Kpad + m;
+  const int32_t mx = a.modes.mx[mg], my = a.modes.my[mg];
+  const float kk = a.modes.kk[mg];
+  const size_t cstride = (size_t)a.plan.nstates * Kpad;
+  const Cplx<float>* cin = a.carry + (size_t)c * cstride + m;
+  Cplx<float> g0 = cin[0];
+  float2 Ra[NP / 2], Ia[NP / 2], Rb[NP / 2], Ib[NP / 2], Sr[NP / 2], Si[NP / 2];
+#pragma unroll
+  for (int q = 0; q < NP / 2; ++q) {
+    const Cplx<float> a0 = cin[(size_t)(1 + 4 * q) * Kpad], b0 = cin[(size_t)(2 + 4 * q) * Kpad];
+    const Cplx<float> a1 = cin[(size_t)(3 + 4 * q) * Kpad], b1 = cin[(size_t)(4 + 4 * q) * Kpad];
+    Ra[q] = make_float2(a0.re, a1.re); Ia[q] = make_float2(a0.im, a1.im);
+    Rb[q] = make_float2(b0.re, b1.re); Ib[q] = make_float2(b0.im, b1.im);
+    Sr[q] = make_float2(0.0f, 0.0f); Si[q] = Sr[q];
+  }
+  Cplx<float> gz = gzc[(size_t)c * Kpad + m];
+  float sk = 0.0f, sz = 0.0f;
+  for (int t = 0; t < cnt; ++t) {
+    const VRec<float> r = rec[t];
+    float cs, sn;
+    phase_cs(phase_turns(mx, my, r.xh, r.yh), trig, cs, sn);
+    const float av = r.q * cs, bv = r.q * sn;
+    const float ek = one_minus_exp_neg(kk * r.zd);
+    const float hr = fmaf(r.zd, g0.re, gz.re), hi = fmaf(r.zd, g0.im, gz.im);
+    gz.re = fmaf(-ek, hr, hr);
+    gz.im = fmaf(-ek, hi, hi);
+    const float xr = fmaf(-ek, g0.re, g0.re), xi = fmaf(-ek, g0.im, g0.im);
+    sk = fmaf(av, xr, fmaf(-bv, xi, sk));
+    sz = fmaf(av, gz.re, fmaf(-bv, gz.im, sz));
+    g0.re = xr + av;
+    g0.im = xi - bv;
+    const float2 Ua = make_float2(av, av), Ub = make_float2(bv, bv);
+    const float2* dre = reinterpret_cast<const float2*>(tabf + t * 2 * NP);
+    const float2* dim = reinterpret_cast<const float2*>(tabf + t * 2 * NP + NP);
+#pragma unroll
+    for (int q = 0; q < NP / 2; ++q) {
+      const float2 Dr = dre[q], Di = dim[q];
+      const float2 nDi = make_float2(-Di.x, -Di.y);
+      // exclusive states D g (before this particle's input)
+      const float2 ar = __ffma2_rn(Dr, Ra[q], __fmul2_rn(nDi, Ia[q]));
+      const float2 ai = __ffma2_rn(Dr, Ia[q], __fmul2_rn(Di, Ra[q]));
+      const float2 br = __ffma2_rn(Dr, Rb[q], __fmul2_rn(nDi, Ib[q]));
+      const float2 bi = __ffma2_rn(Dr, Ib[q], __fmul2_rn(Di, Rb[q]));
+      Sr[q] = __ffma2_rn(Ua, ar, __ffma2_rn(Ub, br, Sr[q]));
+      Si[q] = __ffma2_rn(Ua, ai, __ffma2_rn(Ub, bi, Si[q]));
+      Ra[q] = __fadd2_rn(ar, Ua); Ia[q] = ai;
+      Rb[q] = __fadd2_rn(br, Ub); Ib[q] = bi;
+    }
+  }
+  const size_t ks = (size_t)a.rp.R * Kpad;
+  double D = vc[mg] * (double)sk + vc[ks + mg] * (double)sz;
+#pragma unroll
+  for (int q = 0; q < NP / 2; ++q) {
+    const size_t p0 = 2 * q, p1 = 2 * q + 1;
+    D += vc[(2 + 2 * p0) * ks + mg] * (double)Sr[q].x - vc[(3 + 2 * p0) * ks + mg] * (double)Si[q].x;
+    D += vc[(2 + 2 * p1) * ks + mg] * (double)Sr[q].y - vc[(3 + 2 * p1) * ks + mg] * (double)Si[q].y;
+  }
+  dpart[(size_t)c * Kpad + m] = D;
+}
+
 // ------------------------------------------------------- fixed-order sums
 // Sum of v over the block (blockDim.x a multiple of 32, <= 1024): warp
 // shuffles, then warp 0 over the warps' totals; the result is valid in
@@ -406,24 +489,27 @@ __global__ void vir_walls_kernel(VirArgs<T> a, double* wpart) {
   }
 }
 
-// msum[mg] = sum over the replica's chunks of D(c, m), one thread per
-// (replica, mode), chunks in order (coalesced across modes).
-__global__ void vir_modesum_kernel(Reps rp, const double* dpart, double* msum) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+// msum[mg] = sum over the replica's chunks of D(c, m). One CTA of 32 warps
+// per (replica, 32 modes): lane = mode (coalesced), warp w sums the chunks
+// w, w + 32, ..., then the warps' sums are added in a fixed order.
+constexpr int kSumWarps = 32;
+__global__ void __launch_bounds__(32 * kSumWarps) vir_modesum_kernel(Reps rp, const double* dpart,
+                                                                    double* msum) {
+  __shared__ double part[kSumWarps][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int m = blockIdx.x * 32 + lane;
   const int rep = blockIdx.y;
-  if (m >= rp.Kpad) return;
   const RepInfo& ri = rp.info[rep];
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;    // four interleaved partial sums
-  int j = 0;
-  for (; j + 3 < ri.nch; j += 4) {
-    const size_t c = (size_t)ri.c0 + j;
-    s0 += dpart[c * rp.Kpad + m];
-    s1 += dpart[(c + 1) * rp.Kpad + m];
-    s2 += dpart[(c + 2) * rp.Kpad + m];
-    s3 += dpart[(c + 3) * rp.Kpad + m];
+  double acc = 0.0;
+  if (m < rp.Kpad)
+    for (int j = w; j < ri.nch; j += kSumWarps) acc += dpart[((size_t)ri.c0 + j) * rp.Kpad + m];
+  part[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && m < rp.Kpad) {
+    double t = 0.0;
+    for (int v = 0; v < kSumWarps; ++v) t += part[v][lane];
+    msum[(size_t)rep * rp.Kpad + m] = t;
   }
-  for (; j < ri.nch; ++j) s0 += dpart[((size_t)ri.c0 + j) * rp.Kpad + m];
-  msum[(size_t)rep * rp.Kpad + m] = (s0 + s1) + (s2 + s3);
 }
 
 // One CTA per replica: the lateral sums over modes (weights from the
@@ -475,14 +561,30 @@ __global__ void vir_reduce_kernel(VirArgs<T> a, const double* msum, const double
 }
 
 template <typename T, int NP>
+struct VirPass {
+  static void run(const VirArgs<T>& a, const double* vc, const Cplx<T>* gzc, double* dpart,
+                  size_t sm, dim3 grid, cudaStream_t st) {
+    cudaFuncSetAttribute(vir_pass_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    vir_pass_kernel<T, NP><<<grid, a.plan.KR, sm, st>>>(a, vc, gzc, dpart);
+  }
+};
+template <int NP>
+struct VirPass<float, NP> {
+  static void run(const VirArgs<float>& a, const double* vc, const Cplx<float>* gzc,
+                  double* dpart, size_t sm, dim3 grid, cudaStream_t st) {
+    cudaFuncSetAttribute(vir_pass_f2_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    vir_pass_f2_kernel<NP><<<grid, a.plan.KR, sm, st>>>(a, vc, gzc, dpart);
+  }
+};
+
+template <typename T, int NP>
 int run_pass(const VirArgs<T>& a, const double* vc, const Cplx<T>* gzc, double* dpart,
              cudaStream_t st) {
   const int L = a.rp.L;
   const size_t sm = rec_bytes<T>(L) + sizeof(Cplx<T>) * (size_t)NP * L;
-  cudaFuncSetAttribute(vir_pass_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sm);
-  const dim3 grid(a.rp.nchunks, a.plan.nkr);
-  vir_pass_kernel<T, NP><<<grid, a.plan.KR, sm, st>>>(a, vc, gzc, dpart);
+  VirPass<T, NP>::run(a, vc, gzc, dpart, sm, dim3(a.rp.nchunks, a.plan.nkr), st);
   return 1;
 }
 
@@ -539,7 +641,7 @@ int launch_virial(const VirArgs<T>& a, void* ws, cudaStream_t st) {
       case 12: nl += run_pass<T, 12>(a, vc, gzc, dpart, st); break;
       default: nl += run_pass<T, 16>(a, vc, gzc, dpart, st); break;
     }
-    vir_modesum_kernel<<<dim3((Kpad + 127) / 128, a.rp.R), 128, 0, st>>>(a.rp, dpart, msum);
+    vir_modesum_kernel<<<dim3((Kpad + 31) / 32, a.rp.R), 32 * kSumWarps, 0, st>>>(a.rp, dpart, msum);
     vir_zf_kernel<T><<<a.rp.nchunks, 256, 0, st>>>(a, zpart);
     nl += 2;
     if (a.walls.on && a.walls.nw > 0) {
