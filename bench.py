@@ -617,7 +617,9 @@ def profile_case(kind="single"):
     workload (about 3.3e6 particles) as one batched call, launch shape fixed
     at 512-particle chunks; 'realspace' = the real-space part on the N = 1e5
     FP32 full-k workload (rc = 10); 'single+realspace' = both, one after
-    the other."""
+    the other; 'virial' = two qslab_compute_virial calls on the benchmark
+    workload (N = 1e6); 'virial-small' = the same on N = 2.5e5 at the same
+    density (200 x 200 x 50), small enough for a full ncu capture."""
     import torch
 
     import paper_2403_01521_gb300 as qslab
@@ -636,6 +638,19 @@ def profile_case(kind="single"):
         slab.check()
         torch.cuda.synchronize()
         print("profile case realspace done, E =", float(e.item()))
+        return 0
+    if kind in ("virial", "virial-small"):
+        n = 1_000_000 if kind == "virial" else 250_000
+        L = 400.0 * (n / 1e6) ** 0.5
+        sl = workloads.uniform_slab(n, (L, L, 50.0), 3, alpha=0.1, P=200)
+        slab = qslab.QSlab(0, "fp32c").configure(sl.box, sl.alpha, soe, rbe=(200, 5))
+        pos = torch.tensor(sl.pos, device="cuda", dtype=torch.float32)
+        q = torch.tensor(sl.q, device="cuda", dtype=torch.float32)
+        for _ in range(2):
+            e, _, _, W = slab.compute_virial(pos, q)
+        slab.check()
+        torch.cuda.synchronize()
+        print("profile case", kind, "done, E =", float(e.item()), "W =", W.cpu().numpy().tolist())
         return 0
     if kind == "batched":
         reps = workloads.replicas()[:128]
@@ -671,7 +686,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 512-replica batched measurement")
     ap.add_argument("--profile-case", nargs="?", const="single",
-                    choices=["single", "batched", "realspace", "single+realspace"],
+                    choices=["single", "batched", "realspace", "single+realspace", "virial",
+                             "virial-small"],
                     help="only run two FP32 random-batch calls (for profilers)")
     args = ap.parse_args()
     if args.profile_case:
