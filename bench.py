@@ -358,6 +358,7 @@ def run_ours(args):
         line["batched"] = run_batched(args, qslab, soe, dev, ws, rank, local, peak, smax)
     line["realspace"] = run_realspace(args, qslab, soe, dev, ws)
     line["virial"] = run_virial(args, qslab, soe, dev, ws, sl, P, ms32_max)
+    line["energy_only"] = run_energy_only(args, qslab, soe, dev, ws, sl, P, ms32_max)
     line["md"] = run_md(args, qslab, soe, dev, ws)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         t, desc, cores = cpu_oracle_sample(sl, soe, P, 1000, sample_modes=8)
@@ -500,6 +501,54 @@ def run_md(args, qslab, soe, dev, ws):
     return {"workload": "436 cations in 100x100x30, top wall -0.0436, LJ, alpha=0.3, rc=4/alpha, "
                         "RBE P=100 (Metropolis), BAOAB dt=0.005, FP32C",
             "us_per_step": 1e3 * ms, "steps_per_s": ws / (ms * 1e-3), "steps": reps * chunk}
+
+
+def run_energy_only(args, qslab, soe, dev, ws, sl, P, ms_plain):
+    """The energy-only call (qslab_compute_energy: forward sums, no gather)
+    and its adjoint (qslab_compute_adjoint: the gradient from the stored
+    sorted order and carries) on the headline workload, L2 flushed between
+    calls."""
+    import torch
+    N = sl.N
+    s = qslab.QSlab(dev.index or 0, "fp32c").configure(sl.box, sl.alpha, soe, rbe=(P, 78))
+    pos = torch.tensor(sl.pos, device=dev, dtype=torch.float32)
+    q = torch.tensor(sl.q, device=dev, dtype=torch.float32)
+    e = torch.empty(1, dtype=torch.float64, device=dev)
+    phi = torch.empty(N, dtype=torch.float32, device=dev)
+    F = torch.empty((N, 3), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def energy():
+        qslab.qslab_compute_energy(s.h, N, pos.data_ptr(), q.data_ptr(), e.data_ptr(),
+                                   stream.cuda_stream)
+
+    def adjoint():
+        qslab.qslab_compute_adjoint(s.h, phi.data_ptr(), F.data_ptr(), stream.cuda_stream)
+    for _ in range(max(args.warmup, 3)):
+        energy()
+        adjoint()
+    s.check()
+    steps = max(args.steps, 5)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    torch.cuda.synchronize(dev)
+    for a, b, c in ev:
+        flush.zero_()
+        a.record(stream)
+        energy()
+        b.record(stream)
+        adjoint()
+        c.record(stream)
+    torch.cuda.synchronize(dev)
+    s.check()
+    ms_e = reduce_max(float(np.mean([a.elapsed_time(b) for a, b, _ in ev])), dev)
+    ms_a = reduce_max(float(np.mean([b.elapsed_time(c) for _, b, c in ev])), dev)
+    s.close()
+    return {"workload": "energy only (qslab_compute_energy), then its adjoint "
+                        "(qslab_compute_adjoint), same workload as the headline",
+            "energy_ms_per_call": ms_e, "energy_particles_per_s": job_throughput(N, ws, ms_e),
+            "adjoint_ms_per_call": ms_a, "energy_vs_full_call": ms_e / ms_plain,
+            "steps": steps}
 
 
 def run_virial(args, qslab, soe, dev, ws, sl, P, ms_plain):

@@ -173,6 +173,38 @@ int qslab_compute_batched(qslab_ctx* ctx, int R, const int64_t* offsets,
                           double* energies, void* phi, void* force,
                           void* stream);
 
+/* Energy only, and its adjoint (Section 3.2's recursion run forward for
+ * the energy; the gradient by the bidirectional scans of Appendix E run
+ * afterwards, on demand).
+ * qslab_compute_energy(): the long-range energy of qslab_compute() (same
+ * sort, k-set, sample and k = 0 term) from forward sums only: per mode the
+ * pair energy gam Re sum_beta c_beta sum_i conj(u_i) sum_{j<i} u_j
+ * e^{-beta (z_i - z_j)} (each pair once), without the per-particle gather;
+ * about half the work of the full call.
+ *   energy   device, one double (required)
+ *   N, pos, q, stream: as for qslab_compute()
+ * The call leaves the sorted order, the chunk carries of both directions,
+ * the mode tables (including the random-batch sample) and the k = 0 term in
+ * the context's workspace.
+ * qslab_compute_batched_energy(): the same for R replicas (arguments as
+ * for qslab_compute_batched(); energies required).
+ * qslab_compute_adjoint(): the gradient of that energy, from what the last
+ * energy-only call left: phi_i = dE/dq_i and F_i = -dE/dr_i (device, the
+ * precision's type, N and N x 3 in the caller's order of that call; either
+ * may be NULL, not both), by the bidirectional recurrences over the stored
+ * sorted order with the phases recomputed. Equal to the phi and force of
+ * qslab_compute() on the same inputs and sample. It must follow the
+ * energy-only call on the same stream (or after it completed), with no other
+ * long-range call, MD step or configuration change on the context in
+ * between; otherwise it returns QSLAB_ERR_NOT_CONFIGURED. It may be called
+ * more than once. */
+int qslab_compute_energy(qslab_ctx* ctx, int64_t N, const void* pos, const void* q,
+                         double* energy, void* stream);
+int qslab_compute_batched_energy(qslab_ctx* ctx, int R, const int64_t* offsets,
+                                 const double* boxes, const void* pos, const void* q,
+                                 double* energies, void* stream);
+int qslab_compute_adjoint(qslab_ctx* ctx, void* phi, void* force, void* stream);
+
 /* Virial tensor of the long-range energy, for pressures in the NPT ensemble
  * (Section 4.3: the random-batch dynamics extends to NPT through the virial;
  * Section 2.4: the L_z-dependent constant of the particle-slab potential of

@@ -83,6 +83,9 @@ def load(build_if_missing: bool = True):
         "qslab_compute_static": ([P, ctypes.c_int64, P, P, P, P, P, P], I),
         "qslab_compute_batched": ([P, I, P, P, P, P, P, P, P, P], I),
         "qslab_compute_virial": ([P, ctypes.c_int64, P, P, P, P, P, P, P], I),
+        "qslab_compute_energy": ([P, ctypes.c_int64, P, P, P, P], I),
+        "qslab_compute_batched_energy": ([P, I, P, P, P, P, P, P], I),
+        "qslab_compute_adjoint": ([P, P, P, P], I),
         "qslab_compute_batched_virial": ([P, I, P, P, P, P, P, P, P, P, P], I),
         "qslab_compute_realspace_virial": ([P, ctypes.c_int64, P, P, P, P, P, P, P], I),
         "qslab_autotune": ([P, I, P, P, P, P, P, I, P, P], I),
@@ -200,6 +203,29 @@ def qslab_compute_virial(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr, v
                          stream_ptr):
     _check(load().qslab_compute_virial(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr,
                                        virial_ptr, stream_ptr), "qslab_compute_virial")
+
+
+def qslab_compute_energy(h, N, pos_ptr, q_ptr, energy_ptr, stream_ptr):
+    """Energy only (forward sums); leaves the workspace for qslab_compute_adjoint."""
+    _check(load().qslab_compute_energy(h, N, pos_ptr, q_ptr, energy_ptr, stream_ptr),
+           "qslab_compute_energy")
+
+
+def qslab_compute_batched_energy(h, offsets, boxes, pos_ptr, q_ptr, energies_ptr, stream_ptr):
+    off = np.ascontiguousarray(offsets, np.int64)
+    box = np.ascontiguousarray(boxes, np.float64).reshape(-1, 3)
+    R = off.shape[0] - 1
+    if box.shape[0] != R:
+        raise ValueError("boxes must have one row per replica")
+    _check(load().qslab_compute_batched_energy(h, R, off.ctypes.data, box.ctypes.data, pos_ptr,
+                                               q_ptr, energies_ptr, stream_ptr),
+           "qslab_compute_batched_energy")
+
+
+def qslab_compute_adjoint(h, phi_ptr, force_ptr, stream_ptr):
+    """phi = dE/dq and F = -dE/dr of the last energy-only call."""
+    _check(load().qslab_compute_adjoint(h, phi_ptr, force_ptr, stream_ptr),
+           "qslab_compute_adjoint")
 
 
 def qslab_compute_batched_virial(h, offsets, boxes, pos_ptr, q_ptr, energies_ptr, phi_ptr,
@@ -507,6 +533,61 @@ class QSlab:
         self.last_R = 1
         return energy, phi, force, virial
 
+    def compute_energy(self, pos, q, energy=None):
+        """Energy only (float64[1] CUDA tensor), from forward sums; the
+        workspace is kept for adjoint()."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        if pos.device != dev or q.device != dev:
+            raise ValueError("pos and q must be CUDA tensors on the context's device")
+        pos = pos.to(self.dtype).contiguous()
+        q = q.to(self.dtype).contiguous()
+        N = q.shape[0]
+        if energy is None:
+            energy = torch.empty(1, dtype=torch.float64, device=dev)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        qslab_compute_energy(self.h, N, pos.data_ptr(), q.data_ptr(), energy.data_ptr(), st)
+        self.last_R = 1
+        self._adjoint_n = N
+        return energy
+
+    def compute_batched_energy(self, pos, q, offsets, boxes, energies=None):
+        """Energies of R slabs (float64[R]) from forward sums; the workspace
+        is kept for adjoint()."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        if pos.dtype != self.dtype or q.dtype != self.dtype or not pos.is_contiguous() \
+                or not q.is_contiguous() or pos.device != dev or q.device != dev:
+            raise ValueError("pos and q must be contiguous CUDA tensors of the context's precision")
+        off = np.ascontiguousarray(offsets, np.int64)
+        R = off.shape[0] - 1
+        if int(off[-1]) != q.shape[0]:
+            raise ValueError("offsets[-1] must equal the number of particles")
+        if energies is None:
+            energies = torch.empty(R, dtype=torch.float64, device=dev)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        qslab_compute_batched_energy(self.h, off, boxes, pos.data_ptr(), q.data_ptr(),
+                                     energies.data_ptr(), st)
+        self.last_R = R
+        self._adjoint_n = q.shape[0]
+        return energies
+
+    def adjoint(self, phi=None, force=None):
+        """(phi = dE/dq, F = -dE/dr) of the last energy-only call, in its
+        particle order, as CUDA tensors."""
+        torch = self.torch
+        dev = torch.device("cuda", self.device)
+        N = getattr(self, "_adjoint_n", None)
+        if N is None:
+            raise QslabError(-2, "qslab_compute_adjoint")
+        if phi is None:
+            phi = torch.empty(N, dtype=self.dtype, device=dev)
+        if force is None:
+            force = torch.empty((N, 3), dtype=self.dtype, device=dev)
+        st = torch.cuda.current_stream(dev).cuda_stream
+        qslab_compute_adjoint(self.h, phi.data_ptr(), force.data_ptr(), st)
+        return phi, force
+
     def compute_batched_virial(self, pos, q, offsets, boxes):
         """compute_batched() plus each replica's virial: returns (energies[R],
         phi[N], force[N,3], virial[R,6]) as CUDA tensors."""
@@ -734,25 +815,41 @@ def _autograd():
     import torch
 
     class SlabEnergy(torch.autograd.Function):
-        """E(pos, q) with the exact adjoint: dE/dpos = -F, dE/dq = phi."""
+        """E(pos, q) with the exact adjoint: dE/dpos = -F, dE/dq = phi.
+
+        adjoint=False: the forward runs the full call and keeps phi and F.
+        adjoint=True: the forward runs the energy-only call (forward sums);
+        the backward runs qslab_compute_adjoint, the bidirectional scans over
+        the sorted order the forward left in the workspace (nothing N x K is
+        stored). No other call may use the context between the two."""
 
         @staticmethod
-        def forward(ctx, pos, q, slab: QSlab):
+        def forward(ctx, pos, q, slab: QSlab, adjoint: bool):
+            ctx.dtypes = (pos.dtype, q.dtype)
+            ctx.adjoint = adjoint
+            ctx.slab = slab
+            if adjoint:
+                e = slab.compute_energy(pos.detach(), q.detach())
+                return e[0].to(pos.dtype)
             e, phi, F = slab.compute(pos.detach(), q.detach())
             ctx.save_for_backward(phi, F)
-            ctx.dtypes = (pos.dtype, q.dtype)
             return e[0].to(pos.dtype)
 
         @staticmethod
         def backward(ctx, gE):
-            phi, F = ctx.saved_tensors
+            if ctx.adjoint:
+                phi, F = ctx.slab.adjoint()
+            else:
+                phi, F = ctx.saved_tensors
             gpos = (-gE * F).to(ctx.dtypes[0])
             gq = (gE * phi).to(ctx.dtypes[1])
-            return gpos, gq, None
+            return gpos, gq, None, None
 
     return SlabEnergy
 
 
-def slab_energy(pos, q, slab: QSlab):
-    """Differentiable long-range energy (torch autograd)."""
-    return _autograd().apply(pos, q, slab)
+def slab_energy(pos, q, slab: QSlab, adjoint: bool = False):
+    """Differentiable long-range energy (torch autograd); adjoint=True
+    computes only the energy in the forward and the gradient in the
+    backward (see SlabEnergy)."""
+    return _autograd().apply(pos, q, slab, adjoint)

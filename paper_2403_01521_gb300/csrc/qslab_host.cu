@@ -102,6 +102,7 @@ struct qslab_ctx {
   void* d_rs_ws = nullptr;      // real-space workspace
   size_t rs_ws_bytes = 0;
   cudaStream_t last_stream = nullptr;
+  bool primed = false;          // an energy-only call left its workspace for the adjoint
   bool have_sample = false;
   int last_R = 1;
   cudaEvent_t ev[9] = {};
@@ -657,8 +658,12 @@ int ensure_ws(qslab_ctx* c, size_t bytes) {
 }
 
 template <typename T>
+// what = 0: energy, potentials, forces (and the virial if requested);
+// what = 1: the energy only, from forward sums, leaving the sorted data,
+// carries, mode tables and the k = 0 term in the workspace for the adjoint
+// (run_adjoint).
 int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies, T* phi,
-        T* force, cudaStream_t st, double* virial = nullptr) {
+        T* force, cudaStream_t st, double* virial = nullptr, int what = 0) {
   using PH = typename PhaseT<T>::type;
   const Tables& tb = c->tab;
   const int64_t N = tb.N;
@@ -689,6 +694,7 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
 
   cudaEvent_t* ev = c->timing ? c->ev : nullptr;
   int nl = 0;
+  c->primed = false;
   if (ev) cudaEventRecord(ev[0], st);
   QS_CUDA(cudaMemsetAsync(sums, 0, 16 * (size_t)R, st));
   launch_prepare<T>(rp, pos, q, sw.keys[0], sw.vals[0], R > 1 ? rid : nullptr, sums,
@@ -733,9 +739,32 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
     else c->coef_ready = true;
   }
   if (ev) cudaEventRecord(ev[2], st);
-  launch_kspace<T>(P.sp, rp, modes, c->pairs, zs, dz, qs, xh, yh,
-                   sizeof(T) == 4 ? reinterpret_cast<const float2*>(tab + tb.o_trig) : nullptr,
-                   agg, carry, dec, part, st, ev ? ev + 3 : nullptr);
+  const float2* trig = sizeof(T) == 4 ? reinterpret_cast<const float2*>(tab + tb.o_trig) : nullptr;
+  if (what == 1) {
+    // energy only: pass A and the carries, then the forward pair sums per
+    // mode (no bidirectional gather); the k = 0 term, the j = i constants and
+    // the walls come from the combine kernel with no k-space planes
+    launch_kspace<T>(P.sp, rp, modes, c->pairs, zs, dz, qs, xh, yh, trig, agg, carry, dec, part,
+                     st, ev ? ev + 3 : nullptr, 1);
+    VirArgs<T> va{P.sp, rp, modes, c->pairs, c->alpha, rbe ? 1 : 0, zs, dz, qs, xh, yh, trig,
+                  carry, pos, q, nullptr, energies, nullptr, c->walls, nullptr};
+    nl += 7 + launch_energy_pass<T>(va, ws + P.off_vir, st);
+    if (ev) cudaEventRecord(ev[5], st);
+    QS_CUDA(cudaStreamWaitEvent(st, c->join, 0));
+    if (ev) cudaEventRecord(ev[6], st);
+    launch_combine<T>(rp, 0, part, phi0, fz0, qs, zs, xh, yh, c->walls, perm, echunk, nullptr,
+                      nullptr, energies, st);
+    nl += 2 + launch_energy_add(P.sp, rp, ws + P.off_vir, energies, st);
+    if (ev) cudaEventRecord(ev[7], st);
+    c->launches = nl;
+    c->last_R = R;
+    QS_CUDA(cudaGetLastError());
+    c->last_stream = st;
+    c->primed = true;
+    return QSLAB_OK;
+  }
+  launch_kspace<T>(P.sp, rp, modes, c->pairs, zs, dz, qs, xh, yh, trig, agg, carry, dec, part, st,
+                   ev ? ev + 3 : nullptr);
   nl += 8;
   QS_CUDA(cudaStreamWaitEvent(st, c->join, 0));
   if (ev) cudaEventRecord(ev[6], st);
@@ -754,6 +783,43 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   if (ev) cudaEventRecord(ev[7], st);
   c->launches = nl;
   c->last_R = R;
+  QS_CUDA(cudaGetLastError());
+  c->last_stream = st;
+  return QSLAB_OK;
+}
+
+// The adjoint of an energy-only call (what = 1 above): pass B over the
+// sorted order, carries and mode tables that call left in the workspace
+// (phases recomputed), then the combine kernel with the stored k = 0 term:
+// phi = dE/dq and F = -dE/dr in the caller's order.
+template <typename T>
+int run_adjoint(qslab_ctx* c, const Plan& P, T* phi, T* force, cudaStream_t st) {
+  using PH = typename PhaseT<T>::type;
+  const Tables& tb = c->tab;
+  const int R = tb.R;
+  const Reps rp = reps_view(c);
+  char* ws = static_cast<char*>(c->d_ws);
+  char* tab = static_cast<char*>(c->d_tab);
+  T* zs = reinterpret_cast<T*>(ws + P.off_zs);
+  T* dz = reinterpret_cast<T*>(ws + P.off_dz);
+  T* qs = reinterpret_cast<T*>(ws + P.off_qs);
+  PH* xh = reinterpret_cast<PH*>(ws + P.off_xh);
+  PH* yh = reinterpret_cast<PH*>(ws + P.off_yh);
+  int32_t* perm = reinterpret_cast<int32_t*>(ws + P.off_perm);
+  Cplx<T>* agg = reinterpret_cast<Cplx<T>*>(ws + P.off_agg);
+  Cplx<T>* carry = reinterpret_cast<Cplx<T>*>(ws + P.off_carry);
+  void* dec = ws + P.off_dec;
+  T* part = reinterpret_cast<T*>(ws + P.off_part);
+  double* phi0 = reinterpret_cast<double*>(ws + P.off_phi0);
+  double* fz0 = reinterpret_cast<double*>(ws + P.off_fz0);
+  double* echunk = reinterpret_cast<double*>(ws + P.off_echunk);
+  ModeTab<T> modes = mode_views<T>(tab + tb.o_modes, (size_t)R * tb.Kpad, c->npc);
+  const float2* trig = sizeof(T) == 4 ? reinterpret_cast<const float2*>(tab + tb.o_trig) : nullptr;
+  launch_kspace<T>(P.sp, rp, modes, c->pairs, zs, dz, qs, xh, yh, trig, agg, carry, dec, part, st,
+                   nullptr, 2);
+  launch_combine<T>(rp, P.sp.nkr, part, phi0, fz0, qs, zs, xh, yh, c->walls, perm, echunk, phi,
+                    force, nullptr, st);
+  c->launches = 2;
   QS_CUDA(cudaGetLastError());
   c->last_stream = st;
   return QSLAB_OK;
@@ -778,13 +844,13 @@ int setup_call(qslab_ctx* c, int R, const int64_t* off, const double* box, bool 
 }
 
 int dispatch(qslab_ctx* c, const Plan& P, const void* pos, const void* q, double* energies,
-             void* phi, void* force, cudaStream_t st, double* virial = nullptr) {
+             void* phi, void* force, cudaStream_t st, double* virial = nullptr, int what = 0) {
   if (c->prec == QSLAB_FP64)
     return run<double>(c, P, static_cast<const double*>(pos), static_cast<const double*>(q),
                        energies, static_cast<double*>(phi), static_cast<double*>(force), st,
-                       virial);
+                       virial, what);
   return run<float>(c, P, static_cast<const float*>(pos), static_cast<const float*>(q), energies,
-                    static_cast<float*>(phi), static_cast<float*>(force), st, virial);
+                    static_cast<float*>(phi), static_cast<float*>(force), st, virial, what);
 }
 
 }  // namespace
@@ -858,6 +924,7 @@ int qslab_set_alpha(qslab_ctx* c, double alpha) {
   c->alpha = alpha;
   c->has_alpha = true;
   c->cfg_dirty = true;
+  c->primed = false;
   return QSLAB_OK;
 }
 
@@ -866,6 +933,7 @@ int qslab_set_kcut(qslab_ctx* c, double kc) {
   c->kc = kc;
   c->mode = 1;
   c->cfg_dirty = true;
+  c->primed = false;
   return QSLAB_OK;
 }
 
@@ -878,6 +946,7 @@ int qslab_set_rbe(qslab_ctx* c, int P, uint64_t seed) {
   c->seed = seed;
   c->mode = 2;
   c->cfg_dirty = true;
+  c->primed = false;
   return QSLAB_OK;
 }
 
@@ -901,6 +970,7 @@ int qslab_set_soe(qslab_ctx* c, int M, const double* s_re, const double* s_im,
   c->w_re = trial.w_re; c->w_im = trial.w_im;
   c->has_soe = true;
   c->cfg_dirty = true;
+  c->primed = false;
   return QSLAB_OK;
 }
 
@@ -917,6 +987,7 @@ int qslab_set_tuning(qslab_ctx* c, int chunk, int modes_per_cta) {
     return QSLAB_ERR_INVALID_ARG;
   c->tune_L = chunk;
   c->tune_KR = modes_per_cta;
+  c->primed = false;
   return QSLAB_OK;
 }
 
@@ -967,6 +1038,46 @@ int qslab_compute_batched_virial(qslab_ctx* c, int R, const int64_t* offsets,
   const int rc = setup_call(c, R, offsets, boxes, false, P, true);
   if (rc) return rc;
   return dispatch(c, P, pos, q, energies, phi, force, static_cast<cudaStream_t>(stream), virial);
+}
+
+int qslab_compute_energy(qslab_ctx* c, int64_t N, const void* pos, const void* q,
+                         double* energy, void* stream) {
+  if (!c || !pos || !q || !energy || N < 1 || N > 2147483647LL) return QSLAB_ERR_INVALID_ARG;
+  if (!c->has_box) return QSLAB_ERR_NOT_CONFIGURED;
+  const int64_t off[2] = {0, N};
+  const double box[3] = {c->Lx, c->Ly, c->Lz};
+  Plan P;
+  c->primed = false;
+  const int rc = setup_call(c, 1, off, box, false, P, true);
+  if (rc) return rc;
+  return dispatch(c, P, pos, q, energy, nullptr, nullptr, static_cast<cudaStream_t>(stream),
+                  nullptr, 1);
+}
+
+int qslab_compute_batched_energy(qslab_ctx* c, int R, const int64_t* offsets,
+                                 const double* boxes, const void* pos, const void* q,
+                                 double* energies, void* stream) {
+  if (!c || !pos || !q || !offsets || !boxes || !energies || R < 1 || R > kMaxReplicas)
+    return QSLAB_ERR_INVALID_ARG;
+  Plan P;
+  c->primed = false;
+  const int rc = setup_call(c, R, offsets, boxes, false, P, true);
+  if (rc) return rc;
+  return dispatch(c, P, pos, q, energies, nullptr, nullptr, static_cast<cudaStream_t>(stream),
+                  nullptr, 1);
+}
+
+int qslab_compute_adjoint(qslab_ctx* c, void* phi, void* force, void* stream) {
+  if (!c || (!phi && !force)) return QSLAB_ERR_INVALID_ARG;
+  if (!c->primed || c->cfg_dirty || !c->tab.valid || c->tab.cfg_version != c->cfg_version)
+    return QSLAB_ERR_NOT_CONFIGURED;
+  QS_CUDA(cudaSetDevice(c->device));
+  const Plan P = make_plan(c, false, true);
+  if (P.total > c->ws_bytes) return QSLAB_ERR_NOT_CONFIGURED;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->prec == QSLAB_FP64)
+    return run_adjoint<double>(c, P, static_cast<double*>(phi), static_cast<double*>(force), st);
+  return run_adjoint<float>(c, P, static_cast<float*>(phi), static_cast<float*>(force), st);
 }
 
 int qslab_compute_host(qslab_ctx* c, int64_t N, const void* pos_host, const void* q_host,
@@ -1026,6 +1137,7 @@ int qslab_set_walls(qslab_ctx* c, double sigma_bot, double sigma_top, int nw,
     w.c[i][3] = top[2 * i + 1];
   }
   c->walls = w;
+  c->primed = false;
   return QSLAB_OK;
 }
 
@@ -1036,12 +1148,14 @@ int qslab_set_rbe_sampler(qslab_ctx* c, int kind, int thin) {
   c->sampler = kind;
   c->mh_thin = kind == QSLAB_SAMPLER_METROPOLIS ? thin : 1;
   c->have_sample = false;
+  c->primed = false;
   return QSLAB_OK;
 }
 
 int qslab_clear_walls(qslab_ctx* c) {
   if (!c) return QSLAB_ERR_INVALID_ARG;
   c->walls = WallTab{};
+  c->primed = false;
   return QSLAB_OK;
 }
 

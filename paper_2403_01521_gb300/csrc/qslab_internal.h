@@ -178,7 +178,8 @@ void launch_kspace(const ScanPlan& plan, const Reps& rp, const ModeTab<T>& modes
                    const typename PhaseT<T>::type* yh,
                    const float2* trig,   // FP32: [256] (cos, sin) of j/256 turns
                    Cplx<T>* agg, Cplx<T>* carry, void* dec, T* part,
-                   cudaStream_t st, cudaEvent_t* ev3);  // ev3: 3 events or NULL
+                   cudaStream_t st, cudaEvent_t* ev3,   // ev3: 3 events or NULL
+                   int stage = 0);  // 0: all; 1: pass A + carries; 2: pass B (carries in place)
 // bytes of the chunk-to-chunk decay tables and carry-group transfers
 size_t kspace_decay_bytes(const ScanPlan& pl, const Reps& rp, int fp64);
 // (qslab_carry.cu) the carries of every chunk from the pass-A aggregates;

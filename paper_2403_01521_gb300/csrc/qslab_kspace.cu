@@ -488,22 +488,28 @@ struct FinalKernel<float, NP> {
   }
 };
 
+// stage 0: pass A, carries and pass B; 1: pass A and carries only; 2: pass B
+// only (from the carries a stage-1 launch left in place)
 template <typename T, int NP>
 static void kspace_run(const KParams<T>& P, const PairTab& pairs, void* dec,
-                       cudaStream_t st, cudaEvent_t* ev) {
+                       cudaStream_t st, cudaEvent_t* ev, int stage) {
   const ScanPlan& pl = P.plan;
   const Reps& rp = P.rp;
   dim3 grid(rp.nchunks, pl.nkr);
   const size_t smA = chunk_smem_bytes<T>(rp.L, NP, 0, false);
   const size_t smB = chunk_smem_bytes<T>(rp.L, NP, pl.KR / kWarp, true);
-  cudaFuncSetAttribute(kspace_aggregate_kernel<T, NP>,
-                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
-  kspace_aggregate_kernel<T, NP><<<grid, pl.KR, smA, st>>>(P, pairs);
-  if (ev) cudaEventRecord(ev[0], st);
-  launch_kspace_carries<T>(pl, rp, pairs, P.zs, P.modes.kk, P.agg, P.carry, dec, st);
-  if (ev) cudaEventRecord(ev[1], st);
-  FinalKernel<T, NP>::run(P, pairs, grid, pl.KR, smB, st);
-  if (ev) cudaEventRecord(ev[2], st);
+  if (stage != 2) {
+    cudaFuncSetAttribute(kspace_aggregate_kernel<T, NP>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
+    kspace_aggregate_kernel<T, NP><<<grid, pl.KR, smA, st>>>(P, pairs);
+    if (ev) cudaEventRecord(ev[0], st);
+    launch_kspace_carries<T>(pl, rp, pairs, P.zs, P.modes.kk, P.agg, P.carry, dec, st);
+    if (ev) cudaEventRecord(ev[1], st);
+  }
+  if (stage != 1) {
+    FinalKernel<T, NP>::run(P, pairs, grid, pl.KR, smB, st);
+    if (ev) cudaEventRecord(ev[2], st);
+  }
 }
 
 template <typename T>
@@ -512,14 +518,14 @@ void launch_kspace(const ScanPlan& plan, const Reps& rp, const ModeTab<T>& modes
                    const typename PhaseT<T>::type* xh,
                    const typename PhaseT<T>::type* yh, const float2* trig,
                    Cplx<T>* agg, Cplx<T>* carry, void* dec, T* part,
-                   cudaStream_t st, cudaEvent_t* ev3) {
+                   cudaStream_t st, cudaEvent_t* ev3, int stage) {
   KParams<T> P{plan, rp, modes, (size_t)rp.R * rp.Kpad, zs, dz, qs, xh, yh, trig, agg, carry,
                part};
   switch (plan.np) {
-    case 4: kspace_run<T, 4>(P, pairs, dec, st, ev3); break;
-    case 8: kspace_run<T, 8>(P, pairs, dec, st, ev3); break;
-    case 12: kspace_run<T, 12>(P, pairs, dec, st, ev3); break;
-    default: kspace_run<T, 16>(P, pairs, dec, st, ev3); break;
+    case 4: kspace_run<T, 4>(P, pairs, dec, st, ev3, stage); break;
+    case 8: kspace_run<T, 8>(P, pairs, dec, st, ev3, stage); break;
+    case 12: kspace_run<T, 12>(P, pairs, dec, st, ev3, stage); break;
+    default: kspace_run<T, 16>(P, pairs, dec, st, ev3, stage); break;
   }
 }
 
@@ -527,11 +533,11 @@ void launch_kspace(const ScanPlan& plan, const Reps& rp, const ModeTab<T>& modes
 template void launch_kspace<float>(const ScanPlan&, const Reps&, const ModeTab<float>&,
                                    const PairTab&, const float*, const float*, const float*,
                                    const uint32_t*, const uint32_t*, const float2*, Cplx<float>*,
-                                   Cplx<float>*, void*, float*, cudaStream_t, cudaEvent_t*);
+                                   Cplx<float>*, void*, float*, cudaStream_t, cudaEvent_t*, int);
 template void launch_kspace<double>(const ScanPlan&, const Reps&, const ModeTab<double>&,
                                     const PairTab&, const double*, const double*, const double*,
                                     const uint64_t*, const uint64_t*, const float2*,
                                     Cplx<double>*, Cplx<double>*, void*, double*, cudaStream_t,
-                                    cudaEvent_t*);
+                                    cudaEvent_t*, int);
 
 }  // namespace qslab

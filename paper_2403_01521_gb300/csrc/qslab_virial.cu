@@ -246,9 +246,25 @@ __global__ void __launch_bounds__(kChainT) vir_zchain_kernel(VirArgs<T> a, const
 
 // ------------------------------------------------------------------ the pass
 // Per (chunk, mode): the forward recurrences of beta = k, the SOE pairs and
-// the z-weighted state from the carries, the sums S_k, S_z, S_p over the
-// chunk's particles, and their combination D(c, m) with the coefficients.
-template <typename T, int NP>
+// (WZ) the z-weighted state from the carries. Per particle the coefficients
+// are applied first,
+//   T_i = a_i Y_a + b_i Y_b,  Y_a = v_k Re x_k + v_z Re x_z + sum_p Re(v_p x_a,p),
+//                            Y_b = -v_k Im x_k - v_z Im x_z + sum_p Re(v_p x_b,p),
+// with the exclusive states x (the sums over j < i), so that the terms of
+// the SOE combination cancel per particle, as in the potential of pass B,
+// before anything is summed over particles; D(c, m) = sum over the chunk of
+// T_i, compensated (Kahan). With the energy coefficients (ck, cp of the mode
+// table) and no z-weighted state, D(c, m) is the chunk's share of the mode's
+// pair energy gam Re sum_beta c_beta S_beta (the energy-only call).
+template <typename T>
+__device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
+  const T y = x - c;
+  const T t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+template <typename T, int NP, bool WZ>
 __global__ void vir_pass_kernel(VirArgs<T> a, const double* vc, const Cplx<T>* gzc,
                                 double* dpart) {
   extern __shared__ __align__(32) char smem[];
@@ -267,34 +283,42 @@ __global__ void vir_pass_kernel(VirArgs<T> a, const double* vc, const Cplx<T>* g
   __syncthreads();
   const int m = blockIdx.y * a.plan.KR + threadIdx.x;
   const size_t mg = (size_t)ch.r * Kpad + m;
+  const size_t ks = (size_t)a.rp.R * Kpad;
   const int32_t mx = a.modes.mx[mg], my = a.modes.my[mg];
   const T kk = a.modes.kk[mg];
+  const T vk = (T)vc[mg];
+  const T vz = WZ ? (T)vc[ks + mg] : (T)0;
+  T vpr[NP], vpi[NP];
   const size_t cstride = (size_t)a.plan.nstates * Kpad;
   const Cplx<T>* cin = a.carry + (size_t)c * cstride + m;
   Cplx<T> g0 = cin[0];
-  Cplx<T> ga[NP], gb[NP], sp[NP];
+  Cplx<T> ga[NP], gb[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
     ga[p] = cin[(size_t)(1 + 2 * p) * Kpad];
     gb[p] = cin[(size_t)(2 + 2 * p) * Kpad];
-    sp[p] = Cplx<T>{0, 0};
+    vpr[p] = (T)vc[(2 + 2 * (size_t)p) * ks + mg];
+    vpi[p] = (T)vc[(3 + 2 * (size_t)p) * ks + mg];
   }
-  Cplx<T> gz = gzc[(size_t)c * Kpad + m];
-  T sk = 0, sz = 0;
+  Cplx<T> gz = WZ ? gzc[(size_t)c * Kpad + m] : Cplx<T>{0, 0};
+  T acc = 0, cmp = 0;
   for (int t = 0; t < cnt; ++t) {
     const VRec<T> r = rec[t];
     T cs, sn;
     phase_cs(phase_turns(mx, my, r.xh, r.yh), trig, cs, sn);
     const T av = r.q * cs, bv = r.q * sn;     // u = av - i bv
     const T ek = one_minus_exp_neg(kk * r.zd);
-    // z-weighted state from the state before this particle
-    const T hr = fma(r.zd, g0.re, gz.re), hi = fma(r.zd, g0.im, gz.im);
-    gz.re = fma(-ek, hr, hr);
-    gz.im = fma(-ek, hi, hi);
     // beta = k: exclusive state, then add u
     const T xr = fma(-ek, g0.re, g0.re), xi = fma(-ek, g0.im, g0.im);
-    sk = fma(av, xr, fma(-bv, xi, sk));
-    sz = fma(av, gz.re, fma(-bv, gz.im, sz));
+    T Ya = vk * xr, Yb = -vk * xi;
+    if (WZ) {
+      // z-weighted state from the state before this particle
+      const T hr = fma(r.zd, g0.re, gz.re), hi = fma(r.zd, g0.im, gz.im);
+      gz.re = fma(-ek, hr, hr);
+      gz.im = fma(-ek, hi, hi);
+      Ya = fma(vz, gz.re, Ya);
+      Yb = fma(-vz, gz.im, Yb);
+    }
     g0.re = xr + av;
     g0.im = xi - bv;
     const Cplx<T>* dt = tab + t * NP;
@@ -305,25 +329,20 @@ __global__ void vir_pass_kernel(VirArgs<T> a, const double* vc, const Cplx<T>* g
       const T ai = fma(d.re, ga[p].im, d.im * ga[p].re);
       const T br = fma(d.re, gb[p].re, -d.im * gb[p].im);
       const T bi = fma(d.re, gb[p].im, d.im * gb[p].re);
-      sp[p].re = fma(av, ar, fma(bv, br, sp[p].re));
-      sp[p].im = fma(av, ai, fma(bv, bi, sp[p].im));
+      Ya = fma(vpr[p], ar, fma(-vpi[p], ai, Ya));
+      Yb = fma(vpr[p], br, fma(-vpi[p], bi, Yb));
       ga[p].re = ar + av; ga[p].im = ai;
       gb[p].re = br + bv; gb[p].im = bi;
     }
+    kahan_add(acc, cmp, fma(av, Ya, bv * Yb));
   }
-  const size_t ks = (size_t)a.rp.R * Kpad;
-  double D = vc[mg] * (double)sk + vc[ks + mg] * (double)sz;
-#pragma unroll
-  for (int p = 0; p < NP; ++p)
-    D += vc[(2 + 2 * (size_t)p) * ks + mg] * (double)sp[p].re
-       - vc[(3 + 2 * (size_t)p) * ks + mg] * (double)sp[p].im;
-  dpart[(size_t)c * Kpad + m] = D;
+  dpart[(size_t)c * Kpad + m] = (double)acc - (double)cmp;
 }
 
 // The same pass on the FP32 path with two SOE pairs per 64-bit register
 // (packed FP32 FMAs, __ffma2_rn / __fmul2_rn): the decay table is stored
 // re/im-split per particle so that two pairs' decays load as one float2.
-template <int NP>
+template <int NP, bool WZ>
 __global__ void vir_pass_f2_kernel(VirArgs<float> a, const double* vc, const Cplx<float>* gzc,
                                    double* dpart) {
   extern __shared__ __align__(32) char smem[];
@@ -344,37 +363,46 @@ __global__ void vir_pass_f2_kernel(VirArgs<float> a, const double* vc, const Cpl
   __syncthreads();
   const int m = blockIdx.y * a.plan.KR + threadIdx.x;
   const size_t mg = (size_t)ch.r * Kpad + m;
+  const size_t ks = (size_t)a.rp.R * Kpad;
   const int32_t mx = a.modes.mx[mg], my = a.modes.my[mg];
   const float kk = a.modes.kk[mg];
+  const float vk = (float)vc[mg];
+  const float vz = WZ ? (float)vc[ks + mg] : 0.0f;
   const size_t cstride = (size_t)a.plan.nstates * Kpad;
   const Cplx<float>* cin = a.carry + (size_t)c * cstride + m;
   Cplx<float> g0 = cin[0];
-  float2 Ra[NP / 2], Ia[NP / 2], Rb[NP / 2], Ib[NP / 2], Sr[NP / 2], Si[NP / 2];
+  float2 Ra[NP / 2], Ia[NP / 2], Rb[NP / 2], Ib[NP / 2], Vr[NP / 2], nVi[NP / 2];
 #pragma unroll
   for (int q = 0; q < NP / 2; ++q) {
     const Cplx<float> a0 = cin[(size_t)(1 + 4 * q) * Kpad], b0 = cin[(size_t)(2 + 4 * q) * Kpad];
     const Cplx<float> a1 = cin[(size_t)(3 + 4 * q) * Kpad], b1 = cin[(size_t)(4 + 4 * q) * Kpad];
     Ra[q] = make_float2(a0.re, a1.re); Ia[q] = make_float2(a0.im, a1.im);
     Rb[q] = make_float2(b0.re, b1.re); Ib[q] = make_float2(b0.im, b1.im);
-    Sr[q] = make_float2(0.0f, 0.0f); Si[q] = Sr[q];
+    const size_t p0 = 2 * q, p1 = 2 * q + 1;
+    Vr[q] = make_float2((float)vc[(2 + 2 * p0) * ks + mg], (float)vc[(2 + 2 * p1) * ks + mg]);
+    nVi[q] = make_float2(-(float)vc[(3 + 2 * p0) * ks + mg], -(float)vc[(3 + 2 * p1) * ks + mg]);
   }
-  Cplx<float> gz = gzc[(size_t)c * Kpad + m];
-  float sk = 0.0f, sz = 0.0f;
+  Cplx<float> gz = WZ ? gzc[(size_t)c * Kpad + m] : Cplx<float>{0.0f, 0.0f};
+  float acc = 0.0f, cmp = 0.0f;
   for (int t = 0; t < cnt; ++t) {
     const VRec<float> r = rec[t];
     float cs, sn;
     phase_cs(phase_turns(mx, my, r.xh, r.yh), trig, cs, sn);
     const float av = r.q * cs, bv = r.q * sn;
     const float ek = one_minus_exp_neg(kk * r.zd);
-    const float hr = fmaf(r.zd, g0.re, gz.re), hi = fmaf(r.zd, g0.im, gz.im);
-    gz.re = fmaf(-ek, hr, hr);
-    gz.im = fmaf(-ek, hi, hi);
     const float xr = fmaf(-ek, g0.re, g0.re), xi = fmaf(-ek, g0.im, g0.im);
-    sk = fmaf(av, xr, fmaf(-bv, xi, sk));
-    sz = fmaf(av, gz.re, fmaf(-bv, gz.im, sz));
+    float ya = vk * xr, yb = -vk * xi;
+    if (WZ) {
+      const float hr = fmaf(r.zd, g0.re, gz.re), hi = fmaf(r.zd, g0.im, gz.im);
+      gz.re = fmaf(-ek, hr, hr);
+      gz.im = fmaf(-ek, hi, hi);
+      ya = fmaf(vz, gz.re, ya);
+      yb = fmaf(-vz, gz.im, yb);
+    }
     g0.re = xr + av;
     g0.im = xi - bv;
     const float2 Ua = make_float2(av, av), Ub = make_float2(bv, bv);
+    float2 Ya = make_float2(0.0f, 0.0f), Yb = Ya;
     const float2* dre = reinterpret_cast<const float2*>(tabf + t * 2 * NP);
     const float2* dim = reinterpret_cast<const float2*>(tabf + t * 2 * NP + NP);
 #pragma unroll
@@ -386,21 +414,16 @@ __global__ void vir_pass_f2_kernel(VirArgs<float> a, const double* vc, const Cpl
       const float2 ai = __ffma2_rn(Dr, Ia[q], __fmul2_rn(Di, Ra[q]));
       const float2 br = __ffma2_rn(Dr, Rb[q], __fmul2_rn(nDi, Ib[q]));
       const float2 bi = __ffma2_rn(Dr, Ib[q], __fmul2_rn(Di, Rb[q]));
-      Sr[q] = __ffma2_rn(Ua, ar, __ffma2_rn(Ub, br, Sr[q]));
-      Si[q] = __ffma2_rn(Ua, ai, __ffma2_rn(Ub, bi, Si[q]));
+      Ya = __ffma2_rn(Vr[q], ar, __ffma2_rn(nVi[q], ai, Ya));
+      Yb = __ffma2_rn(Vr[q], br, __ffma2_rn(nVi[q], bi, Yb));
       Ra[q] = __fadd2_rn(ar, Ua); Ia[q] = ai;
       Rb[q] = __fadd2_rn(br, Ub); Ib[q] = bi;
     }
+    ya += Ya.x + Ya.y;
+    yb += Yb.x + Yb.y;
+    kahan_add(acc, cmp, fmaf(av, ya, bv * yb));
   }
-  const size_t ks = (size_t)a.rp.R * Kpad;
-  double D = vc[mg] * (double)sk + vc[ks + mg] * (double)sz;
-#pragma unroll
-  for (int q = 0; q < NP / 2; ++q) {
-    const size_t p0 = 2 * q, p1 = 2 * q + 1;
-    D += vc[(2 + 2 * p0) * ks + mg] * (double)Sr[q].x - vc[(3 + 2 * p0) * ks + mg] * (double)Si[q].x;
-    D += vc[(2 + 2 * p1) * ks + mg] * (double)Sr[q].y - vc[(3 + 2 * p1) * ks + mg] * (double)Si[q].y;
-  }
-  dpart[(size_t)c * Kpad + m] = D;
+  dpart[(size_t)c * Kpad + m] = (double)acc - (double)cmp;
 }
 
 // ------------------------------------------------------- fixed-order sums
@@ -560,32 +583,74 @@ __global__ void vir_reduce_kernel(VirArgs<T> a, const double* msum, const double
   out[5] = tot[3 + 1] - ri.Lz * wv[5];                          // yz
 }
 
-template <typename T, int NP>
+template <typename T, int NP, bool WZ>
 struct VirPass {
   static void run(const VirArgs<T>& a, const double* vc, const Cplx<T>* gzc, double* dpart,
                   size_t sm, dim3 grid, cudaStream_t st) {
-    cudaFuncSetAttribute(vir_pass_kernel<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(vir_pass_kernel<T, NP, WZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm);
-    vir_pass_kernel<T, NP><<<grid, a.plan.KR, sm, st>>>(a, vc, gzc, dpart);
+    vir_pass_kernel<T, NP, WZ><<<grid, a.plan.KR, sm, st>>>(a, vc, gzc, dpart);
   }
 };
-template <int NP>
-struct VirPass<float, NP> {
+template <int NP, bool WZ>
+struct VirPass<float, NP, WZ> {
   static void run(const VirArgs<float>& a, const double* vc, const Cplx<float>* gzc,
                   double* dpart, size_t sm, dim3 grid, cudaStream_t st) {
-    cudaFuncSetAttribute(vir_pass_f2_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(vir_pass_f2_kernel<NP, WZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm);
-    vir_pass_f2_kernel<NP><<<grid, a.plan.KR, sm, st>>>(a, vc, gzc, dpart);
+    vir_pass_f2_kernel<NP, WZ><<<grid, a.plan.KR, sm, st>>>(a, vc, gzc, dpart);
   }
 };
 
-template <typename T, int NP>
+template <typename T, int NP, bool WZ>
 int run_pass(const VirArgs<T>& a, const double* vc, const Cplx<T>* gzc, double* dpart,
              cudaStream_t st) {
   const int L = a.rp.L;
   const size_t sm = rec_bytes<T>(L) + sizeof(Cplx<T>) * (size_t)NP * L;
-  VirPass<T, NP>::run(a, vc, gzc, dpart, sm, dim3(a.rp.nchunks, a.plan.nkr), st);
+  VirPass<T, NP, WZ>::run(a, vc, gzc, dpart, sm, dim3(a.rp.nchunks, a.plan.nkr), st);
   return 1;
+}
+
+template <typename T, bool WZ>
+int pass_np(const VirArgs<T>& a, const double* vc, const Cplx<T>* gzc, double* dpart,
+            cudaStream_t st) {
+  switch (a.plan.np) {
+    case 4: return run_pass<T, 4, WZ>(a, vc, gzc, dpart, st);
+    case 8: return run_pass<T, 8, WZ>(a, vc, gzc, dpart, st);
+    case 12: return run_pass<T, 12, WZ>(a, vc, gzc, dpart, st);
+    default: return run_pass<T, 16, WZ>(a, vc, gzc, dpart, st);
+  }
+}
+
+// Energy coefficients in the layout of the virial table: f = 0: ck =
+// gam c_kk, f = 1: 0, 2 + 2p / 3 + 2p: Re / Im of cp = m_p gam c_{k,p}
+// (the mode table's own values, so that the energy-only call and the full
+// call weight the pair sums identically).
+template <typename T>
+__global__ void energy_coef_kernel(Reps rp, int npc, ModeTab<T> mt, double* vc) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rep = blockIdx.y;
+  if (m >= rp.Kpad) return;
+  const size_t mg = (size_t)rep * rp.Kpad + m;
+  const size_t ks = (size_t)rp.R * rp.Kpad;
+  vc[mg] = (double)mt.ck[mg];
+  vc[ks + mg] = 0.0;
+  for (int p = 0; p < npc; ++p) {
+    vc[(2 + 2 * (size_t)p) * ks + mg] = (double)mt.cp[((size_t)0 * npc + p) * ks + mg];
+    vc[(3 + 2 * (size_t)p) * ks + mg] = (double)mt.cp[((size_t)1 * npc + p) * ks + mg];
+  }
+}
+
+// energies[r] += sum over the replica's modes of msum (fixed order): one
+// warp per replica.
+__global__ void energy_add_kernel(Reps rp, const double* msum, double* energies) {
+  const int rep = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (rep >= rp.R) return;   // whole warps leave together
+  double s = 0.0;
+  for (int m = lane; m < rp.Kpad; m += 32) s += msum[(size_t)rep * rp.Kpad + m];
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) energies[rep] += s;
 }
 
 struct VirLayout {
@@ -635,12 +700,7 @@ int launch_virial(const VirArgs<T>& a, void* ws, cudaStream_t st) {
     vir_zagg_kernel<T><<<dim3(a.rp.nchunks, a.plan.nkr), a.plan.KR, smz, st>>>(a, az);
     vir_zchain_kernel<T><<<dim3(Kpad, a.rp.R), kChainT, 0, st>>>(a, az, gzc);
     nl += 2;
-    switch (a.plan.np) {
-      case 4: nl += run_pass<T, 4>(a, vc, gzc, dpart, st); break;
-      case 8: nl += run_pass<T, 8>(a, vc, gzc, dpart, st); break;
-      case 12: nl += run_pass<T, 12>(a, vc, gzc, dpart, st); break;
-      default: nl += run_pass<T, 16>(a, vc, gzc, dpart, st); break;
-    }
+    nl += pass_np<T, true>(a, vc, gzc, dpart, st);
     vir_modesum_kernel<<<dim3((Kpad + 31) / 32, a.rp.R), 32 * kSumWarps, 0, st>>>(a.rp, dpart, msum);
     vir_zf_kernel<T><<<a.rp.nchunks, 256, 0, st>>>(a, zpart);
     nl += 2;
@@ -655,7 +715,33 @@ int launch_virial(const VirArgs<T>& a, void* ws, cudaStream_t st) {
   return nl;
 }
 
+template <typename T>
+int launch_energy_pass(const VirArgs<T>& a, void* ws, cudaStream_t st) {
+  const VirLayout l = layout(a.plan, a.rp);
+  char* b = static_cast<char*>(ws);
+  double* vc = reinterpret_cast<double*>(b + l.vc);
+  double* dpart = reinterpret_cast<double*>(b + l.dpart);
+  double* msum = reinterpret_cast<double*>(b + l.msum);
+  const int Kpad = a.rp.Kpad;
+  energy_coef_kernel<T><<<dim3((Kpad + 127) / 128, a.rp.R), 128, 0, st>>>(a.rp, a.plan.np,
+                                                                           a.modes, vc);
+  pass_np<T, false>(a, vc, nullptr, dpart, st);
+  vir_modesum_kernel<<<dim3((Kpad + 31) / 32, a.rp.R), 32 * kSumWarps, 0, st>>>(a.rp, dpart, msum);
+  return 3;
+}
+
+int launch_energy_add(const ScanPlan& plan, const Reps& rp, const void* ws, double* energies,
+                      cudaStream_t st) {
+  const VirLayout l = layout(plan, rp);
+  const double* msum = reinterpret_cast<const double*>(static_cast<const char*>(ws) + l.msum);
+  const int64_t thr = (int64_t)rp.R * 32;
+  energy_add_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(rp, msum, energies);
+  return 1;
+}
+
 template int launch_virial<float>(const VirArgs<float>&, void*, cudaStream_t);
 template int launch_virial<double>(const VirArgs<double>&, void*, cudaStream_t);
+template int launch_energy_pass<float>(const VirArgs<float>&, void*, cudaStream_t);
+template int launch_energy_pass<double>(const VirArgs<double>&, void*, cudaStream_t);
 
 }  // namespace qslab

@@ -43,5 +43,16 @@ size_t virial_workspace_bytes(const ScanPlan& plan, const Reps& rp);
 // Issues the virial kernels on st; returns the number of kernels launched.
 template <typename T>
 int launch_virial(const VirArgs<T>& a, void* ws, cudaStream_t st);
+// The k != 0 pair energy of every replica from forward sums only (the
+// energy-only call): per mode, the sum over chunks of
+// gam Re sum_beta c_beta S_beta, kept in ws. Uses a.plan, rp, modes, pairs,
+// the sorted arrays, trig and the forward carries (virial_workspace_bytes of
+// scratch). Returns the number of kernels launched.
+template <typename T>
+int launch_energy_pass(const VirArgs<T>& a, void* ws, cudaStream_t st);
+// energies[r] += the replica's mode energies left in ws by launch_energy_pass
+// (fixed order). Returns the number of kernels launched.
+int launch_energy_add(const ScanPlan& plan, const Reps& rp, const void* ws, double* energies,
+                      cudaStream_t st);
 
 }  // namespace qslab
