@@ -327,6 +327,9 @@ def run_ours(args):
             traffic = None
 
     phases = {k: float(np.mean([p[k] for p in ph32])) for k in qslab.TIMING_PHASES}
+    # measured arithmetic rates of this GPU (project microbenchmark), beside
+    # the peak derived from unit counts and the clock
+    mp = qslab.qslab_measure_peaks(local, stream.cuda_stream)
     line = {
         "metric": METRIC, "value": value, "unit": "particles/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms32_max,
@@ -347,7 +350,9 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                                    f"{smax:.0f} MHz ({peak_kind} max SM clock)",
-                     "work": "K*N*(24*(M+1)+20) FP32 instructions per launch"},
+                     "work": "K*N*(24*(M+1)+20) FP32 instructions per launch",
+                     "measured_tops": {k: v / 1e12 for k, v in mp.items()},
+                     "frac_of_measured_fp32_fma": achieved / (mp["fp32_fma"] / 1e12)},
         "e2e": {"value": job_throughput(N, ws, e2e_ms), "unit": "particles/s",
                 "h2d_bytes_per_step": int(N * 3 * 4 + N * 4),
                 "d2h_bytes_per_step": int(8 + N * 4 + N * 12)},

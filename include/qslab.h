@@ -109,6 +109,16 @@ int qslab_set_neutrality_tol(qslab_ctx* ctx, double tol);
  * 256). Results do not depend on it beyond rounding. */
 int qslab_set_tuning(qslab_ctx* ctx, int chunk, int modes_per_cta);
 
+/* Arithmetic throughput of the device (the paper has no counterpart; it
+ * gives the measured ceilings against which the k-space kernels' FP32
+ * arithmetic is judged). Runs four microbenchmark kernels on `stream` over
+ * 8 blocks per SM, each thread 16 independent dependency chains, timed with
+ * CUDA events (best of 3 after one warm-up), and writes lane operations per
+ * second to out4 (host, 4 doubles): [0] scalar FP32 FMA, [1] packed two-wide
+ * FP32 FMA (__ffma2_rn, counted as two), [2] FP64 FMA, [3] ex2.approx.f32.
+ * Allocates and frees a few KB of device memory; synchronises the stream. */
+int qslab_measure_peaks(int cuda_device, double* out4, void* stream);
+
 /* Launch-shape autotuner (the paper has no counterpart; the launch shape
  * changes no result beyond rounding). Times qslab_compute_batched() on the
  * given replicas (R = 1, offsets {0, N} and boxes = the context's box for a

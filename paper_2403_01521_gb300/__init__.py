@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True):
         "qslab_compute_energy": ([P, ctypes.c_int64, P, P, P, P], I),
         "qslab_compute_batched_energy": ([P, I, P, P, P, P, P, P], I),
         "qslab_compute_adjoint": ([P, P, P, P], I),
+        "qslab_measure_peaks": ([I, P, P], I),
         "qslab_compute_batched_virial": ([P, I, P, P, P, P, P, P, P, P, P], I),
         "qslab_compute_realspace_virial": ([P, ctypes.c_int64, P, P, P, P, P, P, P], I),
         "qslab_autotune": ([P, I, P, P, P, P, P, I, P, P], I),
@@ -203,6 +204,16 @@ def qslab_compute_virial(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr, v
                          stream_ptr):
     _check(load().qslab_compute_virial(h, N, pos_ptr, q_ptr, energy_ptr, phi_ptr, force_ptr,
                                        virial_ptr, stream_ptr), "qslab_compute_virial")
+
+
+def qslab_measure_peaks(device=0, stream_ptr=None):
+    """Measured lane-operation rates of the device (ops/s): FP32 FMA, packed
+    FP32 FMA (two per instruction), FP64 FMA, ex2.approx."""
+    out = np.zeros(4)
+    _check(load().qslab_measure_peaks(int(device), out.ctypes.data, stream_ptr),
+           "qslab_measure_peaks")
+    return {"fp32_fma": float(out[0]), "fp32_ffma2": float(out[1]), "fp64_fma": float(out[2]),
+            "ex2": float(out[3])}
 
 
 def qslab_compute_energy(h, N, pos_ptr, q_ptr, energy_ptr, stream_ptr):
