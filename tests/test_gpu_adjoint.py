@@ -189,3 +189,23 @@ def test_autograd_adjoint_mode(qslab, soe16):
     assert abs(grads[0][0] - grads[1][0]) <= 1e-12 * abs(grads[0][0])
     assert torch.equal(grads[0][1], grads[1][1]) and torch.equal(grads[0][2], grads[1][2])
     slab.close()
+
+
+@pytest.mark.parametrize("n", [1, 2])
+def test_fp64_tiny(qslab, soe16, n):
+    """N = 1 (neutralised by a uniform wall) and N = 2 with equal z."""
+    box = (9.0, 8.0, 4.0)
+    pos = np.array([[1.0, 2.0, 1.5], [6.0, 7.0, 1.5]])[:n]
+    q = np.array([1.0, -1.0])[:n]
+    kc = lattice.kcut_for_tail(0.5, 1e-8)
+    slab = qslab.QSlab(0, "fp64").configure(box, 0.5, soe16, kcut=kc)
+    if n == 1:
+        slab.set_walls(-1.0 / (box[0] * box[1]), 0.0)
+    p, qq = _t(pos, torch.float64), _t(q, torch.float64)
+    e_full, phi_full, F_full = slab.compute(p, qq)
+    e = slab.compute_energy(p, qq)
+    phi, F = slab.adjoint()
+    assert slab.status() == 0
+    assert abs(e.item() - e_full.item()) <= 1e-12 * max(abs(e_full.item()), 1e-300)
+    assert torch.equal(phi, phi_full) and torch.equal(F, F_full)
+    slab.close()

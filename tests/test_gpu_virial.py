@@ -235,3 +235,43 @@ def test_fp32_confined_m24(qslab):
     ref = virial.soe_full_virial(got["pos"], got["q"], sl.box, sl.alpha, *soe, kc=kc)
     ref["pos"] = got["pos"]
     _check_fp32(got["W"], ref)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_fp64_tiny_slabs(qslab, soe16, n):
+    """N = 1, 2, 3 (a lone particle is neutral only with walls; N = 2, 3 with
+    equal z for two of them): the virial against the oracle."""
+    box = (9.0, 8.0, 4.0)
+    pos = np.array([[1.0, 2.0, 1.5], [6.0, 7.0, 1.5], [3.0, 1.0, 3.0]])[:n]
+    q = np.array([1.0, -1.0, 0.0])[:n] if n > 1 else np.array([1.0])
+    if n == 3:
+        q = np.array([1.0, -2.0, 1.0])
+    sl = workloads.Slab("tiny", pos, q, box, 0.5, 16)
+    kc = lattice.kcut_for_tail(sl.alpha, 1e-8)
+    walls = None
+    if n == 1:
+        A = box[0] * box[1]
+        walls = (-0.5 / A, -0.5 / A, [], [], [])
+    got = _gpu_virial(qslab, sl, "fp64", soe16, kc=kc, walls=walls)
+    assert got["status"] == 0
+    ref = virial.soe_full_virial(pos, q, box, sl.alpha, *soe16, kc=kc)
+    W = ref["W"]
+    if walls is not None:
+        ps = virial.wall_virial(pos, q, box, walls[0], walls[1])
+        W = {k: W[k] + ps["W"][k] for k in ORDER}
+    assert _err(got["W"], W) <= FP64_TOL
+
+
+def test_fp64_metropolis_sample(qslab, soe16):
+    """The virial on the paper's Metropolis k-sampler (App. G): the oracle on
+    the modes the chain drew."""
+    sl = workloads.uniform_slab(1500, (36.0, 36.0, 12.0), 47, alpha=0.2)
+    slab = qslab.QSlab(0, "fp64").configure(sl.box, sl.alpha, soe16, rbe=(50, 3))
+    slab.sampler("metropolis", thin=2)
+    pos, q = _tensors(sl, torch.float64)
+    e, _, _, W = slab.compute_virial(pos, q)
+    assert slab.status() == 0
+    mx, my, _ = slab.sampled_modes()
+    ref = virial.soe_rbe_virial(sl.pos, sl.q, sl.box, sl.alpha, *soe16, mx, my, 50)
+    assert _err(W.cpu().numpy(), ref["W"]) <= FP64_TOL
+    slab.close()
