@@ -673,7 +673,8 @@ def profile_case(kind="single"):
     FP32 full-k workload (rc = 10); 'single+realspace' = both, one after
     the other; 'virial' = two qslab_compute_virial calls on the benchmark
     workload (N = 1e6); 'virial-small' = the same on N = 2.5e5 at the same
-    density (200 x 200 x 50), small enough for a full ncu capture."""
+    density (200 x 200 x 50), small enough for a full ncu capture; 'md' =
+    four Langevin steps of the 436-cation system of run_md (no graph)."""
     import torch
 
     import paper_2403_01521_gb300 as qslab
@@ -692,6 +693,25 @@ def profile_case(kind="single"):
         slab.check()
         torch.cuda.synchronize()
         print("profile case realspace done, E =", float(e.item()))
+        return 0
+    if kind == "md":
+        sl = workloads.cations_walls()
+        rng = np.random.default_rng(1)
+        g = (np.arange(8) + 0.5) * 12.5
+        gx, gy, gz = np.meshgrid(g, g, 2.0 + np.arange(7) * 4.3, indexing="ij")
+        pos0 = np.stack([gx.ravel(), gy.ravel(), gz.ravel()], 1)[:sl.N] + rng.uniform(-1, 1, (sl.N, 3))
+        s = qslab.QSlab(0, "fp32c").configure(sl.box, 0.3, soe, rbe=(100, 7), rcut=4 / 0.3)
+        s.sampler("metropolis", 1)
+        s.set_walls(*sl.walls)
+        s.md_configure(0.005, 1.0, 1.0, 1.0, (1.0, 1.0), (1.0, 0.5), 3)
+        pos = torch.tensor(pos0, device="cuda", dtype=torch.float32)
+        vel = torch.tensor(rng.normal(size=(sl.N, 3)), device="cuda", dtype=torch.float32)
+        q = torch.tensor(sl.q, device="cuda", dtype=torch.float32)
+        F, _ = s.md_forces(pos, q, vel)
+        s.md_step(pos, vel, q, F, 4)
+        s.check()
+        torch.cuda.synchronize()
+        print("profile case md done")
         return 0
     if kind in ("virial", "virial-small"):
         n = 1_000_000 if kind == "virial" else 250_000
@@ -741,7 +761,7 @@ def main():
                     help="skip the 512-replica batched measurement")
     ap.add_argument("--profile-case", nargs="?", const="single",
                     choices=["single", "batched", "realspace", "single+realspace", "virial",
-                             "virial-small"],
+                             "virial-small", "md"],
                     help="only run two FP32 random-batch calls (for profilers)")
     args = ap.parse_args()
     if args.profile_case:

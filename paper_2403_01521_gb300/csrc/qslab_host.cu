@@ -454,7 +454,9 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
     L = (int)(want < 32 ? 32 : (want > Lmax ? Lmax : want));
   }
   t.L = L;
-  t.L0 = 128;   // k = 0 chunks: short sequential loops, many threads
+  // k = 0 chunks: short sequential loops, many threads (no longer than the
+  // k-space chunks, so that small slabs get more, shorter chains)
+  t.L0 = std::min(128, L);
   // chunks, k = 0 chunks and carry groups per replica
   for (int r = 0; r < R; ++r) {
     RepInfo& ri = t.info[r];

@@ -28,6 +28,7 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kItems = 8;
 constexpr int kTile = kSortThreads * kItems;
 constexpr int kRadix = 256;
+static_assert(kRadix == kSortThreads, "small_sort_kernel gives each thread one digit");
 
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
@@ -139,6 +140,79 @@ scatter_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
   }
 }
 
+// At most one tile (N <= kTile): every pass in one CTA, with the ranking of
+// scatter_kernel and the digit offsets from a scan over the CTA's own
+// histogram; keys and payloads ping-pong between the two buffers in global
+// memory (L2-resident at this size), passes separated by barriers. Saves the
+// three launches per pass that dominate small sorts.
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads)
+small_sort_kernel(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int N, int passes) {
+  __shared__ uint32_t wcnt[kSortWarps][kRadix];
+  __shared__ uint32_t goff[kRadix];
+  __shared__ uint32_t wsum[kSortWarps];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  for (int p = 0; p < passes; ++p) {
+    const K* kin = (p & 1) ? k1 : k0;
+    const uint32_t* vin = (p & 1) ? v1 : v0;
+    K* kout = (p & 1) ? k0 : k1;
+    uint32_t* vout = (p & 1) ? v0 : v1;
+    const int shift = 8 * p;
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+      for (int ww = 0; ww < kSortWarps; ++ww) wcnt[ww][d] = 0;
+    __syncthreads();
+    const int base = w * 32 * kItems;
+    K key[kItems];
+    uint32_t val[kItems], loc[kItems], dig[kItems];
+    for (int s = 0; s < kItems; ++s) {
+      const int idx = base + s * 32 + lane;
+      const bool valid = idx < N;
+      key[s] = valid ? kin[idx] : (K)0;
+      val[s] = valid ? vin[idx] : 0u;
+      const unsigned d = valid ? ((unsigned)(key[s] >> shift) & 0xFFu) : 0x100u;
+      dig[s] = d;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const unsigned before = valid ? wcnt[w][d & 0xFFu] : 0u;
+      __syncwarp();
+      if (valid && lane == __ffs(peers) - 1) wcnt[w][d & 0xFFu] = before + __popc(peers);
+      __syncwarp();
+      loc[s] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    // per digit (one thread each): offsets of the warps, and the digit total
+    uint32_t tot = 0;
+    {
+      const int d = threadIdx.x;    // kSortThreads == kRadix
+      for (int ww = 0; ww < kSortWarps; ++ww) {
+        const uint32_t c = wcnt[ww][d];
+        wcnt[ww][d] = tot;
+        tot += c;
+      }
+    }
+    // exclusive scan of the digit totals over the CTA
+    uint32_t y = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
+    }
+    if (lane == 31) wsum[w] = y;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int j = 0; j < w; ++j) before += wsum[j];
+    goff[threadIdx.x] = before + y - tot;
+    __syncthreads();
+    for (int s = 0; s < kItems; ++s) {
+      if (dig[s] < 0x100u) {
+        const uint32_t pos = goff[dig[s]] + wcnt[w][dig[s]] + loc[s];
+        kout[pos] = key[s];
+        vout[pos] = val[s];
+      }
+    }
+    __syncthreads();   // the next pass reads what this one wrote
+  }
+}
+
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
@@ -163,6 +237,18 @@ void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes) {
 
 int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaStream_t st) {
   int cur = src;
+  if (N <= kTile) {
+    // small sorts: all passes in one CTA (buffer src is read first)
+    if (key_bytes == 4)
+      small_sort_kernel<uint32_t><<<1, kSortThreads, 0, st>>>(
+          static_cast<uint32_t*>(w.keys[cur]), w.vals[cur], static_cast<uint32_t*>(w.keys[cur ^ 1]),
+          w.vals[cur ^ 1], (int)N, passes);
+    else
+      small_sort_kernel<uint64_t><<<1, kSortThreads, 0, st>>>(
+          static_cast<uint64_t*>(w.keys[cur]), w.vals[cur], static_cast<uint64_t*>(w.keys[cur ^ 1]),
+          w.vals[cur ^ 1], (int)N, passes);
+    return (passes & 1) ? cur ^ 1 : cur;
+  }
   cudaMemsetAsync(w.totals, 0, (size_t)passes * kRadix * 4, st);
   for (int p = 0; p < passes; ++p) {
     const int shift = 8 * p;
