@@ -371,8 +371,8 @@ __global__ void mode_coef_kernel(Reps rp, int npc, const int32_t* list, int rbe,
       const double ar = pr.a_re[p], ai = pr.a_im[p];
       const double wr = pr.w_re[p], wi = pr.w_im[p];
       const double dr = ar * ar - ai * ai - k * k, di = 2 * ar * ai;   // a^2 - k^2
-      const double dd = dr * dr + di * di;
-      const double qr = (wr * dr + wi * di) / dd, qi = (wi * dr - wr * di) / dd;  // w/(a^2-k^2)
+      const double rdd = 1.0 / (dr * dr + di * di);
+      const double qr = (wr * dr + wi * di) * rdd, qi = (wi * dr - wr * di) * rdd;  // w/(a^2-k^2)
       ckk += pr.mult[p] * 2.0 * (ar * qr - ai * qi);     // sum over both nodes of 2 a w/(a^2-k^2)
       cr = -2.0 * k * qr * pr.mult[p] * gam;             // m_p gam c_{k,p}
       ci = -2.0 * k * qi * pr.mult[p] * gam;
@@ -439,6 +439,8 @@ __global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin,
                                                        double alpha, int32_t* sampled) {
   __shared__ int32_t spx[kMhBlock], spy[kMhBlock];
   __shared__ double slw[kMhBlock], slu[kMhBlock];
+  __shared__ int32_t s0x, s0y;
+  __shared__ double s0lw;
   const int rep = blockIdx.x;
   const RepInfo& ri = rp.info[rep];
   const double pi = 3.14159265358979323846;
@@ -450,7 +452,9 @@ __global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin,
   const uint64_t tag = kMhTag + ((uint64_t)rep << 32);
   int cx = 1, cy = 0;         // chain state (thread 0)
   double lw = 0.0;
-  if (threadIdx.x == 0) {
+  // the start state is searched by the last thread, concurrently with the
+  // first round of proposals, and handed to thread 0 after that round's barrier
+  if (threadIdx.x == blockDim.x - 1) {
     for (uint64_t a = 0; a < 64; ++a) {
       U64x4 c;
       c.v[0] = a; c.v[1] = 1; c.v[2] = counter; c.v[3] = tag;
@@ -461,7 +465,9 @@ __global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin,
       mh_propose(w.v[2], w.v[3], sdx, sdy, px, py);
       if (px != 0 || py != 0) { cx = px; cy = py; break; }
     }
-    lw = mh_log_weight(lwx, lwy, ri.mxmax, ri.mymax, cx, cy);
+    s0x = cx;
+    s0y = cy;
+    s0lw = mh_log_weight(lwx, lwy, ri.mxmax, ri.mymax, cx, cy);
   }
   const int64_t n = (int64_t)P * thin;
   for (int64_t b0 = 0; b0 < n; b0 += kMhBlock) {
@@ -479,6 +485,7 @@ __global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin,
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+      if (b0 == 0) { cx = s0x; cy = s0y; lw = s0lw; }
       for (int t = 0; t < cnt; ++t) {
         const int px = spx[t], py = spy[t];
         if (px != 0 || py != 0) {
