@@ -365,6 +365,7 @@ def run_ours(args):
     line["virial"] = run_virial(args, qslab, soe, dev, ws, sl, P, ms32_max)
     line["energy_only"] = run_energy_only(args, qslab, soe, dev, ws, sl, P, ms32_max)
     line["md"] = run_md(args, qslab, soe, dev, ws)
+    line["configs"] = run_configs(args, qslab, dev, ws, smax)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         t, desc, cores = cpu_oracle_sample(sl, soe, P, 1000, sample_modes=8)
         line["cpu_baseline"] = {"value": N / t, "unit": "particles/s", "cores": cores,
@@ -506,6 +507,76 @@ def run_md(args, qslab, soe, dev, ws):
     return {"workload": "436 cations in 100x100x30, top wall -0.0436, LJ, alpha=0.3, rc=4/alpha, "
                         "RBE P=100 (Metropolis), BAOAB dt=0.005, FP32C",
             "us_per_step": 1e3 * ms, "steps_per_s": ws / (ms * 1e-3), "steps": reps * chunk}
+
+
+def run_configs(args, qslab, dev, ws, smax):
+    """The other workloads of the paper's shape, full k-sum, one call per
+    step (median of CUDA-event timings after warm-up, L2 flushed): the
+    1000-particle parity slab, the N = 1e5 slab (FP32 vs FP64) and the
+    strongly confined N = 2e5 slab with M = 24, whose differentiable form
+    (energy-only forward, adjoint backward) is timed too. Particles/s per
+    precision and the recurrence kernel's share of the FP32 peak."""
+    import torch
+
+    import workloads
+    from paper_2403_01521_gb300.soe import load_soe
+    peak = SM_COUNT * FP32_LANES_PER_SM * smax * 1e6
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    cases = [("small_full N=1000 30x30x10 alpha=0.3 M=16 full-k", workloads.small_full(), 16),
+             ("fp32_full N=1e5 100x100x20 alpha=0.25 M=16 full-k", workloads.fp32_full(), 16),
+             ("confined N=2e5 200x200x2 alpha=0.2 M=24 full-k", workloads.confined(), 24)]
+    out = []
+    for name, sl, M in cases:
+        soe = load_soe(M)
+        kc = qslab.kcut_for_tail(sl.alpha, sl.tail)
+        row = {"workload": name, "N": sl.N}
+        for prec in ("fp32c", "fp64"):
+            dt = torch.float32 if prec == "fp32c" else torch.float64
+            s = qslab.QSlab(dev.index or 0, prec).configure(sl.box, sl.alpha, soe, kcut=kc)
+            qslab.qslab_set_timing(s.h, True)
+            pos = torch.tensor(sl.pos, device=dev, dtype=dt)
+            q = torch.tensor(sl.q, device=dev, dtype=dt)
+            outs = s.compute(pos, q)
+            steps = 5 if prec == "fp32c" else 2
+            ms, rec = [], []
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                s.compute(pos, q, *outs)
+                b.record()
+                torch.cuda.synchronize(dev)
+                ms.append(a.elapsed_time(b))
+                rec.append(qslab.qslab_get_timings(s.h)[0]["recurrence"])
+            s.check()
+            K = s.num_modes()
+            t = float(np.median(ms))
+            row[prec] = {"particles_per_s": sl.N / (t * 1e-3), "ms_per_call": t, "modes": K}
+            if prec == "fp32c":
+                work = algorithmic_instr(K, sl.N, M)
+                row[prec]["recurrence_frac"] = work / (float(np.median(rec)) * 1e-3) / peak
+            if prec == "fp32c" and M == 24:
+                # differentiable form: energy-only forward, adjoint backward
+                p_ = pos.clone().requires_grad_(True)
+                q_ = q.clone().requires_grad_(True)
+                for _ in range(2):
+                    qslab.slab_energy(p_, q_, s, adjoint=True).backward()
+                ts = []
+                for _ in range(3):
+                    flush.zero_()
+                    p_.grad = None
+                    q_.grad = None
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    qslab.slab_energy(p_, q_, s, adjoint=True).backward()
+                    b.record()
+                    torch.cuda.synchronize(dev)
+                    ts.append(a.elapsed_time(b))
+                row["autograd_adjoint_ms"] = float(np.median(ts))
+            s.close()
+        row["fp32c_vs_fp64"] = row["fp32c"]["particles_per_s"] / row["fp64"]["particles_per_s"]
+        out.append(row)
+    return out
 
 
 def run_energy_only(args, qslab, soe, dev, ws, sl, P, ms_plain):
