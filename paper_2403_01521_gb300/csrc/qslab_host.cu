@@ -478,11 +478,12 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
         ++ri.nzg;
       }
     }
-    // groups: 32 groups when the chain has 64 chunks or more, else one
+    // groups: about sqrt(nch) groups of about sqrt(nch) chunks (serial depth
+    // of the three carry phases about 3 sqrt(nch)); one group below 8 chunks
     ri.g0 = (int32_t)t.group_rep.size();
     ri.ng = 0;
     if (ri.nch > 0) {
-      const int G = ri.nch >= 64 ? 32 : 1;
+      const int G = ri.nch >= 8 ? std::max(2, (int)std::lround(std::sqrt((double)ri.nch))) : 1;
       const int g = (ri.nch + G - 1) / G;
       for (int a = 0; a < ri.nch; a += g) {
         t.gstart.push_back(ri.c0 + a);
