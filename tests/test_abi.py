@@ -46,6 +46,15 @@ def test_null_context_is_rejected(lib):
     assert lib.qslab_set_box(None, 1.0, 1.0, 1.0) == -1
     assert lib.qslab_compute(None, 10, None, None, None, None, None, None) == -1
     assert lib.qslab_num_modes(None) == -1
+    assert lib.qslab_compute_virial(None, 10, None, None, None, None, None, None, None) == -1
+    assert lib.qslab_compute_batched_virial(None, 1, None, None, None, None, None, None, None,
+                                            None, None) == -1
+    assert lib.qslab_compute_realspace_virial(None, 10, None, None, None, None, None, None,
+                                              None) == -1
+    assert lib.qslab_compute_energy(None, 10, None, None, None, None) == -1
+    assert lib.qslab_compute_batched_energy(None, 1, None, None, None, None, None, None) == -1
+    assert lib.qslab_compute_adjoint(None, None, None, None) == -1
+    assert lib.qslab_measure_peaks(0, None, None) == -1
 
 
 def test_library_is_in_tree():
