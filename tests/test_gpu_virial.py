@@ -275,3 +275,35 @@ def test_fp64_metropolis_sample(qslab, soe16):
     ref = virial.soe_rbe_virial(sl.pos, sl.q, sl.box, sl.alpha, *soe16, mx, my, 50)
     assert _err(W.cpu().numpy(), ref["W"]) <= FP64_TOL
     slab.close()
+
+
+def test_fp64_virial_theorem_with_walls(qslab):
+    """Particles with net charge between charged walls (uniform parts and two
+    Fourier modes), long range plus real space on the GPU: trace W = E, which
+    needs the walls to move with the box, the top wall's L_z term included."""
+    from paper_2403_01521_gb300.soe import load_soe
+    soe = load_soe(16, "accurate")
+    rng = np.random.default_rng(48)
+    n = 600
+    box = (30.0, 30.0, 10.0)
+    pos = np.column_stack([rng.random(n) * box[0], rng.random(n) * box[1], rng.random(n) * box[2]])
+    q = np.where(rng.random(n) < 0.6, 1.0, -1.0)
+    A = box[0] * box[1]
+    Q = q.sum()
+    sb0, st0 = -0.3 * Q / A, -0.7 * Q / A
+    modes = [(1, 0), (1, 2)]
+    sb = [0.004 + 0.002j, -0.003j]
+    st = [0.002 - 0.001j, 0.003 + 0.001j]
+    alpha = 0.5
+    kc = lattice.kcut_for_tail(alpha, 1e-12)
+    slab = qslab.QSlab(0, "fp64").configure(box, alpha, soe, kcut=kc, rcut=9.2)
+    slab.set_walls(sb0, st0, modes, sb, st)
+    pt = torch.tensor(pos, device="cuda")
+    qt = torch.tensor(q, device="cuda")
+    e, _, _, W = slab.compute_virial(pt, qt)
+    es, _, _, Ws = slab.compute_realspace_virial(pt, qt)
+    assert slab.status() == 0
+    Wt = W.cpu().numpy() + Ws.cpu().numpy()
+    E = float(e.item() + es.item())
+    assert abs(Wt[0] + Wt[1] + Wt[2] - E) <= 1e-8 * np.abs(Wt[:3]).max()
+    slab.close()
