@@ -750,7 +750,7 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
     launch_kspace<T>(P.sp, rp, modes, c->pairs, zs, dz, qs, xh, yh, trig, agg, carry, dec, part,
                      st, ev ? ev + 3 : nullptr, 1);
     VirArgs<T> va{P.sp, rp, modes, c->pairs, c->alpha, rbe ? 1 : 0, zs, dz, qs, xh, yh, trig,
-                  carry, pos, q, nullptr, energies, nullptr, c->walls, nullptr};
+                  carry, agg, pos, q, nullptr, energies, nullptr, c->walls, nullptr};
     nl += 7 + launch_energy_pass<T>(va, ws + P.off_vir, st);
     if (ev) cudaEventRecord(ev[5], st);
     QS_CUDA(cudaStreamWaitEvent(st, c->join, 0));
@@ -779,7 +779,7 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
     // tables, forward carries, forces and energies
     VirArgs<T> va{P.sp, rp, modes, c->pairs, c->alpha, rbe ? 1 : 0, zs, dz, qs, xh, yh,
                   sizeof(T) == 4 ? reinterpret_cast<const float2*>(tab + tb.o_trig) : nullptr,
-                  carry, pos, q, force, energies,
+                  carry, agg, pos, q, force, energies,
                   reinterpret_cast<const double*>(tab + tb.o_vdiag), c->walls, virial};
     nl += launch_virial<T>(va, ws + P.off_vir, st);
   }

@@ -255,13 +255,62 @@ __global__ void __launch_bounds__(kChainT) vir_zchain_kernel(VirArgs<T> a, const
 // before anything is summed over particles; D(c, m) = sum over the chunk of
 // T_i, compensated (Kahan). With the energy coefficients (ck, cp of the mode
 // table) and no z-weighted state, D(c, m) is the chunk's share of the mode's
-// pair energy gam Re sum_beta c_beta S_beta (the energy-only call).
+// pair energy gam Re sum_beta c_beta S_beta (the energy-only call); there the
+// pairs are split: the pairs within the chunk come from recurrences started
+// from zero (small states, small rounding), the pairs with earlier chunks
+// from one product per state of the carry G_c and pass A's backward
+// aggregate, sum_{i in c} u_i e^{-beta (z_i - z_start)}, times the decay
+// e^{-beta dz_start} to the carry's reference point.
 template <typename T>
 __device__ __forceinline__ void kahan_add(T& s, T& c, T x) {
   const T y = x - c;
   const T t = s + y;
   c = (t - s) - y;
   s = t;
+}
+
+// The pairs of chunk c with all earlier particles of its slab, for the
+// energy: sum_i Re[conj(u_i) e^{-beta (z_i - z_{s-1})} G_c] for beta = k and
+// sum_i (a_i, b_i) e^{-beta (z_i - z_{s-1})} (G^a_c, G^b_c) for the pairs,
+// with the coefficients: from the carry G_c (at z_{s-1}) and the backward
+// aggregate A_c = sum_i u_i e^{-beta (z_i - z_s)}, joined by e^{-beta dz_s}.
+// decay(p) gives e^{-a_p dz_s} of the chunk's first particle.
+template <typename T, int NP, typename Decay>
+__device__ inline double cross_energy(const VirArgs<T>& a, int c, int m, T kk, Decay decay,
+                                      const double* vc, size_t mg, size_t ks) {
+  const CRange ch = kchunk(a.rp, c);
+  if (ch.first) return 0.0;           // no earlier particles: carry 0
+  const int Kpad = a.rp.Kpad;
+  const size_t cstride = (size_t)a.plan.nstates * Kpad;
+  const size_t dirstride = (size_t)a.rp.nchunks * cstride;
+  const Cplx<T>* G = a.carry + (size_t)c * cstride + m;
+  const Cplx<T>* A = a.agg + dirstride + (size_t)c * cstride + m;
+  const double dz0 = (double)a.dz[ch.start];
+  // beta = k: Re[G e^{-k dz} conj(A)]
+  const double ek = exp(-(double)kk * dz0);
+  const Cplx<T> g = G[0], ab = A[0];
+  double D = vc[mg] * ek * ((double)g.re * (double)ab.re + (double)g.im * (double)ab.im);
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const Cplx<T> d = decay(p);
+    const Cplx<T> gA = G[(size_t)(1 + 2 * p) * Kpad], gB = G[(size_t)(2 + 2 * p) * Kpad];
+    const Cplx<T> aA = A[(size_t)(1 + 2 * p) * Kpad], aB = A[(size_t)(2 + 2 * p) * Kpad];
+    // s = d (gA aA + gB aB), complex; add Re(v s)
+    const double pr = (double)gA.re * aA.re - (double)gA.im * aA.im + (double)gB.re * aB.re -
+                      (double)gB.im * aB.im;
+    const double pi = (double)gA.re * aA.im + (double)gA.im * aA.re + (double)gB.re * aB.im +
+                      (double)gB.im * aB.re;
+    const double sr = (double)d.re * pr - (double)d.im * pi;
+    const double si = (double)d.re * pi + (double)d.im * pr;
+    D += vc[(2 + 2 * (size_t)p) * ks + mg] * sr - vc[(3 + 2 * (size_t)p) * ks + mg] * si;
+  }
+  return D;
+}
+
+template <typename T, int NP>
+__device__ inline double cross_pairs(const VirArgs<T>& a, int c, int m, T kk, const Cplx<T>* tab,
+                                     const double* vc, size_t mg, size_t ks) {
+  return cross_energy<T, NP>(a, c, m, kk, [tab](int p) { return tab[p]; }, vc, mg, ks);
 }
 
 template <typename T, int NP, bool WZ>
@@ -291,12 +340,13 @@ __global__ void vir_pass_kernel(VirArgs<T> a, const double* vc, const Cplx<T>* g
   T vpr[NP], vpi[NP];
   const size_t cstride = (size_t)a.plan.nstates * Kpad;
   const Cplx<T>* cin = a.carry + (size_t)c * cstride + m;
-  Cplx<T> g0 = cin[0];
+  const Cplx<T> zc = {0, 0};
+  Cplx<T> g0 = WZ ? cin[0] : zc;
   Cplx<T> ga[NP], gb[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    ga[p] = cin[(size_t)(1 + 2 * p) * Kpad];
-    gb[p] = cin[(size_t)(2 + 2 * p) * Kpad];
+    ga[p] = WZ ? cin[(size_t)(1 + 2 * p) * Kpad] : zc;
+    gb[p] = WZ ? cin[(size_t)(2 + 2 * p) * Kpad] : zc;
     vpr[p] = (T)vc[(2 + 2 * (size_t)p) * ks + mg];
     vpi[p] = (T)vc[(3 + 2 * (size_t)p) * ks + mg];
   }
@@ -336,7 +386,9 @@ __global__ void vir_pass_kernel(VirArgs<T> a, const double* vc, const Cplx<T>* g
     }
     kahan_add(acc, cmp, fma(av, Ya, bv * Yb));
   }
-  dpart[(size_t)c * Kpad + m] = (double)acc - (double)cmp;
+  double D = (double)acc - (double)cmp;
+  if (!WZ) D += cross_pairs<T, NP>(a, c, m, kk, tab, vc, mg, ks);
+  dpart[(size_t)c * Kpad + m] = D;
 }
 
 // The same pass on the FP32 path with two SOE pairs per 64-bit register
@@ -370,12 +422,15 @@ __global__ void vir_pass_f2_kernel(VirArgs<float> a, const double* vc, const Cpl
   const float vz = WZ ? (float)vc[ks + mg] : 0.0f;
   const size_t cstride = (size_t)a.plan.nstates * Kpad;
   const Cplx<float>* cin = a.carry + (size_t)c * cstride + m;
-  Cplx<float> g0 = cin[0];
+  const Cplx<float> zc = {0.0f, 0.0f};
+  Cplx<float> g0 = WZ ? cin[0] : zc;
   float2 Ra[NP / 2], Ia[NP / 2], Rb[NP / 2], Ib[NP / 2], Vr[NP / 2], nVi[NP / 2];
 #pragma unroll
   for (int q = 0; q < NP / 2; ++q) {
-    const Cplx<float> a0 = cin[(size_t)(1 + 4 * q) * Kpad], b0 = cin[(size_t)(2 + 4 * q) * Kpad];
-    const Cplx<float> a1 = cin[(size_t)(3 + 4 * q) * Kpad], b1 = cin[(size_t)(4 + 4 * q) * Kpad];
+    const Cplx<float> a0 = WZ ? cin[(size_t)(1 + 4 * q) * Kpad] : zc;
+    const Cplx<float> b0 = WZ ? cin[(size_t)(2 + 4 * q) * Kpad] : zc;
+    const Cplx<float> a1 = WZ ? cin[(size_t)(3 + 4 * q) * Kpad] : zc;
+    const Cplx<float> b1 = WZ ? cin[(size_t)(4 + 4 * q) * Kpad] : zc;
     Ra[q] = make_float2(a0.re, a1.re); Ia[q] = make_float2(a0.im, a1.im);
     Rb[q] = make_float2(b0.re, b1.re); Ib[q] = make_float2(b0.im, b1.im);
     const size_t p0 = 2 * q, p1 = 2 * q + 1;
@@ -423,7 +478,12 @@ __global__ void vir_pass_f2_kernel(VirArgs<float> a, const double* vc, const Cpl
     yb += Yb.x + Yb.y;
     kahan_add(acc, cmp, fmaf(av, ya, bv * yb));
   }
-  dpart[(size_t)c * Kpad + m] = (double)acc - (double)cmp;
+  double D = (double)acc - (double)cmp;
+  if (!WZ)
+    D += cross_energy<float, NP>(
+        a, c, m, kk,
+        [tabf](int p) { return Cplx<float>{tabf[p], tabf[NP + p]}; }, vc, mg, ks);
+  dpart[(size_t)c * Kpad + m] = D;
 }
 
 // ------------------------------------------------------- fixed-order sums

@@ -29,6 +29,7 @@ struct VirArgs {
   const typename PhaseT<T>::type* yh;
   const float2* trig;            // FP32: [256] (cos, sin) of j/256 turns
   const Cplx<T>* carry;          // [2][nchunks][nstates][Kpad] (forward half used)
+  const Cplx<T>* agg;            // pass A's aggregates, same layout (energy pass: backward half)
   const T* pos;                  // caller's order: N x 3, q: N, force: N x 3
   const T* q;
   const T* force;
