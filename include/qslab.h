@@ -430,8 +430,9 @@ int qslab_last_status(qslab_ctx* ctx);
 
 /* Per-phase timings of the latest compute(), measured with CUDA events on its
  * stream while timing is enabled (qslab_set_timing(ctx, 1)). ms8 receives, in
- * milliseconds: [0] checks + z-sort + gather, [1] mode table (RBE sampler),
- * [2] k-space chunk aggregates, [3] carries, [4] k-space recurrences with the
+ * milliseconds: [0] checks + z-sort + gather, [1] the wait for the mode
+ * table (sampler and coefficients; built on an internal stream concurrently
+ * with [0], so this is the part that [0] does not cover), [2] k-space chunk aggregates, [3] carries, [4] k-space recurrences with the
  * gather, [5] k = 0 term (it runs on an internal stream concurrently with
  * [1]-[4]), [6] combine + energy, [7] total. *launches (may be NULL)
  * receives the number of kernels the call launched. Synchronises. */

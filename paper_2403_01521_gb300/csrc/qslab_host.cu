@@ -111,6 +111,15 @@ struct qslab_ctx {
   // caller's stream with these events (capturable in a CUDA graph)
   cudaStream_t side = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
+  // an MD force pass runs the real-space call on its own side stream,
+  // concurrently with the long-range call (their outputs are disjoint)
+  cudaStream_t rs_side = nullptr;
+  cudaEvent_t rs_fork = nullptr, rs_join = nullptr;
+  // the mode tables (sampling, Metropolis chain, coefficients) need only
+  // the call counter and the configuration's tables: they are built on a
+  // third side stream, concurrently with the sort and the gather
+  cudaStream_t tab_side = nullptr;
+  cudaEvent_t tab_fork = nullptr, tab_join = nullptr;
 };
 
 namespace {
@@ -450,8 +459,10 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
   if (L <= 0) {
     const int64_t target = (2 * 152 + t.nkr - 1) / t.nkr;
     int64_t want = (N + target - 1) / target;
-    want = ((want + 31) / 32) * 32;
-    L = (int)(want < 32 ? 32 : (want > Lmax ? Lmax : want));
+    // small slabs (N below about 5000): chunks of 16, whose shorter serial
+    // loops beat the extra carry work there; else a multiple of 32
+    want = want <= 16 ? 16 : ((want + 31) / 32) * 32;
+    L = (int)(want > Lmax ? Lmax : want);
   }
   t.L = L;
   // k = 0 chunks: short sequential loops, many threads (no longer than the
@@ -706,6 +717,28 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   if (tol < -1.0) tol = 64.0 * (sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08);
   launch_check_neutral(rp, sums, tol, c->walls.on ? c->walls.sb0 : 0.0,
                        c->walls.on ? c->walls.st0 : 0.0, c->d_status, rbe ? c->d_ctr : nullptr, st);
+  // mode tables: once per configuration for the full k-sum, every call for
+  // RBE (after the counter's advance above), on the table stream
+  const bool want_modes = rbe || !c->coef_ready;
+  if (want_modes) {
+    const double* cdf = reinterpret_cast<const double*>(tab + tb.o_cdf);
+    int32_t* sampled = rbe ? reinterpret_cast<int32_t*>(tab + tb.o_sampled) : nullptr;
+    const bool mh = rbe && c->sampler == QSLAB_SAMPLER_METROPOLIS;
+    QS_CUDA(cudaEventRecord(c->tab_fork, st));
+    QS_CUDA(cudaStreamWaitEvent(c->tab_side, c->tab_fork, 0));
+    if (mh) {
+      launch_mh_chain(rp, c->P, c->mh_thin, c->seed, c->d_ctr, cdf, c->alpha, sampled,
+                      c->tab_side);
+      ++nl;
+    }
+    launch_mode_coef<T>(rp, c->npc, reinterpret_cast<const int32_t*>(tab + tb.o_list),
+                        rbe ? (mh ? 2 : 1) : 0, c->seed, c->d_ctr, cdf, c->pairs, c->alpha, modes,
+                        sampled, c->tab_side);
+    ++nl;
+    QS_CUDA(cudaEventRecord(c->tab_join, c->tab_side));
+    if (rbe) c->have_sample = true;
+    else c->coef_ready = true;
+  }
   int r = radix_sort(sw, N, (int)sizeof(T), (int)sizeof(T), 0, st);
   nl += 2 + 3 * (int)sizeof(T);   // prepare, check + 3 kernels per sort pass
   if (R > 1) {
@@ -725,22 +758,7 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   nl += 6;
   if (ev) cudaEventRecord(ev[8], c->side);
   QS_CUDA(cudaEventRecord(c->join, c->side));
-  // mode tables: once per configuration for the full k-sum, every call for RBE
-  if (rbe || !c->coef_ready) {
-    const double* cdf = reinterpret_cast<const double*>(tab + tb.o_cdf);
-    int32_t* sampled = rbe ? reinterpret_cast<int32_t*>(tab + tb.o_sampled) : nullptr;
-    const bool mh = rbe && c->sampler == QSLAB_SAMPLER_METROPOLIS;
-    if (mh) {
-      launch_mh_chain(rp, c->P, c->mh_thin, c->seed, c->d_ctr, cdf, c->alpha, sampled, st);
-      ++nl;
-    }
-    launch_mode_coef<T>(rp, c->npc, reinterpret_cast<const int32_t*>(tab + tb.o_list),
-                        rbe ? (mh ? 2 : 1) : 0, c->seed, c->d_ctr, cdf, c->pairs, c->alpha, modes,
-                        sampled, st);
-    ++nl;
-    if (rbe) c->have_sample = true;
-    else c->coef_ready = true;
-  }
+  if (want_modes) QS_CUDA(cudaStreamWaitEvent(st, c->tab_join, 0));
   if (ev) cudaEventRecord(ev[2], st);
   const float2* trig = sizeof(T) == 4 ? reinterpret_cast<const float2*>(tab + tb.o_trig) : nullptr;
   if (what == 1) {
@@ -890,7 +908,13 @@ int qslab_create(qslab_ctx** out, int cuda_device, int prec) {
   for (auto& ev : c->ev) cudaEventCreate(&ev);
   if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->rs_side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->rs_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->rs_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->tab_side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->tab_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->tab_join, cudaEventDisableTiming) != cudaSuccess) {
     qslab_destroy(c);
     return QSLAB_ERR_CUDA;
   }
@@ -912,6 +936,12 @@ void qslab_destroy(qslab_ctx* c) {
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->join) cudaEventDestroy(c->join);
   if (c->side) cudaStreamDestroy(c->side);
+  if (c->rs_fork) cudaEventDestroy(c->rs_fork);
+  if (c->rs_join) cudaEventDestroy(c->rs_join);
+  if (c->rs_side) cudaStreamDestroy(c->rs_side);
+  if (c->tab_fork) cudaEventDestroy(c->tab_fork);
+  if (c->tab_join) cudaEventDestroy(c->tab_join);
+  if (c->tab_side) cudaStreamDestroy(c->tab_side);
   delete c;
 }
 
@@ -1314,13 +1344,20 @@ int md_buffers(qslab_ctx* c, int64_t N, MDBufs& b) {
 }
 
 // Forces at pos (long range, real space with LJ pairs, LJ walls) into
-// `force`; with kick, the closing half kick of a step.
+// `force`; with kick, the closing half kick of a step. The real-space call
+// runs on the context's second side stream, forked from `st` and joined
+// back before the closing kernel, so that it overlaps the long-range call.
 template <typename T>
 int md_force_pass(qslab_ctx* c, const Plan& P, int64_t N, const MDBufs& b, const void* pos,
                   const void* q, void* vel, void* force, bool kick, cudaStream_t st) {
-  int rc = dispatch(c, P, pos, q, b.e_lr, nullptr, b.flr, st);
-  if (rc) return rc;
-  rc = realspace_call(c, N, pos, q, b.e_rs, nullptr, b.frs, st, c->lj_eps, c->lj_sigma);
+  QS_CUDA(cudaEventRecord(c->rs_fork, st));
+  QS_CUDA(cudaStreamWaitEvent(c->rs_side, c->rs_fork, 0));
+  int rc = realspace_call(c, N, pos, q, b.e_rs, nullptr, b.frs, c->rs_side, c->lj_eps,
+                          c->lj_sigma);
+  // joined on every path, so that a captured stream never ends with the fork open
+  QS_CUDA(cudaEventRecord(c->rs_join, c->rs_side));
+  if (!rc) rc = dispatch(c, P, pos, q, b.e_lr, nullptr, b.flr, st);
+  QS_CUDA(cudaStreamWaitEvent(st, c->rs_join, 0));
   if (rc) return rc;
   launch_md_end<T>(N, c->md, static_cast<const T*>(pos), static_cast<T*>(vel),
                    static_cast<const T*>(b.flr), static_cast<const T*>(b.frs),

@@ -155,7 +155,13 @@ __global__ void md_energies_kernel(int nb, const double* part, const double* e_l
 template <typename T>
 void launch_md_begin(int64_t N, const MDDev& p, T* pos, T* vel, const T* force,
                      const uint64_t* ctr, cudaStream_t st) {
-  md_begin_kernel<T><<<md_blocks(N), kMdThreads, 0, st>>>(N, p, pos, vel, force, ctr);
+  // the thermostat's normals are FP64 (Box-Muller), and an SM issues FP64 at
+  // a small fraction of its FP32 rate: 64-thread blocks spread a small N
+  // over as many SMs as possible (each particle's result is independent of
+  // the thread that computes it)
+  int64_t b = (N + 63) / 64;
+  if (b > 152 * 16) b = 152 * 16;
+  md_begin_kernel<T><<<(int)b, 64, 0, st>>>(N, p, pos, vel, force, ctr);
 }
 
 template <typename T>

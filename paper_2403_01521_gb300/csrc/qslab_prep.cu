@@ -304,21 +304,28 @@ __device__ __forceinline__ double uniform53(uint64_t w) {
   return (double)(w >> 11) * 1.1102230246251565e-16;   // 2^-53
 }
 
-// Fill the mode tables; thread = (mode, replica). Full k-sum: (mx, my) from
+// Fill the mode tables, per (mode, replica). Full k-sum: (mx, my) from
 // the replica's half-plane list, weight 2 (k and -k), gam = (pi/A) C_k 2.
 // Random batch: (mx, my) drawn here (Philox4x64-10 with counter
 // (m, attempt, call, tag + replica * 2^32) and key (seed, 0); words 0,1 then
 // 2,3 are inverted through the replica's per-axis cumulative tables; the
 // origin is rejected), gam = (pi/A) (H/P) 2 alpha/(sqrt(pi) k) (Eq. 4.7 with
 // 4.9: the Gaussian of C_k cancels against e^{k^2/(4 alpha^2)}).
-template <typename T>
-__global__ void mode_coef_kernel(Reps rp, int npc, const int32_t* list, int rbe, uint64_t seed,
-                                 const uint64_t* ctr, const double* cdf, PairTab pr,
-                                 double alpha, ModeTab<T> mt, int32_t* sampled) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+// A group of G lanes serves one mode: every lane finds the mode and its
+// constants (the same values), lane g takes pairs g, g + G, ..., and the
+// group sums the pair terms with shuffles, so that each warp issues a few
+// pairs' FP64 work instead of all of them.
+template <typename T, int G>
+__global__ void __launch_bounds__(64) mode_coef_kernel(Reps rp, int npc, const int32_t* list,
+                                                       int rbe, uint64_t seed, const uint64_t* ctr,
+                                                       const double* cdf, PairTab pr, double alpha,
+                                                       ModeTab<T> mt, int32_t* sampled) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = tid / G, g = tid % G;
   const int rep = blockIdx.y;
   const int Kpad = rp.Kpad;
-  if (m >= Kpad) return;
+  if (m >= Kpad) return;                  // whole groups: Kpad G is a multiple of the block
+  const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << ((threadIdx.x & 31) & ~(G - 1));
   const RepInfo& ri = rp.info[rep];
   const int K = ri.K;
   const double Lx = ri.Lx, Ly = ri.Ly;
@@ -350,7 +357,7 @@ __global__ void mode_coef_kernel(Reps rp, int npc, const int32_t* list, int rbe,
         const int by = upper_index(cdfy, ri.ny, uniform53(r.v[3])) - ri.mymax;
         if (bx != 0 || by != 0) { mx = bx; my = by; break; }
       }
-      if (sampled) {
+      if (sampled && g == 0) {
         sampled[2 * ((size_t)rep * K + m)] = mx;
         sampled[2 * ((size_t)rep * K + m) + 1] = my;
       }
@@ -365,7 +372,7 @@ __global__ void mode_coef_kernel(Reps rp, int npc, const int32_t* list, int rbe,
               : pi / (Lx * Ly) * 2.0 * (2.0 * alpha * exp(-k * k / (4.0 * alpha * alpha)) / (sqpi * k));
   }
   double ckk = 0.0, sY = 0.0, sZ = 0.0;
-  for (int p = 0; p < npc; ++p) {
+  for (int p = g; p < npc; p += G) {
     double cr = 0, ci = 0, br = 0, bi = 0;
     if (p < pr.np) {
       const double ar = pr.a_re[p], ai = pr.a_im[p];
@@ -386,6 +393,12 @@ __global__ void mode_coef_kernel(Reps rp, int npc, const int32_t* list, int rbe,
     mt.cp[((size_t)2 * npc + p) * ks + mg] = (T)br;
     mt.cp[((size_t)3 * npc + p) * ks + mg] = (T)bi;
   }
+  for (int o = G >> 1; o; o >>= 1) {
+    ckk += __shfl_xor_sync(gmask, ckk, o, G);
+    sY += __shfl_xor_sync(gmask, sY, o, G);
+    sZ += __shfl_xor_sync(gmask, sZ, o, G);
+  }
+  if (g != 0) return;
   const double ck = gam * ckk;
   mt.mx[mg] = mx;
   mt.my[mg] = my;
@@ -401,6 +414,7 @@ __global__ void mode_coef_kernel(Reps rp, int npc, const int32_t* list, int rbe,
 // ================================================= Metropolis k-sampler
 
 constexpr int kMhBlock = 1024;          // chain steps prepared per round
+constexpr int kMhWin = 8;               // earlier states with precomputed decisions
 constexpr uint64_t kMhTag = 0x4D484731ull;
 
 // One proposal of App. G from two words: Box-Muller normals (u1 = 1 -
@@ -432,6 +446,12 @@ __device__ __forceinline__ double mh_log_weight(const double* lwx, const double*
 // its log-weight and log u) into shared memory; thread 0 then runs the
 // chain through them: the origin is rejected (h = 0 there), any other
 // proposal accepted when d >= 0 or log u < d, d the log acceptance ratio.
+// The chain's state is always an earlier proposal of the round (or the state
+// it entered the round with), so the CTA first decides in parallel, for every
+// step t and each of the kMhWin steps j before it, whether t would be
+// accepted from state j (the same FP64 operations with lw = log-weight of
+// j); thread 0 then reads those bits and computes a decision itself only
+// after kMhWin rejections in a row or before the round's first acceptance.
 // Counters: start attempts (a, 1, ctr[1], tag + rep 2^32), steps
 // (eta - 1, 0, ctr[1], tag + rep 2^32), key (seed, 0).
 __global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin, uint64_t seed,
@@ -439,6 +459,7 @@ __global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin,
                                                        double alpha, int32_t* sampled) {
   __shared__ int32_t spx[kMhBlock], spy[kMhBlock];
   __shared__ double slw[kMhBlock], slu[kMhBlock];
+  __shared__ uint8_t sacc[kMhBlock];      // bit w: accepted from state t - 1 - w
   __shared__ int32_t s0x, s0y;
   __shared__ double s0lw;
   const int rep = blockIdx.x;
@@ -452,6 +473,8 @@ __global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin,
   const uint64_t tag = kMhTag + ((uint64_t)rep << 32);
   int cx = 1, cy = 0;         // chain state (thread 0)
   double lw = 0.0;
+  int left = thin;            // steps to the next kept state (thread 0)
+  size_t jo = (size_t)rep * P;
   // the start state is searched by the last thread, concurrently with the
   // first round of proposals, and handed to thread 0 after that round's barrier
   if (threadIdx.x == blockDim.x - 1) {
@@ -484,19 +507,43 @@ __global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin,
       slu[t] = log(uniform53(w.v[2]));      // -inf for u = 0
     }
     __syncthreads();
+    // decisions from the kMhWin states before each step: groups of kMhWin
+    // lanes per step, one ballot per warp (the loop bound is warp-uniform)
+    for (int e0 = 0; e0 < cnt * kMhWin; e0 += blockDim.x) {
+      const int e = e0 + threadIdx.x;
+      const int t = e / kMhWin, j = t - 1 - e % kMhWin;
+      bool acc = false;
+      if (e < cnt * kMhWin && j >= 0) {
+        const double d = slw[t] - slw[j];
+        acc = d >= 0.0 || slu[t] < d;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, acc);
+      const int lane = threadIdx.x & 31;
+      if (e < cnt * kMhWin && lane % kMhWin == 0)
+        sacc[t] = (uint8_t)((bal >> lane) & ((1u << kMhWin) - 1u));
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       if (b0 == 0) { cx = s0x; cy = s0y; lw = s0lw; }
+      int jc = -1;                // the state's step in this round; -1: from before it
       for (int t = 0; t < cnt; ++t) {
         const int px = spx[t], py = spy[t];
         if (px != 0 || py != 0) {
-          const double d = slw[t] - lw;
-          if (d >= 0.0 || slu[t] < d) { cx = px; cy = py; lw = slw[t]; }
+          const int dist = t - 1 - jc;
+          bool acc;
+          if (jc >= 0 && dist < kMhWin) {
+            acc = (sacc[t] >> dist) & 1u;
+          } else {
+            const double d = slw[t] - lw;
+            acc = d >= 0.0 || slu[t] < d;
+          }
+          if (acc) { cx = px; cy = py; lw = slw[t]; jc = t; }
         }
-        const int64_t eta = b0 + t + 1;
-        if (eta % thin == 0) {
-          const size_t j = (size_t)rep * P + (size_t)(eta / thin - 1);
-          sampled[2 * j] = cx;
-          sampled[2 * j + 1] = cy;
+        if (--left == 0) {          // every thin-th state is kept
+          left = thin;
+          sampled[2 * jo] = cx;
+          sampled[2 * jo + 1] = cy;
+          ++jo;
         }
       }
     }
@@ -513,9 +560,20 @@ template <typename T>
 void launch_mode_coef(const Reps& rp, int npc, const int32_t* list, int rbe, uint64_t seed,
                       const uint64_t* ctr, const double* cdf, const PairTab& pairs,
                       double alpha, ModeTab<T> modes, int32_t* sampled, cudaStream_t st) {
-  dim3 grid((rp.Kpad + 127) / 128, rp.R);
-  mode_coef_kernel<T><<<grid, 128, 0, st>>>(rp, npc, list, rbe, seed, ctr, cdf, pairs, alpha,
-                                            modes, sampled);
+  // Kpad is a multiple of 32, so Kpad G threads fill 64-thread blocks exactly
+  if (npc <= 4) {
+    dim3 grid(rp.Kpad * 4 / 64, rp.R);
+    mode_coef_kernel<T, 4><<<grid, 64, 0, st>>>(rp, npc, list, rbe, seed, ctr, cdf, pairs, alpha,
+                                                modes, sampled);
+  } else if (npc <= 8) {
+    dim3 grid(rp.Kpad * 8 / 64, rp.R);
+    mode_coef_kernel<T, 8><<<grid, 64, 0, st>>>(rp, npc, list, rbe, seed, ctr, cdf, pairs, alpha,
+                                                modes, sampled);
+  } else {
+    dim3 grid(rp.Kpad * 16 / 64, rp.R);
+    mode_coef_kernel<T, 16><<<grid, 64, 0, st>>>(rp, npc, list, rbe, seed, ctr, cdf, pairs,
+                                                 alpha, modes, sampled);
+  }
 }
 
 // ============================================================ instantiations

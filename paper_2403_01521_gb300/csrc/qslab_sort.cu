@@ -28,7 +28,6 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kItems = 8;
 constexpr int kTile = kSortThreads * kItems;
 constexpr int kRadix = 256;
-static_assert(kRadix == kSortThreads, "small_sort_kernel gives each thread one digit");
 
 template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
@@ -140,76 +139,49 @@ scatter_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
   }
 }
 
-// At most one tile (N <= kTile): every pass in one CTA, with the ranking of
-// scatter_kernel and the digit offsets from a scan over the CTA's own
-// histogram; keys and payloads ping-pong between the two buffers in global
-// memory (L2-resident at this size), passes separated by barriers. Saves the
-// three launches per pass that dominate small sorts.
+// At most one tile (N <= kTile): a bitonic sort in shared memory of the
+// pairs (key restricted to its low `passes` bytes, input position). The
+// positions are distinct, so the order is total and equals the stable order
+// the LSD passes give; one CTA with one thread per compare-exchange pair.
+// A stage with stride j <= 32 keeps every warp inside its own 64 elements,
+// so only a warp barrier separates two such stages.
 template <typename K>
-__global__ void __launch_bounds__(kSortThreads)
-small_sort_kernel(K* k0, uint32_t* v0, K* k1, uint32_t* v1, int N, int passes) {
-  __shared__ uint32_t wcnt[kSortWarps][kRadix];
-  __shared__ uint32_t goff[kRadix];
-  __shared__ uint32_t wsum[kSortWarps];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  for (int p = 0; p < passes; ++p) {
-    const K* kin = (p & 1) ? k1 : k0;
-    const uint32_t* vin = (p & 1) ? v1 : v0;
-    K* kout = (p & 1) ? k0 : k1;
-    uint32_t* vout = (p & 1) ? v0 : v1;
-    const int shift = 8 * p;
-    for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
-      for (int ww = 0; ww < kSortWarps; ++ww) wcnt[ww][d] = 0;
-    __syncthreads();
-    const int base = w * 32 * kItems;
-    K key[kItems];
-    uint32_t val[kItems], loc[kItems], dig[kItems];
-    for (int s = 0; s < kItems; ++s) {
-      const int idx = base + s * 32 + lane;
-      const bool valid = idx < N;
-      key[s] = valid ? kin[idx] : (K)0;
-      val[s] = valid ? vin[idx] : 0u;
-      const unsigned d = valid ? ((unsigned)(key[s] >> shift) & 0xFFu) : 0x100u;
-      dig[s] = d;
-      const unsigned peers = __match_any_sync(0xffffffffu, d);
-      const unsigned before = valid ? wcnt[w][d & 0xFFu] : 0u;
-      __syncwarp();
-      if (valid && lane == __ffs(peers) - 1) wcnt[w][d & 0xFFu] = before + __popc(peers);
-      __syncwarp();
-      loc[s] = before + __popc(peers & lt);
-    }
-    __syncthreads();
-    // per digit (one thread each): offsets of the warps, and the digit total
-    uint32_t tot = 0;
-    {
-      const int d = threadIdx.x;    // kSortThreads == kRadix
-      for (int ww = 0; ww < kSortWarps; ++ww) {
-        const uint32_t c = wcnt[ww][d];
-        wcnt[ww][d] = tot;
-        tot += c;
+__global__ void __launch_bounds__(1024)
+small_sort_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
+                  K* __restrict__ kout, uint32_t* __restrict__ vout, int N, int n2, int passes) {
+  __shared__ K sk[kTile];
+  __shared__ uint16_t si[kTile];
+  const K mask = passes * 8 >= (int)(8 * sizeof(K)) ? ~(K)0 : (((K)1 << (8 * passes)) - 1);
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    // padding sorts after every key: the largest key and position
+    sk[t] = t < N ? (kin[t] & mask) : ~(K)0;
+    si[t] = t < N ? (uint16_t)t : (uint16_t)0xFFFFu;
+  }
+  __syncthreads();
+  const int half = n2 >> 1;
+  for (int k = 2; k <= n2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < half; t += blockDim.x) {
+        const int a = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+        const int b = a | j;
+        const K ka = sk[a], kb = sk[b];
+        const uint16_t ia = si[a], ib = si[b];
+        const bool gt = ka > kb || (ka == kb && ia > ib);
+        if (gt == ((a & k) == 0)) {     // ascending where bit k of a is clear
+          sk[a] = kb; sk[b] = ka;
+          si[a] = ib; si[b] = ia;
+        }
       }
+      const int jn = j > 1 ? j >> 1 : k;  // the next stage's stride
+      if (j <= 32 && jn <= 32 && blockDim.x >= half) __syncwarp();
+      else __syncthreads();
     }
-    // exclusive scan of the digit totals over the CTA
-    uint32_t y = tot;
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
-      if (lane >= o) y += z;
-    }
-    if (lane == 31) wsum[w] = y;
-    __syncthreads();
-    uint32_t before = 0;
-    for (int j = 0; j < w; ++j) before += wsum[j];
-    goff[threadIdx.x] = before + y - tot;
-    __syncthreads();
-    for (int s = 0; s < kItems; ++s) {
-      if (dig[s] < 0x100u) {
-        const uint32_t pos = goff[dig[s]] + wcnt[w][dig[s]] + loc[s];
-        kout[pos] = key[s];
-        vout[pos] = val[s];
-      }
-    }
-    __syncthreads();   // the next pass reads what this one wrote
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const int i = si[t];
+    kout[t] = kin[i];
+    vout[t] = vin[i];
   }
 }
 
@@ -238,16 +210,19 @@ void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes) {
 int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaStream_t st) {
   int cur = src;
   if (N <= kTile) {
-    // small sorts: all passes in one CTA (buffer src is read first)
+    // small sorts: one CTA, buffer src in, the other out
+    int n2 = 2;
+    while (n2 < N) n2 <<= 1;
+    const int thr = n2 / 2 < 32 ? 32 : n2 / 2;
     if (key_bytes == 4)
-      small_sort_kernel<uint32_t><<<1, kSortThreads, 0, st>>>(
-          static_cast<uint32_t*>(w.keys[cur]), w.vals[cur], static_cast<uint32_t*>(w.keys[cur ^ 1]),
-          w.vals[cur ^ 1], (int)N, passes);
+      small_sort_kernel<uint32_t><<<1, thr, 0, st>>>(
+          static_cast<const uint32_t*>(w.keys[cur]), w.vals[cur],
+          static_cast<uint32_t*>(w.keys[cur ^ 1]), w.vals[cur ^ 1], (int)N, n2, passes);
     else
-      small_sort_kernel<uint64_t><<<1, kSortThreads, 0, st>>>(
-          static_cast<uint64_t*>(w.keys[cur]), w.vals[cur], static_cast<uint64_t*>(w.keys[cur ^ 1]),
-          w.vals[cur ^ 1], (int)N, passes);
-    return (passes & 1) ? cur ^ 1 : cur;
+      small_sort_kernel<uint64_t><<<1, thr, 0, st>>>(
+          static_cast<const uint64_t*>(w.keys[cur]), w.vals[cur],
+          static_cast<uint64_t*>(w.keys[cur ^ 1]), w.vals[cur ^ 1], (int)N, n2, passes);
+    return cur ^ 1;
   }
   cudaMemsetAsync(w.totals, 0, (size_t)passes * kRadix * 4, st);
   for (int p = 0; p < passes; ++p) {
