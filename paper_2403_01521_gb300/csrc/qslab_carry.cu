@@ -23,13 +23,12 @@ namespace qslab {
 // All are 1 (gap 0) where the chain of a replica starts, whose carry is 0.
 // zero_chunks = 0: k-space chunks (L), 1: k = 0 chunks (L0)
 template <typename T>
-__global__ void pair_decay_kernel(Reps rp, int zero_chunks, int np, const T* zs, PairTab pairs,
-                                  Cplx<typename CarryNum<T>::type>* pdec,
-                                  typename CarryNum<T>::type* gaps) {
+__device__ __forceinline__ void pair_decay_at(const Reps& rp, int zero_chunks, int np, const T* zs,
+                                              const PairTab& pairs,
+                                              Cplx<typename CarryNum<T>::type>* pdec,
+                                              typename CarryNum<T>::type* gaps, int e) {
   using CN = typename CarryNum<T>::type;
   const int nch = zero_chunks ? rp.nzchunks : rp.nchunks;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 2 * nch * np) return;
   const int dir = e / (nch * np);
   const int r = e - dir * nch * np;
   const int c = r / np, p = r - c * np;
@@ -40,16 +39,24 @@ __global__ void pair_decay_kernel(Reps rp, int zero_chunks, int np, const T* zs,
   if (gaps && p == 0) gaps[dir * nch + c] = cn_from(gap, (CN*)nullptr);
 }
 
+template <typename T>
+__global__ void pair_decay_kernel(Reps rp, int zero_chunks, int np, const T* zs, PairTab pairs,
+                                  Cplx<typename CarryNum<T>::type>* pdec,
+                                  typename CarryNum<T>::type* gaps) {
+  const int nch = zero_chunks ? rp.nzchunks : rp.nchunks;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < 2 * nch * np) pair_decay_at<T>(rp, zero_chunks, np, zs, pairs, pdec, gaps, e);
+}
+
 // Decay of a pair state across a whole carry group [ca, cb) of k-space
 // chunks, in the group's chain order: forward z_end(cb-1) - z_end(ca-1),
 // backward z_start(cb) - z_start(ca); 0 for the group where the chain starts.
 template <typename T>
-__global__ void group_pair_decay_kernel(Reps rp, int np, const T* zs, PairTab pairs,
-                                        Cplx<typename CarryNum<T>::type>* gpd) {
+__device__ __forceinline__ void group_pair_decay_at(const Reps& rp, int np, const T* zs,
+                                                    const PairTab& pairs,
+                                                    Cplx<typename CarryNum<T>::type>* gpd, int e) {
   using CN = typename CarryNum<T>::type;
   const int NG = rp.ngroups;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 2 * NG * np) return;
   const int dir = e / (NG * np);
   const int r = e - dir * NG * np;
   const int grp = r / np, p = r - grp * np;
@@ -87,18 +94,32 @@ __device__ __forceinline__ double exp_neg_small(double x) {
 }
 
 template <typename T>
-__global__ void mode_decay_kernel(Reps rp, const T* zs, const T* kk,
-                                  typename CarryNum<T>::type* kdec) {
+__device__ __forceinline__ void mode_decay_at(const Reps& rp, const T* zs, const T* kk,
+                                              typename CarryNum<T>::type* kdec, int64_t e) {
   using CN = typename CarryNum<T>::type;
-  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t per_dir = (int64_t)rp.nchunks * rp.Kpad;
-  if (e >= 2 * per_dir) return;
   const int dir = (int)(e / per_dir);
   const int64_t r = e - (int64_t)dir * per_dir;
   const int c = (int)(r / rp.Kpad), m = (int)(r - (int64_t)c * rp.Kpad);
   const CRange ch = kchunk(rp, c);
   const double x = (double)kk[(size_t)ch.r * rp.Kpad + m] * chunk_gap(zs, ch, dir, rp.L);
   kdec[e] = cn_from(exp_neg_small(x), (CN*)nullptr);
+}
+
+// The three decay tables of the k-space carries in one launch: pair decays
+// on [0, ne), group pair decays on [ne, ne + nge), mode decays after them.
+template <typename T>
+__global__ void kspace_decay_kernel(Reps rp, int np, const T* zs, const T* kk, PairTab pairs,
+                                    Cplx<typename CarryNum<T>::type>* pdec,
+                                    Cplx<typename CarryNum<T>::type>* gpd,
+                                    typename CarryNum<T>::type* kdec) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // group decays only serve the three-phase chains
+  const int64_t ne = (int64_t)2 * rp.nchunks * np, nge = rp.kflat ? 0 : (int64_t)2 * rp.ngroups * np;
+  const int64_t nk = (int64_t)2 * rp.nchunks * rp.Kpad;
+  if (e < ne) pair_decay_at<T>(rp, 0, np, zs, pairs, pdec, nullptr, (int)e);
+  else if (e < ne + nge) group_pair_decay_at<T>(rp, np, zs, pairs, gpd, (int)(e - ne));
+  else if (e < ne + nge + nk) mode_decay_at<T>(rp, zs, kk, kdec, e - ne - nge);
 }
 
 // ------------------------------------------------------------------ carries
@@ -108,7 +129,7 @@ __global__ void mode_decay_kernel(Reps rp, const T* zs, const T* kk,
 // and the chains run in three parallel phases: (1) every group composes its
 // output from a zero input, A_g (for beta = k also its decay D_g, the
 // product of the chunks' real decays; a pair's D_g is the closed form of
-// group_pair_decay_kernel); (2) a short chain over the replica's groups
+// group_pair_decay_at); (2) a short chain over the replica's groups
 // gives each group's input; (3) every group replays its chunks from that
 // input and writes the carries. Depth 2g + G instead of G g for G groups of
 // g chunks; the last group of a chain needs no phase 1. Loads and stores
@@ -147,7 +168,7 @@ __global__ void carry_group_kernel(CarryCtx<T> X, const Cplx<T>* __restrict__ ag
   const size_t gidx = (((size_t)dir * X.S + st) * NG + grp) * Kpad + m;
   const CN zero = cn_zero((CN*)nullptr);
   CN cr = zero, ci = zero, pk = cn_from(1.0, (CN*)nullptr);
-  if (replay) { cr = gA[gidx].re; ci = gA[gidx].im; }
+  if (replay && !X.rp.kflat) { cr = gA[gidx].re; ci = gA[gidx].im; }
   const int ca = X.rp.gstart[grp], cb = X.rp.gstart[grp + 1];
   const int len = cb - ca;
   const int cfirst = dir == 0 ? ca : cb - 1;
@@ -298,12 +319,13 @@ void launch_kspace_carries(const ScanPlan& pl, const Reps& rp, const PairTab& pa
                            const T* kk, const Cplx<T>* agg, Cplx<T>* carry, void* dec,
                            cudaStream_t st) {
   const DecayViews<T> v = decay_views<T>(pl, rp, dec);
-  const int ne = 2 * rp.nchunks * pl.np;
-  pair_decay_kernel<T><<<(ne + 255) / 256, 256, 0, st>>>(rp, 0, pl.np, zs, pairs, v.pdec, nullptr);
-  const int nge = 2 * rp.ngroups * pl.np;
-  group_pair_decay_kernel<T><<<(nge + 255) / 256, 256, 0, st>>>(rp, pl.np, zs, pairs, v.gpd);
-  const int64_t nk = (int64_t)2 * rp.nchunks * rp.Kpad;
-  mode_decay_kernel<T><<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(rp, zs, kk, v.kdec);
+  const int64_t nall = (int64_t)2 * rp.nchunks * pl.np +
+                       (rp.kflat ? 0 : (int64_t)2 * rp.ngroups * pl.np) +
+                       (int64_t)2 * rp.nchunks * rp.Kpad;
+  // 64-thread blocks: each thread's FP64 exponentials go to as many SMs as
+  // possible (an SM issues FP64 at a small fraction of its FP32 rate)
+  kspace_decay_kernel<T><<<(unsigned)((nall + 63) / 64), 64, 0, st>>>(
+      rp, pl.np, zs, kk, pairs, v.pdec, v.gpd, v.kdec);
   CarryCtx<T> X;
   X.rp = rp;
   X.S = pl.nstates;
@@ -311,6 +333,12 @@ void launch_kspace_carries(const ScanPlan& pl, const Reps& rp, const PairTab& pa
   X.cs = (size_t)pl.nstates * rp.Kpad;
   X.dirstride = (size_t)rp.nchunks * pl.nstates * rp.Kpad;
   const int64_t ng = (int64_t)2 * X.S * rp.ngroups * rp.Kpad;
+  if (rp.kflat) {
+    // one group per chain: the replay from zero is the whole scan
+    carry_group_kernel<T><<<(unsigned)((ng + 127) / 128), 128, 0, st>>>(
+        X, agg, carry, v.pdec, v.kdec, v.gkD, v.gA, true);
+    return;
+  }
   carry_group_kernel<T><<<(unsigned)((ng + 127) / 128), 128, 0, st>>>(
       X, agg, carry, v.pdec, v.kdec, v.gkD, v.gA, false);
   const int64_t nt = (int64_t)2 * X.S * rp.R * rp.Kpad;
@@ -325,7 +353,7 @@ void launch_pair_decay(const Reps& rp, int zero_chunks, int np, const T* zs, con
   using CN = typename CarryNum<T>::type;
   const int nch = zero_chunks ? rp.nzchunks : rp.nchunks;
   const int ne = 2 * nch * np;
-  pair_decay_kernel<T><<<(ne + 255) / 256, 256, 0, st>>>(
+  pair_decay_kernel<T><<<(ne + 63) / 64, 64, 0, st>>>(
       rp, zero_chunks, np, zs, pairs, static_cast<Cplx<CN>*>(pdec), static_cast<CN*>(gaps));
 }
 

@@ -49,6 +49,7 @@ struct Tables {
   std::vector<double> vdiag;    // 3 R: j = i lateral virial per unit sum q^2 (xx, yy, xy)
   int Kpad = 32, KR = 32, nkr = 1, L = 32, L0 = 128;
   int nchunks = 0, nz = 0, ngroups = 0, nzgroups = 0;
+  int kflat = 1, zflat = 1;     // every replica's carry chains are one group
   int64_t N = 0;
   // device layout of the table buffer
   size_t o_info = 0, o_crep = 0, o_zrep = 0, o_gstart = 0, o_grep = 0, o_zgstart = 0, o_zgrep = 0,
@@ -139,6 +140,7 @@ int cuda_fail(cudaError_t e) {
 bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
 
 constexpr int kMaxReplicas = 1 << 20;
+constexpr int kFlatChunks = 32;   // carry chains shorter than this are one group
 
 // Representatives of conjugate pairs of SOE nodes (multiplicity 2) and real
 // nodes (multiplicity 1); padded with zero-weight entries to a compiled size.
@@ -392,6 +394,7 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
     ri.n = (int32_t)(off[r + 1] - off[r]);
     ri.Lx = box[3 * r]; ri.Ly = box[3 * r + 1]; ri.Lz = box[3 * r + 2];
     ri.area = ri.Lx * ri.Ly;
+    ri.k0pre = 2.0 * kPi / ri.area;
     auto it = seen.find({ri.Lx, ri.Ly});
     if (reuse) {
       const RepInfo& o = prev->info[r];
@@ -468,6 +471,10 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
   // k = 0 chunks: short sequential loops, many threads (no longer than the
   // k-space chunks, so that small slabs get more, shorter chains)
   t.L0 = std::min(128, L);
+  // carry chains shorter than kFlatChunks chunks are one group (a single
+  // serial replay); the rule looks at each replica alone, so that a replica
+  // gets the same arithmetic in a batch as in a call of its own. When every
+  // chain is one group, the group and chain phases are not launched.
   // chunks, k = 0 chunks and carry groups per replica
   for (int r = 0; r < R; ++r) {
     RepInfo& ri = t.info[r];
@@ -481,7 +488,8 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
     ri.zg0 = (int32_t)t.zgroup_rep.size();
     ri.nzg = 0;
     if (ri.nz > 0) {
-      const int G = std::max(1, (int)std::lround(std::sqrt((double)ri.nz)));
+      const int G =
+          ri.nz < kFlatChunks ? 1 : std::max(1, (int)std::lround(std::sqrt((double)ri.nz)));
       const int g = (ri.nz + G - 1) / G;
       for (int a = 0; a < ri.nz; a += g) {
         t.zgstart.push_back(ri.z0 + a);
@@ -490,11 +498,13 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
       }
     }
     // groups: about sqrt(nch) groups of about sqrt(nch) chunks (serial depth
-    // of the three carry phases about 3 sqrt(nch)); one group below 8 chunks
+    // of the three carry phases about 3 sqrt(nch))
     ri.g0 = (int32_t)t.group_rep.size();
     ri.ng = 0;
     if (ri.nch > 0) {
-      const int G = ri.nch >= 8 ? std::max(2, (int)std::lround(std::sqrt((double)ri.nch))) : 1;
+      const int G = ri.nch < kFlatChunks
+                        ? 1
+                        : std::max(2, (int)std::lround(std::sqrt((double)ri.nch)));
       const int g = (ri.nch + G - 1) / G;
       for (int a = 0; a < ri.nch; a += g) {
         t.gstart.push_back(ri.c0 + a);
@@ -502,6 +512,12 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
         ++ri.ng;
       }
     }
+  }
+  t.kflat = 1;
+  t.zflat = 1;
+  for (int r = 0; r < R; ++r) {
+    if (t.info[r].ng > 1) t.kflat = 0;
+    if (t.info[r].nzg > 1) t.zflat = 0;
   }
   t.nchunks = (int)t.chunk_rep.size();
   t.nz = (int)t.zchunk_rep.size();
@@ -605,6 +621,8 @@ Reps reps_view(const qslab_ctx* c) {
   rp.zgstart = reinterpret_cast<const int32_t*>(b + t.o_zgstart);
   rp.zgroup_rep = reinterpret_cast<const int32_t*>(b + t.o_zgrep);
   rp.nzgroups = t.nzgroups;
+  rp.kflat = t.kflat;
+  rp.zflat = t.zflat;
   return rp;
 }
 
@@ -740,13 +758,13 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
     else c->coef_ready = true;
   }
   int r = radix_sort(sw, N, (int)sizeof(T), (int)sizeof(T), 0, st);
-  nl += 2 + 3 * (int)sizeof(T);   // prepare, check + 3 kernels per sort pass
+  nl += 2 + sort_launches(N, (int)sizeof(T));   // prepare, check, the sort
   if (R > 1) {
     // stable second sort on the replica index: replicas contiguous, z-ordered within
     launch_rep_keys(N, sw.vals[r], rid, static_cast<uint32_t*>(sw.keys[r]), st);
     const int passes = R <= 256 ? 1 : (R <= 65536 ? 2 : 3);
     r = radix_sort(sw, N, 4, passes, r, st);
-    nl += 1 + 3 * passes;
+    nl += 1 + sort_launches(N, passes);
   }
   launch_gather<T>(rp, pos, q, sw.vals[r], zs, dz, qs, xh, yh, perm, st);
   ++nl;
@@ -755,7 +773,7 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   QS_CUDA(cudaEventRecord(c->fork, st));
   QS_CUDA(cudaStreamWaitEvent(c->side, c->fork, 0));
   launch_kzero<T>(rp, c->pairs, c->alpha, zs, dz, qs, k0w, phi0, fz0, c->side);
-  nl += 6;
+  nl += rp.zflat ? 4 : 6;
   if (ev) cudaEventRecord(ev[8], c->side);
   QS_CUDA(cudaEventRecord(c->join, c->side));
   if (want_modes) QS_CUDA(cudaStreamWaitEvent(st, c->tab_join, 0));
@@ -769,7 +787,8 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
                      st, ev ? ev + 3 : nullptr, 1);
     VirArgs<T> va{P.sp, rp, modes, c->pairs, c->alpha, rbe ? 1 : 0, zs, dz, qs, xh, yh, trig,
                   carry, agg, pos, q, nullptr, energies, nullptr, c->walls, nullptr};
-    nl += 7 + launch_energy_pass<T>(va, ws + P.off_vir, st);
+    // pass A, decays, 1 or 3 carry kernels
+    nl += (rp.kflat ? 3 : 5) + launch_energy_pass<T>(va, ws + P.off_vir, st);
     if (ev) cudaEventRecord(ev[5], st);
     QS_CUDA(cudaStreamWaitEvent(st, c->join, 0));
     if (ev) cudaEventRecord(ev[6], st);
@@ -786,7 +805,7 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   }
   launch_kspace<T>(P.sp, rp, modes, c->pairs, zs, dz, qs, xh, yh, trig, agg, carry, dec, part, st,
                    ev ? ev + 3 : nullptr);
-  nl += 8;
+  nl += rp.kflat ? 4 : 6;   // pass A, decays, 1 or 3 carry kernels, pass B
   QS_CUDA(cudaStreamWaitEvent(st, c->join, 0));
   if (ev) cudaEventRecord(ev[6], st);
   launch_combine<T>(rp, P.sp.nkr, part, phi0, fz0, qs, zs, xh, yh, c->walls, perm, echunk, phi,

@@ -87,6 +87,7 @@ struct RepInfo {
   int32_t cdfy0, ny;      //   cumulative tables and their lengths
   int32_t mxmax, mymax;
   double Lx, Ly, Lz, area, H, diagq;
+  double k0pre;           // 2 pi / area, the k = 0 term's prefactor
 };
 
 // Geometry of a call, passed to kernels by value.
@@ -94,6 +95,9 @@ struct Reps {
   int R;
   int L, L0;              // particles per k-space / k = 0 chunk
   int nchunks, nzchunks, ngroups, nzgroups;
+  // 1 when every replica's k-space (kflat) or k = 0 (zflat) carry chain is
+  // one group: the carries then come from one replay from zero
+  int kflat, zflat;
   int Kpad;               // modes per replica (multiple of 32)
   int64_t N;              // particles in all replicas
   const RepInfo* info;        // [R]
@@ -140,6 +144,8 @@ void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes);
 // low `passes` bytes; returns the index (0 or 1) of the buffer holding the
 // result.
 int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaStream_t st);
+// kernels radix_sort() launches for N keys and `passes` digits
+int sort_launches(int64_t N, int passes);
 
 // ---- kernels (qslab_prep.cu: checks, gather, combine, mode tables;
 //      qslab_kspace.cu: k != 0 passes; qslab_carry.cu: their carries;

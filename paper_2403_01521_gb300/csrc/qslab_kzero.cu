@@ -30,6 +30,9 @@ struct K0Params {
   Reps rp;
   int npad;          // lanes per chunk (power of two >= np, at least 4)
   double alpha, c1;
+  // per pair representative (host-computed, so that no lane divides in
+  // FP64): multiplicity w/sqrt(pi), 1/s and 2/s + s, real and imaginary parts
+  double cw[2][kMaxPairs], is[2][kMaxPairs], cs[2][kMaxPairs];
 };
 
 // acc + a b, with the product kept exact on the double-float path
@@ -47,6 +50,7 @@ __device__ __forceinline__ DF cn_add(DF acc, float a) { return acc + a; }
 // and dz are staged in shared memory first, so that the sequential loops
 // below read no global memory.
 constexpr int kK0Cpb = 8;
+constexpr int kK0Batch = 8;     // steps whose decays the final kernel computes ahead
 
 __device__ __forceinline__ double shfl_xor_cn(double v, int o) {
   return __shfl_xor_sync(0xffffffffu, v, o);
@@ -179,8 +183,11 @@ __global__ void kzero_group_kernel(K0Params Q, PairTab pr, K0Carry<T> W, bool re
     const int ca = Q.rp.zgstart[grp], cb = Q.rp.zgstart[grp + 1], len = cb - ca;
     const size_t ti = ((size_t)dir * NZG + grp) * npad + p;
     CN sr = zero, si = zero, hr = zero, hi = zero, Dr = one, Di = zero, Gs = zero;
-    if (replay) { const K0State<CN> x = W.zin[ti]; sr = x.Sr; si = x.Si; hr = x.Hr; hi = x.Hi; }
-    constexpr int B = 4;
+    if (replay && !Q.rp.zflat) {
+      const K0State<CN> x = W.zin[ti];
+      sr = x.Sr; si = x.Si; hr = x.Hr; hi = x.Hi;
+    }
+    constexpr int B = 8;
     for (int j0 = 0; j0 < len; j0 += B) {
       Cplx<T> as[B], ah[B];
       Cplx<CN> d[B];
@@ -218,18 +225,33 @@ __global__ void kzero_group_kernel(K0Params Q, PairTab pr, K0Carry<T> W, bool re
   } else if (e < npair + NZG) {
     const int grp = e - npair;
     const int ca = Q.rp.zgstart[grp], cb = Q.rp.zgstart[grp + 1];
+    // a replica with one group starts from zero and ends at its totals
+    CN a = zero, b = zero;
+    if (replay && !Q.rp.zflat) { a = W.zq[2 * grp]; b = W.zq[2 * grp + 1]; }
+    constexpr int B = 8;        // loads issued ahead of the dependent sums
+    for (int c0 = ca; c0 < cb; c0 += B) {
+      CN s0[B], s1[B];
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        if (c0 + u < cb) { s0[u] = W.csum[2 * (c0 + u)]; s1[u] = W.csum[2 * (c0 + u) + 1]; }
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        if (c0 + u < cb) {
+          if (replay) { W.cpre[2 * (c0 + u)] = a; W.cpre[2 * (c0 + u) + 1] = b; }
+          a = a + s0[u];
+          b = b + s1[u];
+        }
+      }
+    }
     if (!replay) {
-      CN a = zero, b = zero;
-      for (int c = ca; c < cb; ++c) { a = a + W.csum[2 * c]; b = b + W.csum[2 * c + 1]; }
       W.zq[2 * grp] = a;
       W.zq[2 * grp + 1] = b;
     } else {
-      CN a = W.zq[2 * grp], b = W.zq[2 * grp + 1];
-      for (int c = ca; c < cb; ++c) {
-        W.cpre[2 * c] = a;
-        W.cpre[2 * c + 1] = b;
-        a = a + W.csum[2 * c];
-        b = b + W.csum[2 * c + 1];
+      if (Q.rp.zflat) {
+        const int rep = Q.rp.zgroup_rep[grp];
+        W.rtot[2 * rep] = a;
+        W.rtot[2 * rep + 1] = b;
       }
     }
   }
@@ -303,18 +325,21 @@ __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
                                    typename CarryNum<T>::type* phi0,
                                    typename CarryNum<T>::type* fz0) {
   using CN = typename CarryNum<T>::type;
-  // per chunk: z, q, dz [L0 + 1] and the potential / derivative sums [L0][2]
+  // per chunk: z, q, dz [L0 + 1] and the potential / derivative sums
+  // [2 directions][L0][2]; 2 npad lanes per chunk, lane = dir npad + pair,
+  // so that the two directions' scans run side by side
   extern __shared__ __align__(16) char ksm_raw[];
-  const int lanes = Q.npad;
+  const int lanes = Q.npad, w2 = 2 * Q.npad;
   const int L0 = Q.rp.L0;
   const int nch = Q.rp.nzchunks;
   const int64_t N = Q.rp.N;
-  const int lc = threadIdx.x / lanes, p = threadIdx.x % lanes;
+  const int lc = threadIdx.x / w2, lq = threadIdx.x % w2;
+  const int dir = lq / lanes, p = lq % lanes;
   const int c = blockIdx.x * kK0Cpb + lc;
-  T* zl = reinterpret_cast<T*>(ksm_raw) + (size_t)lc * (5 * L0 + 3);
+  T* zl = reinterpret_cast<T*>(ksm_raw) + (size_t)lc * (7 * L0 + 3);
   T* ql = zl + (L0 + 1);
   T* dzl = ql + (L0 + 1);
-  T* acc = dzl + (L0 + 1);
+  T* accd = dzl + (L0 + 1);             // [dir][L0][2]
   const bool valid = c < nch;
   CRange ch{0, 0, 0, false, false};
   if (valid) ch = zchunk(Q.rp, c);
@@ -322,63 +347,75 @@ __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
   const int cnt = ch.cnt;
   // stage the chunk; dz[cnt] is the next particle's (the backward scan's
   // first decay; 0 past the replica's end, where its carry is 0)
-  for (int t = p; t <= cnt && valid; t += lanes) {
+  for (int t = lq; t <= cnt && valid; t += w2) {
     const int64_t i = start + t;
     if (t < cnt) { zl[t] = zs[i]; ql[t] = qs[i]; }
     dzl[t] = i < N ? dz[i] : (T)0;
   }
-  for (int t = p; t < L0; t += lanes) { acc[2 * t] = 0; acc[2 * t + 1] = 0; }
+  for (int t = lq; t < 4 * L0; t += w2) accd[t] = 0;
   __syncwarp();
   const bool act = valid && p < pr.np;
-  const double sq = 1.7724538509055160;   // sqrt(pi)
   T cwr = 0, cwi = 0, isr = 0, isi = 0, csr = 0, csi = 0, ar = 1, ai = 0;
   if (act) {
-    // multiplicity times w_p/sqrt(pi), 1/s_p and 2/s_p + s_p
-    const double sr_ = pr.s_re[p], si_ = pr.s_im[p];
-    const double den = sr_ * sr_ + si_ * si_;
-    cwr = (T)(pr.mult[p] * pr.w_re[p] / sq); cwi = (T)(pr.mult[p] * pr.w_im[p] / sq);
-    isr = (T)(sr_ / den); isi = (T)(-si_ / den);
-    csr = (T)(2 * sr_ / den + sr_); csi = (T)(-2 * si_ / den + si_);
+    cwr = (T)Q.cw[0][p]; cwi = (T)Q.cw[1][p];
+    isr = (T)Q.is[0][p]; isi = (T)Q.is[1][p];
+    csr = (T)Q.cs[0][p]; csi = (T)Q.cs[1][p];
     ar = (T)pr.a_re[p]; ai = (T)pr.a_im[p];
   }
   const T alpha = (T)Q.alpha, ialpha = (T)(1.0 / Q.alpha);
-  for (int dir = 0; dir < 2; ++dir) {
+  T* acc = accd + (size_t)dir * 2 * L0;
+  {
     T sr = 0, si = 0, hr = 0, hi = 0;
     if (act) {
       const CN* in = carry + (((size_t)dir * nch + c) * Q.npad + p) * 4;
       sr = cn_to_t(in[0]); si = cn_to_t(in[1]); hr = cn_to_t(in[2]); hi = cn_to_t(in[3]);
     }
-    // every lane runs L0 steps so that the shuffles below see the whole warp
-    for (int n = 0; n < L0; ++n) {
-      const bool live = n < cnt;
-      const int t = dir == 0 ? n : cnt - 1 - n;
-      T pot = 0, der = 0;
-      if (act && live) {
-        const T qq = ql[t];
-        const T dzi = dzl[dir == 0 ? t : t + 1];
-        const Cplx<T> d = cexp_neg(ar, ai, dzi);
-        // H first (uses the previous inclusive S), then S
-        const T tr = fma(dzi, sr, hr), ti = fma(dzi, si, hi);
-        hr = d.re * tr - d.im * ti; hi = fma(d.re, ti, d.im * tr);
-        const T nsr = fma(d.re, sr, fma(-d.im, si, qq));
-        const T nsi = fma(d.re, si, d.im * sr);
-        sr = nsr; si = nsi;
-        // exclusive S (j != i): S - q_i ; H has no j = i term
-        const T xr = sr - qq, xi = si;
-        // pot part: cw [ (1/alpha) S - 2 (1/s) H ]
-        const T ur = xr * ialpha - 2 * (isr * hr - isi * hi);
-        const T ui = xi * ialpha - 2 * (isr * hi + isi * hr);
-        pot = cwr * ur - cwi * ui;
-        // der part: cw [ -(2/s + s) S + 2 alpha H ] with sign +/- by direction
-        const T vr = -(csr * xr - csi * xi) + 2 * alpha * hr;
-        const T vi = -(csr * xi + csi * xr) + 2 * alpha * hi;
-        der = (dir == 0 ? (T)1 : (T)-1) * (cwr * vr - cwi * vi);
+    // every lane runs L0 steps so that the shuffles below see the whole
+    // warp; the decays of a batch of steps are computed first (they do not
+    // depend on the states), then the batch's dependent updates
+    for (int n0 = 0; n0 < L0; n0 += kK0Batch) {
+      Cplx<T> dd[kK0Batch];
+#pragma unroll
+      for (int u = 0; u < kK0Batch; ++u) {
+        const int n = n0 + u;
+        dd[u] = Cplx<T>{0, 0};
+        if (act && n < cnt) dd[u] = cexp_neg(ar, ai, dzl[dir == 0 ? n : cnt - n]);
       }
-      for (int o = lanes >> 1; o; o >>= 1) {
-        pot += __shfl_xor_sync(0xffffffffu, pot, o);
-        der += __shfl_xor_sync(0xffffffffu, der, o);
+#pragma unroll
+      for (int u = 0; u < kK0Batch; ++u) {
+        const int n = n0 + u;
+        if (n >= L0) break;       // the same for every lane
+        const bool live = n < cnt;
+        const int t = dir == 0 ? n : cnt - 1 - n;
+        T pot = 0, der = 0;
+        if (act && live) {
+          const T qq = ql[t];
+          const T dzi = dzl[dir == 0 ? t : t + 1];
+          const Cplx<T> d = dd[u];
+          // H first (uses the previous inclusive S), then S
+          const T tr = fma(dzi, sr, hr), ti = fma(dzi, si, hi);
+          hr = d.re * tr - d.im * ti; hi = fma(d.re, ti, d.im * tr);
+          const T nsr = fma(d.re, sr, fma(-d.im, si, qq));
+          const T nsi = fma(d.re, si, d.im * sr);
+          sr = nsr; si = nsi;
+          // exclusive S (j != i): S - q_i ; H has no j = i term
+          const T xr = sr - qq, xi = si;
+          // pot part: cw [ (1/alpha) S - 2 (1/s) H ]
+          const T ur = xr * ialpha - 2 * (isr * hr - isi * hi);
+          const T ui = xi * ialpha - 2 * (isr * hi + isi * hr);
+          pot = cwr * ur - cwi * ui;
+          // der part: cw [ -(2/s + s) S + 2 alpha H ] with sign +/- by direction
+          const T vr = -(csr * xr - csi * xi) + 2 * alpha * hr;
+          const T vi = -(csr * xi + csi * xr) + 2 * alpha * hi;
+          der = (dir == 0 ? (T)1 : (T)-1) * (cwr * vr - cwi * vi);
+        }
+        // sum over the direction's pair lanes (offsets below npad stay in it)
+        for (int o = lanes >> 1; o; o >>= 1) {
+          pot += __shfl_xor_sync(0xffffffffu, pot, o);
+          der += __shfl_xor_sync(0xffffffffu, der, o);
+        }
+        if (p == 0 && live) { acc[2 * t] = pot; acc[2 * t + 1] = der; }
       }
-      if (p == 0 && live) { acc[2 * t] += pot; acc[2 * t + 1] += der; }
     }
   }
   __syncwarp();
@@ -386,7 +423,8 @@ __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
   // carry type (the terms cancel heavily); the result stays in the carry
   // type and the combine kernel widens it to FP64. Each lane takes a segment
   // of the chunk: its sums, an exclusive scan over the lanes, then the
-  // segment's particles in order.
+  // segment's particles in order. The backward lanes repeat the forward
+  // lanes' scan in their own half of the chunk's lanes and write nothing.
   const int seg = (cnt + lanes - 1) / lanes;
   const int ta = min(cnt, p * seg), tb = min(cnt, ta + seg);
   CN sq0 = cn_zero((CN*)nullptr), sq1 = cn_zero((CN*)nullptr);
@@ -397,11 +435,11 @@ __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
   }
   CN e0 = shfl_up_cn(sq0, 1, lanes), e1 = shfl_up_cn(sq1, 1, lanes);   // exclusive
   if (p == 0) { e0 = cn_zero((CN*)nullptr); e1 = cn_zero((CN*)nullptr); }
-  if (valid) {
+  if (valid && dir == 0) {
     CN Ql = cpre[2 * c] + e0, Pl = cpre[2 * c + 1] + e1;
     const CN Qt = rtot[2 * ch.r], Pt = rtot[2 * ch.r + 1];
     const CN c1 = cn_from(Q.c1, (CN*)nullptr);
-    const CN pre = cn_from(2.0 * 3.14159265358979323846 / Q.rp.info[ch.r].area, (CN*)nullptr);
+    const CN pre = cn_from(Q.rp.info[ch.r].k0pre, (CN*)nullptr);
     for (int t = ta; t < tb; ++t) {
       const int64_t i = start + t;
       const T zt = zl[t], qt = ql[t];
@@ -409,8 +447,11 @@ __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
       const CN Qg = Qt - Ql - cn_from_t(qt, (CN*)nullptr);
       const CN Pg = cn_add_prod(Pt - Pl, -qt, zt);
       const CN lin = zc * (Ql - Qg) - Pl + Pg;
-      const CN pot = c1 * lin + cn_from_t(acc[2 * t], (CN*)nullptr);
-      const CN der = c1 * (Ql - Qg) + cn_from_t(acc[2 * t + 1], (CN*)nullptr);
+      // the two directions' sums, forward first
+      const T ep = accd[2 * t] + accd[2 * L0 + 2 * t];
+      const T ed = accd[2 * t + 1] + accd[2 * L0 + 2 * t + 1];
+      const CN pot = c1 * lin + cn_from_t(ep, (CN*)nullptr);
+      const CN der = c1 * (Ql - Qg) + cn_from_t(ed, (CN*)nullptr);
       phi0[i] = -(pre * pot);
       fz0[i] = pre * der * cn_from_t(qt, (CN*)nullptr);
       Ql = cn_add(Ql, qt);
@@ -436,6 +477,19 @@ void launch_kzero(const Reps& rp, const PairTab& pairs, double alpha, const T* z
   const int npad = kzero_lanes(pairs.np);
   Q.npad = npad;
   double c1 = 0.0;
+  for (int p = 0; p < kMaxPairs; ++p) {
+    Q.cw[0][p] = Q.cw[1][p] = Q.is[0][p] = Q.is[1][p] = Q.cs[0][p] = Q.cs[1][p] = 0.0;
+    if (p >= pairs.np) continue;
+    // multiplicity times w_p/sqrt(pi), 1/s_p and 2/s_p + s_p
+    const double sr = pairs.s_re[p], si = pairs.s_im[p];
+    const double den = sr * sr + si * si;
+    Q.cw[0][p] = pairs.mult[p] * pairs.w_re[p] / 1.7724538509055160;
+    Q.cw[1][p] = pairs.mult[p] * pairs.w_im[p] / 1.7724538509055160;
+    Q.is[0][p] = sr / den;
+    Q.is[1][p] = -si / den;
+    Q.cs[0][p] = 2 * sr / den + sr;
+    Q.cs[1][p] = -2 * si / den + si;
+  }
   for (int p = 0; p < pairs.np; ++p) {
     // c1 = sum over nodes of 2 w/(s sqrt(pi)) = sum over representatives of mult 2 Re(w/s)/sqrt(pi)
     const double den = pairs.s_re[p] * pairs.s_re[p] + pairs.s_im[p] * pairs.s_im[p];
@@ -479,13 +533,16 @@ void launch_kzero(const Reps& rp, const PairTab& pairs, double alpha, const T* z
   kzero_aggregate_kernel<T><<<nblk, thr, sma, st>>>(Q, pairs, zs, qs, agg, csum);
   launch_pair_decay<T>(rp, 1, pairs.np, zs, pairs, pdec, gaps, st);
   const int ng1 = 2 * NZG * npad + NZG;
-  kzero_group_kernel<T><<<(ng1 + 127) / 128, 128, 0, st>>>(Q, pairs, W, false);
-  const int ng2 = 2 * rp.R * npad + rp.R;
-  kzero_chain_kernel<T><<<(ng2 + 127) / 128, 128, 0, st>>>(Q, pairs, W);
+  if (!rp.zflat) {
+    kzero_group_kernel<T><<<(ng1 + 127) / 128, 128, 0, st>>>(Q, pairs, W, false);
+    const int ng2 = 2 * rp.R * npad + rp.R;
+    kzero_chain_kernel<T><<<(ng2 + 127) / 128, 128, 0, st>>>(Q, pairs, W);
+  }
+  // with one group per replica this replay from zero is the whole scan
   kzero_group_kernel<T><<<(ng1 + 127) / 128, 128, 0, st>>>(Q, pairs, W, true);
-  const size_t smf = (size_t)kK0Cpb * (5 * rp.L0 + 3) * sizeof(T);
+  const size_t smf = (size_t)kK0Cpb * (7 * rp.L0 + 3) * sizeof(T);
   cudaFuncSetAttribute(kzero_final_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smf);
-  kzero_final_kernel<T><<<nblk, thr, smf, st>>>(Q, pairs, zs, dz, qs, carry, cpre, rtot, phi0,
+  kzero_final_kernel<T><<<nblk, 2 * thr, smf, st>>>(Q, pairs, zs, dz, qs, carry, cpre, rtot, phi0,
                                                 fz0);
 }
 

@@ -2,6 +2,7 @@
 // sorted gather, the final combine with the energy reduction, and the mode
 // tables (full k-sum list or the random-batch k-sampler).
 #include <cstdint>
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "qslab_df.cuh"
@@ -10,6 +11,8 @@
 #include "qslab_math.cuh"
 
 namespace qslab {
+
+namespace cg = cooperative_groups;
 
 // ====================================================================== prep
 
@@ -415,19 +418,32 @@ __global__ void __launch_bounds__(64) mode_coef_kernel(Reps rp, int npc, const i
 
 constexpr int kMhBlock = 1024;          // chain steps prepared per round
 constexpr int kMhWin = 8;               // earlier states with precomputed decisions
+constexpr int kMhCluster = 8;           // CTAs per replica drawing the proposals
+constexpr int kMhThreads = 512;         // 4 roles x 4 groups of 32 lanes
+constexpr int kMhSlots = 128;           // items per pass of the role warps
+static_assert(kMhBlock <= kMhSlots * kMhCluster, "one pass covers a CTA's proposals");
 constexpr uint64_t kMhTag = 0x4D484731ull;
 
 // One proposal of App. G from two words: Box-Muller normals (u1 = 1 -
 // uniform53(w0) in (0, 1], u2 = uniform53(w1)) scaled by the standard
-// deviations alpha L/(sqrt(2) pi), rounded half away from zero.
+// deviations alpha L/(sqrt(2) pi), rounded half away from zero. The three
+// pieces are separate so that different warps can compute them.
+__device__ __forceinline__ double mh_radius(uint64_t w0) {
+  const double u1 = 1.0 - uniform53(w0);
+  return sqrt(-2.0 * log(u1));
+}
+__device__ __forceinline__ double mh_angle(uint64_t w1) {
+  return 2.0 * 3.14159265358979323846 * uniform53(w1);
+}
+__device__ __forceinline__ void mh_round(double sdx, double sdy, double r, double c, double s,
+                                         int& mx, int& my) {
+  mx = (int)round(sdx * r * c);
+  my = (int)round(sdy * r * s);
+}
 __device__ __forceinline__ void mh_propose(uint64_t w0, uint64_t w1, double sdx, double sdy,
                                            int& mx, int& my) {
-  const double u1 = 1.0 - uniform53(w0);
-  const double u2 = uniform53(w1);
-  const double r = sqrt(-2.0 * log(u1));
-  const double th = 2.0 * 3.14159265358979323846 * u2;
-  mx = (int)round(sdx * r * cos(th));
-  my = (int)round(sdy * r * sin(th));
+  const double r = mh_radius(w0), th = mh_angle(w1);
+  mh_round(sdx, sdy, r, cos(th), sin(th), mx, my);
 }
 
 // log[H(m)/q(m)] from the replica's per-axis tables. A Box-Muller normal is
@@ -441,28 +457,89 @@ __device__ __forceinline__ double mh_log_weight(const double* lwx, const double*
   return lwx[ix] + lwy[iy];
 }
 
-// One CTA per replica. The proposals do not depend on the chain's state
-// (App. G), so the CTA's threads draw kMhBlock of them at a time (proposal,
-// its log-weight and log u) into shared memory; thread 0 then runs the
-// chain through them: the origin is rejected (h = 0 there), any other
-// proposal accepted when d >= 0 or log u < d, d the log acceptance ratio.
-// The chain's state is always an earlier proposal of the round (or the state
-// it entered the round with), so the CTA first decides in parallel, for every
-// step t and each of the kMhWin steps j before it, whether t would be
-// accepted from state j (the same FP64 operations with lw = log-weight of
-// j); thread 0 then reads those bits and computes a decision itself only
-// after kMhWin rejections in a row or before the round's first acceptance.
+// The chain within a round after its first acceptance, as a scan. With the
+// decision bits of the kMhWin states before each step, the state after step
+// t is t - o(t) for an offset o in 0..kMhWin - 1, or kMhWin steps back
+// (o = kMhFar), and step t maps o(t - 1) to o(t): 0 when the step accepts
+// from offset o(t - 1) (bit o(t - 1) of its decisions), o(t - 1) + 1 when it
+// rejects (always for the origin); kMhFar stays kMhFar, where the decision
+// needs the FP64 test (the state is kMhWin or more steps back). A step is a
+// map on the kMhWin + 1 offsets, packed as nibbles, and the maps compose
+// associatively, so a block-wide scan gives every step's offset.
+constexpr int kMhFar = kMhWin;
+using MhMap = unsigned long long;
+constexpr MhMap kMhId = 0x876543210ull;
+static_assert(kMhWin == 8, "nine nibbles");
+__device__ __forceinline__ int mh_at(MhMap f, int o) { return (int)((f >> (4 * o)) & 0xFull); }
+__device__ __forceinline__ MhMap mh_then(MhMap f, MhMap g) {   // f first, then g
+  MhMap h = 0;
+#pragma unroll
+  for (int o = 0; o <= kMhFar; ++o) h |= (MhMap)mh_at(g, mh_at(f, o)) << (4 * o);
+  return h;
+}
+__device__ __forceinline__ MhMap mh_step_map(bool origin, unsigned bits) {
+  MhMap f = (MhMap)kMhFar << (4 * kMhFar);
+#pragma unroll
+  for (int o = 0; o < kMhFar; ++o) {
+    const int out = (!origin && ((bits >> o) & 1u)) ? 0 : o + 1;
+    f |= (MhMap)out << (4 * o);
+  }
+  return f;
+}
+// keep the state after chain step `step` (0-based) when step + 1 is a
+// multiple of thin, as output (step + 1) / thin - 1 of the replica
+__device__ __forceinline__ void mh_keep(int64_t step, int thin, int rep, int P, int x, int y,
+                                        int32_t* sampled) {
+  const int64_t eta = step + 1;
+  if (thin == 1 || eta % thin == 0) {
+    const size_t j = (size_t)rep * P + (size_t)(eta / thin - 1);
+    sampled[2 * j] = x;
+    sampled[2 * j + 1] = y;
+  }
+}
+
+// One cluster of kMhCluster CTAs per replica. The proposals do not depend
+// on the chain's state (App. G), so all CTAs of the cluster draw kMhBlock of
+// them at a time (proposal, its log-weight and log u; CTA r takes steps
+// r, r + kMhCluster, ...) straight into the shared memory of the cluster's
+// first CTA. Within a CTA the FP64 work of a proposal is split by role over
+// warps that sit on different SM sub-partitions (warp w has role w mod 4):
+// role 0 the radius sqrt(-2 ln u1), role 1 cos and sin of the angle, role 2
+// log u; a combine step then rounds the normals and looks up the weights.
+// The first CTA also draws the start attempt 0's two candidates this way.
+// After a cluster barrier the first CTA runs the chain: the origin is
+// rejected (h = 0 there), any other proposal accepted when d >= 0 or
+// log u < d, d the log acceptance ratio. The chain's state is always an
+// earlier proposal of the round (or the state it entered the round with),
+// so the CTA first decides in parallel, for every step t and each of the
+// kMhWin steps j before it, whether t would be accepted from state j (the
+// same FP64 operations with lw = log-weight of j). Thread 0 fixes the start
+// state (searching attempts 1..63 itself only if both candidates are the
+// origin) and takes the steps up to the round's first acceptance; the
+// states after it come from a block scan of the steps' offset maps (see
+// mh_step_map), and thread 0 decides step by step again only after kMhWin
+// rejections in a row.
 // Counters: start attempts (a, 1, ctr[1], tag + rep 2^32), steps
 // (eta - 1, 0, ctr[1], tag + rep 2^32), key (seed, 0).
-__global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin, uint64_t seed,
-                                                       const uint64_t* ctr, const double* cdf,
-                                                       double alpha, int32_t* sampled) {
+__global__ void __cluster_dims__(kMhCluster, 1, 1) __launch_bounds__(kMhThreads)
+mh_chain_kernel(Reps rp, int P, int thin, uint64_t seed, const uint64_t* ctr, const double* cdf,
+                double alpha, int32_t* sampled) {
   __shared__ int32_t spx[kMhBlock], spy[kMhBlock];
   __shared__ double slw[kMhBlock], slu[kMhBlock];
   __shared__ uint8_t sacc[kMhBlock];      // bit w: accepted from state t - 1 - w
-  __shared__ int32_t s0x, s0y;
-  __shared__ double s0lw;
-  const int rep = blockIdx.x;
+  __shared__ double ir[kMhSlots], ic[kMhSlots], isn[kMhSlots], iu[kMhSlots];
+  __shared__ int32_t cand[2][2];          // start attempt 0's candidates (first CTA)
+  __shared__ MhMap s_wmap[kMhThreads / 32], s_wpre[kMhThreads / 32];
+  __shared__ int s_ta, s_tf, s_end;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const bool lead = rank == 0;
+  // the first CTA's arrays, which every CTA of the cluster fills
+  int32_t* lpx = cluster.map_shared_rank(spx, 0);
+  int32_t* lpy = cluster.map_shared_rank(spy, 0);
+  double* llw = cluster.map_shared_rank(slw, 0);
+  double* llu = cluster.map_shared_rank(slu, 0);
+  const int rep = blockIdx.x / kMhCluster;
   const RepInfo& ri = rp.info[rep];
   const double pi = 3.14159265358979323846;
   const double sdx = alpha * ri.Lx / (sqrt(2.0) * pi);
@@ -471,42 +548,59 @@ __global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin,
   const double* lwy = cdf + ri.cdfy0 + ri.nx + ri.ny;
   const uint64_t counter = ctr[1];
   const uint64_t tag = kMhTag + ((uint64_t)rep << 32);
-  int cx = 1, cy = 0;         // chain state (thread 0)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int role = warp & 3, slot = (warp >> 2) * 32 + lane;
+  int cx = 1, cy = 0;         // chain state (thread 0 of the first CTA)
   double lw = 0.0;
-  int left = thin;            // steps to the next kept state (thread 0)
-  size_t jo = (size_t)rep * P;
-  // the start state is searched by the last thread, concurrently with the
-  // first round of proposals, and handed to thread 0 after that round's barrier
-  if (threadIdx.x == blockDim.x - 1) {
-    for (uint64_t a = 0; a < 64; ++a) {
-      U64x4 c;
-      c.v[0] = a; c.v[1] = 1; c.v[2] = counter; c.v[3] = tag;
-      const U64x4 w = philox4x64_10(c, seed, 0ull);
-      int px, py;
-      mh_propose(w.v[0], w.v[1], sdx, sdy, px, py);
-      if (px != 0 || py != 0) { cx = px; cy = py; break; }
-      mh_propose(w.v[2], w.v[3], sdx, sdy, px, py);
-      if (px != 0 || py != 0) { cx = px; cy = py; break; }
-    }
-    s0x = cx;
-    s0y = cy;
-    s0lw = mh_log_weight(lwx, lwy, ri.mxmax, ri.mymax, cx, cy);
-  }
   const int64_t n = (int64_t)P * thin;
   for (int64_t b0 = 0; b0 < n; b0 += kMhBlock) {
     const int cnt = (int)min((int64_t)kMhBlock, n - b0);
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-      U64x4 c;
-      c.v[0] = (uint64_t)(b0 + t); c.v[1] = 0; c.v[2] = counter; c.v[3] = tag;
-      const U64x4 w = philox4x64_10(c, seed, 0ull);
-      int px, py;
-      mh_propose(w.v[0], w.v[1], sdx, sdy, px, py);
-      spx[t] = px;
-      spy[t] = py;
-      slw[t] = mh_log_weight(lwx, lwy, ri.mxmax, ri.mymax, px, py);
-      slu[t] = log(uniform53(w.v[2]));      // -inf for u = 0
+    // the first CTA has finished the previous round's chain
+    if (b0 > 0) cluster.sync();
+    // items: this CTA's proposals t = rank + kMhCluster i, then (first CTA,
+    // first round) the two start candidates
+    const int m = cnt > rank ? (cnt - rank + kMhCluster - 1) / kMhCluster : 0;
+    const int items = m + (lead && b0 == 0 ? 2 : 0);
+    for (int i0 = 0; i0 < items; i0 += kMhSlots) {
+      const int i = i0 + slot;
+      if (i < items && role < 3) {
+        U64x4 c;
+        if (i < m) { c.v[0] = (uint64_t)(b0 + rank + kMhCluster * i); c.v[1] = 0; }
+        else { c.v[0] = 0; c.v[1] = 1; }
+        c.v[2] = counter; c.v[3] = tag;
+        const U64x4 w = philox4x64_10(c, seed, 0ull);
+        const bool second = i >= m && i - m == 1;      // words 2, 3 of attempt 0
+        const uint64_t w0 = second ? w.v[2] : w.v[0], w1 = second ? w.v[3] : w.v[1];
+        if (role == 0) {
+          ir[slot] = mh_radius(w0);
+        } else if (role == 1) {
+          const double th = mh_angle(w1);
+          ic[slot] = cos(th);
+          isn[slot] = sin(th);
+        } else if (i < m) {
+          iu[slot] = log(uniform53(w.v[2]));     // -inf for u = 0
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < kMhSlots && i0 + (int)threadIdx.x < items) {
+        const int j = threadIdx.x, it = i0 + j;
+        int px, py;
+        mh_round(sdx, sdy, ir[j], ic[j], isn[j], px, py);
+        if (it < m) {
+          const int t = rank + kMhCluster * it;
+          lpx[t] = px;
+          lpy[t] = py;
+          llw[t] = mh_log_weight(lwx, lwy, ri.mxmax, ri.mymax, px, py);
+          llu[t] = iu[j];
+        } else {
+          cand[it - m][0] = px;
+          cand[it - m][1] = py;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    cluster.sync();             // the round's proposals are in the first CTA
+    if (!lead) continue;
     // decisions from the kMhWin states before each step: groups of kMhWin
     // lanes per step, one ballot per warp (the loop bound is warp-uniform)
     for (int e0 = 0; e0 < cnt * kMhWin; e0 += blockDim.x) {
@@ -518,33 +612,120 @@ __global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin,
         acc = d >= 0.0 || slu[t] < d;
       }
       const unsigned bal = __ballot_sync(0xffffffffu, acc);
-      const int lane = threadIdx.x & 31;
       if (e < cnt * kMhWin && lane % kMhWin == 0)
         sacc[t] = (uint8_t)((bal >> lane) & ((1u << kMhWin) - 1u));
     }
     __syncthreads();
+    // (1) thread 0: the steps from the round's entry state up to the first
+    // acceptance (FP64 tests against the entry log-weight)
     if (threadIdx.x == 0) {
-      if (b0 == 0) { cx = s0x; cy = s0y; lw = s0lw; }
-      int jc = -1;                // the state's step in this round; -1: from before it
+      if (b0 == 0) {
+        // the start: the first candidate that is not the origin
+        bool found = false;
+        for (int k = 0; k < 2 && !found; ++k) {
+          if (cand[k][0] != 0 || cand[k][1] != 0) { cx = cand[k][0]; cy = cand[k][1]; found = true; }
+        }
+        for (uint64_t a = 1; a < 64 && !found; ++a) {
+          U64x4 c;
+          c.v[0] = a; c.v[1] = 1; c.v[2] = counter; c.v[3] = tag;
+          const U64x4 w = philox4x64_10(c, seed, 0ull);
+          int px, py;
+          mh_propose(w.v[0], w.v[1], sdx, sdy, px, py);
+          if (px != 0 || py != 0) { cx = px; cy = py; found = true; break; }
+          mh_propose(w.v[2], w.v[3], sdx, sdy, px, py);
+          if (px != 0 || py != 0) { cx = px; cy = py; found = true; }
+        }
+        lw = mh_log_weight(lwx, lwy, ri.mxmax, ri.mymax, cx, cy);
+      }
+      int ta = cnt;
       for (int t = 0; t < cnt; ++t) {
-        const int px = spx[t], py = spy[t];
-        if (px != 0 || py != 0) {
-          const int dist = t - 1 - jc;
-          bool acc;
-          if (jc >= 0 && dist < kMhWin) {
-            acc = (sacc[t] >> dist) & 1u;
-          } else {
-            const double d = slw[t] - lw;
-            acc = d >= 0.0 || slu[t] < d;
+        if (spx[t] != 0 || spy[t] != 0) {
+          const double d = slw[t] - lw;
+          if (d >= 0.0 || slu[t] < d) { ta = t; break; }
+        }
+        mh_keep(b0 + t, thin, rep, P, cx, cy, sampled);
+      }
+      if (ta < cnt) mh_keep(b0 + ta, thin, rep, P, spx[ta], spy[ta], sampled);
+      s_ta = ta;
+      s_tf = cnt;
+      s_end = ta;
+    }
+    __syncthreads();
+    const int ta = s_ta;
+    if (ta < cnt) {             // the same for every thread
+      // (2) offsets of the steps (ta, cnt) by a block scan of their maps;
+      // thread i takes steps ta + 1 + 2i and ta + 2 + 2i
+      const int nit = cnt - ta - 1;
+      const int k0 = 2 * (int)threadIdx.x;
+      const int t0 = ta + 1 + k0, t1 = t0 + 1;
+      const MhMap f0 = k0 < nit ? mh_step_map(spx[t0] == 0 && spy[t0] == 0, sacc[t0]) : kMhId;
+      const MhMap f1 = k0 + 1 < nit ? mh_step_map(spx[t1] == 0 && spy[t1] == 0, sacc[t1]) : kMhId;
+      MhMap F = mh_then(f0, f1);
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const MhMap o = __shfl_up_sync(0xffffffffu, F, d);
+        if (lane >= d) F = mh_then(o, F);
+      }
+      MhMap Ex = __shfl_up_sync(0xffffffffu, F, 1);   // this thread's prefix in its warp
+      if (lane == 0) Ex = kMhId;
+      if (lane == 31) s_wmap[warp] = F;
+      __syncthreads();
+      if (warp == 0) {
+        const int nw = (int)(blockDim.x >> 5);
+        MhMap G = lane < nw ? s_wmap[lane] : kMhId;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const MhMap o = __shfl_up_sync(0xffffffffu, G, d);
+          if (lane >= d) G = mh_then(o, G);
+        }
+        if (lane < nw) s_wpre[lane] = G;       // inclusive over warps
+      }
+      __syncthreads();
+      // (3) the offset entering each of this thread's steps, and the first
+      // step entered at kMhFar (from there on thread 0 decides)
+      int oin0 = mh_at(warp > 0 ? s_wpre[warp - 1] : kMhId, 0);
+      oin0 = mh_at(Ex, oin0);
+      const int o0 = mh_at(f0, oin0), o1 = mh_at(f1, o0);
+      if (k0 < nit && oin0 == kMhFar) atomicMin(&s_tf, t0);
+      else if (k0 + 1 < nit && o0 == kMhFar) atomicMin(&s_tf, t1);
+      __syncthreads();
+      const int tf = s_tf;
+      // (4) the kept states of the steps before tf, and the round's end state
+      if (k0 < nit && t0 < tf) {
+        mh_keep(b0 + t0, thin, rep, P, spx[t0 - o0], spy[t0 - o0], sampled);
+        if (t0 == cnt - 1) s_end = t0 - o0;
+      }
+      if (k0 + 1 < nit && t1 < tf) {
+        mh_keep(b0 + t1, thin, rep, P, spx[t1 - o1], spy[t1 - o1], sampled);
+        if (t1 == cnt - 1) s_end = t1 - o1;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int jc = s_end;
+        if (tf < cnt) {
+          // (5) from tf on: the state is kMhWin steps back; decide step by
+          // step with the decision bits where they reach, else in FP64
+          jc = tf - 1 - kMhFar;
+          cx = spx[jc];
+          cy = spy[jc];
+          for (int t = tf; t < cnt; ++t) {
+            if (spx[t] != 0 || spy[t] != 0) {
+              const int dist = t - 1 - jc;
+              bool acc;
+              if (dist < kMhWin) {
+                acc = (sacc[t] >> dist) & 1u;
+              } else {
+                const double d = slw[t] - slw[jc];
+                acc = d >= 0.0 || slu[t] < d;
+              }
+              if (acc) { cx = spx[t]; cy = spy[t]; jc = t; }
+            }
+            mh_keep(b0 + t, thin, rep, P, cx, cy, sampled);
           }
-          if (acc) { cx = px; cy = py; lw = slw[t]; jc = t; }
         }
-        if (--left == 0) {          // every thin-th state is kept
-          left = thin;
-          sampled[2 * jo] = cx;
-          sampled[2 * jo + 1] = cy;
-          ++jo;
-        }
+        cx = spx[jc];
+        cy = spy[jc];
+        lw = slw[jc];
       }
     }
     __syncthreads();
@@ -553,7 +734,8 @@ __global__ void __launch_bounds__(256) mh_chain_kernel(Reps rp, int P, int thin,
 
 void launch_mh_chain(const Reps& rp, int P, int thin, uint64_t seed, const uint64_t* ctr,
                      const double* cdf, double alpha, int32_t* sampled, cudaStream_t st) {
-  mh_chain_kernel<<<rp.R, 256, 0, st>>>(rp, P, thin, seed, ctr, cdf, alpha, sampled);
+  mh_chain_kernel<<<rp.R * kMhCluster, kMhThreads, 0, st>>>(rp, P, thin, seed, ctr, cdf, alpha,
+                                                            sampled);
 }
 
 template <typename T>

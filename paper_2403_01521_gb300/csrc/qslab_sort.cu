@@ -207,6 +207,8 @@ void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes) {
   w.totals = reinterpret_cast<uint32_t*>(p);
 }
 
+int sort_launches(int64_t N, int passes) { return N <= kTile ? 1 : 3 * passes; }
+
 int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaStream_t st) {
   int cur = src;
   if (N <= kTile) {

@@ -65,6 +65,26 @@ def test_metropolis_small_box_rejects(qslab, soe16):
     slab.close()
 
 
+def test_metropolis_long_chain_many_rejections(qslab, soe16):
+    """alpha L = 1.5: most proposals are the origin or rejected, so runs of
+    more than 8 rejections occur (the device then decides from the current
+    state instead of its precomputed 8-step window), and P thin = 2400
+    steps span three rounds of 1024 proposals; still the oracle's chain."""
+    sl = workloads.uniform_slab(100, (6.0, 6.0, 4.0), 6, alpha=0.25)
+    slab = qslab.QSlab(0, "fp64").configure(sl.box, sl.alpha, soe16, rbe=(400, 17)).sampler("metropolis", 6)
+    pos = torch.tensor(sl.pos, device="cuda")
+    q = torch.tensor(sl.q, device="cuda")
+    for call in range(2):
+        slab.compute(pos, q)
+        assert slab.status() == 0
+        mx, my, _ = slab.sampled_modes()
+        omx, omy, rate = lattice.metropolis_modes(400, 17, call, sl.alpha, 6.0, 6.0, thin=6,
+                                                  return_rate=True)
+        assert rate < 0.5
+        assert (mx == omx).all() and (my == omy).all()
+    slab.close()
+
+
 def test_metropolis_batched_streams(qslab, soe16):
     """Every slab of a batch runs its own chain (stream r); a CUDA-graph
     replay draws the next call's chains."""
