@@ -236,9 +236,9 @@ template <typename T>
 void launch_mode_coef(const Reps& rp, int npc, const int32_t* list, int rbe, uint64_t seed,
                       const uint64_t* ctr, const double* cdf, const PairTab& pairs,
                       double alpha, ModeTab<T> modes, int32_t* sampled, cudaStream_t st);
-// The independence Metropolis chain of App. G, one CTA per replica: P
-// samples (every thin-th state of P * thin steps) per replica into
-// `sampled` ([R][P] pairs), with the counter ctr[1].
+// The independence Metropolis chain of App. G, one cluster of 8 CTAs per
+// replica: P samples (every thin-th state of P * thin steps) per replica
+// into `sampled` ([R][P] pairs), with the counter ctr[1].
 void launch_mh_chain(const Reps& rp, int P, int thin, uint64_t seed, const uint64_t* ctr,
                      const double* cdf, double alpha, int32_t* sampled, cudaStream_t st);
 
