@@ -116,10 +116,7 @@ __device__ __forceinline__ double one_minus_exp_neg(double x) { return -expm1(-x
 // single rounding; larger arguments use the library functions.
 __device__ __forceinline__ Cplx<float> cexp_neg(float ar, float ai, float x) {
   const float u = ar * x, v = ai * x;
-  float s, c;
-  sincosf(v, &s, &c);
-  const float m = expf(-u);
-  // small-argument forms
+  // small-argument forms (the usual case: neighbouring particles)
   float em = fmaf(u, 1.0f / 720.0f, -1.0f / 120.0f);   // e^{-u} - 1 = -u + u^2/2 - ...
   em = fmaf(u, em, 1.0f / 24.0f);
   em = fmaf(u, em, -1.0f / 6.0f);
@@ -135,8 +132,11 @@ __device__ __forceinline__ Cplx<float> cexp_neg(float ar, float ai, float x) {
   sv = fmaf(v * v2, sv, v);
   const float re_small = 1.0f + fmaf(em, cm, em + cm);
   const float im_small = -fmaf(em, sv, sv);
-  const bool small = u < 0.0625f && fabsf(v) < 0.0625f;
-  return {small ? re_small : m * c, small ? im_small : -m * s};
+  if (u < 0.0625f && fabsf(v) < 0.0625f) return {re_small, im_small};
+  float s, c;
+  sincosf(v, &s, &c);
+  const float m = expf(-u);
+  return {m * c, -m * s};
 }
 __device__ __forceinline__ Cplx<double> cexp_neg(double ar, double ai, double x) {
   double s, c;
