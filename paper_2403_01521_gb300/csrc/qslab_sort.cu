@@ -12,6 +12,9 @@
 //   scatter stable placement: within a warp, keys are ranked in input order
 //           with __match_any_sync; warps of a tile are ordered by a per-digit
 //           prefix over their counts; tiles by the global scan.
+// Up to one tile of keys (kTile = 2048) one CTA does the whole sort in one
+// launch instead (small_sort_kernel: a bitonic network over (key, input
+// position), which gives the same stable order).
 // Several slabs of one call are sorted by z first and then, stably, by their
 // slab index (a second LSD sort over one or two more digits), which leaves
 // every slab in its own index range and ordered by z within it.
