@@ -147,6 +147,42 @@ def test_batched_equals_single(qslab, mixed, soe16, prec):
         one.close()
 
 
+def test_batched_all_short_chains(qslab, soe16):
+    """Every slab's carry chains shorter than 32 chunks: each is one group,
+    replayed from zero, and the group and chain phases are not launched at
+    all. Each replica against the oracle, and bit for bit against its own
+    single-slab call with the same launch shape."""
+    slabs = [workloads.uniform_slab(100, (14.0, 16.0, 5.0), 111, alpha=0.3),
+             _empty((10.0, 10.0, 5.0)),
+             workloads.uniform_slab(250, (20.0, 18.0, 6.0), 112, alpha=0.3),
+             workloads.uniform_slab(400, (22.0, 22.0, 8.0), 113, alpha=0.3)]
+    kc = lattice.kcut_for_tail(0.3, 1e-8)
+    tuning = (16, 64)            # 7, 16 and 25 chunks of 16 particles
+    got = _run_batched(qslab, slabs, "fp64", soe16, kc=kc, tuning=tuning)
+    assert got["status"] == 0
+    off = got["off"]
+    for r, sl in enumerate(slabs):
+        a, b = off[r], off[r + 1]
+        if a == b:
+            assert got["E"][r] == 0.0
+            continue
+        ref = soe_ewald2d.soe_full(sl.pos, sl.q, sl.box, sl.alpha, *soe16, kc=kc)
+        # energy scale: one slab's E is a small remainder (0.47 against
+        # sum |q phi| / 2 = 213)
+        escale = max(abs(ref["E"]), 0.5 * float(np.abs(sl.q * ref["phi"]).sum()))
+        assert abs(got["E"][r] - ref["E"]) <= FP64_TOL * escale, r
+        assert _maxrel(got["phi"][a:b], ref["phi"]) <= FP64_TOL, r
+        assert _maxrel(got["F"][a:b], ref["F"]) <= FP64_TOL, r
+        one = qslab.QSlab(0, "fp64").configure(sl.box, sl.alpha, soe16, kcut=kc).tuning(*tuning)
+        e, phi, F = one.compute(torch.tensor(sl.pos, device="cuda", dtype=torch.float64),
+                                torch.tensor(sl.q, device="cuda", dtype=torch.float64))
+        assert one.status() == 0
+        assert float(e.item()) == got["E"][r], r
+        assert np.array_equal(phi.cpu().numpy(), got["phi"][a:b]), r
+        assert np.array_equal(F.cpu().numpy(), got["F"][a:b]), r
+        one.close()
+
+
 def test_batched_graph_replay(qslab, mixed, soe16):
     """A CUDA graph of the batched call: every replay draws a fresh sample
     (device-side counter) and equals a plain call made with that counter."""
