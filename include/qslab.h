@@ -391,7 +391,10 @@ int qslab_md_configure(qslab_ctx* ctx, double dt, double mass, double gamma, dou
  * long-range energy (walls included), the real-space energy with the LJ
  * pairs, the LJ wall energy and the kinetic energy of vel (vel may be
  * NULL: 0). Needs qslab_md_configure, the box and rc
- * (QSLAB_ERR_NOT_CONFIGURED). Stream-ordered. */
+ * (QSLAB_ERR_NOT_CONFIGURED). Stream-ordered: the real-space part runs on
+ * an internal stream of the context, forked from `stream` and joined back
+ * to it with events (so it overlaps the long-range call and can be captured
+ * in a CUDA graph together with it). */
 int qslab_md_forces(qslab_ctx* ctx, int64_t N, const void* pos, const void* q, void* vel,
                     void* force, double* energies, void* stream);
 /* nsteps >= 1 BAOAB steps in place: pos, vel (device, 3N) and force (the
