@@ -35,6 +35,11 @@
  *     qslab_destroy().
  *   - Work is ordered on the caller's stream (cudaStream_t passed as void*;
  *     NULL = legacy default stream). qslab_compute() does not synchronise.
+ *     Parts of a call that do not depend on each other (the k = 0 term, the
+ *     mode table, the real-space part of an MD force pass) run on internal
+ *     streams of the context, forked from the caller's stream and joined
+ *     back to it with events before the call's last kernel, so the call as a
+ *     whole stays ordered on that stream and can be captured in a CUDA graph.
  */
 #ifndef QSLAB_H
 #define QSLAB_H
