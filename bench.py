@@ -33,7 +33,6 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "long-range energy+force particles/s at N=1e6 on 1 GB300 (FP32 vs FP64); % roofline"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 L2_BYTES = 129 * 1024 * 1024
 
@@ -154,32 +153,73 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_oracle_sample(sl, soe, P, seed, sample_modes=8, reps=1):
-    """Time the FP64 oracle on a bounded sample: the k = 0 term in full and
-    `sample_modes` of the P random-batch modes; scale the k-space time to P.
-    Returns (seconds per full call, description, cores)."""
+def _omp_threads():
+    """OpenMP threads the oracle's k-space loop runs on (its default is every
+    core this process may use)."""
+    env = os.environ.get("OMP_NUM_THREADS")
+    if env and env.strip().isdigit():
+        return int(env)
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_call(sl, soe, P, seed, modes=None):
+    """Time the FP64 oracle on one random-batch call of the workload: the
+    k-space recursion over `modes` of the P sampled modes (all of them by
+    default; OpenMP over the modes), then the whole k = 0 term (serial).
+    Returns (seconds per full call, description, threads), where a partial
+    mode sample is scaled to the P modes and says so."""
     from oracle import lattice, soe_ewald2d
     Lx, Ly, _ = sl.box
     mx, my = lattice.sample_modes(P, seed, 0, sl.alpha, Lx, Ly)
     H = lattice.H_direct(sl.alpha, Lx, Ly)
     gam = soe_ewald2d.rbe_prefactor(sl.alpha, Lx, Ly, mx, my, H, P)
     soe_ewald2d._load()
-    best = None
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        soe_ewald2d.kspace_pairs(sl.pos, sl.q, sl.box, sl.alpha, *soe, mx[:sample_modes],
-                                 my[:sample_modes], gam[:sample_modes])
-        t1 = time.perf_counter()
-        soe_ewald2d.kzero_pairs(sl.pos, sl.q, sl.box, sl.alpha, *soe)
-        t2 = time.perf_counter()
-        est = (t1 - t0) * P / sample_modes + (t2 - t1)
-        best = est if best is None else min(best, est)
-    desc = (f"oracle (C FP64 recursion, OpenMP) on the full N={sl.N} with {sample_modes} of "
-            f"the {P} sampled k plus the whole k=0 term; k-space time scaled by {P}/{sample_modes}")
-    return best, desc, os.cpu_count()
+    m = P if modes is None else min(int(modes), P)
+    t0 = time.perf_counter()
+    soe_ewald2d.kspace_pairs(sl.pos, sl.q, sl.box, sl.alpha, *soe, mx[:m], my[:m], gam[:m])
+    t1 = time.perf_counter()
+    soe_ewald2d.kzero_pairs(sl.pos, sl.q, sl.box, sl.alpha, *soe)
+    t2 = time.perf_counter()
+    threads = min(_omp_threads(), m)
+    if m == P:
+        desc = (f"oracle (C FP64 recursion) on one full call: N={sl.N}, all {P} sampled k "
+                f"(OpenMP over the modes, {threads} threads) and the k=0 term (serial); "
+                f"k-space {t1 - t0:.2f} s, k=0 {t2 - t1:.2f} s")
+        return (t2 - t0), desc, threads
+    desc = (f"oracle (C FP64 recursion) on N={sl.N} with {m} of the {P} sampled k "
+            f"({threads} threads) and the whole k=0 term (serial); the k-space time "
+            f"({t1 - t0:.2f} s) scaled by {P}/{m}, k=0 {t2 - t1:.2f} s")
+    return (t1 - t0) * P / m + (t2 - t1), desc, threads
+
+
+def cpu_oracle_single_core(P, seed, modes=16):
+    """The same oracle call on one core (OMP_NUM_THREADS=1, in a child
+    process so that the OpenMP runtime starts with one thread), on a stated
+    sample: `modes` of the P sampled k, scaled to P, plus the whole k = 0
+    term. Returns (seconds per full call, description), or (None, reason)."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench, workloads;"
+            "from paper_2403_01521_gb300.soe import load_soe;"
+            "t, d, n = bench.cpu_oracle_call(workloads.rbe_large(), load_soe(16), %d, %d, %d);"
+            "print(json.dumps([t, d]))") % (ROOT, P, seed, modes)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                           env=env, timeout=600)
+        t, d = json.loads(r.stdout.strip().splitlines()[-1])
+        return float(t), "single core: " + d
+    except Exception as exc:  # noqa: BLE001 - reported, not fatal
+        return None, f"single-core run failed: {exc}"
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, timed on the
+    headline workload. Each step is one full random-batch call (all 200
+    sampled modes) when the run has at most 20 steps, else a stated sample
+    of 200 * 20 / steps modes (at least 16) scaled to 200, so that the whole
+    run stays within a few minutes."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
@@ -187,12 +227,14 @@ def run_reference(args):
     from paper_2403_01521_gb300.soe import load_soe
     sl = workloads.rbe_large()
     soe = load_soe(16)
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        cpu_oracle_sample(sl, soe, 200, 11, sample_modes=2)
+    P = 200
+    modes = P if args.steps <= 20 else max(16, (P * 20) // max(args.steps, 1))
+    for _ in range(min(args.warmup, 1)):
+        cpu_oracle_call(sl, soe, P, 11, modes=16)
     times = []
     desc = cores = None
     for _ in range(args.steps):
-        t, desc, cores = cpu_oracle_sample(sl, soe, 200, 11, sample_modes=8)
+        t, desc, cores = cpu_oracle_call(sl, soe, P, 11, modes=modes)
         times.append(t)
     sec = float(np.mean(times))
     value = sl.N / sec
@@ -204,7 +246,7 @@ def run_reference(args):
                                    "alpha=0.1, P=200 random-batch k per call, M=16 SOE",
                        "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "particles/s", "cores": cores,
-                             "kind": "oracle", "sample": desc},
+                             "kind": "oracle", "sample": f"each of the {args.steps} steps: " + desc},
             "e2e": {"value": value, "unit": "particles/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -232,27 +274,30 @@ def run_ours(args):
     sl = workloads.rbe_large(seed=3 + rank)
     N = sl.N
 
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+
     def make(prec):
-        s = qslab.QSlab(local, prec).configure(sl.box, sl.alpha, soe, rbe=(P, 1000 + rank))
-        qslab.qslab_set_timing(s.h, True)
-        return s
+        return qslab.QSlab(local, prec).configure(sl.box, sl.alpha, soe, rbe=(P, 1000 + rank))
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def timed(slab, dtype, steps, warmup, sampler=None):
+    def timed(slab, dtype, steps, warmup, sampler=None, phase_steps=0):
+        """Time `steps` calls with the library's per-phase events off and
+        nothing read back between calls; then, if phase_steps > 0, as many
+        more calls with the per-phase events on (read after each call) for
+        the phase breakdown and the recurrence kernel's duration."""
         pos = torch.tensor(sl.pos, device=dev, dtype=dtype)
         q = torch.tensor(sl.q, device=dev, dtype=dtype)
         e = torch.empty(1, dtype=torch.float64, device=dev)
         phi = torch.empty(N, dtype=dtype, device=dev)
         F = torch.empty((N, 3), dtype=dtype, device=dev)
+        qslab.qslab_set_timing(slab.h, False)
         for _ in range(warmup):
             slab.compute(pos, q, e, phi, F)
         slab.check()
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        phases = []
-        launches = 0
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
@@ -263,25 +308,33 @@ def run_ours(args):
             ev0[i].record(stream)
             slab.compute(pos, q, e, phi, F)
             ev1[i].record(stream)
-            ph, nl = qslab.qslab_get_timings(slab.h)
-            phases.append(ph)
-            launches += nl
         torch.cuda.synchronize(dev)
         clocks = sampler.stop() if sampler else None
         if ws > 1:
             torch.distributed.barrier()
         slab.check()
         ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        phases, launches = [], 0
+        if phase_steps:
+            qslab.qslab_set_timing(slab.h, True)
+            for i in range(phase_steps):
+                flush.zero_()
+                slab.compute(pos, q, e, phi, F)
+                ph, nl = qslab.qslab_get_timings(slab.h)
+                phases.append(ph)
+                launches = nl
+            qslab.qslab_set_timing(slab.h, False)
+            slab.check()
         return float(np.mean(ms)), phases, launches, clocks, float(e.item())
 
     # ---- FP32C (headline)
     s32 = make("fp32c")
     ms32, ph32, nl32, clocks, E32 = timed(s32, torch.float32, args.steps, args.warmup,
-                                          ClockSampler(local))
+                                          ClockSampler(local), phase_steps=min(args.steps, 20))
     # ---- FP64 (reported beside it)
     s64 = make("fp64")
     st64 = max(1, min(args.steps, 3))
-    ms64, ph64, nl64, _, E64 = timed(s64, torch.float64, st64, 1)
+    ms64, _, _, _, E64 = timed(s64, torch.float64, st64, 1)
     s64.close()
 
     # slowest rank decides
@@ -314,7 +367,7 @@ def run_ours(args):
     work = algorithmic_instr(P, N, M)
     achieved = work / (rec_ms * 1e-3) / 1e12
     smax = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = SM_COUNT * FP32_LANES_PER_SM * smax * 1e6 / 1e12
+    peak = sm_count * FP32_LANES_PER_SM * smax * 1e6 / 1e12
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tpath):
@@ -338,18 +391,23 @@ def run_ours(args):
         "config": {"workload": "rbe_large: N=1e6 charges +-1 uniform in 400x400x50, alpha=0.1, "
                                "P=200 random-batch k per call (sampled on the device), "
                                "M=16 SOE (conditioned table), compensated FP32 "
-                               "(FP64 chunk carries, FP64 k=0 term and reductions)",
+                               "(FP32 phases and in-chunk scans, double-float chunk carries "
+                               "and k=0 prefix sums, FP64 reductions)",
                    "N": N, "P": P, "M": M, "per_rank": "independent replica",
                    "l2": "flushed between steps (256 MB write, untimed)"},
         "fp64": {"value": job_throughput(N, ws, ms64_max), "unit": "particles/s", "ms_per_step": ms64_max,
                  "steps": st64, "energy": E64},
         "energy_fp32c": E32,
         "phases_ms": phases,
-        "roofline": {"bound": "alu", "kernel": "kspace_final_kernel (recurrences + gather)",
+        "roofline": {"bound": "alu", "kernel": "kspace_final_f2_kernel (recurrences + gather)",
                      "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
-                                   f"{smax:.0f} MHz ({peak_kind} max SM clock)",
+                     "kernel_ms": rec_ms,
+                     "timing": f"CUDA events around the kernel on its stream, mean of "
+                               f"{len(ph32)} calls after the timed loop (same inputs, L2 "
+                               f"flushed)",
+                     "peak_basis": f"{sm_count} SMs (device query) x {FP32_LANES_PER_SM} FP32 "
+                                   f"lanes x {smax:.0f} MHz ({peak_kind} max SM clock)",
                      "work": "K*N*(24*(M+1)+20) FP32 instructions per launch",
                      "measured_tops": {k: v / 1e12 for k, v in mp.items()},
                      "frac_of_measured_fp32_fma": achieved / (mp["fp32_fma"] / 1e12)},
@@ -357,7 +415,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(N * 3 * 4 + N * 4),
                 "d2h_bytes_per_step": int(8 + N * 4 + N * 12)},
         "clocks": clocks,
-        "gpu_launches": int(nl32),
+        "gpu_launches": int(nl32) * args.steps,
+        "gpu_launches_per_step": int(nl32),
     }
     if not args.no_batched:
         line["batched"] = run_batched(args, qslab, soe, dev, ws, rank, local, peak, smax)
@@ -365,11 +424,14 @@ def run_ours(args):
     line["virial"] = run_virial(args, qslab, soe, dev, ws, sl, P, ms32_max)
     line["energy_only"] = run_energy_only(args, qslab, soe, dev, ws, sl, P, ms32_max)
     line["md"] = run_md(args, qslab, soe, dev, ws)
-    line["configs"] = run_configs(args, qslab, dev, ws, smax)
+    line["configs"] = run_configs(args, qslab, dev, ws, smax, sm_count)
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        t, desc, cores = cpu_oracle_sample(sl, soe, P, 1000, sample_modes=8)
+        t, desc, cores = cpu_oracle_call(sl, soe, P, 1000)
+        t1, desc1 = cpu_oracle_single_core(P, 1000)
         line["cpu_baseline"] = {"value": N / t, "unit": "particles/s", "cores": cores,
-                                "kind": "oracle", "sample": desc}
+                                "kind": "oracle", "sample": desc,
+                                "single_core_value": (N / t1) if t1 else None,
+                                "single_core_sample": desc1}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -509,7 +571,7 @@ def run_md(args, qslab, soe, dev, ws):
             "us_per_step": 1e3 * ms, "steps_per_s": ws / (ms * 1e-3), "steps": reps * chunk}
 
 
-def run_configs(args, qslab, dev, ws, smax):
+def run_configs(args, qslab, dev, ws, smax, sm_count):
     """The other workloads of the paper's shape, full k-sum, one call per
     step (median of CUDA-event timings after warm-up, L2 flushed): the
     1000-particle parity slab, the N = 1e5 slab (FP32 vs FP64) and the
@@ -520,7 +582,7 @@ def run_configs(args, qslab, dev, ws, smax):
 
     import workloads
     from paper_2403_01521_gb300.soe import load_soe
-    peak = SM_COUNT * FP32_LANES_PER_SM * smax * 1e6
+    peak = sm_count * FP32_LANES_PER_SM * smax * 1e6
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     cases = [("small_full N=1000 30x30x10 alpha=0.3 M=16 full-k", workloads.small_full(), 16),
              ("fp32_full N=1e5 100x100x20 alpha=0.25 M=16 full-k", workloads.fp32_full(), 16),

@@ -26,7 +26,11 @@
  *
  * Conventions shared by all calls:
  *   - Return value 0 on success, a negative QSLAB_ERR_* code otherwise.
- *     qslab_strerror() gives a message. A failed call changes nothing.
+ *     qslab_strerror() gives a message. A failed call changes no
+ *     configuration, no random-batch counter and no output; a failed device
+ *     allocation may leave the context without its workspace (allocated
+ *     again by the next call), which ends the state an energy-only call left
+ *     for qslab_compute_adjoint().
  *   - A context belongs to one host thread at a time and to one CUDA device
  *     (chosen at creation; every call makes it current).
  *   - Device pointers are plain CUDA device addresses (for example from
@@ -53,9 +57,13 @@ extern "C" {
 typedef struct qslab_ctx qslab_ctx;
 
 /* Precision of positions, charges, potentials and forces, and of the
- * arithmetic. QSLAB_FP64: everything in FP64. QSLAB_FP32C: FP32 inputs and
- * outputs, FP32 phases and scans, with FP64 chunk carries, an FP64 k = 0
- * term and FP64 reductions. */
+ * arithmetic. QSLAB_FP64: everything in FP64. QSLAB_FP32C (compensated
+ * FP32): FP32 inputs and outputs; FP32 phases and FP32 recurrences within
+ * each chunk of sorted particles (the k != 0 scans and the k = 0 scans of
+ * the exponential sums); double-float (two FP32 numbers, about 48 bits)
+ * chunk-to-chunk carries of both, and double-float prefix sums of q and q z
+ * for the |z| part of the k = 0 term; the per-particle sums over mode
+ * ranges, the j = i constants and the energy reduction in FP64. */
 #define QSLAB_FP64 0
 #define QSLAB_FP32C 1
 
@@ -67,7 +75,9 @@ typedef struct qslab_ctx qslab_ctx;
 #define QSLAB_ERR_NONNEUTRAL (-5)     /* |sum q| above tolerance (Thm 2.1)   */
 #define QSLAB_ERR_ALLOC (-6)          /* device or host allocation failed    */
 #define QSLAB_ERR_CUDA (-7)           /* a CUDA runtime call failed          */
-#define QSLAB_ERR_TIMEOUT (-8)        /* a bounded device wait gave up       */
+#define QSLAB_ERR_TIMEOUT (-8)        /* reserved: a bounded device wait gave
+                                         up (no kernel of this version waits
+                                         on another CTA, so none returns it) */
 #define QSLAB_ERR_TOO_LARGE (-9)      /* exceeds qslab_compute_static's scratch */
 
 /* Create a context on CUDA device `cuda_device` with precision `prec`
@@ -449,6 +459,20 @@ int qslab_get_timings(qslab_ctx* ctx, double* ms8, int* launches);
 
 /* Message for a return code. */
 const char* qslab_strerror(int code);
+
+/* Diagnostics (the paper has no counterpart; for tests of the library's
+ * own error handling).
+ * qslab_debug_alloc_count(): the number of device allocations (cudaMalloc)
+ * the library has made in this process, over all contexts.
+ * qslab_debug_fail_alloc(n): the next n device allocations of the library
+ * fail as an out-of-memory cudaMalloc would, decided on the host without
+ * calling the CUDA runtime (no GPU fault); n = 0 turns this off. A call
+ * whose allocation fails returns QSLAB_ERR_ALLOC. When growing a buffer the
+ * library allocates the new one before releasing the old one; if that
+ * fails it releases the old buffer and tries once more (so one injected
+ * failure is absorbed, two fail the call). */
+long long qslab_debug_alloc_count(void);
+int qslab_debug_fail_alloc(int n);
 
 #ifdef __cplusplus
 }

@@ -120,7 +120,9 @@ def _assemble(q, box, alpha, phik, Fk, phi0, fz0, Dk):
     phi = phik + phi0 + q * diag
     F = Fk.copy()
     F[:, 2] += fz0
-    return {"E": 0.5 * float(q @ phi), "phi": phi, "F": F}
+    # the three parts of E: k != 0 pairs, k = 0 pairs, j = i constants and self
+    parts = (0.5 * float(q @ phik), 0.5 * float(q @ phi0), 0.5 * diag * float(q @ q))
+    return {"E": 0.5 * float(q @ phi), "phi": phi, "F": F, "E_parts": parts}
 
 
 def soe_full(pos, q, box, alpha, s, w, kc=None, tail=1e-8, modes=None):

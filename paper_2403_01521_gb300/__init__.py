@@ -108,6 +108,8 @@ def load(build_if_missing: bool = True):
         "qslab_set_timing": ([P, I], I),
         "qslab_get_timings": ([P, P, P], I),
         "qslab_strerror": ([I], ctypes.c_char_p),
+        "qslab_debug_alloc_count": ([], ctypes.c_longlong),
+        "qslab_debug_fail_alloc": ([I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -395,6 +397,14 @@ def qslab_strerror(code: int) -> str:
 
 
 # ---------------------------------------------------------------- wrapper
+
+
+def qslab_debug_alloc_count() -> int:
+    return int(load().qslab_debug_alloc_count())
+
+
+def qslab_debug_fail_alloc(n: int):
+    _check(load().qslab_debug_fail_alloc(int(n)), "qslab_debug_fail_alloc")
 
 
 def kcut_for_tail(alpha: float, tail: float) -> float:

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <map>
 #include <utility>
@@ -59,6 +60,7 @@ struct Tables {
 
 struct qslab_ctx {
   int device = 0;
+  int sm_count = 152;           // multiprocessors of the device (queried at creation)
   int prec = QSLAB_FP64;
   // configuration
   double Lx = 0, Ly = 0, Lz = 0, alpha = 0;
@@ -138,6 +140,52 @@ int cuda_fail(cudaError_t e) {
   } while (0)
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+// Every device allocation of the library goes through lib_malloc: it counts
+// them (qslab_debug_alloc_count) and, for failure-injection tests, makes the
+// next g_fail_allocs of them fail as an out-of-memory cudaMalloc would, on
+// the host, without calling the runtime.
+std::atomic<long long> g_alloc_count{0};
+std::atomic<int> g_fail_allocs{0};
+
+cudaError_t lib_malloc(void** p, size_t bytes) {
+  int left = g_fail_allocs.load();
+  while (left > 0) {
+    if (g_fail_allocs.compare_exchange_weak(left, left - 1)) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+  }
+  const cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) ++g_alloc_count;
+  return e;
+}
+
+// Grow a device buffer to at least `need` bytes. The new buffer is allocated
+// before the old one is released, so that a failed allocation leaves the old
+// buffer and its contents in place; only when that fails is the old buffer
+// released (*released = true) and the allocation tried once more.
+int grow_buffer(void** buf, size_t* have, size_t need, bool* released) {
+  if (need <= *have && *buf) return QSLAB_OK;
+  void* nb = nullptr;
+  cudaError_t e = lib_malloc(&nb, need);
+  if (e != cudaSuccess && *buf) {
+    cudaDeviceSynchronize();
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    if (released) *released = true;
+    e = lib_malloc(&nb, need);
+  }
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (*buf) {
+    cudaDeviceSynchronize();
+    cudaFree(*buf);
+  }
+  *buf = nb;
+  *have = need;
+  return QSLAB_OK;
+}
 
 constexpr int kMaxReplicas = 1 << 20;
 constexpr int kFlatChunks = 32;   // carry chains shorter than this are one group
@@ -350,6 +398,41 @@ bool same_key(const Tables& t, const qslab_ctx* c, int R, const int64_t* off, co
          std::memcmp(t.box.data(), box, sizeof(double) * 3 * R) == 0;
 }
 
+// Automatic chunk length of the k-space passes. The passes run two CTAs per
+// SM, one per (chunk, mode range), all of about the same duration, so the
+// grid runs in waves of 2 x SMs CTAs:
+//   - small problems: about one wave, chunks of 16 below about 5000
+//     particles (shorter serial loops beat the extra carry work there), else
+//     a multiple of 32;
+//   - large ones: the longest chunks, except that among the multiples of 32
+//     in [3/4 Lmax, Lmax] the one whose last wave is fullest is taken (a last
+//     wave of 0.4 leaves most SMs idle for one CTA time);
+//   - FP32 with four or more mode ranges (full k-sums of thousands of modes,
+//     whose parallelism comes from the modes): at most 256 particles, which
+//     halves the FP32 steps between two double-float carries and costs no
+//     time there.
+int auto_chunk(const qslab_ctx* c, const Tables& t, int R, const int64_t* off, int64_t N) {
+  const bool dp = c->prec == QSLAB_FP64;
+  int Lmax = dp ? 256 : 512;
+  if (!dp && t.nkr >= 4) Lmax = 256;
+  const int64_t slots = 2 * (int64_t)c->sm_count;
+  const int64_t target = (slots + t.nkr - 1) / t.nkr;
+  int64_t want = (N + target - 1) / target;
+  want = want <= 16 ? 16 : ((want + 31) / 32) * 32;
+  if (want < Lmax) return (int)want;
+  int best = Lmax;
+  double best_eff = -1.0;
+  for (int L = Lmax; L >= (3 * Lmax) / 4; L -= 32) {
+    int64_t ctas = 0;
+    for (int r = 0; r < R; ++r) ctas += (off[r + 1] - off[r] + L - 1) / L;
+    ctas *= t.nkr;
+    const int64_t waves = (ctas + slots - 1) / slots;
+    const double eff = (double)ctas / (double)(waves * slots);
+    if (eff > best_eff + 0.02) { best_eff = eff; best = L; }
+  }
+  return best;
+}
+
 // Host part of the tables of a call (no device work). Validates the replica
 // offsets and boxes.
 int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* box, Tables& t,
@@ -457,16 +540,8 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
   }
   if ((size_t)R * t.Kpad > ((size_t)1 << 31) / 64) return QSLAB_ERR_INVALID_ARG;
   // chunk length: about two CTAs per SM over all replicas and mode ranges
-  const int Lmax = dp ? 256 : 512;
   int L = c->tune_L;
-  if (L <= 0) {
-    const int64_t target = (2 * 152 + t.nkr - 1) / t.nkr;
-    int64_t want = (N + target - 1) / target;
-    // small slabs (N below about 5000): chunks of 16, whose shorter serial
-    // loops beat the extra carry work there; else a multiple of 32
-    want = want <= 16 ? 16 : ((want + 31) / 32) * 32;
-    L = (int)(want > Lmax ? Lmax : want);
-  }
+  if (L <= 0) L = auto_chunk(c, t, R, off, N);
   t.L = L;
   // k = 0 chunks: short sequential loops, many threads (no longer than the
   // k-space chunks, so that small slabs get more, shorter chains)
@@ -547,8 +622,11 @@ int build_tables(const qslab_ctx* c, int R, const int64_t* off, const double* bo
   return QSLAB_OK;
 }
 
-// Upload the host tables into a device buffer of at least t.bytes.
-int upload_tables(const Tables& t, void* dst) {
+// Upload the host tables into a device buffer of at least t.bytes, ordered
+// on the call's stream (after the work of earlier calls on it that may still
+// read the buffer, before this call's kernels; the pageable source is staged
+// by the runtime before cudaMemcpyAsync returns).
+int upload_tables(const Tables& t, void* dst, cudaStream_t st) {
   std::vector<char> stage(t.o_sampled, 0);
   auto put = [&stage](size_t o, const void* src, size_t b) {
     if (b) std::memcpy(stage.data() + o, src, b);
@@ -570,30 +648,29 @@ int upload_tables(const Tables& t, void* dst) {
   }
   put(t.o_trig, trig, sizeof(trig));
   put(t.o_vdiag, t.vdiag.data(), sizeof(double) * t.vdiag.size());
-  QS_CUDA(cudaMemcpy(dst, stage.data(), stage.size(), cudaMemcpyHostToDevice));
+  QS_CUDA(cudaMemcpyAsync(dst, stage.data(), stage.size(), cudaMemcpyHostToDevice, st));
   return QSLAB_OK;
 }
 
 // Make c->tab describe (R, off, box), rebuilding and uploading if needed.
-int select_tables(qslab_ctx* c, int R, const int64_t* off, const double* box) {
+// New tables end what an energy-only call left for its adjoint.
+int select_tables(qslab_ctx* c, int R, const int64_t* off, const double* box, cudaStream_t st) {
   int rc = ensure_config(c);
   if (rc) return rc;
   if (same_key(c->tab, c, R, off, box)) return QSLAB_OK;
   Tables t;
   rc = build_tables(c, R, off, box, t, &c->tab);
   if (rc) return rc;
-  c->tab.valid = false;
-  if (t.bytes > c->tab_bytes) {
-    if (c->d_tab) {
-      cudaDeviceSynchronize();
-      cudaFree(c->d_tab);
-    }
-    c->d_tab = nullptr;
-    c->tab_bytes = 0;
-    QS_CUDA(cudaMalloc(&c->d_tab, t.bytes));
-    c->tab_bytes = t.bytes;
+  bool released = false;
+  rc = grow_buffer(&c->d_tab, &c->tab_bytes, t.bytes, &released);
+  if (released) {
+    c->tab.valid = false;
+    c->primed = false;
   }
-  rc = upload_tables(t, c->d_tab);
+  if (rc) return rc;
+  c->tab.valid = false;
+  c->primed = false;
+  rc = upload_tables(t, c->d_tab, st);
   if (rc) return rc;
   c->tab = std::move(t);
   c->coef_ready = false;
@@ -677,16 +754,10 @@ Plan make_plan(const qslab_ctx* c, bool host_io, bool virial = false) {
 }
 
 int ensure_ws(qslab_ctx* c, size_t bytes) {
-  if (bytes <= c->ws_bytes) return QSLAB_OK;
-  if (c->d_ws) {
-    cudaDeviceSynchronize();
-    cudaFree(c->d_ws);
-  }
-  c->d_ws = nullptr;
-  c->ws_bytes = 0;
-  QS_CUDA(cudaMalloc(&c->d_ws, bytes));
-  c->ws_bytes = bytes;
-  return QSLAB_OK;
+  bool released = false;
+  const int rc = grow_buffer(&c->d_ws, &c->ws_bytes, bytes, &released);
+  if (released) c->primed = false;   // the adjoint's stored state is gone
+  return rc;
 }
 
 template <typename T>
@@ -875,9 +946,9 @@ int status_code(unsigned f) {
 
 // Tables and workspace for one call; on success P describes the workspace.
 int setup_call(qslab_ctx* c, int R, const int64_t* off, const double* box, bool host_io,
-               Plan& P, bool virial = false) {
+               Plan& P, cudaStream_t st, bool virial = false) {
   QS_CUDA(cudaSetDevice(c->device));
-  int rc = select_tables(c, R, off, box);
+  int rc = select_tables(c, R, off, box, st);
   if (rc) return rc;
   P = make_plan(c, host_io, virial);
   return ensure_ws(c, P.total);
@@ -909,8 +980,12 @@ int qslab_create(qslab_ctx** out, int cuda_device, int prec) {
   if (!c) return QSLAB_ERR_ALLOC;
   c->device = cuda_device;
   c->prec = prec;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cuda_device) == cudaSuccess &&
+      sms > 0)
+    c->sm_count = sms;
   void* small = nullptr;
-  cudaError_t e = cudaMalloc(&small, 256);
+  cudaError_t e = lib_malloc(&small, 256);
   if (e != cudaSuccess) {
     delete c;
     return cuda_fail(e);
@@ -1050,7 +1125,7 @@ int qslab_compute(qslab_ctx* c, int64_t N, const void* pos, const void* q,
   const int64_t off[2] = {0, N};
   const double box[3] = {c->Lx, c->Ly, c->Lz};
   Plan P;
-  const int rc = setup_call(c, 1, off, box, false, P);
+  const int rc = setup_call(c, 1, off, box, false, P, static_cast<cudaStream_t>(stream));
   if (rc) return rc;
   return dispatch(c, P, pos, q, energy, phi, force, static_cast<cudaStream_t>(stream));
 }
@@ -1061,7 +1136,7 @@ int qslab_compute_batched(qslab_ctx* c, int R, const int64_t* offsets, const dou
   if (!c || !pos || !q || !offsets || !boxes || R < 1 || R > kMaxReplicas)
     return QSLAB_ERR_INVALID_ARG;
   Plan P;
-  const int rc = setup_call(c, R, offsets, boxes, false, P);
+  const int rc = setup_call(c, R, offsets, boxes, false, P, static_cast<cudaStream_t>(stream));
   if (rc) return rc;
   return dispatch(c, P, pos, q, energies, phi, force, static_cast<cudaStream_t>(stream));
 }
@@ -1074,7 +1149,7 @@ int qslab_compute_virial(qslab_ctx* c, int64_t N, const void* pos, const void* q
   const int64_t off[2] = {0, N};
   const double box[3] = {c->Lx, c->Ly, c->Lz};
   Plan P;
-  const int rc = setup_call(c, 1, off, box, false, P, true);
+  const int rc = setup_call(c, 1, off, box, false, P, static_cast<cudaStream_t>(stream), true);
   if (rc) return rc;
   return dispatch(c, P, pos, q, energy, phi, force, static_cast<cudaStream_t>(stream), virial);
 }
@@ -1087,7 +1162,7 @@ int qslab_compute_batched_virial(qslab_ctx* c, int R, const int64_t* offsets,
       R > kMaxReplicas)
     return QSLAB_ERR_INVALID_ARG;
   Plan P;
-  const int rc = setup_call(c, R, offsets, boxes, false, P, true);
+  const int rc = setup_call(c, R, offsets, boxes, false, P, static_cast<cudaStream_t>(stream), true);
   if (rc) return rc;
   return dispatch(c, P, pos, q, energies, phi, force, static_cast<cudaStream_t>(stream), virial);
 }
@@ -1100,7 +1175,7 @@ int qslab_compute_energy(qslab_ctx* c, int64_t N, const void* pos, const void* q
   const double box[3] = {c->Lx, c->Ly, c->Lz};
   Plan P;
   c->primed = false;
-  const int rc = setup_call(c, 1, off, box, false, P, true);
+  const int rc = setup_call(c, 1, off, box, false, P, static_cast<cudaStream_t>(stream), true);
   if (rc) return rc;
   return dispatch(c, P, pos, q, energy, nullptr, nullptr, static_cast<cudaStream_t>(stream),
                   nullptr, 1);
@@ -1113,7 +1188,7 @@ int qslab_compute_batched_energy(qslab_ctx* c, int R, const int64_t* offsets,
     return QSLAB_ERR_INVALID_ARG;
   Plan P;
   c->primed = false;
-  const int rc = setup_call(c, R, offsets, boxes, false, P, true);
+  const int rc = setup_call(c, R, offsets, boxes, false, P, static_cast<cudaStream_t>(stream), true);
   if (rc) return rc;
   return dispatch(c, P, pos, q, energies, nullptr, nullptr, static_cast<cudaStream_t>(stream),
                   nullptr, 1);
@@ -1139,7 +1214,7 @@ int qslab_compute_host(qslab_ctx* c, int64_t N, const void* pos_host, const void
   const int64_t off[2] = {0, N};
   const double box[3] = {c->Lx, c->Ly, c->Lz};
   Plan P;
-  int rc = setup_call(c, 1, off, box, true, P);
+  int rc = setup_call(c, 1, off, box, true, P, static_cast<cudaStream_t>(stream));
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t tsz = c->prec == QSLAB_FP64 ? 8 : 4;
@@ -1247,16 +1322,8 @@ int realspace_call(qslab_ctx* c, int64_t N, const void* pos, const void* q, doub
   g.hz = c->Lz / g.ncz;
   QS_CUDA(cudaSetDevice(c->device));
   const size_t need = rs_workspace_bytes(g);
-  if (need > c->rs_ws_bytes) {
-    if (c->d_rs_ws) {
-      cudaDeviceSynchronize();
-      cudaFree(c->d_rs_ws);
-    }
-    c->d_rs_ws = nullptr;
-    c->rs_ws_bytes = 0;
-    QS_CUDA(cudaMalloc(&c->d_rs_ws, need));
-    c->rs_ws_bytes = need;
-  }
+  const int grc = grow_buffer(&c->d_rs_ws, &c->rs_ws_bytes, need, nullptr);
+  if (grc) return grc;
   if (c->prec == QSLAB_FP64)
     launch_realspace<double>(g, static_cast<const double*>(pos), static_cast<const double*>(q),
                              c->d_rs_ws, c->d_status, energy, static_cast<double*>(phi),
@@ -1343,16 +1410,8 @@ int md_buffers(qslab_ctx* c, int64_t N, MDBufs& b) {
   const size_t tsz = c->prec == QSLAB_FP64 ? 8 : 4;
   const size_t f = a256(3 * tsz * (size_t)N);
   const size_t need = 2 * f + a256(16 * (size_t)md_blocks(N)) + 256;
-  if (need > c->md_bytes) {
-    if (c->d_md) {
-      cudaDeviceSynchronize();
-      cudaFree(c->d_md);
-    }
-    c->d_md = nullptr;
-    c->md_bytes = 0;
-    QS_CUDA(cudaMalloc(&c->d_md, need));
-    c->md_bytes = need;
-  }
+  const int grc = grow_buffer(&c->d_md, &c->md_bytes, need, nullptr);
+  if (grc) return grc;
   char* p = static_cast<char*>(c->d_md);
   b.flr = p;
   b.frs = p + f;
@@ -1390,7 +1449,7 @@ int md_run(qslab_ctx* c, int64_t N, void* pos, void* vel, const void* q, void* f
   const int64_t off[2] = {0, N};
   const double box[3] = {c->Lx, c->Ly, c->Lz};
   Plan P;
-  int rc = setup_call(c, 1, off, box, false, P);
+  int rc = setup_call(c, 1, off, box, false, P, st);
   if (rc) return rc;
   MDBufs b;
   rc = md_buffers(c, N, b);
@@ -1559,7 +1618,7 @@ int qslab_autotune(qslab_ctx* c, int R, const int64_t* offsets, const double* bo
       c->tune_L = L;
       c->tune_KR = kr;
       Plan P;
-      rc = setup_call(c, R, offsets, boxes, false, P);
+      rc = setup_call(c, R, offsets, boxes, false, P, st);
       if (rc == QSLAB_ERR_ALLOC) { rc = QSLAB_OK; cudaGetLastError(); continue; }
       if (rc) break;
       rc = dispatch(c, P, pos, q, nullptr, nullptr, nullptr, st);   // warm-up
@@ -1612,6 +1671,14 @@ const char* qslab_strerror(int code) {
     case QSLAB_ERR_TOO_LARGE: return "problem too large for the fixed scratch of qslab_compute_static";
     default: return "unknown error";
   }
+}
+
+long long qslab_debug_alloc_count(void) { return g_alloc_count.load(); }
+
+int qslab_debug_fail_alloc(int n) {
+  if (n < 0) return QSLAB_ERR_INVALID_ARG;
+  g_fail_allocs.store(n);
+  return QSLAB_OK;
 }
 
 }  // extern "C"
@@ -1690,12 +1757,14 @@ extern "C" int qslab_compute_static(qslab_ctx* c, int64_t N, const void* pos, co
   const double box[3] = {c->Lx, c->Ly, c->Lz};
   if (c->mode == 2 && (axis_mmax(c->alpha, c->Lx) > 1000000 || axis_mmax(c->alpha, c->Ly) > 1000000))
     return QSLAB_ERR_TOO_LARGE;
-  rc = build_tables(&t, 1, off, box, t.tab);
+  Tables tb;
+  rc = build_tables(&t, 1, off, box, tb, c->tab.valid ? &c->tab : nullptr);
   if (rc) return rc;
+  t.tab = std::move(tb);
   if (t.tab.bytes > t.tab_bytes) return QSLAB_ERR_TOO_LARGE;
   const Plan P = make_plan(&t, false);
   if (P.total > t.ws_bytes) return QSLAB_ERR_TOO_LARGE;
-  rc = upload_tables(t.tab, t.d_tab);   // fits: no allocation
+  rc = upload_tables(t.tab, t.d_tab, st);   // fits: no allocation
   if (rc) return rc;
   t.coef_ready = false;
   // the status word starts from zero on every call

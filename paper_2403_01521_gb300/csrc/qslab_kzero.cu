@@ -1,6 +1,8 @@
 // The k = 0 term of the SOE-Ewald2D long-range part (Eq. 3.26 and its z
-// derivative): FP64 (or double-float) prefix sums for the |z| part and SOE
-// scans over the z-sorted particles for the exponential part.
+// derivative): prefix sums for the |z| part (FP64 on the FP64 path,
+// double-float on the FP32 path) and SOE scans over the z-sorted particles
+// for the exponential part (within a chunk in the path precision, FP32 on
+// the FP32 path; carries between chunks in FP64 or double-float).
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -19,9 +21,10 @@ namespace qslab {
 //        + sum_l (w_l/sqrt(pi)) [ -(2/s_l + s_l)(S_l^f - S_l^b) + 2 alpha (H_l^f - H_l^b) ]
 // with S_l = sum_j q_j e^{-a_l |z_ij|} and H_l = sum_j q_j |z_ij| e^{-a_l |z_ij|}
 // split into j < i (f) and j > i (b), c1 = sum_l 2 w_l/(s_l sqrt(pi)). The
-// |z| sums come from FP64 prefix sums of q and q z (they cancel heavily).
-// S and H are scanned in the path precision T, per chunk of L0 particles
-// with FP64 carries between chunks; H is carried without cancellation:
+// |z| sums come from prefix sums of q and q z in the carry type (FP64, or
+// double-float on the FP32 path: they cancel heavily). S and H are scanned
+// in the path precision T, per chunk of L0 particles, with carries between
+// chunks in the carry type; H is carried without cancellation:
 //   H_i = d_i (H_{i-1} + dz_i S_{i-1}),  S_i = d_i S_{i-1} + q_i  (inclusive).
 // One thread per (chunk, SOE pair representative); the lanes of a chunk sit
 // in one warp and are summed by shuffles.

@@ -388,8 +388,12 @@ __global__ void __launch_bounds__(64) mode_coef_kernel(Reps rp, int npc, const i
       ci = -2.0 * k * qi * pr.mult[p] * gam;
       br = cr * ar - ci * ai;                            // times a_p
       bi = cr * ai + ci * ar;
-      sY += cr;
-      sZ += br;
+      // the kernels remove the j = i term with sY and sZ; summing the
+      // coefficients as the kernels see them (rounded to T) makes that
+      // removal exact up to one rounding of sY (rounded one by one, the
+      // mismatch would leave a bias of q_i^2 times it in every potential)
+      sY += (double)(T)cr;
+      sZ += (double)(T)br;
     }
     mt.cp[((size_t)0 * npc + p) * ks + mg] = (T)cr;
     mt.cp[((size_t)1 * npc + p) * ks + mg] = (T)ci;
@@ -410,8 +414,8 @@ __global__ void __launch_bounds__(64) mode_coef_kernel(Reps rp, int npc, const i
   mt.kk[mg] = (T)k;
   mt.ck[mg] = (T)ck;
   mt.ckk[mg] = (T)(ck * k);
-  mt.sY[mg] = (T)(ck + sY);
-  mt.sZ[mg] = (T)(ck * k + sZ);
+  mt.sY[mg] = (T)((double)(T)ck + sY);
+  mt.sZ[mg] = (T)((double)(T)(ck * k) + sZ);
 }
 
 // ================================================= Metropolis k-sampler

@@ -1,14 +1,15 @@
 """GPU: the full k-sum at N = 1e6 (400 x 400 x 50, alpha = 0.1, kc at
 Gaussian tail 1e-8: 9392 lattice vectors, 4696 half-plane modes, M = 16).
 
-The oracle's energy of this configuration (positions rounded to FP32) is
-stored in tests/golden/rbe_large_fullk.json, written by
-tests/golden/make_golden.py from the oracle alone (about 8 minutes on 8
-cores). Against it: the FP64 path to 1e-10 relative, the FP32 path to 1e-6.
-Per-particle oracle values are out of reach at this size (every particle
-pairs with 1e6 others over 9392 modes), so the FP32 forces and potentials
-are checked against the FP64 path's (RMS relative 1e-5), and both against
-the zero net force of a neutral slab without walls.
+The oracle's energy of this configuration (positions rounded to FP32) and
+its potentials and forces at 512 seeded particles are stored in
+tests/golden/rbe_large_fullk.json, written by tests/golden/make_golden.py
+from the oracle alone (about 10 minutes on 8 cores). Against them: the FP64
+path to 1e-10 (energy; max-norm of phi and F over the sample), the FP32 path
+to 1e-6 (energy) and 1e-5 (RMS of phi and F over the sample). Every
+particle's FP32 phi and F are also checked against the FP64 path's (RMS
+relative 1e-5), and both against the zero net force of a neutral slab
+without walls.
 """
 import json
 import os
@@ -36,6 +37,10 @@ def _rmsrel(a, b):
     return float(np.sqrt(((a - b) ** 2).mean()) / np.sqrt((b ** 2).mean()))
 
 
+def _maxrel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
 def test_full_k_1e6(qslab, soe16):
     from golden_check import fingerprint_matches
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
@@ -55,8 +60,15 @@ def test_full_k_1e6(qslab, soe16):
         out[prec] = (float(e.item()), phi.double().cpu().numpy(), F.double().cpu().numpy())
         slab.close()
     E_ref = gold["E_fullk"]
+    idx = np.array(gold["sample_idx"])
+    phi_ref = np.array(gold["phi"])
+    F_ref = np.array(gold["F"])
     assert abs(out["fp64"][0] - E_ref) <= 1e-10 * abs(E_ref)
+    assert _maxrel(out["fp64"][1][idx], phi_ref) <= 1e-10
+    assert _maxrel(out["fp64"][2][idx], F_ref) <= 1e-10
     assert abs(out["fp32c"][0] - E_ref) <= 1e-6 * abs(E_ref)
+    assert _rmsrel(out["fp32c"][1][idx], phi_ref) <= 1e-5
+    assert _rmsrel(out["fp32c"][2][idx], F_ref) <= 1e-5
     assert _rmsrel(out["fp32c"][1], out["fp64"][1]) <= 1e-5
     assert _rmsrel(out["fp32c"][2], out["fp64"][2]) <= 1e-5
     for prec in out:
