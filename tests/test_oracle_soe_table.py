@@ -100,3 +100,19 @@ def test_erf_bound(M):
     s, w = load_soe(M)
     err, bound = soe_check.erf_error(0.3, 10.0, s, w)
     assert err <= bound
+
+
+@pytest.mark.parametrize("M", [4, 8])
+def test_fit_reproduces_the_shipped_table(M):
+    """Re-run the matrix-pencil fit (50-digit arithmetic) with the shipped
+    table's interval and sample count: it gives the shipped nodes and
+    weights, and the shipped sup-norm error."""
+    pytest.importorskip("mpmath")
+    from paper_2403_01521_gb300 import soe
+    info = soe.table_info(M)
+    s, w = soe.fit_gaussian_soe(M, info["X"], info["samples"])
+    s0, w0 = soe.load_soe(M)
+    o, o0 = np.lexsort((s.imag, s.real)), np.lexsort((s0.imag, s0.real))
+    assert np.abs(s[o] - s0[o0]).max() <= 1e-12 * np.abs(s0).max()
+    assert np.abs(w[o] - w0[o0]).max() <= 1e-12 * np.abs(w0).max()
+    assert abs(soe.sup_error(s, w) - info["sup_error"]) <= 1e-3 * info["sup_error"]
