@@ -79,6 +79,10 @@ typedef struct qslab_ctx qslab_ctx;
                                          up (no kernel of this version waits
                                          on another CTA, so none returns it) */
 #define QSLAB_ERR_TOO_LARGE (-9)      /* exceeds qslab_compute_static's scratch */
+#define QSLAB_ERR_INTERNAL (-10)      /* debug build: an internal index check
+                                         failed (a library bug, not an input
+                                         error); the release build never
+                                         returns it */
 
 /* Create a context on CUDA device `cuda_device` with precision `prec`
  * (QSLAB_FP64 or QSLAB_FP32C). *out receives the handle. */

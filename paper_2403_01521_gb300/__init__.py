@@ -37,6 +37,7 @@ QSLAB_ERR_ALLOC = -6
 QSLAB_ERR_CUDA = -7
 QSLAB_ERR_TIMEOUT = -8
 QSLAB_ERR_TOO_LARGE = -9
+QSLAB_ERR_INTERNAL = -10
 _PREC = {"fp64": QSLAB_FP64, "fp32c": QSLAB_FP32C}
 
 _lib = None
@@ -59,11 +60,13 @@ def load(build_if_missing: bool = True):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
-    if not _build.up_to_date():
+    # QSLAB_LIBRARY=debug selects the debug build (internal index checks)
+    debug = os.environ.get("QSLAB_LIBRARY", "") == "debug"
+    path = _build.DEBUG_LIB if debug else _build.LIB
+    if not _build.up_to_date(path):
         if not build_if_missing:
-            raise RuntimeError(f"libqslab.so missing or stale at {path}")
-        _build.build()
+            raise RuntimeError(f"{os.path.basename(path)} missing or stale at {path}")
+        _build.build(debug=debug)
     lib = ctypes.CDLL(path)
     P = ctypes.c_void_p
     D = ctypes.c_double

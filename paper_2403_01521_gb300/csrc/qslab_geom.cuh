@@ -45,6 +45,13 @@ __device__ __forceinline__ CRange zchunk(const Reps& rp, int c) {
   return x;
 }
 
+// A chunk of L (or L0) particles inside the particle arrays (debug-build
+// checks of the chunk tables).
+__device__ __forceinline__ bool chunk_ok(const Reps& rp, const CRange& ch, int L) {
+  return ch.r >= 0 && ch.r < rp.R && ch.cnt >= 1 && ch.cnt <= L && ch.start >= 0 &&
+         ch.start + ch.cnt <= rp.N;
+}
+
 inline int chunk_threads(int L) {
   const int t = ((L + 31) / 32) * 32;
   return t < 256 ? t : 256;

@@ -700,6 +700,7 @@ Reps reps_view(const qslab_ctx* c) {
   rp.nzgroups = t.nzgroups;
   rp.kflat = t.kflat;
   rp.zflat = t.zflat;
+  rp.status = c->d_status;
   return rp;
 }
 
@@ -726,7 +727,7 @@ Plan make_plan(const qslab_ctx* c, bool host_io, bool virial = false) {
   auto take = [&o](size_t b) { size_t r = o; o += a256(b); return r; };
   P.off_sort = take(sort_workspace_bytes(N, dp ? 8 : 4));
   P.off_rid = take(t.R > 1 ? 4 * (size_t)N : 0);
-  P.off_sums = take(16 * (size_t)t.R);
+  P.off_sums = take(16 * (size_t)t.nchunks);
   P.off_zs = take(tsz * N);
   P.off_dz = take(tsz * N);
   P.off_qs = take(tsz * N);
@@ -776,6 +777,7 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   char* tab = static_cast<char*>(c->d_tab);
   SortWork sw;
   sort_bind_workspace(sw, ws + P.off_sort, N, sizeof(T));
+  sw.status = c->d_status;
   int32_t* rid = reinterpret_cast<int32_t*>(ws + P.off_rid);
   double* sums = reinterpret_cast<double*>(ws + P.off_sums);
   T* zs = reinterpret_cast<T*>(ws + P.off_zs);
@@ -799,7 +801,6 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
   int nl = 0;
   c->primed = false;
   if (ev) cudaEventRecord(ev[0], st);
-  QS_CUDA(cudaMemsetAsync(sums, 0, 16 * (size_t)R, st));
   launch_prepare<T>(rp, pos, q, sw.keys[0], sw.vals[0], R > 1 ? rid : nullptr, sums,
                     c->d_status, st);
   double tol = c->neutral_tol;
@@ -837,7 +838,8 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
     r = radix_sort(sw, N, 4, passes, r, st);
     nl += 1 + sort_launches(N, passes);
   }
-  launch_gather<T>(rp, pos, q, sw.vals[r], zs, dz, qs, xh, yh, perm, st);
+  launch_gather<T>(rp, pos, q, sw.vals[r], R == 1 ? sw.keys[r] : nullptr, zs, dz, qs, xh, yh,
+                   perm, st);
   ++nl;
   if (ev) cudaEventRecord(ev[1], st);
   // k = 0 term on the side stream, concurrent with the k-space kernels
@@ -941,6 +943,7 @@ int status_code(unsigned f) {
   if (f & kStZRange) return QSLAB_ERR_Z_OUT_OF_RANGE;
   if (f & kStNonneutral) return QSLAB_ERR_NONNEUTRAL;
   if (f & kStTimeout) return QSLAB_ERR_TIMEOUT;
+  if (f & kStDebug) return QSLAB_ERR_INTERNAL;
   return QSLAB_OK;
 }
 
@@ -1669,6 +1672,7 @@ const char* qslab_strerror(int code) {
     case QSLAB_ERR_CUDA: return "CUDA runtime error";
     case QSLAB_ERR_TIMEOUT: return "bounded device wait gave up";
     case QSLAB_ERR_TOO_LARGE: return "problem too large for the fixed scratch of qslab_compute_static";
+    case QSLAB_ERR_INTERNAL: return "internal index check failed (debug build)";
     default: return "unknown error";
   }
 }

@@ -107,6 +107,7 @@ struct Reps {
   const int32_t* group_rep;   // [ngroups]
   const int32_t* zgstart;     // [nzgroups + 1] first k = 0 chunk of each k = 0 carry group
   const int32_t* zgroup_rep;  // [nzgroups]
+  unsigned* status;           // the call's status word (debug-build index checks)
 };
 
 // Charged walls at z = 0 (bottom) and z = Lz (top), the same for every
@@ -128,7 +129,22 @@ enum StatusBits : unsigned {
   kStZRange = 2u,
   kStNonneutral = 4u,
   kStTimeout = 8u,
+  kStDebug = 16u,     // debug builds: an internal index check failed
 };
+
+// Index checks of the debug build (compiled with -DQSLAB_DEBUG): a failed
+// check sets kStDebug in the status word and the kernel skips the access it
+// guards (no trap); in the release build the check is `true` and costs
+// nothing.
+#ifdef QSLAB_DEBUG
+__device__ __forceinline__ bool qs_dcheck(bool ok, unsigned* status) {
+  if (!ok && status) atomicOr(status, (unsigned)kStDebug);
+  return ok;
+}
+#define QS_DCHECK(ok, status) qslab::qs_dcheck((ok), (status))
+#else
+#define QS_DCHECK(ok, status) (true)
+#endif
 
 // ---- sort (qslab_sort.cu)
 struct SortWork {
@@ -137,6 +153,7 @@ struct SortWork {
   uint32_t* counts;       // [256][nblocks]
   uint32_t* totals;       // [passes][256] digit totals
   int nblocks;
+  unsigned* status;       // debug-build index checks (may be NULL)
 };
 size_t sort_workspace_bytes(int64_t N, int key_bytes);
 void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes);
@@ -150,13 +167,14 @@ int sort_launches(int64_t N, int passes);
 // ---- kernels (qslab_prep.cu: checks, gather, combine, mode tables;
 //      qslab_kspace.cu: k != 0 passes; qslab_carry.cu: their carries;
 //      qslab_kzero.cu: the k = 0 term)
-// Input checks and z keys, one CTA per k-space chunk; per-replica sums of q
-// and |q| (sums[2r], sums[2r+1]); rid (may be NULL) receives the replica of
+// Input checks and z keys, one CTA per k-space chunk; per-chunk sums of q
+// and |q| (sums[2c], sums[2c+1]); rid (may be NULL) receives the replica of
 // every particle.
 template <typename T>
 void launch_prepare(const Reps& rp, const T* pos, const T* q, void* keys, uint32_t* vals,
                     int32_t* rid, double* sums, unsigned* status, cudaStream_t st);
-// Per-replica neutrality check of particles and walls together:
+// Per-replica neutrality check of particles and walls together, from the
+// chunk sums of launch_prepare:
 // |sum q + area (sb0 + st0)| <= tol (sum |q| + area (|sb0| + |st0|)), with
 // sb0 = st0 = 0 without walls; when ctr is not NULL also advances the
 // random-batch counter: ctr[1] = ctr[0]++ (the counter this call uses).
@@ -165,9 +183,10 @@ void launch_check_neutral(const Reps& rp, const double* sums, double tol, double
 // Second sort key: keys[i] = rid[perm[i]].
 void launch_rep_keys(int64_t N, const uint32_t* perm, const int32_t* rid, uint32_t* keys,
                      cudaStream_t st);
+// zkeys: the sorted z keys (single-slab calls) or NULL (z gathered from pos)
 template <typename T>
-void launch_gather(const Reps& rp, const T* pos, const T* q, const uint32_t* perm, T* zs,
-                   T* dz, T* qs, typename PhaseT<T>::type* xh,
+void launch_gather(const Reps& rp, const T* pos, const T* q, const uint32_t* perm,
+                   const void* zkeys, T* zs, T* dz, T* qs, typename PhaseT<T>::type* xh,
                    typename PhaseT<T>::type* yh, int32_t* perm_out, cudaStream_t st);
 
 struct ScanPlan {

@@ -79,9 +79,16 @@ __global__ void kzero_aggregate_kernel(K0Params Q, PairTab pr, const T* zs,
   const int c = blockIdx.x * kK0Cpb + lc;
   T* zl = reinterpret_cast<T*>(kag_raw) + (size_t)lc * 2 * L0;
   T* ql = zl + L0;
-  const bool valid = c < Q.rp.nzchunks;
+  bool valid = c < Q.rp.nzchunks;
   CRange ch{0, 0, 0, false, false};
-  if (valid) ch = zchunk(Q.rp, c);
+  if (valid) {
+    ch = zchunk(Q.rp, c);
+    // debug builds: a chunk outside the arrays is left out
+    if (!QS_DCHECK(chunk_ok(Q.rp, ch, Q.rp.L0), Q.rp.status)) {
+      valid = false;
+      ch = CRange{0, 0, 0, false, false};
+    }
+  }
   const int64_t start = ch.start;
   const int cnt = ch.cnt;
   for (int t = p; t < cnt; t += lanes) { zl[t] = zs[start + t]; ql[t] = qs[start + t]; }
@@ -343,9 +350,16 @@ __global__ void kzero_final_kernel(K0Params Q, PairTab pr, const T* zs,
   T* ql = zl + (L0 + 1);
   T* dzl = ql + (L0 + 1);
   T* accd = dzl + (L0 + 1);             // [dir][L0][2]
-  const bool valid = c < nch;
+  bool valid = c < nch;
   CRange ch{0, 0, 0, false, false};
-  if (valid) ch = zchunk(Q.rp, c);
+  if (valid) {
+    ch = zchunk(Q.rp, c);
+    // debug builds: a chunk outside the arrays is left out
+    if (!QS_DCHECK(chunk_ok(Q.rp, ch, L0), Q.rp.status)) {
+      valid = false;
+      ch = CRange{0, 0, 0, false, false};
+    }
+  }
   const int64_t start = ch.start;
   const int cnt = ch.cnt;
   // stage the chunk; dz[cnt] is the next particle's (the backward scan's

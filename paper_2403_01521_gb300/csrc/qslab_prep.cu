@@ -30,13 +30,15 @@ template <> struct KeyOf<double> {
 
 // One CTA per k-space chunk (chunks are contiguous in the caller's order as
 // well): finiteness and z-range checks, the z keys, the replica index and
-// the replica's sums of q and |q|.
+// the chunk's sums of q and |q| (csums[2c], csums[2c+1]; summed per replica
+// in a fixed order by the neutrality check).
 template <typename T>
 __global__ void prepare_kernel(Reps rp, const T* __restrict__ pos, const T* __restrict__ q,
                                typename KeyOf<T>::type* keys, uint32_t* vals, int32_t* rid,
                                double* sums, unsigned* status) {
   __shared__ double red[2][32];
   const CRange ch = kchunk(rp, blockIdx.x);
+  if (!QS_DCHECK(chunk_ok(rp, ch, rp.L), rp.status)) return;
   const double Lz = rp.info[ch.r].Lz;
   double sq = 0.0, sa = 0.0;
   unsigned flags = 0;
@@ -62,8 +64,8 @@ __global__ void prepare_kernel(Reps rp, const T* __restrict__ pos, const T* __re
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
     for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { a += red[0][j]; b += red[1][j]; }
-    atomicAdd(&sums[2 * ch.r], a);
-    atomicAdd(&sums[2 * ch.r + 1], b);
+    sums[2 * blockIdx.x] = a;
+    sums[2 * blockIdx.x + 1] = b;
   }
 }
 
@@ -74,26 +76,42 @@ void launch_prepare(const Reps& rp, const T* pos, const T* q, void* keys, uint32
       rp, pos, q, static_cast<typename KeyOf<T>::type*>(keys), vals, rid, sums, status);
 }
 
+// One warp per replica: the replica's sums of q and |q| from its chunks'
+// partial sums (fixed order), then the neutrality check.
 __global__ void check_neutral_kernel(Reps rp, const double* sums, double tol, double sb0,
                                      double st0, unsigned* status, uint64_t* ctr) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < rp.R && tol >= 0.0) {
-    // particles and walls together (the neutrality condition of Section 2.4)
-    const double a = rp.info[r].area;
-    const double net = sums[2 * r] + a * (sb0 + st0);
-    const double mag = sums[2 * r + 1] + a * (fabs(sb0) + fabs(st0));
-    if (fabs(net) > tol * mag) atomicOr(status, kStNonneutral);
-  }
-  if (ctr && r == 0) {
+  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int r = (int)(gt >> 5), lane = threadIdx.x & 31;
+  if (ctr && gt == 0) {
     const uint64_t c = ctr[0];
     ctr[1] = c;
     ctr[0] = c + 1;
+  }
+  if (r >= rp.R) return;      // whole warps leave together
+  const RepInfo& ri = rp.info[r];
+  double sq = 0.0, sa = 0.0;
+  for (int j = lane; j < ri.nch; j += 32) {
+    sq += sums[2 * (ri.c0 + j)];
+    sa += sums[2 * (ri.c0 + j) + 1];
+  }
+  for (int o = 16; o; o >>= 1) {
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+  }
+  if (lane == 0 && tol >= 0.0) {
+    // particles and walls together (the neutrality condition of Section 2.4)
+    const double a = ri.area;
+    const double net = sq + a * (sb0 + st0);
+    const double mag = sa + a * (fabs(sb0) + fabs(st0));
+    if (fabs(net) > tol * mag) atomicOr(status, kStNonneutral);
   }
 }
 
 void launch_check_neutral(const Reps& rp, const double* sums, double tol, double sb0,
                           double st0, unsigned* status, uint64_t* ctr, cudaStream_t st) {
-  check_neutral_kernel<<<(rp.R + 255) / 256, 256, 0, st>>>(rp, sums, tol, sb0, st0, status, ctr);
+  const int64_t thr = (int64_t)rp.R * 32;
+  check_neutral_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(rp, sums, tol, sb0, st0,
+                                                                     status, ctr);
 }
 
 __global__ void rep_keys_kernel(int64_t N, const uint32_t* __restrict__ perm,
@@ -112,47 +130,74 @@ void launch_rep_keys(int64_t N, const uint32_t* perm, const int32_t* rid, uint32
 
 // ==================================================================== gather
 
-__device__ __forceinline__ uint32_t to_fixed(float x, double L) {
-  double f = (double)x / L;
-  f -= floor(f);
-  if (!(f < 1.0)) f = 0.0;
-  return (uint32_t)(uint64_t)(f * 4294967296.0);
+// Fixed-point fraction x/L of a turn: floor(x 2^32/L) mod 2^32 (FP32 path,
+// from the FP64 product with the scale k = 2^32/L and a round-down
+// conversion) or frac(x/L) 2^64 (FP64 path, with ik = 1/L). One product per
+// coordinate instead of an FP64 division.
+__device__ __forceinline__ uint32_t to_fixed(float x, double k, double) {
+  return (uint32_t)(uint64_t)__double2ll_rd((double)x * k);
 }
-__device__ __forceinline__ uint64_t to_fixed(double x, double L) {
-  double f = x / L;
+__device__ __forceinline__ uint64_t to_fixed(double x, double, double ik) {
+  double f = x * ik;
   f -= floor(f);
   if (!(f < 1.0)) f = 0.0;
   return (uint64_t)(f * 18446744073709551616.0);
 }
 
+template <typename T> struct KeyVal;
+template <> struct KeyVal<float> {
+  __device__ static float z(const void* keys, int64_t i) {
+    return __uint_as_float(static_cast<const uint32_t*>(keys)[i]);
+  }
+};
+template <> struct KeyVal<double> {
+  __device__ static double z(const void* keys, int64_t i) {
+    return __longlong_as_double((long long)static_cast<const uint64_t*>(keys)[i]);
+  }
+};
+
 // One CTA per k-space chunk: the sorted SoA arrays, with dz = 0 at the first
-// particle of every replica.
+// particle of every replica. zkeys (may be NULL): the sorted z keys of a
+// single-slab call (the z values' own bits), read in order instead of
+// gathering z from the positions.
 template <typename T>
 __global__ void gather_kernel(Reps rp, const T* __restrict__ pos, const T* __restrict__ q,
-                              const uint32_t* __restrict__ perm, T* zs, T* dz, T* qs,
-                              typename PhaseT<T>::type* xh, typename PhaseT<T>::type* yh,
+                              const uint32_t* __restrict__ perm, const void* zkeys, T* zs, T* dz,
+                              T* qs, typename PhaseT<T>::type* xh, typename PhaseT<T>::type* yh,
                               int32_t* perm_out) {
   const CRange ch = kchunk(rp, blockIdx.x);
+  if (!QS_DCHECK(chunk_ok(rp, ch, rp.L), rp.status)) return;
   const double Lx = rp.info[ch.r].Lx, Ly = rp.info[ch.r].Ly;
+  const double kx = 4294967296.0 / Lx, ky = 4294967296.0 / Ly;   // FP32 path
+  const double ikx = 1.0 / Lx, iky = 1.0 / Ly;                     // FP64 path
   for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
     const int64_t i = ch.start + t;
     const uint32_t o = perm[i];
-    const T z = pos[3 * (int64_t)o + 2];
+    if (!QS_DCHECK(o < (uint64_t)rp.N, rp.status)) continue;
+    const bool first = t == 0 && ch.first;
+    T z, zp;
+    if (zkeys) {
+      z = KeyVal<T>::z(zkeys, i);
+      zp = first ? z : KeyVal<T>::z(zkeys, i - 1);
+    } else {
+      z = pos[3 * (int64_t)o + 2];
+      zp = first ? z : pos[3 * (int64_t)perm[i - 1] + 2];
+    }
     zs[i] = z;
-    dz[i] = (t == 0 && ch.first) ? (T)0 : z - pos[3 * (int64_t)perm[i - 1] + 2];
+    dz[i] = first ? (T)0 : z - zp;
     qs[i] = q[o];
-    xh[i] = to_fixed(pos[3 * (int64_t)o], Lx);
-    yh[i] = to_fixed(pos[3 * (int64_t)o + 1], Ly);
+    xh[i] = to_fixed(pos[3 * (int64_t)o], kx, ikx);
+    yh[i] = to_fixed(pos[3 * (int64_t)o + 1], ky, iky);
     perm_out[i] = (int32_t)o;
   }
 }
 
 template <typename T>
-void launch_gather(const Reps& rp, const T* pos, const T* q, const uint32_t* perm, T* zs,
-                   T* dz, T* qs, typename PhaseT<T>::type* xh,
+void launch_gather(const Reps& rp, const T* pos, const T* q, const uint32_t* perm,
+                   const void* zkeys, T* zs, T* dz, T* qs, typename PhaseT<T>::type* xh,
                    typename PhaseT<T>::type* yh, int32_t* perm_out, cudaStream_t st) {
-  gather_kernel<T><<<rp.nchunks, chunk_threads(rp.L), 0, st>>>(rp, pos, q, perm, zs, dz, qs,
-                                                                xh, yh, perm_out);
+  gather_kernel<T><<<rp.nchunks, chunk_threads(rp.L), 0, st>>>(rp, pos, q, perm, zkeys, zs, dz,
+                                                                qs, xh, yh, perm_out);
 }
 
 // ================================================================== combine
@@ -182,6 +227,7 @@ __global__ void combine_kernel(Reps rp, int nkr, const T* __restrict__ part,
   // per-mode constants of this chunk's box: kx, ky, k, Cb (re, im), Ct (re, im)
   __shared__ T wk[kMaxWallModes][7];
   const CRange ch = kchunk(rp, blockIdx.x);
+  if (!QS_DCHECK(chunk_ok(rp, ch, rp.L), rp.status)) return;
   const RepInfo& ri = rp.info[ch.r];
   const double diagq = ri.diagq;
   const double Lz = ri.Lz;
@@ -244,6 +290,7 @@ __global__ void combine_kernel(Reps rp, int nkr, const T* __restrict__ part,
       fz += qq * gz;
     }
     const int32_t o = perm[i];
+    if (!QS_DCHECK(o >= 0 && o < rp.N, rp.status)) continue;
     if (phi_out) phi_out[o] = (T)(ph + pw);
     if (force_out) {
       force_out[3 * (int64_t)o] = (T)fx;
@@ -766,8 +813,8 @@ void launch_mode_coef(const Reps& rp, int npc, const int32_t* list, int rbe, uin
 #define QSLAB_INST(T, PH)                                                                        \
   template void launch_prepare<T>(const Reps&, const T*, const T*, void*, uint32_t*, int32_t*,   \
                                   double*, unsigned*, cudaStream_t);                             \
-  template void launch_gather<T>(const Reps&, const T*, const T*, const uint32_t*, T*, T*, T*,   \
-                                 PH*, PH*, int32_t*, cudaStream_t);                              \
+  template void launch_gather<T>(const Reps&, const T*, const T*, const uint32_t*, const void*,  \
+                                 T*, T*, T*, PH*, PH*, int32_t*, cudaStream_t);                  \
   template void launch_combine<T>(const Reps&, int, const T*, const void*, const void*,          \
                                   const T*, const T*, const PH*, const PH*, const WallTab&,       \
                                   const int32_t*, double*, T*, T*, double*, cudaStream_t);       \

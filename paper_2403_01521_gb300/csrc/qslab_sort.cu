@@ -96,7 +96,8 @@ template <typename K>
 __global__ void __launch_bounds__(kSortThreads)
 scatter_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
                K* __restrict__ kout, uint32_t* __restrict__ vout, int64_t N,
-               int shift, const uint32_t* __restrict__ offsets, int nblocks) {
+               int shift, const uint32_t* __restrict__ offsets, int nblocks,
+               unsigned* status) {
   __shared__ uint32_t wcnt[kSortWarps][kRadix];
   __shared__ uint32_t goff[kRadix];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -136,8 +137,10 @@ scatter_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
   for (int s = 0; s < kItems; ++s) {
     if (dig[s] < 0x100u) {
       const uint32_t pos = goff[dig[s]] + wcnt[w][dig[s]] + loc[s];
-      kout[pos] = key[s];
-      vout[pos] = val[s];
+      if (QS_DCHECK(pos < (uint64_t)N, status)) {
+        kout[pos] = key[s];
+        vout[pos] = val[s];
+      }
     }
   }
 }
@@ -151,7 +154,8 @@ scatter_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
 template <typename K>
 __global__ void __launch_bounds__(1024)
 small_sort_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
-                  K* __restrict__ kout, uint32_t* __restrict__ vout, int N, int n2, int passes) {
+                  K* __restrict__ kout, uint32_t* __restrict__ vout, int N, int n2, int passes,
+                  unsigned* status) {
   __shared__ K sk[kTile];
   __shared__ uint16_t si[kTile];
   const K mask = passes * 8 >= (int)(8 * sizeof(K)) ? ~(K)0 : (((K)1 << (8 * passes)) - 1);
@@ -183,6 +187,7 @@ small_sort_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
   __syncthreads();
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     const int i = si[t];
+    if (!QS_DCHECK(i < N, status)) continue;
     kout[t] = kin[i];
     vout[t] = vin[i];
   }
@@ -208,6 +213,7 @@ void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes) {
   w.counts = reinterpret_cast<uint32_t*>(p);
   p += align256((size_t)w.nblocks * kRadix * 4);
   w.totals = reinterpret_cast<uint32_t*>(p);
+  w.status = nullptr;
 }
 
 int sort_launches(int64_t N, int passes) { return N <= kTile ? 1 : 3 * passes; }
@@ -222,11 +228,11 @@ int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaS
     if (key_bytes == 4)
       small_sort_kernel<uint32_t><<<1, thr, 0, st>>>(
           static_cast<const uint32_t*>(w.keys[cur]), w.vals[cur],
-          static_cast<uint32_t*>(w.keys[cur ^ 1]), w.vals[cur ^ 1], (int)N, n2, passes);
+          static_cast<uint32_t*>(w.keys[cur ^ 1]), w.vals[cur ^ 1], (int)N, n2, passes, w.status);
     else
       small_sort_kernel<uint64_t><<<1, thr, 0, st>>>(
           static_cast<const uint64_t*>(w.keys[cur]), w.vals[cur],
-          static_cast<uint64_t*>(w.keys[cur ^ 1]), w.vals[cur ^ 1], (int)N, n2, passes);
+          static_cast<uint64_t*>(w.keys[cur ^ 1]), w.vals[cur ^ 1], (int)N, n2, passes, w.status);
     return cur ^ 1;
   }
   cudaMemsetAsync(w.totals, 0, (size_t)passes * kRadix * 4, st);
@@ -239,14 +245,14 @@ int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaS
       hist_kernel<uint32_t><<<w.nblocks, kSortThreads, 0, st>>>(kin, N, shift, w.counts, tot, w.nblocks);
       scan_kernel<<<kRadix, kSortThreads, 0, st>>>(w.counts, tot, w.nblocks);
       scatter_kernel<uint32_t><<<w.nblocks, kSortThreads, 0, st>>>(
-          kin, w.vals[cur], kout, w.vals[cur ^ 1], N, shift, w.counts, w.nblocks);
+          kin, w.vals[cur], kout, w.vals[cur ^ 1], N, shift, w.counts, w.nblocks, w.status);
     } else {
       auto* kin = static_cast<const uint64_t*>(w.keys[cur]);
       auto* kout = static_cast<uint64_t*>(w.keys[cur ^ 1]);
       hist_kernel<uint64_t><<<w.nblocks, kSortThreads, 0, st>>>(kin, N, shift, w.counts, tot, w.nblocks);
       scan_kernel<<<kRadix, kSortThreads, 0, st>>>(w.counts, tot, w.nblocks);
       scatter_kernel<uint64_t><<<w.nblocks, kSortThreads, 0, st>>>(
-          kin, w.vals[cur], kout, w.vals[cur ^ 1], N, shift, w.counts, w.nblocks);
+          kin, w.vals[cur], kout, w.vals[cur ^ 1], N, shift, w.counts, w.nblocks, w.status);
     }
     cur ^= 1;
   }
