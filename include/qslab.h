@@ -75,9 +75,9 @@ typedef struct qslab_ctx qslab_ctx;
 #define QSLAB_ERR_NONNEUTRAL (-5)     /* |sum q| above tolerance (Thm 2.1)   */
 #define QSLAB_ERR_ALLOC (-6)          /* device or host allocation failed    */
 #define QSLAB_ERR_CUDA (-7)           /* a CUDA runtime call failed          */
-#define QSLAB_ERR_TIMEOUT (-8)        /* reserved: a bounded device wait gave
-                                         up (no kernel of this version waits
-                                         on another CTA, so none returns it) */
+#define QSLAB_ERR_TIMEOUT (-8)        /* a bounded device wait gave up (the
+                                         z-sort's look-back between CTAs);
+                                         the call's outputs are unspecified */
 #define QSLAB_ERR_TOO_LARGE (-9)      /* exceeds qslab_compute_static's scratch */
 #define QSLAB_ERR_INTERNAL (-10)      /* debug build: an internal index check
                                          failed (a library bug, not an input
@@ -477,6 +477,14 @@ const char* qslab_strerror(int code);
  * failure is absorbed, two fail the call). */
 long long qslab_debug_alloc_count(void);
 int qslab_debug_fail_alloc(int n);
+/* qslab_debug_stall_sort(tile): in the next long-range call (of any
+ * context in this process) the z-sort's first digit pass leaves tile
+ * `tile` (4096 keys each, in order) without its published counts, so that
+ * the next tile's bounded wait runs out (about 0.1 to 1 s): the call then
+ * completes with QSLAB_ERR_TIMEOUT in the status word and unspecified
+ * outputs, and the context stays usable. Applies only to calls with more
+ * than 2048 particles (smaller sorts run in one CTA and do not wait). */
+int qslab_debug_stall_sort(int tile);
 
 #ifdef __cplusplus
 }

@@ -113,6 +113,7 @@ def load(build_if_missing: bool = True):
         "qslab_strerror": ([I], ctypes.c_char_p),
         "qslab_debug_alloc_count": ([], ctypes.c_longlong),
         "qslab_debug_fail_alloc": ([I], I),
+        "qslab_debug_stall_sort": ([I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -408,6 +409,10 @@ def qslab_debug_alloc_count() -> int:
 
 def qslab_debug_fail_alloc(n: int):
     _check(load().qslab_debug_fail_alloc(int(n)), "qslab_debug_fail_alloc")
+
+
+def qslab_debug_stall_sort(tile: int):
+    _check(load().qslab_debug_stall_sort(int(tile)), "qslab_debug_stall_sort")
 
 
 def kcut_for_tail(alpha: float, tail: float) -> float:

@@ -829,14 +829,14 @@ int run(qslab_ctx* c, const Plan& P, const T* pos, const T* q, double* energies,
     if (rbe) c->have_sample = true;
     else c->coef_ready = true;
   }
-  int r = radix_sort(sw, N, (int)sizeof(T), (int)sizeof(T), 0, st);
-  nl += 2 + sort_launches(N, (int)sizeof(T));   // prepare, check, the sort
+  int r = radix_sort(sw, N, (int)sizeof(T), (int)sizeof(T), 0, st, true);
+  nl += 2 + sort_launches(N, (int)sizeof(T), true);   // prepare, check, the sort
   if (R > 1) {
     // stable second sort on the replica index: replicas contiguous, z-ordered within
     launch_rep_keys(N, sw.vals[r], rid, static_cast<uint32_t*>(sw.keys[r]), st);
     const int passes = R <= 256 ? 1 : (R <= 65536 ? 2 : 3);
-    r = radix_sort(sw, N, 4, passes, r, st);
-    nl += 1 + sort_launches(N, passes);
+    r = radix_sort(sw, N, 4, passes, r, st, true);
+    nl += 1 + sort_launches(N, passes, true);
   }
   launch_gather<T>(rp, pos, q, sw.vals[r], R == 1 ? sw.keys[r] : nullptr, zs, dz, qs, xh, yh,
                    perm, st);
@@ -1678,6 +1678,12 @@ const char* qslab_strerror(int code) {
 }
 
 long long qslab_debug_alloc_count(void) { return g_alloc_count.load(); }
+
+int qslab_debug_stall_sort(int tile) {
+  if (tile < 0) return QSLAB_ERR_INVALID_ARG;
+  sort_debug_stall(tile);
+  return QSLAB_OK;
+}
 
 int qslab_debug_fail_alloc(int n) {
   if (n < 0) return QSLAB_ERR_INVALID_ARG;

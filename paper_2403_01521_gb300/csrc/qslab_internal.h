@@ -153,16 +153,26 @@ struct SortWork {
   uint32_t* counts;       // [256][nblocks]
   uint32_t* totals;       // [passes][256] digit totals
   int nblocks;
-  unsigned* status;       // debug-build index checks (may be NULL)
+  void* os_state;         // single-pass (onesweep) look-back state
+  size_t os_bytes;
+  unsigned* status;       // status word: debug-build index checks, the
+                          // single-pass sort's bounded waits (may be NULL)
 };
 size_t sort_workspace_bytes(int64_t N, int key_bytes);
 void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes);
 // Stable sort of keys[src]/vals[src] (keys of key_bytes = 4 or 8) on their
 // low `passes` bytes; returns the index (0 or 1) of the buffer holding the
-// result.
-int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaStream_t st);
+// result. onesweep (needs w.status): one kernel per digit with a bounded
+// decoupled look-back instead of three; a wait that gives up sets
+// kStTimeout, and the sorted arrays are then unspecified (the indices in
+// vals may be out of range: consumers clamp them).
+int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaStream_t st,
+               bool onesweep = false);
 // kernels radix_sort() launches for N keys and `passes` digits
-int sort_launches(int64_t N, int passes);
+int sort_launches(int64_t N, int passes, bool onesweep = false);
+// test hook: in the next single-pass sort, the tile of this ticket in the
+// first pass publishes nothing (its successor's bounded wait runs out)
+void sort_debug_stall(int tile);
 
 // ---- kernels (qslab_prep.cu: checks, gather, combine, mode tables;
 //      qslab_kspace.cu: k != 0 passes; qslab_carry.cu: their carries;

@@ -147,6 +147,18 @@ __device__ inline void load_chunk(const KParams<T>& P, ChunkSmem<T>& s,
 }
 
 // ------------------------------------------------------------------ pass A
+// the two table entries of a pair (16 bytes on the FP32 path: one load)
+__device__ __forceinline__ void load_pair(const Cplx<float>* e, Cplx<float>& a, Cplx<float>& b) {
+  const float4 v = *reinterpret_cast<const float4*>(e);
+  a = Cplx<float>{v.x, v.y};
+  b = Cplx<float>{v.z, v.w};
+}
+__device__ __forceinline__ void load_pair(const Cplx<double>* e, Cplx<double>& a,
+                                          Cplx<double>& b) {
+  a = e[0];
+  b = e[1];
+}
+
 template <typename T, int NP>
 __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
   extern __shared__ __align__(32) char smem[];
@@ -160,13 +172,14 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
   ChunkSmem<T> s = carve<T>(smem, P.rp.L, NP, 0, false);
   load_chunk<T>(P, s, start, cnt);
   __syncthreads();
-  // E tables: [t][0][p] = e^{-a_p (z_end - z_t)}, [t][1][p] = e^{-a_p (z_t - z_start)}
+  // E tables: [t][p][0] = e^{-a_p (z_end - z_t)}, [t][p][1] = e^{-a_p (z_t - z_start)}
+  // (a pair's two entries adjacent: one 16-byte load on the FP32 path)
   const T zend = s.zl[cnt - 1], zst = s.zl[0];
   for (int e = threadIdx.x; e < NP * cnt; e += blockDim.x) {
     const int t = e / NP, p = e - t * NP;
     const T ar = (T)pairs.a_re[p], ai = (T)pairs.a_im[p];
-    s.tab[(2 * t) * NP + p] = cexp_neg(ar, ai, zend - s.zl[t]);
-    s.tab[(2 * t + 1) * NP + p] = cexp_neg(ar, ai, s.zl[t] - zst);
+    s.tab[2 * (t * NP + p)] = cexp_neg(ar, ai, zend - s.zl[t]);
+    s.tab[2 * (t * NP + p) + 1] = cexp_neg(ar, ai, s.zl[t] - zst);
   }
   __syncthreads();
   const int m = blockIdx.y * pl.KR + threadIdx.x;
@@ -189,8 +202,8 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
     const Cplx<T>* Et = s.tab + 2 * t * NP;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
-      const Cplx<T> Ef = Et[p];
-      const Cplx<T> Eb = Et[NP + p];
+      Cplx<T> Ef, Eb;
+      load_pair(Et + 2 * p, Ef, Eb);
       fa[p].re = fma(Ef.re, a, fa[p].re); fa[p].im = fma(Ef.im, a, fa[p].im);
       fb[p].re = fma(Ef.re, b, fb[p].re); fb[p].im = fma(Ef.im, b, fb[p].im);
       ba[p].re = fma(Eb.re, a, ba[p].re); ba[p].im = fma(Eb.im, a, ba[p].im);

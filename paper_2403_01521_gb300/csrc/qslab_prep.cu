@@ -28,6 +28,13 @@ template <> struct KeyOf<double> {
   }
 };
 
+__device__ __forceinline__ double shfl_xor_cn(double v, int o) {
+  return __shfl_xor_sync(0xffffffffu, v, o);
+}
+__device__ __forceinline__ DF shfl_xor_cn(DF v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
 // One CTA per k-space chunk (chunks are contiguous in the caller's order as
 // well): finiteness and z-range checks, the z keys, the replica index and
 // the chunk's sums of q and |q| (csums[2c], csums[2c+1]; summed per replica
@@ -40,26 +47,32 @@ __global__ void prepare_kernel(Reps rp, const T* __restrict__ pos, const T* __re
   const CRange ch = kchunk(rp, blockIdx.x);
   if (!QS_DCHECK(chunk_ok(rp, ch, rp.L), rp.status)) return;
   const double Lz = rp.info[ch.r].Lz;
-  double sq = 0.0, sa = 0.0;
+  // the largest T not above Lz: z <= Lz exactly when z <= Lzlo
+  T Lzlo = (T)Lz;
+  if ((double)Lzlo > Lz) Lzlo = nextafter(Lzlo, (T)0);
+  // the sums in the carry type: FP64, or double-float on the FP32 path
+  // (whose FP32 charges sum exactly enough in it, without FP64 operations)
+  using CN = typename CarryNum<T>::type;
+  CN sq = cn_zero((CN*)nullptr), sa = sq;
   unsigned flags = 0;
   for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
     const int64_t i = ch.start + t;
     const T x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2], qi = q[i];
     if (!isfinite(x) || !isfinite(y) || !isfinite(z) || !isfinite(qi)) flags |= kStNonfinite;
-    else if (!(z >= (T)0) || !((double)z <= Lz)) flags |= kStZRange;
+    else if (!(z >= (T)0) || !(z <= Lzlo)) flags |= kStZRange;
     keys[i] = KeyOf<T>::key(z);
     vals[i] = (uint32_t)i;
     if (rid) rid[i] = ch.r;
-    sq += (double)qi;
-    sa += fabs((double)qi);
+    sq = sq + qi;
+    sa = sa + (T)fabs(qi);
   }
   if (flags) atomicOr(status, flags);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int o = 16; o; o >>= 1) {
-    sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    sa += __shfl_xor_sync(0xffffffffu, sa, o);
+    sq = sq + shfl_xor_cn(sq, o);
+    sa = sa + shfl_xor_cn(sa, o);
   }
-  if (lane == 0) { red[0][w] = sq; red[1][w] = sa; }
+  if (lane == 0) { red[0][w] = cn_to_double(sq); red[1][w] = cn_to_double(sa); }
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
@@ -76,21 +89,20 @@ void launch_prepare(const Reps& rp, const T* pos, const T* q, void* keys, uint32
       rp, pos, q, static_cast<typename KeyOf<T>::type*>(keys), vals, rid, sums, status);
 }
 
-// One warp per replica: the replica's sums of q and |q| from its chunks'
-// partial sums (fixed order), then the neutrality check.
+// One CTA per replica: the replica's sums of q and |q| from its chunks'
+// partial sums (a fixed order), then the neutrality check.
 __global__ void check_neutral_kernel(Reps rp, const double* sums, double tol, double sb0,
                                      double st0, unsigned* status, uint64_t* ctr) {
-  const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int r = (int)(gt >> 5), lane = threadIdx.x & 31;
-  if (ctr && gt == 0) {
+  __shared__ double red[2][32];
+  const int r = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (ctr && r == 0 && threadIdx.x == 0) {
     const uint64_t c = ctr[0];
     ctr[1] = c;
     ctr[0] = c + 1;
   }
-  if (r >= rp.R) return;      // whole warps leave together
   const RepInfo& ri = rp.info[r];
   double sq = 0.0, sa = 0.0;
-  for (int j = lane; j < ri.nch; j += 32) {
+  for (int j = threadIdx.x; j < ri.nch; j += blockDim.x) {
     sq += sums[2 * (ri.c0 + j)];
     sa += sums[2 * (ri.c0 + j) + 1];
   }
@@ -98,27 +110,29 @@ __global__ void check_neutral_kernel(Reps rp, const double* sums, double tol, do
     sq += __shfl_xor_sync(0xffffffffu, sq, o);
     sa += __shfl_xor_sync(0xffffffffu, sa, o);
   }
-  if (lane == 0 && tol >= 0.0) {
+  if (lane == 0) { red[0][w] = sq; red[1][w] = sa; }
+  __syncthreads();
+  if (threadIdx.x == 0 && tol >= 0.0) {
+    double a = 0.0, b = 0.0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { a += red[0][j]; b += red[1][j]; }
     // particles and walls together (the neutrality condition of Section 2.4)
-    const double a = ri.area;
-    const double net = sq + a * (sb0 + st0);
-    const double mag = sa + a * (fabs(sb0) + fabs(st0));
+    const double ar = ri.area;
+    const double net = a + ar * (sb0 + st0);
+    const double mag = b + ar * (fabs(sb0) + fabs(st0));
     if (fabs(net) > tol * mag) atomicOr(status, kStNonneutral);
   }
 }
 
 void launch_check_neutral(const Reps& rp, const double* sums, double tol, double sb0,
                           double st0, unsigned* status, uint64_t* ctr, cudaStream_t st) {
-  const int64_t thr = (int64_t)rp.R * 32;
-  check_neutral_kernel<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(rp, sums, tol, sb0, st0,
-                                                                     status, ctr);
+  check_neutral_kernel<<<rp.R, 256, 0, st>>>(rp, sums, tol, sb0, st0, status, ctr);
 }
 
 __global__ void rep_keys_kernel(int64_t N, const uint32_t* __restrict__ perm,
                                 const int32_t* __restrict__ rid, uint32_t* keys) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x)
-    keys[i] = (uint32_t)rid[perm[i]];
+    keys[i] = (uint32_t)rid[perm[i] < (uint64_t)N ? perm[i] : 0];   // clamped as in the gather
 }
 
 void launch_rep_keys(int64_t N, const uint32_t* perm, const int32_t* rid, uint32_t* keys,
@@ -172,8 +186,11 @@ __global__ void gather_kernel(Reps rp, const T* __restrict__ pos, const T* __res
   const double ikx = 1.0 / Lx, iky = 1.0 / Ly;                     // FP64 path
   for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
     const int64_t i = ch.start + t;
-    const uint32_t o = perm[i];
+    uint32_t o = perm[i];
     if (!QS_DCHECK(o < (uint64_t)rp.N, rp.status)) continue;
+    // a sort whose bounded wait gave up (status TIMEOUT) leaves indices
+    // that may be out of range: clamp, so that the call stays in bounds
+    if (o >= (uint64_t)rp.N) o = 0;
     const bool first = t == 0 && ch.first;
     T z, zp;
     if (zkeys) {
@@ -181,7 +198,9 @@ __global__ void gather_kernel(Reps rp, const T* __restrict__ pos, const T* __res
       zp = first ? z : KeyVal<T>::z(zkeys, i - 1);
     } else {
       z = pos[3 * (int64_t)o + 2];
-      zp = first ? z : pos[3 * (int64_t)perm[i - 1] + 2];
+      uint32_t op = first ? o : perm[i - 1];
+      if (op >= (uint64_t)rp.N) op = 0;
+      zp = first ? z : pos[3 * (int64_t)op + 2];
     }
     zs[i] = z;
     dz[i] = first ? (T)0 : z - zp;
@@ -243,6 +262,49 @@ __global__ void combine_kernel(Reps rp, int nkr, const T* __restrict__ part,
   }
   __syncthreads();
   const int64_t N = rp.N;
+  if constexpr (sizeof(T) == 4) {
+    if (!W.on) {
+      // FP32 path without walls: the sums in double-float (FP64 runs at
+      // 1/76 of FP32 on this part), each output rounded once from them
+      const DF dq = df_from(diagq);
+      DF e2 = {0.0f, 0.0f};
+      for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
+        const int64_t i = ch.start + t;
+        DF sp = {0.0f, 0.0f}, sx = sp, sy = sp, sz = sp;
+        for (int r = 0; r < nkr; ++r) {
+          const T* b = part + (size_t)r * 4 * N;
+          sp = sp + (float)b[i];
+          sx = sx + (float)b[N + i];
+          sy = sy + (float)b[2 * N + i];
+          sz = sz + (float)b[3 * N + i];
+        }
+        const float qq = (float)qs[i];
+        const DF q2 = df_from(qq);
+        const DF ph = sp + reinterpret_cast<const DF*>(phi0)[i] + q2 * dq;
+        const DF fz = sz * q2 + reinterpret_cast<const DF*>(fz0)[i];
+        const int32_t o = perm[i];
+        if (!QS_DCHECK(o >= 0 && o < rp.N, rp.status)) continue;
+        if (phi_out) phi_out[o] = (T)df_to_float(ph);
+        if (force_out) {
+          force_out[3 * (int64_t)o] = (T)df_to_float(sx * q2);
+          force_out[3 * (int64_t)o + 1] = (T)df_to_float(sy * q2);
+          force_out[3 * (int64_t)o + 2] = (T)df_to_float(fz);
+        }
+        const DF qp = q2 * ph;
+        e2 = e2 + DF{0.5f * qp.hi, 0.5f * qp.lo};
+      }
+      for (int o = 16; o; o >>= 1)
+        e2 = e2 + DF{__shfl_xor_sync(0xffffffffu, e2.hi, o), __shfl_xor_sync(0xffffffffu, e2.lo, o)};
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = df_to_double(e2);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double s = 0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[j];
+        echunk[blockIdx.x] = s;
+      }
+      return;
+    }
+  }
   double e = 0.0;
   for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
     const int64_t i = ch.start + t;

@@ -18,6 +18,7 @@
 // Several slabs of one call are sorted by z first and then, stably, by their
 // slab index (a second LSD sort over one or two more digits), which leaves
 // every slab in its own index range and ordered by z within it.
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -193,14 +194,173 @@ small_sort_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin,
   }
 }
 
+// ---------------------------------------------------------------- onesweep
+// One kernel per digit pass, with the offsets of earlier tiles found by a
+// decoupled look-back (Merrill and Garland's single-pass prefix scan, as
+// used for radix sorting by Adinets and Merrill's Onesweep): tiles take
+// tickets in launch order; each publishes its digit counts at once
+// (aggregate), reads back through the earlier tiles' words until an
+// inclusive prefix, and publishes its own inclusive prefix. The global digit
+// offsets come from one histogram of every pass's digit over all keys,
+// taken before the first pass. A tile waits only on tiles with smaller
+// tickets, which are already running, so every wait ends; each wait is
+// still bounded: after kSpinLimit polls the tile records a timeout in the
+// status word, publishes an error word (its successors stop there), and
+// scatters nothing. Every later pass of the sort then does nothing, and the
+// consumers of the permutation clamp its entries, so a timed-out sort leaves
+// wrong values but no access out of range.
+constexpr int kOsItems = 16;
+constexpr int kOsTile = kSortThreads * kOsItems;   // 4096 keys per tile
+constexpr uint32_t kFlagAgg = 1u, kFlagInc = 2u, kFlagErr = 3u;
+constexpr int kSpinLimit = 1 << 20;
+
+// all passes' digit histograms in one read of the keys
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads)
+os_hist_kernel(const K* __restrict__ keys, int64_t N, int passes, uint32_t* gtot) {
+  __shared__ uint32_t h[8][kRadix];
+  for (int e = threadIdx.x; e < passes * kRadix; e += blockDim.x) h[e / kRadix][e % kRadix] = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const K k = keys[i];
+    for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(unsigned)(k >> (8 * p)) & 0xFFu], 1u);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < passes * kRadix; e += blockDim.x) {
+    const uint32_t v = h[e / kRadix][e % kRadix];
+    if (v) atomicAdd(&gtot[e], v);
+  }
+}
+
+__device__ __forceinline__ uint64_t os_word(uint32_t flag, uint32_t count) {
+  return ((uint64_t)flag << 32) | count;
+}
+
+// stall: the tile of this ticket publishes nothing (a test of the bounded
+// wait; -1 in normal use)
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads)
+os_pass_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
+               uint32_t* __restrict__ vout, int64_t N, int shift, const uint32_t* __restrict__ gtot,
+               unsigned long long* tstat, unsigned* ticket, unsigned* status, int stall) {
+  __shared__ uint32_t wcnt[kSortWarps][kRadix];
+  __shared__ uint32_t toff[kRadix];
+  __shared__ uint32_t goff[kRadix];
+  __shared__ uint32_t wsum[kSortWarps];
+  __shared__ int tile_s, bad_s;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    tile_s = (int)atomicAdd(ticket, 1u);
+    bad_s = (status && (*(volatile unsigned*)status & kStTimeout)) ? 1 : 0;
+  }
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x)
+    for (int ww = 0; ww < kSortWarps; ++ww) wcnt[ww][d] = 0;
+  __syncthreads();
+  const int tile = tile_s;
+  unsigned long long* my = tstat + (size_t)tile * kRadix;
+  if (bad_s) {   // an earlier pass timed out: publish errors, move nothing
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) atomicExch(&my[d], os_word(kFlagErr, 0));
+    return;
+  }
+  // ranks within the tile: per warp in input order (match_any), then warps
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t base = (int64_t)tile * kOsTile + (int64_t)w * 32 * kOsItems;
+  K key[kOsItems];
+  uint32_t val[kOsItems], loc[kOsItems], dig[kOsItems];
+#pragma unroll
+  for (int s = 0; s < kOsItems; ++s) {
+    const int64_t idx = base + s * 32 + lane;
+    const bool valid = idx < N;
+    key[s] = valid ? kin[idx] : (K)0;
+    val[s] = valid ? vin[idx] : 0u;
+    const unsigned d = valid ? ((unsigned)(key[s] >> shift) & 0xFFu) : 0x100u;
+    dig[s] = d;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const unsigned before = valid ? wcnt[w][d & 0xFFu] : 0u;
+    __syncwarp();
+    if (valid && lane == __ffs(peers) - 1) wcnt[w][d & 0xFFu] = before + __popc(peers);
+    __syncwarp();
+    loc[s] = before + __popc(peers & lt);
+  }
+  __syncthreads();
+  // one thread per digit: warp prefix, the tile's count, publish, look back
+  const int d = threadIdx.x;      // kSortThreads == kRadix
+  uint32_t run = 0;
+  for (int ww = 0; ww < kSortWarps; ++ww) {
+    const uint32_t c = wcnt[ww][d];
+    wcnt[ww][d] = run;
+    run += c;
+  }
+  const bool stalled = tile == stall;
+  if (!stalled) atomicExch(&my[d], os_word(tile == 0 ? kFlagInc : kFlagAgg, run));
+  uint32_t prefix = 0;
+  bool err = stalled;
+  if (tile > 0 && !stalled) {
+    int j = tile - 1;
+    int spins = 0;
+    while (true) {
+      const uint64_t v = *(volatile unsigned long long*)&tstat[(size_t)j * kRadix + d];
+      const uint32_t f = (uint32_t)(v >> 32);
+      if (f == 0u) {
+        if (++spins > kSpinLimit) { err = true; break; }
+        __nanosleep(64);
+        continue;
+      }
+      if (f == kFlagErr) { err = true; break; }
+      prefix += (uint32_t)v;
+      if (f == kFlagInc) break;
+      --j;
+    }
+    atomicExch(&my[d], err ? os_word(kFlagErr, 0) : os_word(kFlagInc, prefix + run));
+  }
+  toff[d] = prefix;
+  // exclusive scan of the global digit totals (the same in every tile)
+  const uint32_t g = gtot[d];
+  uint32_t y = g;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t z = __shfl_up_sync(0xffffffffu, y, o);
+    if (lane >= o) y += z;
+  }
+  if (lane == 31) wsum[w] = y;
+  const unsigned anyerr = __syncthreads_or(err ? 1 : 0);
+  uint32_t b = 0;
+  for (int ww = 0; ww < w; ++ww) b += wsum[ww];
+  goff[d] = b + y - g;
+  __syncthreads();
+  if (anyerr) {
+    if (threadIdx.x == 0 && status) atomicOr(status, (unsigned)kStTimeout);
+    return;
+  }
+#pragma unroll
+  for (int s = 0; s < kOsItems; ++s) {
+    if (dig[s] < 0x100u) {
+      const uint64_t pos = (uint64_t)goff[dig[s]] + toff[dig[s]] + wcnt[w][dig[s]] + loc[s];
+      if (pos < (uint64_t)N) {
+        kout[pos] = key[s];
+        vout[pos] = val[s];
+      }
+    }
+  }
+}
+
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+// onesweep state: [passes][tiles][256] look-back words, [passes] tickets,
+// [passes][256] global digit totals (cleared together before a sort)
+size_t os_state_bytes(int64_t N, int passes) {
+  const int64_t nt = (N + kOsTile - 1) / kOsTile;
+  return align256((size_t)passes * nt * kRadix * 8) + align256((size_t)passes * 4) +
+         align256((size_t)passes * kRadix * 4);
+}
+
 size_t sort_workspace_bytes(int64_t N, int key_bytes) {
   const int64_t nb = (N + kTile - 1) / kTile;
   return 2 * align256((size_t)N * key_bytes) + 2 * align256((size_t)N * 4) +
-         align256((size_t)nb * kRadix * 4) + align256(8 * kRadix * 4);
+         align256((size_t)nb * kRadix * 4) + align256(8 * kRadix * 4) +
+         os_state_bytes(N, key_bytes);
 }
 
 void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes) {
@@ -213,12 +373,51 @@ void sort_bind_workspace(SortWork& w, void* base, int64_t N, int key_bytes) {
   w.counts = reinterpret_cast<uint32_t*>(p);
   p += align256((size_t)w.nblocks * kRadix * 4);
   w.totals = reinterpret_cast<uint32_t*>(p);
+  p += align256(8 * kRadix * 4);
+  w.os_state = p;
+  w.os_bytes = os_state_bytes(N, key_bytes);
   w.status = nullptr;
 }
 
-int sort_launches(int64_t N, int passes) { return N <= kTile ? 1 : 3 * passes; }
+namespace {
+std::atomic<int> g_sort_stall{-1};
+}
 
-int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaStream_t st) {
+void sort_debug_stall(int tile) { g_sort_stall.store(tile); }
+
+int sort_launches(int64_t N, int passes, bool onesweep) {
+  if (N <= kTile) return 1;
+  return onesweep ? 1 + passes : 3 * passes;
+}
+
+template <typename K>
+static int onesweep_sort(SortWork& w, int64_t N, int passes, int src, cudaStream_t st) {
+  const int64_t nt = (N + kOsTile - 1) / kOsTile;
+  char* p = static_cast<char*>(w.os_state);
+  auto* tstat = reinterpret_cast<unsigned long long*>(p);
+  p += align256((size_t)passes * nt * kRadix * 8);
+  auto* tickets = reinterpret_cast<unsigned*>(p);
+  p += align256((size_t)passes * 4);
+  auto* gtot = reinterpret_cast<uint32_t*>(p);
+  cudaMemsetAsync(w.os_state, 0, os_state_bytes(N, passes), st);
+  int hb = (int)((N + kSortThreads * 16 - 1) / (kSortThreads * 16));
+  if (hb > 152 * 8) hb = 152 * 8;
+  os_hist_kernel<K><<<hb, kSortThreads, 0, st>>>(static_cast<const K*>(w.keys[src]), N, passes,
+                                                  gtot);
+  const int stall = g_sort_stall.exchange(-1);
+  int cur = src;
+  for (int q = 0; q < passes; ++q) {
+    os_pass_kernel<K><<<(unsigned)nt, kSortThreads, 0, st>>>(
+        static_cast<const K*>(w.keys[cur]), w.vals[cur], static_cast<K*>(w.keys[cur ^ 1]),
+        w.vals[cur ^ 1], N, 8 * q, gtot + (size_t)q * kRadix, tstat + (size_t)q * nt * kRadix,
+        tickets + q, w.status, q == 0 ? stall : -1);
+    cur ^= 1;
+  }
+  return cur;
+}
+
+int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaStream_t st,
+               bool onesweep) {
   int cur = src;
   if (N <= kTile) {
     // small sorts: one CTA, buffer src in, the other out
@@ -234,6 +433,10 @@ int radix_sort(SortWork& w, int64_t N, int key_bytes, int passes, int src, cudaS
           static_cast<const uint64_t*>(w.keys[cur]), w.vals[cur],
           static_cast<uint64_t*>(w.keys[cur ^ 1]), w.vals[cur ^ 1], (int)N, n2, passes, w.status);
     return cur ^ 1;
+  }
+  if (onesweep && w.status) {
+    if (key_bytes == 4) return onesweep_sort<uint32_t>(w, N, passes, src, st);
+    return onesweep_sort<uint64_t>(w, N, passes, src, st);
   }
   cudaMemsetAsync(w.totals, 0, (size_t)passes * kRadix * 4, st);
   for (int p = 0; p < passes; ++p) {

@@ -113,3 +113,28 @@ def test_failed_create(qslab):
     assert err.value.code == -6
     h = qslab.qslab_create(0, qslab.QSLAB_FP64)
     qslab.qslab_destroy(h)
+
+
+def test_bounded_wait_times_out(qslab, soe16):
+    """The z-sort's look-back between CTAs waits a bounded time: with one
+    tile made to publish nothing (a host-side test hook), the next tile's
+    wait runs out, the call reports QSLAB_ERR_TIMEOUT (no GPU fault, no
+    hang), and the context stays usable: the same call again gives the
+    first result bit for bit."""
+    box = (40.0, 40.0, 20.0)
+    sl = workloads.uniform_slab(20000, box, 46, alpha=0.25)     # 5 sort tiles of 4096
+    slab = qslab.QSlab(0, "fp32c").configure(box, 0.25, soe16, rbe=(64, 3))
+    p = torch.tensor(sl.pos, device="cuda", dtype=torch.float32)
+    q = torch.tensor(sl.q, device="cuda", dtype=torch.float32)
+    e, phi, F = slab.compute(p, q)
+    assert slab.status() == 0
+    E0, phi0 = float(e.item()), phi.cpu().numpy()
+    slab.set_rng_state(3, 0)
+    qslab.qslab_debug_stall_sort(2)
+    slab.compute(p, q)
+    assert slab.status() == -8
+    slab.set_rng_state(3, 0)
+    e, phi, F = slab.compute(p, q)
+    assert slab.status() == 0
+    assert float(e.item()) == E0 and (phi.cpu().numpy() == phi0).all()
+    slab.close()
