@@ -334,7 +334,7 @@ def run_ours(args):
     # ---- FP64 (reported beside it)
     s64 = make("fp64")
     st64 = max(1, min(args.steps, 3))
-    ms64, _, _, _, E64 = timed(s64, torch.float64, st64, 1)
+    ms64, ph64, _, _, E64 = timed(s64, torch.float64, st64, 1, phase_steps=1)
     s64.close()
 
     # slowest rank decides
@@ -396,7 +396,15 @@ def run_ours(args):
                    "N": N, "P": P, "M": M, "per_rank": "independent replica",
                    "l2": "flushed between steps (256 MB write, untimed)"},
         "fp64": {"value": job_throughput(N, ws, ms64_max), "unit": "particles/s", "ms_per_step": ms64_max,
-                 "steps": st64, "energy": E64},
+                 "steps": st64, "energy": E64,
+                 "roofline": {"bound": "fp64", "kernel": "kspace_final_kernel<double> (recurrences "
+                                                       "+ gather, FP64)",
+                              "achieved": work / (ph64[0]["recurrence"] * 1e-3) / 1e12,
+                              "peak": mp["fp64_fma"] / 1e12, "unit": "Tinstr/s",
+                              "frac": work / (ph64[0]["recurrence"] * 1e-3) / mp["fp64_fma"],
+                              "kernel_ms": ph64[0]["recurrence"],
+                              "peak_basis": "measured FP64 FMA rate (qslab_measure_peaks)",
+                              "work": "the same K*N*(24*(M+1)+20) count, in FP64 instructions"}},
         "energy_fp32c": E32,
         "phases_ms": phases,
         "roofline": {"bound": "alu", "kernel": "kspace_final_f2_kernel (recurrences + gather)",

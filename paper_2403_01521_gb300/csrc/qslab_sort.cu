@@ -213,6 +213,7 @@ constexpr int kOsItems = 16;
 constexpr int kOsTile = kSortThreads * kOsItems;   // 4096 keys per tile
 constexpr uint32_t kFlagAgg = 1u, kFlagInc = 2u, kFlagErr = 3u;
 constexpr int kSpinLimit = 1 << 20;
+constexpr int kOsWindow = 8;       // earlier tiles' words read per round of the look-back
 
 // all passes' digit histograms in one read of the keys
 template <typename K>
@@ -297,20 +298,36 @@ os_pass_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* _
   uint32_t prefix = 0;
   bool err = stalled;
   if (tile > 0 && !stalled) {
+    // read back eight earlier tiles' words at a time (independent loads),
+    // consume them in order up to an inclusive prefix, or up to a word not
+    // yet published, which is polled again
     int j = tile - 1;
     int spins = 0;
-    while (true) {
-      const uint64_t v = *(volatile unsigned long long*)&tstat[(size_t)j * kRadix + d];
-      const uint32_t f = (uint32_t)(v >> 32);
-      if (f == 0u) {
+    bool done = false;
+    while (!done) {
+      uint64_t v[kOsWindow];
+#pragma unroll
+      for (int u = 0; u < kOsWindow; ++u)
+        v[u] = j - u >= 0 ? *(volatile unsigned long long*)&tstat[(size_t)(j - u) * kRadix + d]
+                          : os_word(kFlagInc, 0);
+      int used = 0;
+      bool wait = false;
+#pragma unroll
+      for (int u = 0; u < kOsWindow; ++u) {
+        if (done || wait) continue;
+        const uint32_t f = (uint32_t)(v[u] >> 32);
+        if (f == 0u) { wait = true; continue; }
+        if (f == kFlagErr) { err = true; done = true; continue; }
+        prefix += (uint32_t)v[u];
+        ++used;
+        if (f == kFlagInc) done = true;
+      }
+      if (done) break;
+      j -= used;
+      if (wait) {
         if (++spins > kSpinLimit) { err = true; break; }
         __nanosleep(64);
-        continue;
       }
-      if (f == kFlagErr) { err = true; break; }
-      prefix += (uint32_t)v;
-      if (f == kFlagInc) break;
-      --j;
     }
     atomicExch(&my[d], err ? os_word(kFlagErr, 0) : os_word(kFlagInc, prefix + run));
   }
