@@ -722,6 +722,10 @@ Plan make_plan(const qslab_ctx* c, bool host_io, bool virial = false) {
   s.nkr = t.nkr;
   s.np = c->npc;
   s.nstates = 1 + 2 * c->npc;
+  s.rem = 0;
+  if (!dp)
+    for (const RepInfo& ri : t.info)
+      if ((ri.K % kWarp >= 1 && ri.K % kWarp <= 8) || t.Kpad - ri.K >= kWarp) s.rem = 1;
   const Reps rp = reps_view(c);
   size_t o = 0;
   auto take = [&o](size_t b) { size_t r = o; o += a256(b); return r; };

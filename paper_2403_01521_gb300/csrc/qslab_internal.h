@@ -204,6 +204,11 @@ struct ScanPlan {
   int nkr;          // number of mode ranges (KR * nkr = Kpad)
   int np;           // pair representatives compiled for (4, 8, 12, 16)
   int nstates;      // 1 + 2 np
+  // FP32 pass B: 1 when some warp of some replica holds at most 8 real
+  // modes (K mod 32 in 1..8: it runs as a remainder warp, both directions at
+  // once, two lanes per mode) or none (K <= Kpad - 32: it only clears its
+  // output slots)
+  int rem;
 };
 
 template <typename T>

@@ -341,30 +341,191 @@ __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
 // the decay table is stored re/im-split per particle so that the decays of
 // two pairs load as one float2; the potential and force sums keep one
 // partial sum per lane, added at the end of the step.
-template <int NP>
+// Coefficients of the pairs one lane carries: NQ pair groups (two pairs per
+// float2) of one mode, from group q0 on. A lane that carries the whole mode
+// (NQ = NP/2) takes the mode table's j = i sums; a lane that carries part of
+// it forms the partial sums of its own pairs the same way (FP64 sum of the
+// FP32-rounded coefficients, one rounding), and only the mode's lead lane
+// carries the beta = k coefficients ck, ckk.
+template <int NQ>
 struct ModeCoefF2 {
   int32_t mx, my;
   float kx, ky, kk, ck, ckk, sY, sZ;
-  float2 cpr[NP / 2], ncpi[NP / 2], cbr[NP / 2], ncbi[NP / 2];   // ncpi = -cpi, ncbi = -cbi
+  float2 cpr[NQ], ncpi[NQ], cbr[NQ], ncbi[NQ];   // ncpi = -cpi, ncbi = -cbi
 };
 
-template <int NP>
+template <int NP, int NQ>
 __device__ __forceinline__ void load_mode_f2(const ModeTab<float>& mt, size_t kstride, size_t m,
-                                             ModeCoefF2<NP>& c) {
+                                             int q0, bool lead, ModeCoefF2<NQ>& c) {
   c.mx = mt.mx[m]; c.my = mt.my[m];
   c.kx = mt.kx[m]; c.ky = mt.ky[m]; c.kk = mt.kk[m];
-  c.ck = mt.ck[m]; c.ckk = mt.ckk[m]; c.sY = mt.sY[m]; c.sZ = mt.sZ[m];
+  c.ck = lead ? mt.ck[m] : 0.0f;
+  c.ckk = lead ? mt.ckk[m] : 0.0f;
+  double sy = 0.0, sz = 0.0;
 #pragma unroll
-  for (int q = 0; q < NP / 2; ++q) {
-    const int p0 = 2 * q, p1 = 2 * q + 1;
+  for (int q = 0; q < NQ; ++q) {
+    const int p0 = 2 * (q0 + q), p1 = p0 + 1;
     c.cpr[q] = make_float2(mt.cp[(0 * NP + p0) * kstride + m], mt.cp[(0 * NP + p1) * kstride + m]);
     c.ncpi[q] = make_float2(-mt.cp[(1 * NP + p0) * kstride + m], -mt.cp[(1 * NP + p1) * kstride + m]);
     c.cbr[q] = make_float2(mt.cp[(2 * NP + p0) * kstride + m], mt.cp[(2 * NP + p1) * kstride + m]);
     c.ncbi[q] = make_float2(-mt.cp[(3 * NP + p0) * kstride + m], -mt.cp[(3 * NP + p1) * kstride + m]);
+    sy += (double)c.cpr[q].x; sy += (double)c.cpr[q].y;
+    sz += (double)c.cbr[q].x; sz += (double)c.cbr[q].y;
+  }
+  if (NQ == NP / 2) {
+    c.sY = mt.sY[m]; c.sZ = mt.sZ[m];
+  } else {
+    c.sY = (float)((double)c.ck + sy);
+    c.sZ = (float)((double)c.ckk + sz);
   }
 }
 
+// A lane's recurrence states: the beta = k state and, per pair group, the
+// a- and b-states of two pairs (re and im parts split over two float2).
+template <int NQ>
+struct F2State {
+  Cplx<float> g0;
+  float2 Ra[NQ], Ia[NQ], Rb[NQ], Ib[NQ];
+};
+
+// the carried states of one direction (cin: the chunk's state 0 of this mode)
+template <int NQ>
+__device__ __forceinline__ void f2_load_state(const Cplx<float>* cin, int Kpad, int q0,
+                                              F2State<NQ>& st) {
+  st.g0 = cin[0];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int qq = q0 + q;
+    const Cplx<float> a0 = cin[(size_t)(1 + 4 * qq) * Kpad], b0 = cin[(size_t)(2 + 4 * qq) * Kpad];
+    const Cplx<float> a1 = cin[(size_t)(3 + 4 * qq) * Kpad], b1 = cin[(size_t)(4 + 4 * qq) * Kpad];
+    st.Ra[q] = make_float2(a0.re, a1.re); st.Ia[q] = make_float2(a0.im, a1.im);
+    st.Rb[q] = make_float2(b0.re, b1.re); st.Ib[q] = make_float2(b0.im, b1.im);
+  }
+}
+
+// One step of a lane's recurrences at particle record r (dzd: the distance
+// its decays span; dre, dim: their re and im rows from this lane's first
+// pair group) and the lane's four output terms of that particle:
+// Re e^{ik.rho} Y, kx and ky times Im e^{ik.rho} Y, zsign Re e^{ik.rho} Z.
+template <int NQ>
+__device__ __forceinline__ void f2_step(F2State<NQ>& st, const ModeCoefF2<NQ>& mc,
+                                        const Rec<float>& r, float dzd, const float2* trig,
+                                        const float2* dre, const float2* dim, float zsign,
+                                        float* out) {
+  const float2 minus1 = make_float2(-1.0f, -1.0f);
+  float cs, sn;
+  phase_cs(phase_turns(mc.mx, mc.my, r.xh, r.yh), trig, cs, sn);
+  const float a = r.q * cs, b = r.q * sn;
+  // beta = k: as in the scalar kernel
+  const float ek = one_minus_exp_neg(mc.kk * dzd);
+  st.g0.re += fmaf(-ek, st.g0.re, a);
+  st.g0.im += fmaf(-ek, st.g0.im, -b);
+  const float2 Ua = make_float2(a, a), Ub = make_float2(b, b);
+  float2 Ya = make_float2(0.0f, 0.0f), Yb = Ya, Za = Ya, Zb = Ya;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const float2 Dr = dre[q], Di = dim[q];
+    const float2 nDi = __fmul2_rn(Di, minus1);
+    // a-state: (R + iI) <- D (R + iI) + a ; b-state likewise with b
+    const float2 ra = __ffma2_rn(Dr, st.Ra[q], __ffma2_rn(nDi, st.Ia[q], Ua));
+    const float2 ia = __ffma2_rn(Dr, st.Ia[q], __fmul2_rn(Di, st.Ra[q]));
+    const float2 rb = __ffma2_rn(Dr, st.Rb[q], __ffma2_rn(nDi, st.Ib[q], Ub));
+    const float2 ib = __ffma2_rn(Dr, st.Ib[q], __fmul2_rn(Di, st.Rb[q]));
+    st.Ra[q] = ra; st.Ia[q] = ia; st.Rb[q] = rb; st.Ib[q] = ib;
+    Ya = __ffma2_rn(mc.cpr[q], ra, __ffma2_rn(mc.ncpi[q], ia, Ya));
+    Yb = __ffma2_rn(mc.cpr[q], rb, __ffma2_rn(mc.ncpi[q], ib, Yb));
+    Za = __ffma2_rn(mc.cbr[q], ra, __ffma2_rn(mc.ncbi[q], ia, Za));
+    Zb = __ffma2_rn(mc.cbr[q], rb, __ffma2_rn(mc.ncbi[q], ib, Zb));
+  }
+  // Y = ck G0 + sum_p Re(cp Ga) - i sum_p Re(cp Gb), Z likewise with cbp
+  float Yr = fmaf(mc.ck, st.g0.re, Ya.x + Ya.y);
+  float Yi = fmaf(mc.ck, st.g0.im, -(Yb.x + Yb.y));
+  float Zr = fmaf(mc.ckk, st.g0.re, Za.x + Za.y);
+  float Zi = fmaf(mc.ckk, st.g0.im, -(Zb.x + Zb.y));
+  // the sums above include j = i; remove it (coefficients sY, sZ times u_i)
+  Yr = fmaf(-mc.sY, a, Yr); Yi = fmaf(mc.sY, b, Yi);
+  Zr = fmaf(-mc.sZ, a, Zr); Zi = fmaf(mc.sZ, b, Zi);
+  const float W2 = cs * Yi + sn * Yr;         // Im e^{i k.rho} Y
+  out[0] = cs * Yr - sn * Yi;                 // Re e^{i k.rho} Y
+  out[1] = mc.kx * W2;
+  out[2] = mc.ky * W2;
+  out[3] = zsign * (cs * Zr - sn * Zi);       // Re e^{i k.rho} Z
+}
+
+// per-step decays of particle t: tabf[t][0][p] = Re, tabf[t][1][p] = Im of
+// e^{-a_p dz_t}, t = 0..cnt (t = cnt: next chunk)
 template <int NP>
+__device__ __forceinline__ void step_decays_f2(float* tabf, const ChunkSmem<float>& s,
+                                               const PairTab& pairs, int cnt) {
+  for (int e = threadIdx.x; e < NP * (cnt + 1); e += blockDim.x) {
+    const int t = e / NP, p = e - t * NP;
+    const Cplx<float> d = cexp_neg((float)pairs.a_re[p], (float)pairs.a_im[p], s.rec[t].dz);
+    tabf[t * 2 * NP + p] = d.re;
+    tabf[t * 2 * NP + NP + p] = d.im;
+  }
+}
+
+// The remainder modes. A warp whose 32 modes hold only r = 1..8 real ones
+// (K mod 32 of its slab; the rest padding) would still cost a full warp's
+// two passes over the chunk. Instead (NQR > 0) that warp runs the forward
+// recurrences on lanes 0-15 and the backward ones on lanes 16-31 at the same
+// time (each half at its own particle), each mode's pairs spread over two
+// lanes of a half (NQR = NP/4 pair groups per lane): one pass over the chunk
+// at about 40% of a full warp's instructions. The lanes' partial Y, Z enter
+// the outputs linearly, so a half's sum over its 16 lanes is its sum over
+// modes and pairs; only a mode's lead lane carries the beta = k
+// coefficients. The halves write two slot rows (the warp's and one extra).
+template <int NP, int NQR>
+__device__ __forceinline__ void f2_remainder_warp(const KParams<float>& P, const ChunkSmem<float>& s,
+                                                  const float* tabf, int c, int cnt, int k0,
+                                                  int lane, float* slot_f, float* slot_b,
+                                                  float* idle) {
+  constexpr int NQ = NP / 2, SP = NQ / NQR;
+  const CRange ch = kchunk(P.rp, c);
+  const int Kpad = P.rp.Kpad;
+  const int dir = lane >> 4, h = lane & 15;
+  // modes k0 + h / SP; past K they are padding (zero coefficients, m < Kpad)
+  const int m = k0 + h / SP, q0 = (h % SP) * NQR;
+  ModeCoefF2<NQR> mc;
+  load_mode_f2<NP, NQR>(P.modes, P.kstride, (size_t)ch.r * Kpad + m, q0, h % SP == 0, mc);
+  const int S = P.plan.nstates;
+  F2State<NQR> st;
+  f2_load_state<NQR>(P.carry + (size_t)dir * P.rp.nchunks * S * Kpad + ((size_t)c * S) * Kpad + m,
+                     Kpad, q0, st);
+  const float zsign = dir == 0 ? 1.0f : -1.0f;
+  float* myslot = dir == 0 ? slot_f : slot_b;
+  for (int n0 = 0; n0 < cnt; n0 += 4) {
+    float buf[16];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + j;
+      if (n < cnt) {
+        const int t = dir == 0 ? n : cnt - 1 - n;
+        const int td = dir == 0 ? t : t + 1;
+        const Rec<float> r = s.rec[t];
+        const float dzd = dir == 0 ? r.dz : s.rec[td].dz;
+        f2_step<NQR>(st, mc, r, dzd, s.trig,
+                     reinterpret_cast<const float2*>(tabf + td * 2 * NP) + q0,
+                     reinterpret_cast<const float2*>(tabf + td * 2 * NP + NP) + q0, zsign,
+                     buf + 4 * j);
+      } else {
+        buf[4 * j + 0] = buf[4 * j + 1] = buf[4 * j + 2] = buf[4 * j + 3] = 0.0f;
+      }
+    }
+    // every lane now holds one (particle, quantity) total of its half
+    const float v = half_warp_reduce16<float>(buf, lane);
+    const int g = h >> 2, qn = h & 3;
+    const bool own = n0 + g < cnt;
+    const int tt = dir == 0 ? n0 + g : cnt - 1 - (n0 + g);
+    float* dst = own ? myslot + tt * 4 + qn : idle + lane;
+    *dst = v;
+  }
+}
+
+// NQR: pair groups per lane of a remainder warp (0: every warp runs as a full
+// one). Which warps are remainder warps depends only on the slab's K and the
+// mode range, so a slab gets the same arithmetic in a batch as on its own.
+template <int NP, int NQR>
 __global__ void kspace_final_f2_kernel(KParams<float> P, PairTab pairs) {
   extern __shared__ __align__(32) char smem[];
   const ScanPlan& pl = P.plan;
@@ -375,106 +536,72 @@ __global__ void kspace_final_f2_kernel(KParams<float> P, PairTab pairs) {
   if (!QS_DCHECK(chunk_ok(P.rp, ch, L), P.rp.status)) return;
   const int64_t start = ch.start;
   const int cnt = ch.cnt;
-  ChunkSmem<float> s = carve<float>(smem, L, NP, W, true);
+  // real modes of this CTA's range; with at most 8 in its last partial warp
+  // that warp is a remainder warp and takes the extra slot row W
+  const int kin = min(max(P.rp.info[ch.r].K - (int)blockIdx.y * pl.KR, 0), pl.KR);
+  const bool rem_cta = NQR > 0 && (kin & (kWarp - 1)) >= 1 && (kin & (kWarp - 1)) <= 8;
+  const int Wslots = W + (rem_cta ? 1 : 0);
+  ChunkSmem<float> s = carve<float>(smem, L, NP, W + (NQR > 0 ? 1 : 0), true);
   load_chunk<float>(P, s, start, cnt);
   __syncthreads();
-  // per-step decays of particle t: tabf[t][0][p] = Re, tabf[t][1][p] = Im of
-  // e^{-a_p dz_t}, t = 0..cnt (t = cnt: next chunk)
   float* tabf = reinterpret_cast<float*>(s.tab);
-  for (int e = threadIdx.x; e < NP * (cnt + 1); e += blockDim.x) {
-    const int t = e / NP, p = e - t * NP;
-    const Cplx<float> d = cexp_neg((float)pairs.a_re[p], (float)pairs.a_im[p], s.rec[t].dz);
-    tabf[t * 2 * NP + p] = d.re;
-    tabf[t * 2 * NP + NP + p] = d.im;
-  }
+  step_decays_f2<NP>(tabf, s, pairs, cnt);
   __syncthreads();
+  constexpr int NQ = NP / 2;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int m = blockIdx.y * pl.KR + threadIdx.x;
-  ModeCoefF2<NP> mc;
-  load_mode_f2<NP>(P.modes, P.kstride, (size_t)ch.r * Kpad + m, mc);
-  const int S = pl.nstates;
-  const size_t dirstride = (size_t)P.rp.nchunks * S * Kpad;
-  float* slot = s.slots + (size_t)w * L * 4;
-  const float2 minus1 = make_float2(-1.0f, -1.0f);
+  const int nreal = min(max(kin - w * kWarp, 0), kWarp);   // this warp's real modes
+  if (NQR > 0 && nreal == 0) {
+    float* slot = s.slots + (size_t)w * L * 4;                 // padding only
+    for (int e = lane; e < cnt * 4; e += kWarp) slot[e] = 0.0f;
+  } else if (NQR > 0 && nreal <= 8) {
+    if constexpr (NQR > 0)
+      f2_remainder_warp<NP, NQR>(P, s, tabf, c, cnt, blockIdx.y * pl.KR + w * kWarp, lane,
+                                 s.slots + (size_t)w * L * 4, s.slots + (size_t)W * L * 4,
+                                 s.idle + w * kWarp);
+  } else {
+    const int m = blockIdx.y * pl.KR + threadIdx.x;
+    ModeCoefF2<NQ> mc;
+    load_mode_f2<NP, NQ>(P.modes, P.kstride, (size_t)ch.r * Kpad + m, 0, true, mc);
+    const int S = pl.nstates;
+    const size_t dirstride = (size_t)P.rp.nchunks * S * Kpad;
+    float* slot = s.slots + (size_t)w * L * 4;
 
-  // both directions unrolled: the direction-dependent indices and signs fold
-  // into each copy of the loop (measured 3% faster)
+    // both directions unrolled: the direction-dependent indices and signs fold
+    // into each copy of the loop (measured 3% faster)
 #pragma unroll
-  for (int dir = 0; dir < 2; ++dir) {
-    const Cplx<float>* cin = P.carry + dir * dirstride + ((size_t)c * S) * Kpad + m;
-    Cplx<float> g0 = cin[0];
-    float2 Ra[NP / 2], Ia[NP / 2], Rb[NP / 2], Ib[NP / 2];
+    for (int dir = 0; dir < 2; ++dir) {
+      F2State<NQ> st;
+      f2_load_state<NQ>(P.carry + dir * dirstride + ((size_t)c * S) * Kpad + m, Kpad, 0, st);
+      const float zsign = dir == 0 ? 1.0f : -1.0f;
+      for (int n0 = 0; n0 < cnt; n0 += 4) {
+        float buf[16];
 #pragma unroll
-    for (int q = 0; q < NP / 2; ++q) {
-      const Cplx<float> a0 = cin[(size_t)(1 + 4 * q) * Kpad], b0 = cin[(size_t)(2 + 4 * q) * Kpad];
-      const Cplx<float> a1 = cin[(size_t)(3 + 4 * q) * Kpad], b1 = cin[(size_t)(4 + 4 * q) * Kpad];
-      Ra[q] = make_float2(a0.re, a1.re); Ia[q] = make_float2(a0.im, a1.im);
-      Rb[q] = make_float2(b0.re, b1.re); Ib[q] = make_float2(b0.im, b1.im);
-    }
-    const float zsign = dir == 0 ? 1.0f : -1.0f;
-    for (int n0 = 0; n0 < cnt; n0 += 4) {
-      float buf[16];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int n = n0 + j;
-        if (n < cnt) {
-          const int t = dir == 0 ? n : cnt - 1 - n;
-          const int td = dir == 0 ? t : t + 1;      // index of the decay to apply
-          const Rec<float> r = s.rec[t];
-          const float dzd = dir == 0 ? r.dz : s.rec[td].dz;
-          float cs, sn;
-          phase_cs(phase_turns(mc.mx, mc.my, r.xh, r.yh), s.trig, cs, sn);
-          const float a = r.q * cs, b = r.q * sn;
-          // beta = k: as in the scalar kernel
-          const float ek = one_minus_exp_neg(mc.kk * dzd);
-          g0.re += fmaf(-ek, g0.re, a);
-          g0.im += fmaf(-ek, g0.im, -b);
-          const float2 Ua = make_float2(a, a), Ub = make_float2(b, b);
-          float2 Ya = make_float2(0.0f, 0.0f), Yb = Ya, Za = Ya, Zb = Ya;
-          const float2* dre = reinterpret_cast<const float2*>(tabf + td * 2 * NP);
-          const float2* dim = reinterpret_cast<const float2*>(tabf + td * 2 * NP + NP);
-#pragma unroll
-          for (int q = 0; q < NP / 2; ++q) {
-            const float2 Dr = dre[q], Di = dim[q];
-            const float2 nDi = __fmul2_rn(Di, minus1);
-            // a-state: (R + iI) <- D (R + iI) + a ; b-state likewise with b
-            const float2 ra = __ffma2_rn(Dr, Ra[q], __ffma2_rn(nDi, Ia[q], Ua));
-            const float2 ia = __ffma2_rn(Dr, Ia[q], __fmul2_rn(Di, Ra[q]));
-            const float2 rb = __ffma2_rn(Dr, Rb[q], __ffma2_rn(nDi, Ib[q], Ub));
-            const float2 ib = __ffma2_rn(Dr, Ib[q], __fmul2_rn(Di, Rb[q]));
-            Ra[q] = ra; Ia[q] = ia; Rb[q] = rb; Ib[q] = ib;
-            Ya = __ffma2_rn(mc.cpr[q], ra, __ffma2_rn(mc.ncpi[q], ia, Ya));
-            Yb = __ffma2_rn(mc.cpr[q], rb, __ffma2_rn(mc.ncpi[q], ib, Yb));
-            Za = __ffma2_rn(mc.cbr[q], ra, __ffma2_rn(mc.ncbi[q], ia, Za));
-            Zb = __ffma2_rn(mc.cbr[q], rb, __ffma2_rn(mc.ncbi[q], ib, Zb));
+        for (int j = 0; j < 4; ++j) {
+          const int n = n0 + j;
+          if (n < cnt) {
+            const int t = dir == 0 ? n : cnt - 1 - n;
+            const int td = dir == 0 ? t : t + 1;      // index of the decay to apply
+            const Rec<float> r = s.rec[t];
+            const float dzd = dir == 0 ? r.dz : s.rec[td].dz;
+            f2_step<NQ>(st, mc, r, dzd, s.trig,
+                        reinterpret_cast<const float2*>(tabf + td * 2 * NP),
+                        reinterpret_cast<const float2*>(tabf + td * 2 * NP + NP), zsign,
+                        buf + 4 * j);
+          } else {
+            buf[4 * j + 0] = buf[4 * j + 1] = buf[4 * j + 2] = buf[4 * j + 3] = 0.0f;
           }
-          // Y = ck G0 + sum_p Re(cp Ga) - i sum_p Re(cp Gb), Z likewise with cbp
-          float Yr = fmaf(mc.ck, g0.re, Ya.x + Ya.y);
-          float Yi = fmaf(mc.ck, g0.im, -(Yb.x + Yb.y));
-          float Zr = fmaf(mc.ckk, g0.re, Za.x + Za.y);
-          float Zi = fmaf(mc.ckk, g0.im, -(Zb.x + Zb.y));
-          // the sums above include j = i; remove it (coefficients sY, sZ times u_i)
-          Yr = fmaf(-mc.sY, a, Yr); Yi = fmaf(mc.sY, b, Yi);
-          Zr = fmaf(-mc.sZ, a, Zr); Zi = fmaf(mc.sZ, b, Zi);
-          const float W2 = cs * Yi + sn * Yr;         // Im e^{i k.rho} Y
-          buf[4 * j + 0] = cs * Yr - sn * Yi;         // Re e^{i k.rho} Y
-          buf[4 * j + 1] = mc.kx * W2;
-          buf[4 * j + 2] = mc.ky * W2;
-          buf[4 * j + 3] = zsign * (cs * Zr - sn * Zi);   // Re e^{i k.rho} Z
-        } else {
-          buf[4 * j + 0] = buf[4 * j + 1] = buf[4 * j + 2] = buf[4 * j + 3] = 0.0f;
         }
+        const float v = warp_reduce16<float>(buf, lane);
+        // every even lane now holds one (particle, quantity) total; all lanes
+        // store (the others into an idle row) so that the warp does not diverge
+        const int idx = lane >> 1, g = idx >> 2, qn = idx & 3;
+        const bool own = !(lane & 1) && n0 + g < cnt;
+        const int tt = dir == 0 ? n0 + g : cnt - 1 - (n0 + g);
+        float* dst = own ? slot + tt * 4 + qn : s.idle + w * kWarp + lane;
+        *dst = (dir == 0 ? 0.0f : *dst) + v;
       }
-      const float v = warp_reduce16<float>(buf, lane);
-      // every even lane now holds one (particle, quantity) total; all lanes
-      // store (the others into an idle row) so that the warp does not diverge
-      const int idx = lane >> 1, g = idx >> 2, qn = idx & 3;
-      const bool own = !(lane & 1) && n0 + g < cnt;
-      const int tt = dir == 0 ? n0 + g : cnt - 1 - (n0 + g);
-      float* dst = own ? slot + tt * 4 + qn : s.idle + w * kWarp + lane;
-      *dst = (dir == 0 ? 0.0f : *dst) + v;
+      __syncwarp();
     }
-    __syncwarp();
   }
   __syncthreads();
   // sum the warps' slots and write this mode range's partial outputs
@@ -482,7 +609,7 @@ __global__ void kspace_final_f2_kernel(KParams<float> P, PairTab pairs) {
   for (int e = threadIdx.x; e < cnt * 4; e += blockDim.x) {
     const int t = e >> 2, qn = e & 3;
     float acc = 0;
-    for (int ww = 0; ww < W; ++ww) acc += s.slots[((size_t)ww * L + t) * 4 + qn];
+    for (int ww = 0; ww < Wslots; ++ww) acc += s.slots[((size_t)ww * L + t) * 4 + qn];
     out[(size_t)qn * P.rp.N + start + t] = acc;
   }
 }
@@ -499,11 +626,17 @@ struct FinalKernel {
 };
 template <int NP>
 struct FinalKernel<float, NP> {
+  template <int NQR>
+  static void go(const KParams<float>& P, const PairTab& pairs, dim3 grid, int threads, size_t sm,
+                 cudaStream_t st) {
+    cudaFuncSetAttribute(kspace_final_f2_kernel<NP, NQR>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kspace_final_f2_kernel<NP, NQR><<<grid, threads, sm, st>>>(P, pairs);
+  }
   static void run(const KParams<float>& P, const PairTab& pairs, dim3 grid, int threads, size_t sm,
                   cudaStream_t st) {
-    cudaFuncSetAttribute(kspace_final_f2_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sm);
-    kspace_final_f2_kernel<NP><<<grid, threads, sm, st>>>(P, pairs);
+    if (P.plan.rem) go<NP / 4>(P, pairs, grid, threads, sm, st);
+    else go<0>(P, pairs, grid, threads, sm, st);
   }
 };
 
@@ -516,7 +649,8 @@ static void kspace_run(const KParams<T>& P, const PairTab& pairs, void* dec,
   const Reps& rp = P.rp;
   dim3 grid(rp.nchunks, pl.nkr);
   const size_t smA = chunk_smem_bytes<T>(rp.L, NP, 0, false);
-  const size_t smB = chunk_smem_bytes<T>(rp.L, NP, pl.KR / kWarp, true);
+  // pass B: with remainder warps (FP32), one more slot row
+  const size_t smB = chunk_smem_bytes<T>(rp.L, NP, pl.KR / kWarp + (pl.rem ? 1 : 0), true);
   if (stage != 2) {
     cudaFuncSetAttribute(kspace_aggregate_kernel<T, NP>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);

@@ -190,4 +190,23 @@ __device__ __forceinline__ T warp_reduce16(T (&v)[16], int lane) {
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// The same over each half-warp apart (lanes 0-15 and 16-31): afterwards lane
+// l holds its half's total of value index l % 16.
+template <typename T>
+__device__ __forceinline__ T half_warp_reduce16(T (&v)[16], int lane) {
+#pragma unroll
+  for (int lvl = 0; lvl < 4; ++lvl) {
+    const int half = 8 >> lvl;         // 8, 4, 2, 1 values exchanged
+    const int mask = 8 >> lvl;         // xor 8, 4, 2, 1
+    const bool up = lane & mask;
+#pragma unroll
+    for (int j = 0; j < half; ++j) {
+      const T send = up ? v[j] : v[j + half];
+      const T keep = up ? v[j + half] : v[j];
+      v[j] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+    }
+  }
+  return v[0];
+}
+
 }  // namespace qslab
