@@ -225,6 +225,214 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
   }
 }
 
+// ------------------------------------------------ pass A on the tensor cores
+// On the FP32 path the chunk aggregates are one matrix product per chunk:
+// rows (mode, a | b), a = q cos(k.rho) and b = q sin(k.rho) of each particle;
+// columns (direction, pair, re | im) of the exponential tables
+// E_f(t, p) = e^{-a_p (z_end - z_t)} and E_b(t, p) = e^{-a_p (z_t - z_start)};
+// the sum runs over the chunk's particles t. It runs as mma.sync m16n8k8
+// TF32 products at FP32-level accuracy: each operand x = x_hi + x_lo with
+// x_hi = x rounded to TF32 and x_lo = x - x_hi (exact), rounded to TF32
+// again, and the product as a_hi b_hi + a_hi b_lo + a_lo b_hi (the dropped
+// a_lo b_lo is below 2^-22 of it). Eight k-steps (64 particles) accumulate
+// in the MMA's FP32 accumulators and are then added to FP32 sums in
+// registers: measured RMS error 3.5e-8 of sum |a E| over 480 particles, as
+// for sequential FP32 FMAs (one accumulator over all 60 k-steps: 2.5e-7).
+// The beta = k term, whose exponent depends on the mode, stays scalar.
+//
+// A warp owns 32 modes and runs them as two halves of 16: two m-tiles of 8
+// modes, rows g = the a-state and g + 8 = the b-state of mode g. A lane
+// (group g = lane / 4, q4 = lane % 4) forms the phases of its m-tiles' mode g
+// at particles k0 + q4 and k0 + q4 + 4 of each k-step, which are exactly its
+// A-fragment entries; its accumulators hold columns 2 q4, 2 q4 + 1 of each
+// n-tile: the (re, im) of one (direction, pair) for the a- and the b-state.
+// The E table rows have a stride of 4 NP + 8 floats, so that the B-fragment
+// loads (row k0 + q4 (+4), column 8 j + g) hit 32 different banks.
+
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// x = hi + lo, both TF32
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+// d += a b (16 x 8 x 8, TF32 inputs, FP32 accumulation)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// shared memory of the tensor-core pass A: E table [L8][4 NP + 8] (L8: L
+// rounded up to whole k-steps of 8), records [L + 1], z [L], sin/cos table
+__host__ __device__ inline size_t tc_agg_smem_bytes(int L, int NP) {
+  const size_t L8 = ((size_t)L + 7) & ~(size_t)7;
+  return align_up(sizeof(float) * L8 * (4 * NP + 8)) + align_up(sizeof(Rec<float>) * (L + 1)) +
+         align_up(sizeof(float) * L) + align_up(sizeof(float2) * kTrig);
+}
+
+template <int NP>
+__global__ void kspace_aggregate_tc_kernel(KParams<float> P, PairTab pairs) {
+  extern __shared__ __align__(32) char smem[];
+  constexpr int NC = 4 * NP;        // columns: direction, pair, re | im
+  constexpr int NS = NC + 8;        // E table row stride (floats)
+  constexpr int NT = NC / 8;        // n-tiles
+  constexpr int KB = 8;             // k-steps accumulated in the MMA before an FP32 add
+  const ScanPlan& pl = P.plan;
+  const int c = blockIdx.x;
+  const int L = P.rp.L, Kpad = P.rp.Kpad;
+  const CRange ch = kchunk(P.rp, c);
+  if (!QS_DCHECK(chunk_ok(P.rp, ch, L), P.rp.status)) return;
+  const int64_t start = ch.start;
+  const int cnt = ch.cnt;
+  const int cnt8 = (cnt + 7) & ~7;  // whole k-steps: at most L rounded up to 8
+  float* etab = reinterpret_cast<float*>(smem);
+  ChunkSmem<float> s;
+  {
+    char* p = smem + align_up(sizeof(float) * ((size_t)(L + 7) & ~(size_t)7) * NS);
+    s.tab = nullptr;
+    s.rec = reinterpret_cast<Rec<float>*>(p); p += align_up(sizeof(Rec<float>) * (L + 1));
+    s.zl = reinterpret_cast<float*>(p); p += align_up(sizeof(float) * L);
+    s.trig = reinterpret_cast<float2*>(p);
+    s.slots = s.idle = nullptr;
+  }
+  load_chunk<float>(P, s, start, cnt);
+  __syncthreads();
+  // E table; rows cnt..cnt8-1 zero (their a, b are zero too)
+  const float zend = s.zl[cnt - 1], zst = s.zl[0];
+  for (int e = threadIdx.x; e < NP * cnt8; e += blockDim.x) {
+    const int t = e / NP, p = e - t * NP;
+    Cplx<float> ef = {0.0f, 0.0f}, eb = {0.0f, 0.0f};
+    if (t < cnt) {
+      const float ar = (float)pairs.a_re[p], ai = (float)pairs.a_im[p];
+      ef = cexp_neg(ar, ai, zend - s.zl[t]);
+      eb = cexp_neg(ar, ai, s.zl[t] - zst);
+    }
+    float* row = etab + (size_t)t * NS;
+    row[2 * p] = ef.re;
+    row[2 * p + 1] = ef.im;
+    row[2 * NP + 2 * p] = eb.re;
+    row[2 * NP + 2 * p + 1] = eb.im;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int g = lane >> 2, q4 = lane & 3;
+  const int Kr = P.rp.info[ch.r].K;
+  const int S = pl.nstates;
+  const size_t dirstride = (size_t)P.rp.nchunks * S * Kpad;
+  Cplx<float>* af = P.agg + ((size_t)c * S) * Kpad;
+  const size_t mrow = (size_t)ch.r * Kpad;
+  for (int h = 0; h < 2; ++h) {
+    const int mb = blockIdx.y * pl.KR + w * kWarp + h * 16;   // first mode of the half
+    if (mb >= Kr) {
+      // padding only: zero aggregates (the carries read every mode)
+      for (int e = lane; e < 2 * S * 16; e += kWarp) {
+        const int m = mb + (e & 15), st = (e >> 4) % S, dir = (e >> 4) / S;
+        af[dir * dirstride + (size_t)st * Kpad + m] = Cplx<float>{0.0f, 0.0f};
+      }
+      continue;
+    }
+    int32_t mx[2], my[2];
+    float kk[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const size_t m = mrow + mb + 8 * i + g;
+      mx[i] = P.modes.mx[m]; my[i] = P.modes.my[m]; kk[i] = P.modes.kk[m];
+    }
+    float run[2][NT][4];
+    Cplx<float> f0[2], b0[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      f0[i] = b0[i] = Cplx<float>{0.0f, 0.0f};
+#pragma unroll
+      for (int j = 0; j < NT; ++j) run[i][j][0] = run[i][j][1] = run[i][j][2] = run[i][j][3] = 0.0f;
+    }
+    for (int kb = 0; kb < cnt8; kb += 8 * KB) {
+      float fr[2][NT][4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) fr[i][j][0] = fr[i][j][1] = fr[i][j][2] = fr[i][j][3] = 0.0f;
+      const int kend = min(kb + 8 * KB, cnt8);
+      for (int k0 = kb; k0 < kend; k0 += 8) {
+        // B fragments: rows k0 + q4 and k0 + q4 + 4, column 8 j + g
+        uint32_t bh[NT][2], bl[NT][2];
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+          for (int r = 0; r < 2; ++r)
+            tf32_split(etab[(size_t)(k0 + q4 + 4 * r) * NS + 8 * j + g], bh[j][r], bl[j][r]);
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          uint32_t ah[4], al[4];
+#pragma unroll
+          for (int r = 0; r < 2; ++r) {
+            const int t = k0 + q4 + 4 * r;
+            const int tc = t < cnt ? t : cnt - 1;
+            const Rec<float> rr = s.rec[tc];
+            float cs, sn;
+            phase_cs(phase_turns(mx[i], my[i], rr.xh, rr.yh), s.trig, cs, sn);
+            const float qv = t < cnt ? rr.q : 0.0f;
+            const float a = qv * cs, b = qv * sn;   // u = a - i b
+            const float zt = s.zl[tc];
+            const float ef = exp_neg_term(kk[i] * (zend - zt));
+            const float eb = exp_neg_term(kk[i] * (zt - zst));
+            f0[i].re = fmaf(ef, a, f0[i].re); f0[i].im = fmaf(-ef, b, f0[i].im);
+            b0[i].re = fmaf(eb, a, b0[i].re); b0[i].im = fmaf(-eb, b, b0[i].im);
+            // A fragment: (row g, col q4) a(t0), (g + 8, q4) b(t0), (g, q4 + 4) a(t1), (g + 8, q4 + 4) b(t1)
+            tf32_split(a, ah[2 * r], al[2 * r]);
+            tf32_split(b, ah[2 * r + 1], al[2 * r + 1]);
+          }
+          // the three products (NT independent MMAs between dependent ones)
+#pragma unroll
+          for (int j = 0; j < NT; ++j) mma_tf32(fr[i][j], al, bh[j][0], bh[j][1]);
+#pragma unroll
+          for (int j = 0; j < NT; ++j) mma_tf32(fr[i][j], ah, bl[j][0], bl[j][1]);
+#pragma unroll
+          for (int j = 0; j < NT; ++j) mma_tf32(fr[i][j], ah, bh[j][0], bh[j][1]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) run[i][j][e] += fr[i][j][e];
+    }
+    // the beta = k sums over the mode's four lanes
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int o = 1; o < 4; o <<= 1) {
+        f0[i].re += __shfl_xor_sync(0xffffffffu, f0[i].re, o);
+        f0[i].im += __shfl_xor_sync(0xffffffffu, f0[i].im, o);
+        b0[i].re += __shfl_xor_sync(0xffffffffu, b0[i].re, o);
+        b0[i].im += __shfl_xor_sync(0xffffffffu, b0[i].im, o);
+      }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int m = mb + 8 * i + g;
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int n = 8 * j + 2 * q4;              // columns n (re) and n + 1 (im)
+        const int dir = n / (2 * NP), p = (n - dir * 2 * NP) >> 1;
+        Cplx<float>* base = af + dir * dirstride + m;
+        base[(size_t)(1 + 2 * p) * Kpad] = Cplx<float>{run[i][j][0], run[i][j][1]};   // sum a E
+        base[(size_t)(2 + 2 * p) * Kpad] = Cplx<float>{run[i][j][2], run[i][j][3]};   // sum b E
+      }
+      if (q4 == 0) {
+        af[m] = f0[i];
+        af[dirstride + m] = b0[i];
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ pass B
 template <typename T, int NP>
 __global__ void kspace_final_kernel(KParams<T> P, PairTab pairs) {
@@ -640,6 +848,35 @@ struct FinalKernel<float, NP> {
   }
 };
 
+// pass A launcher: the tensor-core kernel on the FP32 path up to 8 pairs (at
+// 12 it was slower than the scalar kernel: 4.85 vs 4.69 ms on the confined
+// slab, its 181 registers allowing one CTA per SM), the scalar one otherwise
+template <typename T, int NP>
+struct AggKernel {
+  static void run(const KParams<T>& P, const PairTab& pairs, dim3 grid, int threads, size_t sm,
+                  cudaStream_t st) {
+    cudaFuncSetAttribute(kspace_aggregate_kernel<T, NP>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kspace_aggregate_kernel<T, NP><<<grid, threads, sm, st>>>(P, pairs);
+  }
+};
+template <int NP>
+struct AggKernel<float, NP> {
+  static void run(const KParams<float>& P, const PairTab& pairs, dim3 grid, int threads,
+                  size_t smA, cudaStream_t st) {
+    if constexpr (NP <= 8) {
+      const size_t sm = tc_agg_smem_bytes(P.rp.L, NP);
+      cudaFuncSetAttribute(kspace_aggregate_tc_kernel<NP>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      kspace_aggregate_tc_kernel<NP><<<grid, threads, sm, st>>>(P, pairs);
+    } else {
+      cudaFuncSetAttribute(kspace_aggregate_kernel<float, NP>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
+      kspace_aggregate_kernel<float, NP><<<grid, threads, smA, st>>>(P, pairs);
+    }
+  }
+};
+
 // stage 0: pass A, carries and pass B; 1: pass A and carries only; 2: pass B
 // only (from the carries a stage-1 launch left in place)
 template <typename T, int NP>
@@ -652,9 +889,7 @@ static void kspace_run(const KParams<T>& P, const PairTab& pairs, void* dec,
   // pass B: with remainder warps (FP32), one more slot row
   const size_t smB = chunk_smem_bytes<T>(rp.L, NP, pl.KR / kWarp + (pl.rem ? 1 : 0), true);
   if (stage != 2) {
-    cudaFuncSetAttribute(kspace_aggregate_kernel<T, NP>,
-                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smA);
-    kspace_aggregate_kernel<T, NP><<<grid, pl.KR, smA, st>>>(P, pairs);
+    AggKernel<T, NP>::run(P, pairs, grid, pl.KR, smA, st);
     if (ev) cudaEventRecord(ev[0], st);
     launch_kspace_carries<T>(pl, rp, pairs, P.zs, P.modes.kk, P.agg, P.carry, dec, st);
     if (ev) cudaEventRecord(ev[1], st);

@@ -342,3 +342,25 @@ def test_net_force_and_fp32_invariance(qslab, soe16):
     sh.pos[:, 1] = (sh.pos[:, 1] + 3.5) % 50.0
     b = _run(qslab, sh, "fp64", soe16, kc=kc)
     assert abs(a["E"] - b["E"]) <= 1e-11 * abs(a["E"])
+
+
+# FP32C launch shapes: automatic; chunk lengths that are not whole k-steps
+# of the tensor-core aggregates (37, 100: ragged tails of 5 and 0 or 4
+# particles); one warp of modes; a random batch of 200 modes (a warp with
+# 8 real modes runs as a remainder warp) in several chunk lengths
+@pytest.mark.parametrize("tuning", [(0, 0), (37, 0), (100, 64), (16, 32)])
+def test_fp32c_full_k_launch_shapes(qslab, small_full, soe16, tuning):
+    sl = small_full
+    kc = lattice.kcut_for_tail(sl.alpha, sl.tail)
+    got = _run(qslab, sl, "fp32c", soe16, kc=kc, tuning=tuning)
+    ref = soe_ewald2d.soe_full(got["pos"], got["q"], sl.box, sl.alpha, *soe16, kc=kc)
+    _check_fp32(got, ref)
+
+
+@pytest.mark.parametrize("chunk", [0, 37, 64, 200])
+def test_fp32c_rbe_launch_shapes(qslab, soe16, chunk):
+    sl = workloads.uniform_slab(3000, (40.0, 40.0, 15.0), 41, alpha=0.2)
+    got = _run(qslab, sl, "fp32c", soe16, rbe=(200, 9), tuning=(chunk, 0))
+    mx, my, _ = got["modes"]
+    ref = soe_ewald2d.soe_rbe(got["pos"], got["q"], sl.box, sl.alpha, *soe16, mx, my)
+    _check_fp32(got, ref, escale=0.5 * float(np.abs(got["q"] * ref["phi"]).sum()))
