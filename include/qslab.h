@@ -288,10 +288,12 @@ int qslab_compute_host(qslab_ctx* ctx, int64_t N, const void* pos_host,
  * The paper has no counterpart; this is an interface variant only.
  *   - Arguments, layouts and results as for qslab_compute(); the context must
  *     be configured. Its own device buffers are not used; the mode and
- *     sampler tables are rebuilt in the array on every call (host-side
- *     configuration work only, no device allocation).
+ *     sampler tables are copied into the array on every call, in the call's
+ *     stream order (the mode list, the sampling distribution and the per-box
+ *     constants are reused on the host while the configuration and the box
+ *     stay the same; no device allocation).
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress), once per device.
  *   - Limits: the tables must fit 8 MiB and the workspace the remaining
  *     56 MiB (at P = 200 random-batch modes about 1.7e5 particles in FP32C);
  *     larger problems return QSLAB_ERR_TOO_LARGE before any device work.
