@@ -364,3 +364,17 @@ def test_fp32c_rbe_launch_shapes(qslab, soe16, chunk):
     mx, my, _ = got["modes"]
     ref = soe_ewald2d.soe_rbe(got["pos"], got["q"], sl.box, sl.alpha, *soe16, mx, my)
     _check_fp32(got, ref, escale=0.5 * float(np.abs(got["q"] * ref["phi"]).sum()))
+
+
+@pytest.mark.parametrize("M,kind", [(8, "conditioned"), (24, "conditioned"), (16, "accurate")])
+def test_fp32c_other_soe_tables(qslab, M, kind):
+    """FP32C with the other SOE tables: 4 pair representatives (tensor-core
+    aggregates with two n-tiles), 12 (the scalar aggregate kernel) and the
+    accurate M = 16 table."""
+    from paper_2403_01521_gb300.soe import load_soe
+    soe = load_soe(M, kind)
+    sl = workloads.uniform_slab(3000, (25.0, 20.0, 9.0), 33, alpha=0.4)
+    kc = lattice.kcut_for_tail(sl.alpha, 1e-8)
+    got = _run(qslab, sl, "fp32c", soe, kc=kc, tuning=(64, 0))
+    ref = soe_ewald2d.soe_full(got["pos"], got["q"], sl.box, sl.alpha, *soe, kc=kc)
+    _check_fp32(got, ref, escale=sum(abs(x) for x in ref["E_parts"]))
