@@ -234,11 +234,12 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
 // TF32 products at FP32-level accuracy: each operand x = x_hi + x_lo with
 // x_hi = x rounded to 11 significant bits (exact in TF32) and x_lo = x - x_hi
 // (exact) rounded to TF32, and the product as a_hi b_hi + a_hi b_lo +
-// a_lo b_hi (the dropped a_lo b_lo is below 2^-22 of it). Eight k-steps (64 particles) accumulate
-// in the MMA's FP32 accumulators and are then added to FP32 sums in
-// registers: measured RMS error 3.5e-8 of sum |a E| over 480 particles, as
-// for sequential FP32 FMAs (one accumulator over all 60 k-steps: 2.5e-7).
-// The beta = k term, whose exponent depends on the mode, stays scalar.
+// a_lo b_hi (the dropped a_lo b_lo is below 2^-22 of it). Eight k-steps (64
+// particles) accumulate in the MMA's FP32 accumulators and are then added to
+// FP32 sums in registers: measured RMS error 3.5e-8 of sum |a E| over 480
+// particles, as for sequential FP32 FMAs (one accumulator over all 60
+// k-steps: 2.5e-7). The beta = k term, whose exponent depends on the mode,
+// stays scalar.
 //
 // A warp owns 32 modes and runs them as two halves of 16: two m-tiles of 8
 // modes, rows g = the a-state and g + 8 = the b-state of mode g. A lane
