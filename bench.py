@@ -391,8 +391,9 @@ def run_ours(args):
         "config": {"workload": "rbe_large: N=1e6 charges +-1 uniform in 400x400x50, alpha=0.1, "
                                "P=200 random-batch k per call (sampled on the device), "
                                "M=16 SOE (conditioned table), compensated FP32 "
-                               "(FP32 phases and in-chunk scans, double-float chunk carries "
-                               "and k=0 prefix sums, FP64 reductions)",
+                               "(FP32 phases and in-chunk scans, chunk aggregates as split-TF32 "
+                               "tensor-core products with FP32 accumulation, double-float chunk "
+                               "carries, k=0 prefix sums and per-particle reductions)",
                    "N": N, "P": P, "M": M, "per_rank": "independent replica",
                    "l2": "flushed between steps (256 MB write, untimed)"},
         "fp64": {"value": job_throughput(N, ws, ms64_max), "unit": "particles/s", "ms_per_step": ms64_max,

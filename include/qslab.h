@@ -60,10 +60,13 @@ typedef struct qslab_ctx qslab_ctx;
  * arithmetic. QSLAB_FP64: everything in FP64. QSLAB_FP32C (compensated
  * FP32): FP32 inputs and outputs; FP32 phases and FP32 recurrences within
  * each chunk of sorted particles (the k != 0 scans and the k = 0 scans of
- * the exponential sums); double-float (two FP32 numbers, about 48 bits)
- * chunk-to-chunk carries of both, and double-float prefix sums of q and q z
- * for the |z| part of the k = 0 term; the per-particle sums over mode
- * ranges, the j = i constants and the energy reduction in FP64. */
+ * the exponential sums); the k != 0 chunk aggregates (up to 8 SOE pair
+ * representatives) as tensor-core TF32 products of split operands
+ * (x = x_hi + x_lo) with FP32 accumulation, at FP32-level accuracy;
+ * double-float (two FP32 numbers, about 48 bits) chunk-to-chunk carries,
+ * and double-float prefix sums of q and q z for the |z| part of the k = 0
+ * term; the per-particle sums over mode ranges, the j = i constants and the
+ * energy reduction in double-float (in FP64 when charged walls are set). */
 #define QSLAB_FP64 0
 #define QSLAB_FP32C 1
 
