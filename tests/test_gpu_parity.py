@@ -378,3 +378,15 @@ def test_fp32c_other_soe_tables(qslab, M, kind):
     got = _run(qslab, sl, "fp32c", soe, kc=kc, tuning=(64, 0))
     ref = soe_ewald2d.soe_full(got["pos"], got["q"], sl.box, sl.alpha, *soe, kc=kc)
     _check_fp32(got, ref, escale=sum(abs(x) for x in ref["E_parts"]))
+
+
+@pytest.mark.parametrize("tuning", [(0, 0), (64, 64), (48, 32)])
+def test_fp32c_remainder_warp_mode_ranges(qslab, soe16, tuning):
+    """A full k-sum of 295 half-plane modes (295 = 9 * 32 + 7): the warp
+    holding the last 7 modes runs as a remainder warp in the last of several
+    mode ranges; the warps past K hold padding only."""
+    sl = workloads.uniform_slab(2500, (26.0, 24.0, 9.0), 47, alpha=0.4)
+    kc = lattice.kcut_for_tail(sl.alpha, 1e-8)
+    got = _run(qslab, sl, "fp32c", soe16, kc=kc, tuning=tuning)
+    ref = soe_ewald2d.soe_full(got["pos"], got["q"], sl.box, sl.alpha, *soe16, kc=kc)
+    _check_fp32(got, ref, escale=sum(abs(x) for x in ref["E_parts"]))
