@@ -60,7 +60,7 @@ typedef struct qslab_ctx qslab_ctx;
  * arithmetic. QSLAB_FP64: everything in FP64. QSLAB_FP32C (compensated
  * FP32): FP32 inputs and outputs; FP32 phases and FP32 recurrences within
  * each chunk of sorted particles (the k != 0 scans and the k = 0 scans of
- * the exponential sums); the k != 0 chunk aggregates (up to 8 SOE pair
+ * the exponential sums); the k != 0 chunk aggregates (up to 12 SOE pair
  * representatives) as tensor-core TF32 products of split operands
  * (x = x_hi + x_lo) with FP32 accumulation, at FP32-level accuracy;
  * double-float (two FP32 numbers, about 48 bits) chunk-to-chunk carries,

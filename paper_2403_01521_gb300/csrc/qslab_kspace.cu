@@ -241,8 +241,9 @@ __global__ void kspace_aggregate_kernel(KParams<T> P, PairTab pairs) {
 // k-steps: 2.5e-7). The beta = k term, whose exponent depends on the mode,
 // stays scalar.
 //
-// A warp owns 32 modes and runs them as two halves of 16: two m-tiles of 8
-// modes, rows g = the a-state and g + 8 = the b-state of mode g. A lane
+// A warp owns 32 modes and runs them in passes over the chunk of MT m-tiles
+// of 8 modes (two halves of 16 up to 8 pairs, four quarters of 8 above):
+// rows g = the a-state and g + 8 = the b-state of mode g. A lane
 // (group g = lane / 4, q4 = lane % 4) forms the phases of its m-tiles' mode g
 // at particles k0 + q4 and k0 + q4 + 4 of each k-step, which are exactly its
 // A-fragment entries; its accumulators hold columns 2 q4, 2 q4 + 1 of each
@@ -289,6 +290,9 @@ __global__ void kspace_aggregate_tc_kernel(KParams<float> P, PairTab pairs) {
   constexpr int NS = NC + 8;        // E table row stride (floats)
   constexpr int NT = NC / 8;        // n-tiles
   constexpr int KB = 8;             // k-steps accumulated in the MMA before an FP32 add
+  // m-tiles (8 modes each) in flight per pass over the chunk: two up to 8
+  // pairs, one above (register budget)
+  constexpr int MT = NP <= 8 ? 2 : 1, MB = 8 * MT;
   const ScanPlan& pl = P.plan;
   const int c = blockIdx.x;
   const int L = P.rp.L, Kpad = P.rp.Kpad;
@@ -333,35 +337,35 @@ __global__ void kspace_aggregate_tc_kernel(KParams<float> P, PairTab pairs) {
   const size_t dirstride = (size_t)P.rp.nchunks * S * Kpad;
   Cplx<float>* af = P.agg + ((size_t)c * S) * Kpad;
   const size_t mrow = (size_t)ch.r * Kpad;
-  for (int h = 0; h < 2; ++h) {
-    const int mb = blockIdx.y * pl.KR + w * kWarp + h * 16;   // first mode of the half
+  for (int h = 0; h < kWarp / MB; ++h) {
+    const int mb = blockIdx.y * pl.KR + w * kWarp + h * MB;   // first mode of the pass
     if (mb >= Kr) {
       // padding only: zero aggregates (the carries read every mode)
-      for (int e = lane; e < 2 * S * 16; e += kWarp) {
-        const int m = mb + (e & 15), st = (e >> 4) % S, dir = (e >> 4) / S;
+      for (int e = lane; e < 2 * S * MB; e += kWarp) {
+        const int m = mb + e % MB, st = (e / MB) % S, dir = (e / MB) / S;
         af[dir * dirstride + (size_t)st * Kpad + m] = Cplx<float>{0.0f, 0.0f};
       }
       continue;
     }
-    int32_t mx[2], my[2];
-    float kk[2];
+    int32_t mx[MT], my[MT];
+    float kk[MT];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < MT; ++i) {
       const size_t m = mrow + mb + 8 * i + g;
       mx[i] = P.modes.mx[m]; my[i] = P.modes.my[m]; kk[i] = P.modes.kk[m];
     }
-    float run[2][NT][4];
-    Cplx<float> f0[2], b0[2];
+    float run[MT][NT][4];
+    Cplx<float> f0[MT], b0[MT];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < MT; ++i) {
       f0[i] = b0[i] = Cplx<float>{0.0f, 0.0f};
 #pragma unroll
       for (int j = 0; j < NT; ++j) run[i][j][0] = run[i][j][1] = run[i][j][2] = run[i][j][3] = 0.0f;
     }
     for (int kb = 0; kb < cnt8; kb += 8 * KB) {
-      float fr[2][NT][4];
+      float fr[MT][NT][4];
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < MT; ++i)
 #pragma unroll
         for (int j = 0; j < NT; ++j) fr[i][j][0] = fr[i][j][1] = fr[i][j][2] = fr[i][j][3] = 0.0f;
       const int kend = min(kb + 8 * KB, cnt8);
@@ -374,7 +378,7 @@ __global__ void kspace_aggregate_tc_kernel(KParams<float> P, PairTab pairs) {
           for (int r = 0; r < 2; ++r)
             tf32_split(etab[(size_t)(k0 + q4 + 4 * r) * NS + 8 * j + g], bh[j][r], bl[j][r]);
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < MT; ++i) {
           uint32_t ah[4], al[4];
 #pragma unroll
           for (int r = 0; r < 2; ++r) {
@@ -404,7 +408,7 @@ __global__ void kspace_aggregate_tc_kernel(KParams<float> P, PairTab pairs) {
         }
       }
 #pragma unroll
-      for (int i = 0; i < 2; ++i)
+      for (int i = 0; i < MT; ++i)
 #pragma unroll
         for (int j = 0; j < NT; ++j)
 #pragma unroll
@@ -412,7 +416,7 @@ __global__ void kspace_aggregate_tc_kernel(KParams<float> P, PairTab pairs) {
     }
     // the beta = k sums over the mode's four lanes
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < MT; ++i)
 #pragma unroll
       for (int o = 1; o < 4; o <<= 1) {
         f0[i].re += __shfl_xor_sync(0xffffffffu, f0[i].re, o);
@@ -421,7 +425,7 @@ __global__ void kspace_aggregate_tc_kernel(KParams<float> P, PairTab pairs) {
         b0[i].im += __shfl_xor_sync(0xffffffffu, b0[i].im, o);
       }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < MT; ++i) {
       const int m = mb + 8 * i + g;
 #pragma unroll
       for (int j = 0; j < NT; ++j) {
@@ -854,9 +858,10 @@ struct FinalKernel<float, NP> {
   }
 };
 
-// pass A launcher: the tensor-core kernel on the FP32 path up to 8 pairs (at
-// 12 it was slower than the scalar kernel: 4.85 vs 4.69 ms on the confined
-// slab, its 181 registers allowing one CTA per SM), the scalar one otherwise
+// pass A launcher: the tensor-core kernel on the FP32 path up to 12 pairs
+// (at 12 with one m-tile per pass: confined slab 4.69 -> 4.40 ms; two m-tiles
+// took 181 registers, one CTA per SM, and 4.85 ms), the scalar one otherwise
+// (16 pairs: 218 registers)
 template <typename T, int NP>
 struct AggKernel {
   static void run(const KParams<T>& P, const PairTab& pairs, dim3 grid, int threads, size_t sm,
@@ -870,7 +875,7 @@ template <int NP>
 struct AggKernel<float, NP> {
   static void run(const KParams<float>& P, const PairTab& pairs, dim3 grid, int threads,
                   size_t smA, cudaStream_t st) {
-    if constexpr (NP <= 8) {
+    if constexpr (NP <= 12) {
       const size_t sm = tc_agg_smem_bytes(P.rp.L, NP);
       cudaFuncSetAttribute(kspace_aggregate_tc_kernel<NP>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
