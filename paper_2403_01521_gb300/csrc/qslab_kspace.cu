@@ -689,7 +689,7 @@ __device__ __forceinline__ void step_decays_f2(float* tabf, const ChunkSmem<floa
 // recurrences on lanes 0-15 and the backward ones on lanes 16-31 at the same
 // time (each half at its own particle), each mode's pairs spread over two
 // lanes of a half (NQR = NP/4 pair groups per lane): one pass over the chunk
-// at about 40% of a full warp's instructions. The lanes' partial Y, Z enter
+// at about 45% of a full warp's instructions. The lanes' partial Y, Z enter
 // the outputs linearly, so a half's sum over its 16 lanes is its sum over
 // modes and pairs; only a mode's lead lane carries the beta = k
 // coefficients. The halves write two slot rows (the warp's and one extra).
